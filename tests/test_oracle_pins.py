@@ -1,0 +1,387 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+generator outputs, quadrature of the bilinear forms from their definitions,
+closed forms (constant coefficient, laminates), a dense direct solve, the
+paper's identities (symmetry, Voigt-Reuss bounds, Euler homogeneity) and
+finite differences.  CPU only.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_12227_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers --
+def _gauss2():
+    g = 1.0 / np.sqrt(3.0)
+    return [(0.5 - 0.5 * g, 0.5), (0.5 + 0.5 * g, 0.5)]   # (point, weight) on [0,1]
+
+
+def _bilinear_grad(v4, t1, t2, h):
+    """Gradient of the bilinear interpolant of local values (00,01,10,11) at (t1,t2) in [0,1]^2."""
+    v00, v01, v10, v11 = v4
+    d1 = ((v10 - v00) * (1 - t2) + (v11 - v01) * t2) / h
+    d2 = ((v01 - v00) * (1 - t1) + (v11 - v10) * t1) / h
+    return d1, d2
+
+
+def _cell_vals(x, c1, c2):
+    n = x.shape[0]
+    p1, p2 = (c1 + 1) % n, (c2 + 1) % n
+    return (x[c1, c2], x[c1, p2], x[p1, c2], x[p1, p2])
+
+
+def _quad_energy(coef, u, v, h, scheme):
+    """int a grad(u_h).grad(v_h) by quadrature, cell by cell (no element matrix).
+
+    consistent: 2x2 Gauss (exact for Q1); lumped: the d1.d1 term with the
+    trapezoid rule in x2 and the d2.d2 term with the trapezoid rule in x1."""
+    n = coef.shape[0]
+    total = 0.0
+    g = _gauss2()
+    trap = [(0.0, 0.5), (1.0, 0.5)]
+    for c1 in range(n):
+        for c2 in range(n):
+            uu, vv = _cell_vals(u, c1, c2), _cell_vals(v, c1, c2)
+            s = 0.0
+            if scheme == oracle.SCHEME_CONSISTENT:
+                for t1, w1 in g:
+                    for t2, w2 in g:
+                        du, dv = _bilinear_grad(uu, t1, t2, h), _bilinear_grad(vv, t1, t2, h)
+                        s += w1 * w2 * (du[0] * dv[0] + du[1] * dv[1])
+            else:
+                for t1, w1 in g:
+                    for t2, w2 in trap:
+                        du, dv = _bilinear_grad(uu, t1, t2, h), _bilinear_grad(vv, t1, t2, h)
+                        s += w1 * w2 * du[0] * dv[0]
+                for t1, w1 in trap:
+                    for t2, w2 in g:
+                        du, dv = _bilinear_grad(uu, t1, t2, h), _bilinear_grad(vv, t1, t2, h)
+                        s += w1 * w2 * du[1] * dv[1]
+            total += coef[c1, c2] * s * h * h
+    return total
+
+
+def _random_coef(n, seed, lo=1.0, hi=10.0):
+    g = np.random.default_rng(seed)
+    return np.where(g.random((n, n)) < 0.45, hi, lo)
+
+
+# ------------------------------------------------------------------ field --
+def test_splitmix64_published_vectors():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert [oracle.splitmix64_output(1234567, k) for k in range(1, 6)] == vals
+
+
+def test_field_union_matches_predicate():
+    # brute force: cell covered iff some inclusion's (wrapped) square contains it
+    for d in [workloads.realization(4, 8, 10.0, 3, 0), workloads.realization(3, 4, 10.0, 5, 2),
+              workloads.realization(2, 16, 10.0, 9, 1, side_units=0.5)]:
+        n = d["L"] * d["m0"]
+        s = d["incl_cells"]
+        c = oracle.corners(d)
+        assert c.min() >= 0 and c.max() < n
+        i1, i2 = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        cov = np.zeros((n, n), dtype=bool)
+        for k in range(d["n_incl"]):
+            cov |= (((i1 - c[k, 0]) % n) < s) & (((i2 - c[k, 1]) % n) < s)
+        np.testing.assert_array_equal(oracle.gen_field(d).astype(bool), cov)
+
+
+def test_field_coverage_statistics():
+    # E[covered fraction] = 1 - (1 - s^2/n^2)^N_inc for independent uniform corners
+    fr = []
+    for k in range(400):
+        d = workloads.realization(8, 4, 10.0, 11, k)
+        fr.append(oracle.gen_field(d).mean())
+    d = workloads.realization(8, 4, 10.0, 11, 0)
+    n, s, N = 32, d["incl_cells"], d["n_incl"]
+    expect = 1.0 - (1.0 - s * s / (n * n)) ** N
+    fr = np.asarray(fr)
+    assert abs(fr.mean() - expect) < 4 * fr.std() / np.sqrt(len(fr)) + 1e-3
+
+
+def test_corner_marginals_uniform():
+    d = workloads.realization(64, 8, 10.0, 1, 0)   # n = 512, 2867 inclusions
+    c = oracle.corners(d).ravel()
+    hist = np.bincount(c // 64, minlength=8)
+    expect = c.size / 8
+    chi2 = ((hist - expect) ** 2 / expect).sum()
+    assert chi2 < 30.0      # 7 dof: p ~ 1e-4
+
+
+# --------------------------------------------------------------- assembly --
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_element_matrix_equals_quadrature(scheme):
+    h = 0.125
+    E = oracle.element_matrix(scheme, h)
+    for a in range(4):
+        for b in range(4):
+            ea = np.zeros(4); ea[a] = 1
+            eb = np.zeros(4); eb[b] = 1
+            # one cell of a 2x2 torus would wrap; use the local formula directly
+            s = 0.0
+            g = _gauss2()
+            trap = [(0.0, 0.5), (1.0, 0.5)]
+            if scheme == oracle.SCHEME_CONSISTENT:
+                for t1, w1 in g:
+                    for t2, w2 in g:
+                        du, dv = _bilinear_grad(ea, t1, t2, h), _bilinear_grad(eb, t1, t2, h)
+                        s += w1 * w2 * (du[0] * dv[0] + du[1] * dv[1])
+            else:
+                for t1, w1 in g:
+                    for t2, w2 in trap:
+                        du, dv = _bilinear_grad(ea, t1, t2, h), _bilinear_grad(eb, t1, t2, h)
+                        s += w1 * w2 * du[0] * dv[0]
+                for t1, w1 in trap:
+                    for t2, w2 in g:
+                        du, dv = _bilinear_grad(ea, t1, t2, h), _bilinear_grad(eb, t1, t2, h)
+                        s += w1 * w2 * du[1] * dv[1]
+            assert abs(E[a, b] - s * h * h) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_stiffness_equals_quadrature_bilinear_form(scheme):
+    n, h = 6, 0.25
+    coef = _random_coef(n, 1)
+    csr = oracle.assemble(coef, h, scheme)
+    g = np.random.default_rng(2)
+    for _ in range(3):
+        u = g.standard_normal((n, n))
+        v = g.standard_normal((n, n))
+        lhs = float(u.ravel() @ oracle.spmv(csr, v))
+        rhs = _quad_energy(coef, u, v, h, scheme)
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_stiffness_structure(scheme):
+    n, h = 8, 0.5
+    coef = _random_coef(n, 4)
+    A = oracle.csr_to_dense(oracle.assemble(coef, h, scheme), n * n)
+    assert np.abs(A - A.T).max() < 1e-14
+    assert np.abs(A.sum(axis=1)).max() < 1e-13            # constants in the kernel
+    ev = np.linalg.eigvalsh(A)
+    assert ev[0] > -1e-12 and ev[1] > 1e-6                  # PSD, one-dimensional kernel
+    rowptr = oracle.assemble(coef, h, scheme)[0]
+    width = np.diff(rowptr)
+    assert (width == (9 if scheme == oracle.SCHEME_CONSISTENT else 5)).all() or \
+        (scheme == oracle.SCHEME_LUMPED and (width <= 9).all())
+
+
+def test_lumped_constant_is_fd_laplacian():
+    # the paper's lumped scheme with a = 1 is exactly its 5-point A_Delta
+    n = 8
+    A = oracle.csr_to_dense(oracle.assemble(np.ones((n, n)), 0.5, oracle.SCHEME_LUMPED), n * n)
+    D = _paper_A_Delta(n)
+    assert np.abs(A - D).max() < 1e-14
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_rhs_equals_quadrature(scheme):
+    # f_i . v = -int a d_i v_h, by Gauss quadrature of the bilinear interpolant
+    n, h = 6, 0.25
+    coef = _random_coef(n, 5)
+    f = oracle.rhs(coef, h, scheme)
+    v = np.random.default_rng(6).standard_normal((n, n))
+    for i in range(2):
+        s = 0.0
+        for c1 in range(n):
+            for c2 in range(n):
+                vv = _cell_vals(v, c1, c2)
+                for t1, w1 in _gauss2():
+                    for t2, w2 in _gauss2():
+                        s += coef[c1, c2] * w1 * w2 * _bilinear_grad(vv, t1, t2, h)[i] * h * h
+        assert abs(float((f[i] * v).sum()) + s) < 1e-13
+        assert abs(f[i].sum()) < 1e-13
+
+
+# ---------------------------------------------------------- preconditioner --
+def _paper_A_Delta(n):
+    """A_Delta = (-Delta_P) (x) I + I (x) (-Delta_P), Delta_P of Eq. "BC_Neu_peri"."""
+    DP = -2 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    DP[0, -1] = DP[-1, 0] = 1
+    I = np.eye(n)
+    return np.kron(-DP, I) + np.kron(I, -DP)
+
+
+def test_laplacian_eigenvalues_closed_form():
+    n = 8
+    ev = np.sort(np.linalg.eigvalsh(_paper_A_Delta(n)))
+    cf = np.sort([oracle.laplacian_eig(n, k1, k2) for k1 in range(n) for k2 in range(n)])
+    assert np.abs(ev - cf).max() < 1e-12
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.3])
+def test_precond_inverts_B(delta):
+    n, c0 = 16, 5.5
+    r = np.random.default_rng(7).standard_normal((n, n))
+    if delta == 0.0:
+        r -= r.mean()
+    z = oracle.precond(r, c0, delta)
+    B = c0 * _paper_A_Delta(n) + delta * np.eye(n * n)
+    assert np.abs(B @ z.ravel() - r.ravel()).max() < 1e-12
+    if delta == 0.0:
+        assert abs(z.mean()) < 1e-14
+
+
+# ------------------------------------------------------------------ solver --
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_pcg_matches_dense_direct_solve(scheme):
+    for n, m0, seed in [(8, 4, 1), (16, 8, 2)]:
+        L = n // m0
+        h = 1.0 / m0
+        coef = _random_coef(n, seed)
+        csr = oracle.assemble(coef, h, scheme)
+        A = oracle.csr_to_dense(csr, n * n)
+        f = oracle.rhs(coef, h, scheme)
+        ones = np.ones(n * n) / n
+        for i in range(2):
+            u, it, rr = oracle.pcg(csr, f[i], 5.5, 1e-14, 2000)
+            # bordered system fixes the mean to zero (textbook dense solve)
+            K = np.block([[A, ones[:, None]], [ones[None, :], np.zeros((1, 1))]])
+            x = np.linalg.solve(K, np.concatenate([f[i].ravel(), [0.0]]))[:-1]
+            assert np.abs(u.ravel() - x).max() < 1e-10 * max(1.0, np.abs(x).max())
+            assert rr < 1e-12
+        Ae, Af = oracle.a_hom(coef, np.stack([oracle.pcg(csr, f[i], 5.5, 1e-14, 2000)[0]
+                                              for i in range(2)]), h, L, scheme)
+        assert np.abs(Ae - Af).max() < 1e-11
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_constant_coefficient_gives_cI(scheme):
+    n, m0 = 16, 4
+    r = oracle.solve_coef(np.full((n, n), 3.25), n // m0, m0, c0=3.25, scheme=scheme)
+    assert (r["iters"] == 0).all()
+    assert np.abs(r["A_energy"] - 3.25 * np.eye(2)).max() < 1e-13
+    assert np.abs(r["A_flux"] - 3.25 * np.eye(2)).max() < 1e-13
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_laminate_harmonic_and_arithmetic_means(scheme, axis):
+    # coefficient varying along x_{axis+1} only: A along that axis is the harmonic
+    # mean, across it the arithmetic mean, off-diagonals zero (exact for Q1)
+    n, m0 = 32, 4
+    prof = np.array([1.0, 1.0, 7.0, 2.5, 2.5, 2.5, 10.0, 1.0] * 4)
+    coef = np.repeat(prof[:, None], n, axis=1) if axis == 0 else np.repeat(prof[None, :], n, axis=0)
+    r = oracle.solve_coef(coef, n // m0, m0, c0=5.5, scheme=scheme, tol=1e-14)
+    harm, arith = 1.0 / np.mean(1.0 / prof), np.mean(prof)
+    expect = np.diag([harm, arith]) if axis == 0 else np.diag([arith, harm])
+    for key in ("A_energy", "A_flux"):
+        assert np.abs(r[key] - expect).max() < 1e-12 * arith
+
+
+def test_symmetry_and_flux_asymmetry_trend():
+    # energy form symmetric by construction; flux asymmetry shrinks with the
+    # tolerance (the trend of the paper's symmetry-vs-tolerance table)
+    d = workloads.realization(4, 8, 5.0, 2, 0, side_units=0.5)   # contrast 5
+    asym = []
+    for tol in (1e-4, 1e-7, 1e-10, 1e-13):
+        r = oracle.solve_realization(d, tol=tol, want_u=False)
+        assert abs(r["A_energy"][0, 1] - r["A_energy"][1, 0]) < 1e-14
+        asym.append(abs(r["A_flux"][0, 1] - r["A_flux"][1, 0]))
+    assert asym[-1] < 1e-11
+    assert asym[0] > asym[-1]
+
+
+def test_voigt_reuss_bounds():
+    for k in range(3):
+        d = workloads.realization(4, 8, 10.0, 21, k)
+        r = oracle.solve_realization(d, tol=1e-12)
+        coef = np.where(r["mask"] == 1, d["a_incl"], d["a_matrix"])
+        harm, arith = 1.0 / np.mean(1.0 / coef), np.mean(coef)
+        ev = np.linalg.eigvalsh(r["A_energy"])
+        assert harm < ev[0] <= ev[1] < arith
+        assert abs(r["mean_a"] - arith) < 1e-14
+
+
+def test_energy_form_above_converged_for_inexact_solve():
+    d = workloads.realization(4, 8, 10.0, 5, 0)
+    ref = oracle.solve_realization(d, tol=1e-13, want_u=False)["A_energy"]
+    for tol in (1e-2, 1e-3, 1e-5):
+        A = oracle.solve_realization(d, tol=tol, want_u=False)["A_energy"]
+        assert A[0, 0] >= ref[0, 0] - 1e-15 and A[1, 1] >= ref[1, 1] - 1e-15
+
+
+# ---------------------------------------------------------------- gradient --
+def _solve_u(coef, m0, scheme=oracle.SCHEME_CONSISTENT, c0=5.5):
+    n = coef.shape[0]
+    return oracle.solve_coef(coef, n // m0, m0, c0=c0, scheme=scheme, tol=1e-14, max_iter=5000)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_gradient_euler_identity(scheme):
+    # A is 1-homogeneous in a: sum_c a_c dA_ij/da_c = A_ij
+    n, m0 = 16, 4
+    coef = _random_coef(n, 8)
+    r = _solve_u(coef, m0, scheme)
+    for i in range(2):
+        for j in range(2):
+            G = np.zeros((2, 2)); G[i, j] = 1
+            g = oracle.a_hom_grad(r["u"], G, 1.0 / m0, n // m0, scheme)
+            assert abs((coef * g).sum() - r["A_energy"][i, j]) < 1e-12
+            if i == j:
+                assert g.min() >= 0.0
+
+
+def test_gradient_constant_field_closed_form():
+    n, m0 = 8, 4
+    r = _solve_u(np.full((n, n), 2.0), m0)
+    h, L = 1.0 / m0, n // m0
+    for i in range(2):
+        for j in range(2):
+            G = np.zeros((2, 2)); G[i, j] = 1
+            g = oracle.a_hom_grad(r["u"], G, h, L)
+            assert np.abs(g - (1.0 if i == j else 0.0) * h * h / L ** 2).max() < 1e-15
+
+
+def test_gradient_matches_central_differences():
+    n, m0 = 8, 4
+    coef = _random_coef(n, 9)
+    r = _solve_u(coef, m0)
+    G = np.array([[0.7, -0.4], [0.25, 1.3]])
+    g = oracle.a_hom_grad(r["u"], G, 1.0 / m0, n // m0)
+    eps = 1e-5
+    for c in [(0, 0), (3, 5), (7, 7), (2, 6)]:
+        cp, cm = coef.copy(), coef.copy()
+        cp[c] += eps
+        cm[c] -= eps
+        fd = ((G * _solve_u(cp, m0)["A_energy"]).sum() -
+              (G * _solve_u(cm, m0)["A_energy"]).sum()) / (2 * eps)
+        assert abs(fd - g[c]) < 1e-8 * max(1.0, abs(g[c])) + 1e-9
+
+
+# -------------------------------------------------------------- statistics --
+def test_statistics_match_numpy():
+    g = np.random.default_rng(3)
+    A = g.standard_normal((50, 2, 2))
+    A[:, 1, 0] = A[:, 0, 1]
+    L = 16
+    s = oracle.statistics(A, L)
+    flat = A.reshape(50, 4)
+    np.testing.assert_allclose(s["mean"].ravel(), flat.mean(axis=0), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(s["Q"], L ** 2 * np.cov(flat, rowvar=False, ddof=1), rtol=1e-12,
+                               atol=1e-13)
+    np.testing.assert_allclose(s["var"].ravel(), flat.var(axis=0, ddof=1), rtol=1e-12)
+    assert abs(s["std12_paper"] - np.sqrt((flat[:, 1] ** 2).mean())) < 1e-14
+    assert abs(s["stddiff_paper"] - np.sqrt(((flat[:, 0] - flat[:, 3]) ** 2).mean())) < 1e-14
+    # symmetric A => the paper's identities among Q's entries hold exactly
+    Q = s["Q"]
+    assert abs(Q[1, 1] - Q[1, 2]) < 1e-12 and abs(Q[2, 2] - Q[1, 2]) < 1e-12
+
+
+def test_workload_inclusion_counts():
+    assert workloads.realization(4, 8, 10, 0, 0)["n_incl"] == 11
+    assert workloads.realization(32, 16, 10, 0, 0)["n_incl"] == 717
+    assert workloads.realization(64, 16, 100, 0, 0)["n_incl"] == 2867
+    assert workloads.realization(256, 8, 100, 0, 0)["n_incl"] == 45875
+    assert workloads.realization(8, 8, 10, 0, 0)["n_incl"] == 45
+    assert workloads.realization(16, 8, 10, 0, 0)["n_incl"] == 179
