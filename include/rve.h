@@ -1,0 +1,217 @@
+/*
+ * rve.h -- C ABI of librve, a GB300 (sm_103a) implementation of the
+ * representative-volume-element (RVE) corrector method of Khoromskaia,
+ * Khoromskij & Otto, arXiv:1903.12227.
+ *
+ * For each random realization of a two-valued coefficient field on the
+ * periodic cell [0,L)^2 (overlapping axis-parallel square inclusions, Sec. 2,
+ * Eqs. "Stoch-decomp", "coef_diag") the library
+ *   1. generates the field                         (rve_gen_field),
+ *   2. solves the two Q1-FEM corrector problems    (rve_solve_correctors)
+ *      -div a (e_i + grad phi_i) = 0, i = 1,2 (Eqs. "RHS_grad1",
+ *      "Ellipt_variat", "FEM_Galerk") by preconditioned CG with the paper's
+ *      preconditioner B = c0 A_Delta + delta I (Sec. 3.4),
+ *   3. reduces them to the 2x2 homogenized matrix   (rve_a_hom)
+ *      (Eqs. "A_hom_m", "Ahom_m_entry", "wg01"),
+ *   4. returns the derivative of sum_ij G_ij A_ij with respect to every cell
+ *      value                                        (rve_a_hom_backward).
+ *
+ * Grid and layout.  A realization has n = L*m0 nodes per axis (grid step
+ * h = 1/m0 on the torus [0,L)^2); n must be a power of two with
+ * 32 <= n <= 2048 (the preconditioner's radix-2 transforms).  Node (i1,i2)
+ * is at (i1 h, i2 h); cell (c1,c2) is the square whose lower-left node is
+ * (c1,c2).  Linear index i1*n + i2 (i2 contiguous; the paper's big-endian
+ * order, Sec. 3.2).  A batch of realizations is packed back to back in
+ * descriptor order; realization b starts at node offset sum_{b'<b} n_b'^2.
+ *
+ *   mask   uint32 words, n*n/32 per realization: bit (c % 32) of word
+ *          (c / 32), c = c1*n + c2, is set iff cell (c1,c2) is covered.
+ *   coef   double, n*n per realization: general cell values a_c (may be NULL
+ *          where documented; the mask and the two values are used then).
+ *   vec    double2 (or float2 for the FP32 helpers), one per node: the two
+ *          correctors' values interleaved, x = corrector 1, y = corrector 2.
+ *   A      double [batch][4] = (a11, a12, a21, a22).
+ *
+ * Memory ownership.  The caller allocates every buffer (device memory unless
+ * stated otherwise) and keeps it alive until the work on `stream` is done.
+ * The library allocates no device memory: solvers take a caller-provided
+ * workspace whose size rve_workspace_size() returns.  Every call is
+ * asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ * default stream) unless stated otherwise.
+ *
+ * Errors.  Invalid arguments return RVE_EINVAL before anything is launched.
+ * A failed launch returns RVE_ECUDA.  Per-realization solver outcomes
+ * (non-convergence, NaN, time-out) are reported in rve_solve_info.status and
+ * do not fail the call.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RVE_OK = 0,
+    RVE_EINVAL = 1,     /* invalid argument (nothing launched)              */
+    RVE_ENOCONV = 2,    /* max_iter reached before the tolerance            */
+    RVE_ENAN = 3,       /* NaN/Inf met in a reduction                        */
+    RVE_ETIMEOUT = 4,   /* a bounded device-side wait gave up               */
+    RVE_ECUDA = 5,      /* a CUDA call failed                               */
+    RVE_ENOMEM = 6      /* workspace smaller than rve_workspace_size()      */
+} rve_status;
+
+typedef enum {
+    RVE_FP64 = 0,       /* every step in FP64                                */
+    RVE_MIXED = 1       /* FP32 stencil/transform/vectors; FP64 dots, outer
+                           true-residual refinement and A_hom               */
+} rve_precision;
+
+typedef enum {
+    RVE_Q1_CONSISTENT = 0,  /* Q1 element matrix K1(x)M1 + M1(x)K1, 9-point */
+    RVE_Q1_LUMPED = 1       /* trapezoid mass (the paper's I-hat, Eq.
+                               "As_Kron"), 5-point                          */
+} rve_scheme;
+
+typedef enum {
+    RVE_PATH_FUSED = 0,     /* batched fused pipeline (3 passes/iteration)  */
+    RVE_PATH_PLAIN = 1,     /* unfused textbook PCG, one kernel per BLAS-1
+                               step; FP64 only                              */
+    RVE_PATH_PERSISTENT = 2 /* one cooperative persistent launch for the
+                               whole batch (uneven sizes allowed)           */
+} rve_path;
+
+/* One realization (Sec. 2 and 3.1): L unit cells per axis, m0 grid cells per
+ * unit length, n_incl square inclusions of incl_cells x incl_cells grid
+ * cells each, lower-left corners uniform on the grid nodes (drawn with
+ * SplitMix64 from (seed, index)), overlaps allowed.  Coefficient a_matrix
+ * outside and a_incl inside the covered set (Eq. "coef_diag").  48 bytes. */
+typedef struct {
+    int32_t L, m0, incl_cells, n_incl;
+    double a_matrix, a_incl;
+    uint64_t seed, index;
+} rve_realization;
+
+/* Solver options (Sec. 3.4).  Zero-initialised fields take defaults. */
+typedef struct {
+    int32_t scheme;      /* rve_scheme                                      */
+    int32_t precision;   /* rve_precision                                   */
+    int32_t path;        /* rve_path                                        */
+    int32_t max_iter;    /* cap on CG iterations per corrector (0 = 20000)  */
+    double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (0=1e-10)*/
+    double delta;        /* preconditioner shift; 0 = drop the constant mode*/
+    double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-5)*/
+    int32_t tile_rows;   /* stencil tile height, 0 = tuned default          */
+    int32_t col_tile;    /* columns per transform tile, 0 = tuned default   */
+    int32_t check_every; /* host convergence poll period (0 = 8)            */
+    int32_t timeout_ms;  /* persistent path: bound on each grid-wide wait
+                            (0 = 2000 ms)                                   */
+} rve_solve_opts;
+
+/* Per-realization solver report (device memory, one per realization). */
+typedef struct {
+    int32_t iters[2];     /* CG iterations (operator applications) per corrector */
+    int32_t status;       /* rve_status                                           */
+    int32_t refinements;  /* FP64 true-residual evaluations                       */
+    double relres[2];     /* last FP64 true relative residual per corrector       */
+} rve_solve_info;
+
+/* Human-readable name of a status code (static string). */
+const char* rve_status_string(int32_t status);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int32_t rve_version(void);
+
+/* Number of uint32 mask words / nodes of a batch (host-side arithmetic). */
+int64_t rve_mask_words(const rve_realization* r, int32_t batch);
+int64_t rve_nodes(const rve_realization* r, int32_t batch);
+
+/* Field generation (Sec. 2 and 3.1, Eq. "Stoch-decomp"): writes the covered
+ * set of every realization as a bitmask.  r: host array [batch].
+ * mask: device, rve_mask_words() words, fully overwritten. */
+rve_status rve_gen_field(const rve_realization* r, int32_t batch, uint32_t* mask,
+                         void* stream);
+
+/* Galerkin right-hand sides f_i = -int a d_i psi (Eq. "FEM_discr_RHS"),
+ * with the stiffness's quadrature (Sec. 4.3): f[node] = (f_1, f_2).
+ * Coefficients from coef (device doubles) if non-NULL, else from mask. */
+rve_status rve_rhs(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                   const double* coef, double* f, void* stream);
+
+/* y = A x, A the Q1 stiffness of Eq. "FEM_matrix" assembled as in Eq.
+ * "As_Kron", applied matrix-free as a 9-point (consistent) or 5-point
+ * (lumped) periodic stencil.  precision = RVE_FP64: x, y are double2 per
+ * node; RVE_MIXED: float2 per node, FP32 arithmetic. */
+rve_status rve_apply_stiffness(const rve_realization* r, int32_t batch,
+                               const uint32_t* mask, const double* coef,
+                               int32_t scheme, int32_t precision,
+                               const void* x, void* y, void* stream);
+
+/* y = B^{-1} x with B = c0 A_Delta + delta I (Sec. 3.4), A_Delta the
+ * periodic 5-point Laplacian (Eq. "Lap_Kron"), c0 = (a_matrix + a_incl)/2
+ * (Lemma "Cond_Number").  delta = 0 drops the constant mode.  Applied by
+ * separable real (Hartley) transforms along each axis.  x, y as in
+ * rve_apply_stiffness; x and y may alias.  ws: device workspace of at least
+ * rve_workspace_size(r, batch, NULL) bytes. */
+rve_status rve_apply_precond(const rve_realization* r, int32_t batch, double delta,
+                             int32_t precision, const void* x, void* y,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes needed by rve_solve_correctors / rve_a_hom /
+ * rve_apply_precond for this batch and these options (opts may be NULL for
+ * defaults).  Returns 0 for invalid arguments. */
+size_t rve_workspace_size(const rve_realization* r, int32_t batch,
+                          const rve_solve_opts* opts);
+
+/* Solve both corrector problems of every realization (Sec. 3.4, 4.1):
+ * PCG from u = 0 until the FP64 true residual meets opts->tol.
+ * mask / coef: as in rve_rhs (coef overrides the mask when non-NULL; c0
+ * still comes from a_matrix and a_incl).  u: device double2 per node,
+ * overwritten with the correctors (mean zero up to rounding).  info: device
+ * rve_solve_info[batch].  ws: device workspace.  With the fused path the
+ * call polls convergence every opts->check_every iterations (a stream
+ * synchronisation); the persistent path launches once and does not sync. */
+rve_status rve_solve_correctors(const rve_realization* r, int32_t batch,
+                                const uint32_t* mask, const double* coef,
+                                const rve_solve_opts* opts, double* u,
+                                rve_solve_info* info, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* Homogenized matrix of every realization from its correctors u.
+ * A: energy form a_ij = (1/L^2) int (e_j + grad phi_j).a(e_i + grad phi_i)
+ * (Eq. "wg01" as rewritten in its symmetry argument), evaluated exactly as
+ * mean(a) delta_ij - (f_i.u_j + f_j.u_i - u_i.A u_j)/L^2 in FP64.
+ * A_flux (nullable): flux form of Eq. "Ahom_m_entry",
+ * a_ij = mean(a) delta_ij - f_j.u_i / L^2.  Both device double[batch][4]. */
+rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                     const double* coef, int32_t scheme, const double* u,
+                     double* A, double* A_flux, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Adjoint of the energy form: grad_coef[cell] = d(sum_ij gradA_ij a_ij)/d a_c
+ * = (1/L^2) sum_ij gradA_ij int_cell (e_i + grad phi_i).(e_j + grad phi_j)
+ * (the problem is self-adjoint, so no second solve).  gradA: device
+ * double[batch][4]; grad_coef: device double per cell, overwritten. */
+rve_status rve_a_hom_backward(const rve_realization* r, int32_t batch,
+                              int32_t scheme, const double* u, const double* gradA,
+                              double* grad_coef, void* stream);
+
+/* Whole pipeline with HOST inputs and outputs: copies the descriptors in,
+ * generates the fields, solves, reduces, and copies A (and info) back into
+ * host memory; returns after the results are in host memory.  ws: device
+ * workspace of rve_homogenize_workspace_size() bytes (holds the masks and
+ * correctors too).  A_host: double[batch][4]; info_host nullable. */
+size_t rve_homogenize_workspace_size(const rve_realization* r, int32_t batch,
+                                     const rve_solve_opts* opts);
+rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
+                               const rve_solve_opts* opts, double* A_host,
+                               rve_solve_info* info_host, void* ws, size_t ws_bytes,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

@@ -1,0 +1,374 @@
+// rve_api.cu -- the C ABI of librve (declared in include/rve.h): argument
+// validation, plan and workspace layout, and dispatch to the launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rve_common.cuh"
+#include "rve_internal.h"
+
+namespace rve {
+
+static uint64_t host_sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int ilog2(int v) {
+    int p = 0;
+    while ((1 << p) < v) ++p;
+    return p;
+}
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+constexpr int MIN_N = 32, MAX_N = 2048;
+constexpr size_t MAX_SMEM = 227 * 1024;
+
+static rve_solve_opts defaults(const rve_solve_opts* o) {
+    rve_solve_opts r;
+    std::memset(&r, 0, sizeof(r));
+    if (o) r = *o;
+    if (r.max_iter <= 0) r.max_iter = 20000;
+    if (!(r.tol > 0.0)) r.tol = 1e-10;
+    if (!(r.inner_tol > 0.0)) r.inner_tol = 1e-5;
+    if (r.check_every <= 0) r.check_every = 8;
+    if (r.timeout_ms <= 0) r.timeout_ms = 2000;
+    return r;
+}
+
+static void default_tiles(int n, size_t vb, const rve_solve_opts& o, Tiles& t) {
+    t.tU = std::min(n, 2048 / n);
+    if (vb == 8) t.tS = (n >= 2048) ? 4 : 8;
+    else t.tS = (n >= 2048) ? 2 : (n >= 1024 ? 4 : 8);
+    int tc = (int)(65536 / (2 * (size_t)n * vb));
+    int c = 1;
+    while (c * 2 <= tc) c *= 2;
+    t.tC = std::max(c, vb == 8 ? 4 : 2);
+    if (o.tile_rows > 0) t.tS = o.tile_rows;
+    if (o.col_tile > 0) t.tC = o.col_tile;
+    t.tS = std::min(t.tS, n);
+    t.tC = std::min(t.tC, n);
+}
+
+rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
+                     Plan& p, bool need_vectors) {
+    if (!r || batch <= 0 || batch > (1 << 22)) return RVE_EINVAL;
+    const rve_solve_opts o = defaults(opts);
+    if (o.scheme != RVE_Q1_CONSISTENT && o.scheme != RVE_Q1_LUMPED) return RVE_EINVAL;
+    if (o.precision != RVE_FP64 && o.precision != RVE_MIXED) return RVE_EINVAL;
+    if (o.path != RVE_PATH_FUSED && o.path != RVE_PATH_PLAIN && o.path != RVE_PATH_PERSISTENT)
+        return RVE_EINVAL;
+    if (o.path == RVE_PATH_PLAIN && o.precision != RVE_FP64) return RVE_EINVAL;
+    if (!std::isfinite(o.delta) || o.delta < 0.0 || !(o.tol < 1.0) || !(o.inner_tol < 1.0))
+        return RVE_EINVAL;
+    p.batch = batch;
+    p.precision = o.precision;
+    p.scheme = o.scheme;
+    p.path = o.path;
+    p.vbytes = (o.precision == RVE_MIXED) ? 8 : 16;
+    p.desc.resize(batch);
+    p.startS.assign(batch + 1, 0);
+    p.startU.assign(batch + 1, 0);
+    p.startC.assign(batch + 1, 0);
+    p.startA.assign(batch + 1, 0);
+    p.nodes = 0;
+    p.words = 0;
+    p.max_log2n = 5;
+    p.smemS = p.smemU = p.smemC = 0;
+    int64_t maxnb = 0;
+    for (int b = 0; b < batch; ++b) {
+        const rve_realization& x = r[b];
+        if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
+        const int64_t n64 = (int64_t)x.L * x.m0;
+        if (n64 < MIN_N || n64 > MAX_N || !pow2((int)n64)) return RVE_EINVAL;
+        const int n = (int)n64;
+        if (x.incl_cells <= 0 || x.incl_cells > n || x.n_incl < 0) return RVE_EINVAL;
+        if ((int64_t)x.n_incl * x.incl_cells > (1LL << 30)) return RVE_EINVAL;
+        if (!std::isfinite(x.a_matrix) || !std::isfinite(x.a_incl) || !(x.a_matrix > 0.0) ||
+            !(x.a_incl > 0.0))
+            return RVE_EINVAL;
+        Tiles t;
+        default_tiles(n, p.vbytes, o, t);
+        if (!pow2(t.tS) || !pow2(t.tC) || n % t.tS || n % t.tC) return RVE_EINVAL;
+        RDesc& d = p.desc[b];
+        std::memset(&d, 0, sizeof(d));
+        d.n = n;
+        d.log2n = ilog2(n);
+        d.L = x.L;
+        d.s = x.incl_cells;
+        d.n_incl = x.n_incl;
+        d.tS = t.tS;
+        d.tU = t.tU;
+        d.tC = t.tC;
+        d.node_off = p.nodes;
+        d.word_off = p.words;
+        d.a_matrix = x.a_matrix;
+        d.a_incl = x.a_incl;
+        d.h = 1.0 / (double)x.m0;
+        d.c0 = 0.5 * (x.a_matrix + x.a_incl);
+        d.inv_vol = 1.0 / ((double)x.L * (double)x.L);
+        d.key = host_sm64_mix(x.seed + (x.index + 1) * 0x9E3779B97F4A7C15ull);
+        p.nodes += (int64_t)n * n;
+        p.words += ((int64_t)n * n) / 32;
+        p.max_log2n = std::max(p.max_log2n, d.log2n);
+        p.startS[b + 1] = p.startS[b] + n / t.tS;
+        p.startU[b + 1] = p.startU[b] + n / t.tU;
+        p.startC[b + 1] = p.startC[b] + n / t.tC;
+        p.startA[b + 1] = p.startA[b] + (int32_t)(((int64_t)n * n) / 1024);
+        maxnb = std::max<int64_t>(maxnb, ((int64_t)n * n) / 1024);
+        const size_t vb = p.vbytes;
+        p.smemS = std::max(p.smemS, ((size_t)(t.tS + 2) * n + 2 * (size_t)t.tU * n) * vb);
+        p.smemU = std::max(p.smemU, 2 * (size_t)t.tU * n * vb);
+        p.smemC = std::max(p.smemC, 2 * (size_t)t.tC * n * vb);
+    }
+    // the plain path and the standalone preconditioner run FP64 transforms
+    // with the same row geometry: keep their shared memory within bounds too
+    if (p.smemS > MAX_SMEM || p.smemU * 3 / 2 > MAX_SMEM || p.smemC > MAX_SMEM) return RVE_EINVAL;
+    p.tilesS = p.startS[batch];
+    p.tilesU = p.startU[batch];
+    p.tilesC = p.startC[batch];
+    p.tilesA = p.startA[batch];
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off = align_up(off + bytes);
+        return o2;
+    };
+    const size_t tab = (size_t)2 << p.max_log2n;
+    p.o_desc = take(sizeof(RDesc) * batch);
+    p.o_startS = take(sizeof(int32_t) * (batch + 1));
+    p.o_startU = take(sizeof(int32_t) * (batch + 1));
+    p.o_startC = take(sizeof(int32_t) * (batch + 1));
+    p.o_startA = take(sizeof(int32_t) * (batch + 1));
+    p.o_tw64 = take(sizeof(double2) * tab);
+    p.o_tw32 = take(sizeof(float2) * tab);
+    p.o_lap = take(sizeof(double) * tab);
+    p.o_state = take(sizeof(RState) * batch);
+    p.o_partS = take(sizeof(double) * 2 * (size_t)std::max<int64_t>(p.tilesS, maxnb));
+    p.o_partU = take(sizeof(double) * 2 * (size_t)p.tilesU);
+    p.o_partC = take(sizeof(double) * 2 * (size_t)p.tilesC);
+    p.o_partA = take(sizeof(double) * 8 * (size_t)p.tilesA);
+    p.o_ctl = take(sizeof(int32_t) * 64);
+    if (need_vectors) {
+        const size_t vec = (size_t)p.nodes * p.vbytes;
+        p.o_X = take(vec);
+        p.o_R = take(vec);
+        p.o_Q = take(vec);
+        p.o_T = take(vec);
+        p.o_P0 = take(vec);
+        p.o_P1 = take(vec);
+    }
+    p.total = off;
+    return RVE_OK;
+}
+
+}  // namespace rve
+
+using namespace rve;
+
+static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* rve_status_string(int32_t status) {
+    switch (status) {
+        case RVE_OK: return "RVE_OK";
+        case RVE_EINVAL: return "RVE_EINVAL: invalid argument";
+        case RVE_ENOCONV: return "RVE_ENOCONV: no convergence within max_iter";
+        case RVE_ENAN: return "RVE_ENAN: NaN or Inf in a reduction";
+        case RVE_ETIMEOUT: return "RVE_ETIMEOUT: a bounded device-side wait gave up";
+        case RVE_ECUDA: return "RVE_ECUDA: a CUDA call failed";
+        case RVE_ENOMEM: return "RVE_ENOMEM: workspace too small";
+        default: return "unknown rve_status";
+    }
+}
+
+int32_t rve_version(void) { return 100; }
+
+int64_t rve_mask_words(const rve_realization* r, int32_t batch) {
+    Plan p;
+    if (make_plan(r, batch, nullptr, p, false) != RVE_OK) return -1;
+    return p.words;
+}
+
+int64_t rve_nodes(const rve_realization* r, int32_t batch) {
+    Plan p;
+    if (make_plan(r, batch, nullptr, p, false) != RVE_OK) return -1;
+    return p.nodes;
+}
+
+rve_status rve_gen_field(const rve_realization* r, int32_t batch, uint32_t* mask, void* stream) {
+    Plan p;
+    rve_status st = make_plan(r, batch, nullptr, p, false);
+    if (st != RVE_OK) return st;
+    if (!mask) return RVE_EINVAL;
+    return launch_gen_field(p, nullptr, mask, as_stream(stream)) == cudaSuccess ? RVE_OK
+                                                                               : RVE_ECUDA;
+}
+
+rve_status rve_rhs(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                   const double* coef, double* f, void* stream) {
+    Plan p;
+    rve_status st = make_plan(r, batch, nullptr, p, false);
+    if (st != RVE_OK) return st;
+    if (!f || (!mask && !coef)) return RVE_EINVAL;
+    return launch_rhs(p, nullptr, mask, coef, f, as_stream(stream)) == cudaSuccess ? RVE_OK
+                                                                                  : RVE_ECUDA;
+}
+
+rve_status rve_apply_stiffness(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                               const double* coef, int32_t scheme, int32_t precision,
+                               const void* x, void* y, void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.scheme = scheme;
+    o.precision = precision;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, false);
+    if (st != RVE_OK) return st;
+    if (!x || !y || x == y || (!mask && !coef)) return RVE_EINVAL;
+    return launch_stiffness(p, nullptr, mask, coef, scheme, precision, x, y, as_stream(stream)) ==
+                   cudaSuccess
+               ? RVE_OK
+               : RVE_ECUDA;
+}
+
+size_t rve_workspace_size(const rve_realization* r, int32_t batch, const rve_solve_opts* opts) {
+    Plan p;
+    rve_solve_opts o = defaults(opts);
+    if (!opts) o.precision = RVE_FP64;   // large enough for either precision
+    if (make_plan(r, batch, &o, p, true) != RVE_OK) return 0;
+    return p.total;
+}
+
+rve_status rve_apply_precond(const rve_realization* r, int32_t batch, double delta,
+                             int32_t precision, const void* x, void* y, void* ws,
+                             size_t ws_bytes, void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = precision;
+    o.delta = delta;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, true);
+    if (st != RVE_OK) return st;
+    if (!x || !y || !ws) return RVE_EINVAL;
+    if (ws_bytes < p.total) return RVE_ENOMEM;
+    return launch_precond(p, ws, delta, precision, x, y, as_stream(stream)) == cudaSuccess
+               ? RVE_OK
+               : RVE_ECUDA;
+}
+
+rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                                const double* coef, const rve_solve_opts* opts, double* u,
+                                rve_solve_info* info, void* ws, size_t ws_bytes, void* stream) {
+    const rve_solve_opts o = defaults(opts);
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, true);
+    if (st != RVE_OK) return st;
+    if (!u || !info || !ws || (!mask && !coef)) return RVE_EINVAL;
+    if (ws_bytes < p.total) return RVE_ENOMEM;
+    if (o.path == RVE_PATH_PLAIN)
+        return run_solve_plain(p, ws, mask, coef, o, u, info, as_stream(stream));
+    return run_solve_fused(p, ws, mask, coef, o, u, info, as_stream(stream));
+}
+
+rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                     const double* coef, int32_t scheme, const double* u, double* A,
+                     double* A_flux, void* ws, size_t ws_bytes, void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.scheme = scheme;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, false);
+    if (st != RVE_OK) return st;
+    if (!u || !A || !ws || (!mask && !coef)) return RVE_EINVAL;
+    if (ws_bytes < p.total) return RVE_ENOMEM;
+    if (upload_plan(p, ws, as_stream(stream)) != RVE_OK) return RVE_ECUDA;
+    return launch_a_hom(p, ws, mask, coef, scheme, u, A, A_flux, as_stream(stream)) == cudaSuccess
+               ? RVE_OK
+               : RVE_ECUDA;
+}
+
+rve_status rve_a_hom_backward(const rve_realization* r, int32_t batch, int32_t scheme,
+                              const double* u, const double* gradA, double* grad_coef,
+                              void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.scheme = scheme;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, false);
+    if (st != RVE_OK) return st;
+    if (!u || !gradA || !grad_coef) return RVE_EINVAL;
+    return launch_backward(p, nullptr, scheme, u, gradA, grad_coef, as_stream(stream)) ==
+                   cudaSuccess
+               ? RVE_OK
+               : RVE_ECUDA;
+}
+
+// Host pipeline: [mask | u | A | info | solver workspace] inside ws.
+static size_t homog_layout(const Plan& p, size_t* o_mask, size_t* o_u, size_t* o_A,
+                           size_t* o_info, size_t* o_ws) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off = align_up(off + bytes);
+        return o2;
+    };
+    *o_mask = take(sizeof(uint32_t) * (size_t)p.words);
+    *o_u = take(sizeof(double2) * (size_t)p.nodes);
+    *o_A = take(sizeof(double) * 4 * (size_t)p.batch);
+    *o_info = take(sizeof(rve_solve_info) * (size_t)p.batch);
+    *o_ws = take(p.total);
+    return off;
+}
+
+size_t rve_homogenize_workspace_size(const rve_realization* r, int32_t batch,
+                                     const rve_solve_opts* opts) {
+    Plan p;
+    if (make_plan(r, batch, opts, p, true) != RVE_OK) return 0;
+    size_t a, b, c, d, e;
+    return homog_layout(p, &a, &b, &c, &d, &e);
+}
+
+rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
+                               const rve_solve_opts* opts, double* A_host,
+                               rve_solve_info* info_host, void* ws, size_t ws_bytes,
+                               void* stream) {
+    const rve_solve_opts o = defaults(opts);
+    Plan p;
+    rve_status st = make_plan(r_host, batch, &o, p, true);
+    if (st != RVE_OK) return st;
+    if (!A_host || !ws) return RVE_EINVAL;
+    size_t om, ou, oa, oi, ow;
+    const size_t need = homog_layout(p, &om, &ou, &oa, &oi, &ow);
+    if (ws_bytes < need) return RVE_ENOMEM;
+    char* w = static_cast<char*>(ws);
+    cudaStream_t s = as_stream(stream);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(w + om);
+    double* u = reinterpret_cast<double*>(w + ou);
+    double* A = reinterpret_cast<double*>(w + oa);
+    rve_solve_info* info = reinterpret_cast<rve_solve_info*>(w + oi);
+    if (launch_gen_field(p, nullptr, mask, s) != cudaSuccess) return RVE_ECUDA;
+    st = rve_solve_correctors(r_host, batch, mask, nullptr, &o, u, info, w + ow, p.total, stream);
+    if (st != RVE_OK) return st;
+    st = rve_a_hom(r_host, batch, mask, nullptr, o.scheme, u, A, nullptr, w + ow, p.total, stream);
+    if (st != RVE_OK) return st;
+    if (cudaMemcpyAsync(A_host, A, sizeof(double) * 4 * (size_t)batch, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return RVE_ECUDA;
+    if (info_host &&
+        cudaMemcpyAsync(info_host, info, sizeof(rve_solve_info) * (size_t)batch,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return RVE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+}  // extern "C"

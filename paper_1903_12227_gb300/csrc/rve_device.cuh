@@ -1,0 +1,219 @@
+// rve_device.cuh -- device-side building blocks of librve (sm_103a).
+//
+// * complex helpers on float2 / double2;
+// * DotAcc: per-thread dot-product accumulators.  FP64 data accumulate in
+//   double.  FP32 data form each product exactly (fmaf error-free
+//   transformation) and sum it in a double-float (hi, lo) pair, so every
+//   inner product reaches FP64-class accuracy without FP64 arithmetic per
+//   element; partial sums leave the thread as double;
+// * deterministic warp / block reductions (fixed tree order);
+// * a shared-memory Stockham FFT of length n = 2^p (radix 8, then 4 or 2)
+//   used for the separable transforms of the preconditioner;
+// * the Hartley "pair" post-processing: the complex DFT Z of a + i b (a, b
+//   real) gives the Hartley transforms of a and b, because
+//   H_a(k) = Re A_k - Im A_k with A_k = (Z_k + conj Z_{-k}) / 2, and the
+//   same for b with B_k = (Z_k - conj Z_{-k}) / 2i.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rve {
+
+// ---------------------------------------------------------------- types --
+template <typename V> struct ScalarOf;
+template <> struct ScalarOf<float2> { typedef float T; };
+template <> struct ScalarOf<double2> { typedef double T; };
+
+template <typename V> __device__ __forceinline__ V mk(typename ScalarOf<V>::T x,
+                                                       typename ScalarOf<V>::T y);
+template <> __device__ __forceinline__ float2 mk<float2>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// multiply by -i: (x + iy)(-i) = y - ix
+template <typename V> __device__ __forceinline__ V cmul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+
+// ------------------------------------------------------- dot accumulator --
+template <typename T> struct DotAcc;
+
+template <> struct DotAcc<double> {
+    double s;
+    __device__ __forceinline__ DotAcc() : s(0.0) {}
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// double-float accumulation: exact product (hi + lo), then TwoSum into
+// (s_hi, s_lo) (Knuth's TwoSum; Dekker/Ogita-Rump-Oishi error-free
+// transformations).
+template <> struct DotAcc<float> {
+    float hi, lo;
+    __device__ __forceinline__ DotAcc() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ void add(float a, float b) {
+        float p = a * b;
+        float pe = fmaf(a, b, -p);        // exact: a*b = p + pe
+        float t = hi + p;
+        float bv = t - hi;
+        float e = (hi - (t - bv)) + (p - bv);  // exact: hi + p = t + e
+        hi = t;
+        lo += e + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// --------------------------------------------------- deterministic reduce --
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of `v` over the block in a fixed order; result valid in thread 0.
+// `scratch` holds at least blockDim.x/32 doubles.  Ends with a barrier so
+// that scratch can be reused.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < nw ? scratch[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Fixed-order sum of `count` doubles at src[k*stride] by one warp; every
+// lane gets the result.
+__device__ __forceinline__ double warp_sum_array(const double* __restrict__ src, int count,
+                                                 int stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int k = lane; k < count; k += 32) s += src[(int64_t)k * stride];
+    return warp_sum(s);
+}
+
+// ------------------------------------------------------------ radix DFTs --
+// Forward (exp(-2 pi i rs/R)) in-register DFTs.
+template <typename V> __device__ __forceinline__ void dft2(V& a, V& b) {
+    V t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <typename V> __device__ __forceinline__ void dft4(V& u0, V& u1, V& u2, V& u3) {
+    V s02 = cadd(u0, u2), d02 = csub(u0, u2);
+    V s13 = cadd(u1, u3), d13 = cmul_mi(csub(u1, u3));
+    u0 = cadd(s02, s13);
+    u2 = csub(s02, s13);
+    u1 = cadd(d02, d13);
+    u3 = csub(d02, d13);
+}
+
+template <typename V> __device__ __forceinline__ void dft8(V* u) {
+    typedef typename ScalarOf<V>::T T;
+    const T c = (T)0.70710678118654752440084436210484903928;
+    V e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+    V o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
+    dft4(e0, e1, e2, e3);
+    dft4(o0, o1, o2, o3);
+    // twiddles W8^s = exp(-i pi s/4): 1, c(1-i), -i, -c(1+i)
+    V t1 = mk<V>(c * (o1.x + o1.y), c * (o1.y - o1.x));
+    V t2 = cmul_mi(o2);
+    V t3 = mk<V>(c * (o3.y - o3.x), -c * (o3.x + o3.y));
+    u[0] = cadd(e0, o0); u[4] = csub(e0, o0);
+    u[1] = cadd(e1, t1); u[5] = csub(e1, t1);
+    u[2] = cadd(e2, t2); u[6] = csub(e2, t2);
+    u[3] = cadd(e3, t3); u[7] = csub(e3, t3);
+}
+
+// -------------------------------------------------------- Stockham FFT --
+// Forward DFT (unnormalised) of length n = 2^log2n on `nseq` sequences in
+// shared memory.  Element i of sequence q is A[q*seqstride + i*stride].
+// B is a second buffer of the same shape (ping-pong).  tw[m] =
+// exp(-2 pi i m / n), m < n.  SEQ_FAST picks the work-to-thread mapping:
+// consecutive threads on consecutive sequences (columns stored side by side)
+// or on consecutive butterflies (rows).  Called by all threads of the block
+// (tid in [0, nthr)); contains barriers.  Returns the buffer holding the
+// result (A or B).
+template <typename V, bool SEQ_FAST>
+__device__ V* smem_fft(V* A, V* B, int log2n, int stride, int seqstride, int nseq,
+                       const V* __restrict__ tw, int tid, int nthr) {
+    const int n = 1 << log2n;
+    int log2Ns = 0;
+    int rem = log2n;
+    while (rem > 0) {
+        const int lr = rem >= 3 ? 3 : rem;     // radix 8, then a 4 or 2 tail
+        const int log2units = log2n - lr;      // butterflies per sequence
+        const int units = 1 << log2units;
+        const int total = units * nseq;
+        const int Ns = 1 << log2Ns;
+        const int twshift = log2n - log2Ns - lr;   // m = r*k << twshift
+        for (int w = tid; w < total; w += nthr) {
+            int q, j;
+            if (SEQ_FAST) { q = w % nseq; j = w / nseq; }
+            else { q = w >> log2units; j = w & (units - 1); }
+            const V* in = A + (int64_t)q * seqstride;
+            V* out = B + (int64_t)q * seqstride;
+            const int k = j & (Ns - 1);
+            const int base = ((j - k) << lr) + k;
+            if (lr == 3) {
+                V u[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) u[r] = in[(j + r * units) * stride];
+                if (Ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) u[r] = cmul(u[r], tw[(r * k) << twshift]);
+                }
+                dft8(u);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) out[(base + r * Ns) * stride] = u[r];
+            } else if (lr == 2) {
+                V u0 = in[j * stride], u1 = in[(j + units) * stride];
+                V u2 = in[(j + 2 * units) * stride], u3 = in[(j + 3 * units) * stride];
+                if (Ns > 1) {
+                    u1 = cmul(u1, tw[k << twshift]);
+                    u2 = cmul(u2, tw[(2 * k) << twshift]);
+                    u3 = cmul(u3, tw[(3 * k) << twshift]);
+                }
+                dft4(u0, u1, u2, u3);
+                out[base * stride] = u0;
+                out[(base + Ns) * stride] = u1;
+                out[(base + 2 * Ns) * stride] = u2;
+                out[(base + 3 * Ns) * stride] = u3;
+            } else {
+                V u0 = in[j * stride], u1 = in[(j + units) * stride];
+                if (Ns > 1) u1 = cmul(u1, tw[k << twshift]);
+                dft2(u0, u1);
+                out[base * stride] = u0;
+                out[(base + Ns) * stride] = u1;
+            }
+        }
+        __syncthreads();
+        V* t = A; A = B; B = t;
+        log2Ns += lr;
+        rem -= lr;
+    }
+    (void)n;
+    return A;
+}
+
+// Hartley pair from the DFT Z of (a + i b): returns (H_a(k), H_b(k)).
+template <typename V> __device__ __forceinline__ V hartley_pair(V zk, V zm) {
+    typedef typename ScalarOf<V>::T T;
+    const T hf = (T)0.5;
+    return mk<V>(hf * ((zk.x + zm.x) - (zk.y - zm.y)), hf * ((zk.y + zm.y) + (zk.x - zm.x)));
+}
+
+}  // namespace rve

@@ -1,0 +1,89 @@
+// rve_internal.h -- host-side plan, workspace layout and kernel launchers
+// shared by the translation units of librve (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rve.h"
+
+namespace rve {
+
+struct RDesc;
+
+// Solver phases of one realization (fused pipeline).
+enum : int32_t { PH_REFINE = 0, PH_ITER = 1, PH_DONE = 2 };
+
+// Per-realization solver state (device), written only by the control kernel
+// (and the initialiser); read by the pipeline kernels one launch later.
+struct RState {
+    int32_t phase, parity, refinements, status;
+    int32_t iters[2];
+    int32_t active[2];   // corrector still iterating in the current cycle
+    int32_t cdone[2];    // corrector met the outer tolerance
+    int32_t final_pass, pad;
+    double fnorm[2];     // ||f_c||
+    double s[2];         // scale of the current inner system (||r64|| at restart)
+    double rho[2];       // r.z of the current residual
+    double alpha[2];     // pending step length (lagged solution update)
+    double beta[2];      // direction update factor for the next stencil pass
+    double target[2];    // inner-cycle relative residual target
+    double relres[2];    // last true relative residual
+};
+
+// Tile geometry of one realization for the fused kernels.
+struct Tiles {
+    int tS;   // node rows per stencil tile
+    int tU;   // rows per row-transform block
+    int tC;   // columns per column-transform block
+};
+
+struct Plan {
+    int batch = 0;
+    int precision = RVE_FP64;
+    int scheme = RVE_Q1_CONSISTENT;
+    int path = RVE_PATH_FUSED;
+    size_t vbytes = 16;             // bytes of one node pair (float2 / double2)
+    int64_t nodes = 0, words = 0;
+    int max_log2n = 0;
+    std::vector<RDesc> desc;        // host copy
+    std::vector<int32_t> startS, startU, startC, startA;
+    int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0;
+    size_t smemS = 0, smemU = 0, smemC = 0;
+    // workspace offsets (bytes)
+    size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
+    size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0;
+    size_t o_state = 0, o_partS = 0, o_partU = 0, o_partC = 0, o_partA = 0, o_ctl = 0;
+    size_t o_X = 0, o_R = 0, o_Q = 0, o_T = 0, o_P0 = 0, o_P1 = 0;
+    size_t total = 0;
+};
+
+// Validates descriptors and fills plan (host only).  opts may be NULL.
+rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
+                     Plan& plan, bool need_vectors);
+
+// Uploads descriptors/tile tables and fills the lookup tables in ws.
+rve_status upload_plan(const Plan& plan, void* ws, cudaStream_t s);
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_gen_field(const Plan& p, void* ws, uint32_t* mask, cudaStream_t s);
+cudaError_t launch_rhs(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                       double* f, cudaStream_t s);
+cudaError_t launch_stiffness(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                             int scheme, int precision, const void* x, void* y, cudaStream_t s);
+cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision, const void* x,
+                           void* y, cudaStream_t s);
+rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                           const rve_solve_opts& o, double* u, rve_solve_info* info,
+                           cudaStream_t s);
+rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                           const rve_solve_opts& o, double* u, rve_solve_info* info,
+                           cudaStream_t s);
+cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                         int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
+cudaError_t launch_backward(const Plan& p, void* ws, int scheme, const double* u,
+                            const double* gradA, double* grad_coef, cudaStream_t s);
+
+}  // namespace rve

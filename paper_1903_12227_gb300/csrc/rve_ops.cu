@@ -1,0 +1,305 @@
+// rve_ops.cu -- field generation, right-hand sides, stiffness apply,
+// homogenized matrix and its adjoint (sm_103a).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "rve_common.cuh"
+#include "rve_internal.h"
+
+namespace rve {
+
+// ------------------------------------------------------------ SplitMix64 --
+// Steele, Lea & Flood (OOPSLA 2014): output k (k >= 1) of the stream seeded
+// with s is mix(s + k * GAMMA).  Realization key = output (index+1) of the
+// run seed's stream; draw `ctr` under `tag` = output ((tag << 40) + ctr + 1)
+// of the key's stream.
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint32_t tag, uint64_t ctr) {
+    return sm64_mix(key + (((uint64_t)tag << 40) + ctr + 1) * 0x9E3779B97F4A7C15ull);
+}
+// uniform integer below n: high word of the 128-bit product (Lemire 2019,
+// no rejection)
+__device__ __forceinline__ int uniform_below(uint64_t v, uint32_t n) {
+    return (int)__umul64hi(v, (uint64_t)n);
+}
+constexpr uint32_t TAG_CORNER = 1u;
+
+// One thread per (inclusion, row of its square): sets the square's cells of
+// that row in the bitmask (Eq. "Stoch-decomp": the covered set is the union
+// of the inclusions, overlaps allowed, periodic wrap).
+__global__ void k_gen_field(const __grid_constant__ DescChunk ch, uint32_t* __restrict__ mask) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= ch.start[ch.count]) return;
+    const int b = find_real(ch.start, ch.count, (int)gid);
+    const RDesc& d = ch.d[b];
+    const int w = (int)gid - ch.start[b];
+    const int k = w / d.s, d1 = w - k * d.s;
+    const int c1 = uniform_below(sm64_draw(d.key, TAG_CORNER, 2ull * k), (uint32_t)d.n);
+    const int c2 = uniform_below(sm64_draw(d.key, TAG_CORNER, 2ull * k + 1), (uint32_t)d.n);
+    const int i1 = (c1 + d1) & (d.n - 1);
+    uint32_t* row = mask + d.word_off + (((int64_t)i1 * d.n) >> 5);
+    // columns c2 .. c2+s-1 (mod n), split at the wrap, then into words
+    int j = c2, left = d.s;
+    while (left > 0) {
+        const int run = min(left, d.n - j);   // until the wrap
+        int jj = j, rl = run;
+        while (rl > 0) {
+            const int bit = jj & 31;
+            const int take = min(rl, 32 - bit);
+            const uint32_t m = (take == 32) ? 0xffffffffu : (((1u << take) - 1u) << bit);
+            atomicOr(row + (jj >> 5), m);
+            jj += take;
+            rl -= take;
+        }
+        left -= run;
+        j = 0;
+    }
+}
+
+// ------------------------------------------------------ RHS / stiffness --
+// Work unit = 256 nodes (n*n is a multiple of 1024 for n >= 32).
+constexpr int NODE_TILE = 256;
+
+__global__ void k_rhs(const __grid_constant__ DescChunk ch, CoefSrc cs, double2* __restrict__ f) {
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t node = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
+    f[d.node_off + node] = rhs_at(cells_at(cs, d, i, j), d.h);
+}
+
+template <typename V>
+__device__ __forceinline__ V ldv(const V* __restrict__ x, const RDesc& d, int i, int j) {
+    return x[d.node_off + ((int64_t)(i & (d.n - 1)) << d.log2n) + (j & (d.n - 1))];
+}
+
+template <int SCHEME, typename V>
+__global__ void k_stiffness(const __grid_constant__ DescChunk ch, CoefSrc cs,
+                            const V* __restrict__ x, V* __restrict__ y) {
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t node = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
+    const Cells4 a = cells_at(cs, d, i, j);
+    y[d.node_off + node] = stencil_apply<SCHEME, V>(
+        a, ldv(x, d, i - 1, j - 1), ldv(x, d, i - 1, j), ldv(x, d, i - 1, j + 1),
+        ldv(x, d, i, j - 1), ldv(x, d, i, j), ldv(x, d, i, j + 1),
+        ldv(x, d, i + 1, j - 1), ldv(x, d, i + 1, j), ldv(x, d, i + 1, j + 1));
+}
+
+// ------------------------------------------------------------- adjoint --
+// Local element action (E v)_a for the unit-coefficient element matrix
+// E = K1 (x) M1 + M1 (x) K1, local order 00, 01, 10, 11.
+template <int SCHEME>
+__device__ __forceinline__ void elem_apply(const double v[4], double Ev[4]) {
+    const double w0 = Weights<SCHEME>::w0, w1 = Weights<SCHEME>::w1;
+    const double dg = 2.0 * w0, e = w1 - w0, g = -2.0 * w1;
+    Ev[0] = dg * v[0] + e * (v[1] + v[2]) + g * v[3];
+    Ev[1] = dg * v[1] + e * (v[0] + v[3]) + g * v[2];
+    Ev[2] = dg * v[2] + e * (v[0] + v[3]) + g * v[1];
+    Ev[3] = dg * v[3] + e * (v[1] + v[2]) + g * v[0];
+}
+
+// grad[c] = (1/L^2) sum_ij G_ij (xi_i + P_c u_i)^T E (xi_j + P_c u_j): the
+// explicit derivative of the energy form (the correctors are stationary).
+template <int SCHEME>
+__global__ void k_backward(const __grid_constant__ DescChunk ch, const double2* __restrict__ u,
+                           const double* __restrict__ G, double* __restrict__ grad) {
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t cell = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const int c1 = (int)(cell >> d.log2n), c2 = (int)(cell & (d.n - 1));
+    const double2 u00 = ldv(u, d, c1, c2), u01 = ldv(u, d, c1, c2 + 1);
+    const double2 u10 = ldv(u, d, c1 + 1, c2), u11 = ldv(u, d, c1 + 1, c2 + 1);
+    const double h = d.h;
+    double v1[4] = {u00.x, u01.x, h + u10.x, h + u11.x};   // x_1 + phi_1
+    double v2[4] = {u00.y, h + u01.y, u10.y, h + u11.y};   // x_2 + phi_2
+    double E1[4], E2[4];
+    elem_apply<SCHEME>(v1, E1);
+    elem_apply<SCHEME>(v2, E2);
+    double e11 = 0, e12 = 0, e22 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        e11 += v1[k] * E1[k];
+        e12 += v1[k] * E2[k];
+        e22 += v2[k] * E2[k];
+    }
+    const double* Gb = G + 4 * (int64_t)b;   // G is offset to the chunk's first realization
+    grad[d.node_off + cell] = d.inv_vol * (Gb[0] * e11 + (Gb[1] + Gb[2]) * e12 + Gb[3] * e22);
+}
+
+// ---------------------------------------------------------------- A_hom --
+// Per tile of 1024 nodes: partial sums of
+//   [0] sum a_c          [1..4] F_ij = f_i . u_j   (i,j = 1,2)
+//   [5] E_11 = u_1.A u_1 [6] E_12 = u_1.A u_2      [7] E_22 = u_2.A u_2
+// (E_21 is taken equal to E_12 so that the energy form is exactly symmetric).
+constexpr int AHOM_TILE = 1024;
+constexpr int AHOM_NP = 8;
+
+template <int SCHEME>
+__global__ void __launch_bounds__(256) k_a_hom_part(const RDesc* __restrict__ desc,
+                                                    const int32_t* __restrict__ start, int batch,
+                                                    CoefSrc cs, const double2* __restrict__ u,
+                                                    double* __restrict__ part) {
+    __shared__ double red[8];
+    const int b = find_real(start, batch, blockIdx.x);
+    const RDesc d = desc[b];
+    const int64_t base = (int64_t)(blockIdx.x - start[b]) * AHOM_TILE;
+    double acc[AHOM_NP];
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) acc[k] = 0.0;
+    for (int t = threadIdx.x; t < AHOM_TILE; t += blockDim.x) {
+        const int64_t node = base + t;
+        const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
+        const Cells4 a = cells_at(cs, d, i, j);
+        const double2 f = rhs_at(a, d.h);
+        const double2 q = stencil_apply<SCHEME, double2>(
+            a, ldv(u, d, i - 1, j - 1), ldv(u, d, i - 1, j), ldv(u, d, i - 1, j + 1),
+            ldv(u, d, i, j - 1), ldv(u, d, i, j), ldv(u, d, i, j + 1),
+            ldv(u, d, i + 1, j - 1), ldv(u, d, i + 1, j), ldv(u, d, i + 1, j + 1));
+        const double2 uu = ldv(u, d, i, j);
+        acc[0] += a.z00;
+        acc[1] = fma(f.x, uu.x, acc[1]);
+        acc[2] = fma(f.x, uu.y, acc[2]);
+        acc[3] = fma(f.y, uu.x, acc[3]);
+        acc[4] = fma(f.y, uu.y, acc[4]);
+        acc[5] = fma(uu.x, q.x, acc[5]);
+        acc[6] = fma(uu.x, q.y, acc[6]);
+        acc[7] = fma(uu.y, q.y, acc[7]);
+    }
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) {
+        const double s = block_sum(acc[k], red);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * AHOM_NP + k] = s;
+    }
+}
+
+// One warp per realization: fixed-order sum of the tile partials, then
+//   energy a_ij = mean(a) d_ij - (F_ij + F_ji - E_ij) / L^2
+//   flux   a_ij = mean(a) d_ij - F_ji / L^2            (F_ij = f_i . u_j)
+__global__ void k_a_hom_final(const RDesc* __restrict__ desc, const int32_t* __restrict__ start,
+                              int batch, const double* __restrict__ part, double* __restrict__ A,
+                              double* __restrict__ Af) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= batch) return;
+    const RDesc d = desc[b];
+    const int t0 = start[b], nt = start[b + 1] - start[b];
+    double s[AHOM_NP];
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) s[k] = warp_sum_array(part + (int64_t)t0 * AHOM_NP + k, nt, AHOM_NP);
+    if ((threadIdx.x & 31) != 0) return;
+    const double mean_a = s[0] / ((double)d.n * (double)d.n);
+    const double F11 = s[1], F12 = s[2], F21 = s[3], F22 = s[4];
+    const double E11 = s[5], E12 = s[6], E22 = s[7];
+    const double iv = d.inv_vol;
+    A[4 * b + 0] = mean_a - (2.0 * F11 - E11) * iv;
+    A[4 * b + 1] = -(F12 + F21 - E12) * iv;
+    A[4 * b + 2] = -(F21 + F12 - E12) * iv;
+    A[4 * b + 3] = mean_a - (2.0 * F22 - E22) * iv;
+    if (Af) {
+        Af[4 * b + 0] = mean_a - F11 * iv;
+        Af[4 * b + 1] = -F21 * iv;   // a_12 = -f_2.u_1 / L^2
+        Af[4 * b + 2] = -F12 * iv;   // a_21 = -f_1.u_2 / L^2
+        Af[4 * b + 3] = mean_a - F22 * iv;
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+// Splits the plan's realizations into chunks and calls `fn(chunk, first)`
+// with start[] = prefix sums of units(d) over the chunk.
+template <typename UnitsFn, typename LaunchFn>
+static cudaError_t for_chunks(const Plan& p, UnitsFn units, LaunchFn fn) {
+    for (int b0 = 0; b0 < p.batch; b0 += CHUNK) {
+        DescChunk ch;
+        ch.count = std::min(CHUNK, p.batch - b0);
+        ch.start[0] = 0;
+        for (int k = 0; k < ch.count; ++k) {
+            ch.d[k] = p.desc[b0 + k];
+            ch.start[k + 1] = ch.start[k] + (int32_t)units(ch.d[k]);
+        }
+        for (int k = ch.count + 1; k <= CHUNK; ++k) ch.start[k] = ch.start[ch.count];
+        cudaError_t e = fn(ch, b0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gen_field(const Plan& p, void* /*ws*/, uint32_t* mask, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)p.words, s);
+    if (e != cudaSuccess) return e;
+    return for_chunks(p, [](const RDesc& d) { return (int64_t)d.n_incl * d.s; },
+                      [&](const DescChunk& ch, int) {
+                          const int total = ch.start[ch.count];
+                          if (total == 0) return cudaSuccess;
+                          k_gen_field<<<(total + 255) / 256, 256, 0, s>>>(ch, mask);
+                          return cudaGetLastError();
+                      });
+}
+
+static int64_t node_tiles(const RDesc& d) { return ((int64_t)d.n * d.n) / NODE_TILE; }
+
+cudaError_t launch_rhs(const Plan& p, void*, const uint32_t* mask, const double* coef, double* f,
+                       cudaStream_t s) {
+    CoefSrc cs{mask, coef};
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int) {
+        k_rhs<<<ch.start[ch.count], NODE_TILE, 0, s>>>(ch, cs, reinterpret_cast<double2*>(f));
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_stiffness(const Plan& p, void*, const uint32_t* mask, const double* coef,
+                             int scheme, int precision, const void* x, void* y, cudaStream_t s) {
+    CoefSrc cs{mask, coef};
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int) {
+        const int g = ch.start[ch.count];
+        if (precision == RVE_FP64) {
+            const double2* xx = static_cast<const double2*>(x);
+            double2* yy = static_cast<double2*>(y);
+            if (scheme == RVE_Q1_LUMPED) k_stiffness<1, double2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
+            else k_stiffness<0, double2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
+        } else {
+            const float2* xx = static_cast<const float2*>(x);
+            float2* yy = static_cast<float2*>(y);
+            if (scheme == RVE_Q1_LUMPED) k_stiffness<1, float2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
+            else k_stiffness<0, float2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
+        }
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_backward(const Plan& p, void*, int scheme, const double* u, const double* gradA,
+                            double* grad_coef, cudaStream_t s) {
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int first) {
+        const double* G = gradA + 4 * (int64_t)first;
+        const double2* uu = reinterpret_cast<const double2*>(u);
+        const int g = ch.start[ch.count];
+        if (scheme == RVE_Q1_LUMPED) k_backward<1><<<g, NODE_TILE, 0, s>>>(ch, uu, G, grad_coef);
+        else k_backward<0><<<g, NODE_TILE, 0, s>>>(ch, uu, G, grad_coef);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                         int scheme, const double* u, double* A, double* A_flux, cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
+    const int32_t* start = reinterpret_cast<const int32_t*>(w + p.o_startA);
+    double* part = reinterpret_cast<double*>(w + p.o_partA);
+    CoefSrc cs{mask, coef};
+    const double2* uu = reinterpret_cast<const double2*>(u);
+    if (scheme == RVE_Q1_LUMPED)
+        k_a_hom_part<1><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+    else
+        k_a_hom_part<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_a_hom_final<<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    return cudaGetLastError();
+}
+
+}  // namespace rve

@@ -1,0 +1,681 @@
+// rve_solver.cu -- preconditioned CG for the two corrector problems
+// (Sec. 3.4 and 4.1), batched over realizations, on sm_103a.
+//
+// Preconditioner (Sec. 3.4): B = c0 A_Delta + delta I with A_Delta the
+// periodic 5-point Laplacian.  On the torus B is diagonalised by the
+// separable real Hartley transform H (x) H, (H (x) H)^2 = n^2 I, so
+//   B^{-1} r = (H (x) H) diag(1 / (n^2 sigma)) (H (x) H) r,
+//   sigma(k1,k2) = c0 (4 sin^2(pi k1/n) + 4 sin^2(pi k2/n)) + delta,
+// the constant mode being dropped when delta = 0.  Each 1D Hartley pass
+// transforms the two correctors at once: the complex DFT of (r_1 + i r_2)
+// along the axis is split into H r_1 and H r_2 (see hartley_pair).  Since
+// the transform is orthogonal up to n, r.z = (1/n^2) sum (H(x)H r)^2 / sigma
+// is read off in the transform domain.
+//
+// Fused pipeline (one CG step = three passes over the vectors + a control
+// kernel; both correctors of a realization travel together as a pair):
+//   S  z = row-Hartley(t) on the tile + halo rows, p_new = z + beta p_old,
+//      x += alpha_prev p_old (the solution update lags one step),
+//      q = A p_new, partial p.q                                  (ITER)
+//      or r64 = f - A(u + s (x + alpha p)) in FP64, partial |r64|^2 (REFINE)
+//   U  alpha = rho / p.q, r -= alpha q, partial |r|^2, t = row-Hartley(r)
+//      (REFINE: u += s (x + alpha p), x = 0, r = r64 / |r64|)
+//   C  column Hartley, scale 1/(n^2 sigma), partial rho, column Hartley
+//   K  per realization: reduce the partials in a fixed order, set alpha,
+//      beta, convergence and the next phase.
+// In MIXED precision x, r, q, t, p are float2 and u is double2: every
+// REFINE step recomputes the true residual in FP64 and restarts the FP32
+// inner iteration on the scaled residual equation (iterative refinement).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "rve_common.cuh"
+#include "rve_internal.h"
+
+namespace rve {
+
+struct Ctx {
+    int batch;
+    const RDesc* __restrict__ desc;
+    const int32_t* __restrict__ startS;
+    const int32_t* __restrict__ startU;
+    const int32_t* __restrict__ startC;
+    RState* __restrict__ st;
+    double* __restrict__ partS;
+    double* __restrict__ partU;
+    double* __restrict__ partC;
+    Tables tb;
+    CoefSrc cs;
+    double2* __restrict__ u;
+    void* X;
+    void* R;
+    void* Q;
+    void* T;
+    void* P0;
+    void* P1;
+    double tol, inner_tol, delta;
+    int max_iter;
+    int* ndone;
+};
+
+// ------------------------------------------------------------- tables --
+// tw64[n + m] = exp(-2 pi i m / n), lap[n + m] = 4 sin^2(pi m / n) for every
+// n = 2^p <= 2^maxlog; computed with sincospi/sinpi.
+__global__ void k_tables(double2* tw64, float2* tw32, double* lap, int total) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < 2 || idx >= total) return;
+    const int p = 31 - __clz(idx);
+    const int n = 1 << p, m = idx - n;
+    double sn, cs;
+    sincospi(-2.0 * (double)m / (double)n, &sn, &cs);
+    tw64[idx] = make_double2(cs, sn);
+    tw32[idx] = make_float2((float)cs, (float)sn);
+    const double s1 = sinpi((double)m / (double)n);
+    lap[idx] = 4.0 * s1 * s1;
+}
+
+// ---------------------------------------------------- row Hartley helper --
+// Loads `g` rows (global row indices row0 .. row0+g-1, wrapped) of `in` into
+// F0, transforms them along the row and writes the Hartley pair of each row
+// into out_smem (row-major, n per row).  256 threads.
+template <typename V>
+__device__ void rows_hartley_to_smem(const V* __restrict__ in, const RDesc& d, int row0, int g,
+                                     V* F0, V* F1, V* out_smem, const Tables& tb) {
+    const int n = d.n, tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < g * n; idx += nthr) {
+        const int q = idx >> d.log2n, j = idx & (n - 1);
+        const int row = (row0 + q) & (n - 1);
+        F0[idx] = in[d.node_off + ((int64_t)row << d.log2n) + j];
+    }
+    __syncthreads();
+    V* res = smem_fft<V, false>(F0, F1, d.log2n, 1, n, g, twiddles<V>(tb, n), tid, nthr);
+    for (int idx = tid; idx < g * n; idx += nthr) {
+        const int q = idx >> d.log2n, k = idx & (n - 1);
+        const V* z = res + q * n;
+        out_smem[idx] = hartley_pair(z[k], z[(n - k) & (n - 1)]);
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------- S kernel --
+template <typename V>
+__device__ __forceinline__ V axpy2(V y, double ax, double ay, V x) {
+    typedef typename ScalarOf<V>::T T;
+    V r;
+    r.x = y.x + (T)ax * x.x;
+    r.y = y.y + (T)ay * x.y;
+    return r;
+}
+
+template <typename V>
+__device__ __forceinline__ double2 refine_w(const Ctx& c, const RDesc& d, const RState& s, int i,
+                                            int j, const V* P) {
+    const int64_t node = d.node_off + ((int64_t)(i & (d.n - 1)) << d.log2n) + (j & (d.n - 1));
+    const double2 uu = c.u[node];
+    const double2 xx = to_d2(static_cast<const V*>(c.X)[node]);
+    const double2 pp = to_d2(P[node]);
+    return make_double2(uu.x + s.s[0] * (xx.x + s.alpha[0] * pp.x),
+                        uu.y + s.s[1] * (xx.y + s.alpha[1] * pp.y));
+}
+
+template <typename V, int SCHEME>
+__global__ void __launch_bounds__(256) k_fused_S(const Ctx c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    const int tile = blockIdx.x;
+    const int b = find_real(c.startS, c.batch, tile);
+    const RState& s = c.st[b];
+    const int phase = s.phase;
+    if (phase == PH_DONE) return;
+    const RDesc d = c.desc[b];
+    const int n = d.n, TR = d.tS;
+    const int r0 = (tile - c.startS[b]) * TR;
+    const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+    V* Pnew = static_cast<V*>(s.parity ? c.P0 : c.P1);
+    V* X = static_cast<V*>(c.X);
+    V* Q = static_cast<V*>(c.Q);
+    DotAcc<double> a64x, a64y;   // REFINE: exact FP64 |r64|^2
+    typedef typename ScalarOf<V>::T T;
+    DotAcc<T> ax, ay;            // ITER: p.q
+
+    if (phase == PH_REFINE) {
+        for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
+            const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
+            const Cells4 a = cells_at(c.cs, d, i, j);
+            const double2 f = rhs_at(a, d.h);
+            const double2 Aw = stencil_apply<SCHEME, double2>(
+                a, refine_w(c, d, s, i - 1, j - 1, Pold), refine_w(c, d, s, i - 1, j, Pold),
+                refine_w(c, d, s, i - 1, j + 1, Pold), refine_w(c, d, s, i, j - 1, Pold),
+                refine_w(c, d, s, i, j, Pold), refine_w(c, d, s, i, j + 1, Pold),
+                refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
+                refine_w(c, d, s, i + 1, j + 1, Pold));
+            const double2 r64 = make_double2(f.x - Aw.x, f.y - Aw.y);
+            Q[d.node_off + ((int64_t)i << d.log2n) + j] = from_d2<V>(r64);
+            a64x.add(r64.x, r64.x);
+            a64y.add(r64.y, r64.y);
+        }
+        const double sx = block_sum(a64x.value(), red);
+        const double sy = block_sum(a64y.value(), red);
+        if (threadIdx.x == 0) {
+            c.partS[2 * (int64_t)tile] = sx;
+            c.partS[2 * (int64_t)tile + 1] = sy;
+        }
+        return;
+    }
+
+    // ---- ITER ----
+    const int G = d.tU;                       // rows per transform group
+    V* Pt = reinterpret_cast<V*>(smem_raw);  // (TR+2) x n: z, then p_new
+    V* F0 = Pt + (TR + 2) * n;
+    V* F1 = F0 + G * n;
+    for (int g0 = 0; g0 < TR + 2; g0 += G) {
+        const int g = min(G, TR + 2 - g0);
+        rows_hartley_to_smem<V>(static_cast<const V*>(c.T), d, r0 - 1 + g0, g, F0, F1,
+                                Pt + g0 * n, c.tb);
+    }
+    const double bx = s.beta[0], by = s.beta[1];
+    const double alx = s.alpha[0], aly = s.alpha[1];
+    for (int idx = threadIdx.x; idx < (TR + 2) * n; idx += blockDim.x) {
+        const int q = idx >> d.log2n, j = idx & (n - 1);
+        const int row = (r0 - 1 + q) & (n - 1);
+        const int64_t node = d.node_off + ((int64_t)row << d.log2n) + j;
+        const V po = Pold[node];
+        const V pn = axpy2(Pt[idx], bx, by, po);
+        Pt[idx] = pn;
+        if (q >= 1 && q <= TR) {
+            Pnew[node] = pn;
+            X[node] = axpy2(X[node], alx, aly, po);
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
+        const int q = idx >> d.log2n, j = idx & (n - 1);
+        const int i = r0 + q;
+        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
+        const V* up = Pt + q * n;          // row i-1
+        const V* mid = up + n;             // row i
+        const V* dn = mid + n;             // row i+1
+        const Cells4 a = cells_at(c.cs, d, i, j);
+        const V qv = stencil_apply<SCHEME, V>(a, up[jm], up[j], up[jp], mid[jm], mid[j], mid[jp],
+                                              dn[jm], dn[j], dn[jp]);
+        Q[d.node_off + ((int64_t)i << d.log2n) + j] = qv;
+        ax.add(mid[j].x, qv.x);
+        ay.add(mid[j].y, qv.y);
+    }
+    const double sx = block_sum(ax.value(), red);
+    const double sy = block_sum(ay.value(), red);
+    if (threadIdx.x == 0) {
+        c.partS[2 * (int64_t)tile] = sx;
+        c.partS[2 * (int64_t)tile + 1] = sy;
+    }
+}
+
+// ----------------------------------------------------------- U kernel --
+// The reductions of another kernel's partials, done redundantly (and
+// identically) by every consumer block: warp 0 sums them in a fixed order.
+__device__ __forceinline__ void reduce_pair(const double* part, int t0, int nt, double* out2) {
+    if (threadIdx.x < 32) {
+        const double a = warp_sum_array(part + 2 * (int64_t)t0, nt, 2);
+        const double b = warp_sum_array(part + 2 * (int64_t)t0 + 1, nt, 2);
+        if (threadIdx.x == 0) { out2[0] = a; out2[1] = b; }
+    }
+    __syncthreads();
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    __shared__ double sc[2];
+    const int blk = blockIdx.x;
+    const int b = find_real(c.startU, c.batch, blk);
+    const RState& s = c.st[b];
+    const int phase = s.phase;
+    if (phase == PH_DONE) return;
+    const RDesc d = c.desc[b];
+    const int n = d.n, G = d.tU;
+    const int row0 = (blk - c.startU[b]) * G;
+    typedef typename ScalarOf<V>::T T;
+    V* R = static_cast<V*>(c.R);
+    V* X = static_cast<V*>(c.X);
+    const V* Q = static_cast<const V*>(c.Q);
+    V* F0 = reinterpret_cast<V*>(smem_raw);
+    V* F1 = F0 + G * n;
+    reduce_pair(c.partS, c.startS[b], c.startS[b + 1] - c.startS[b], sc);
+    DotAcc<T> ax, ay;
+    if (phase == PH_ITER) {
+        const double alx = s.active[0] ? s.rho[0] / sc[0] : 0.0;
+        const double aly = s.active[1] ? s.rho[1] / sc[1] : 0.0;
+        for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
+            const int64_t node = d.node_off + ((int64_t)row0 << d.log2n) + idx;
+            const V rr = axpy2(R[node], -alx, -aly, Q[node]);
+            R[node] = rr;
+            F0[idx] = rr;
+            ax.add(rr.x, rr.x);
+            ay.add(rr.y, rr.y);
+        }
+    } else {   // REFINE
+        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+        const double nx = sqrt(sc[0]), ny = sqrt(sc[1]);
+        const bool first = (s.refinements == 0);
+        const bool cx = first ? (nx == 0.0) : (nx <= c.tol * s.fnorm[0]);
+        const bool cy = first ? (ny == 0.0) : (ny <= c.tol * s.fnorm[1]);
+        const double ix = cx ? 0.0 : 1.0 / nx, iy = cy ? 0.0 : 1.0 / ny;
+        for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
+            const int64_t node = d.node_off + ((int64_t)row0 << d.log2n) + idx;
+            const double2 xx = to_d2(X[node]);
+            const double2 pp = to_d2(Pold[node]);
+            double2 uu = c.u[node];
+            uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
+            uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
+            c.u[node] = uu;
+            X[node] = from_d2<V>(make_double2(0.0, 0.0));
+            const double2 q = to_d2(Q[node]);
+            const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
+            R[node] = rr;
+            F0[idx] = rr;
+            ax.add(rr.x, rr.x);
+            ay.add(rr.y, rr.y);
+        }
+    }
+    const double sx = block_sum(ax.value(), red);
+    const double sy = block_sum(ay.value(), red);
+    if (threadIdx.x == 0) {
+        c.partU[2 * (int64_t)blk] = sx;
+        c.partU[2 * (int64_t)blk + 1] = sy;
+    }
+    __syncthreads();
+    // row Hartley of r -> t
+    V* res = smem_fft<V, false>(F0, F1, d.log2n, 1, n, G, twiddles<V>(c.tb, n), threadIdx.x,
+                                blockDim.x);
+    V* Tv = static_cast<V*>(c.T);
+    for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
+        const int q = idx >> d.log2n, k = idx & (n - 1);
+        const V* z = res + q * n;
+        Tv[d.node_off + ((int64_t)(row0 + q) << d.log2n) + k] = hartley_pair(z[k], z[(n - k) & (n - 1)]);
+    }
+}
+
+// ----------------------------------------------------------- C kernel --
+// Column Hartley pass, diagonal scale 1/(n^2 sigma), partial rho, column
+// Hartley pass; in place on t.  `rho_part` may be null (plain path).
+template <typename V>
+__device__ void col_transform_tile(V* T, const RDesc& d, int c0, int C, V* F0, V* F1,
+                                   const Tables& tb, double delta, double* red,
+                                   double* rho_part) {
+    typedef typename ScalarOf<V>::T Ts;
+    const int n = d.n, tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < n * C; idx += nthr) {
+        const int i = idx / C, cc = idx - i * C;
+        F0[idx] = T[d.node_off + ((int64_t)i << d.log2n) + c0 + cc];
+    }
+    __syncthreads();
+    V* res = smem_fft<V, true>(F0, F1, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
+    V* oth = (res == F0) ? F1 : F0;
+    const double n2 = (double)n * (double)n;
+    const Ts n2c0 = (Ts)(n2 * d.c0), n2d = (Ts)(n2 * delta);
+    DotAcc<Ts> ax, ay;
+    for (int idx = tid; idx < n * C; idx += nthr) {
+        const int k1 = idx / C, cc = idx - k1 * C;
+        const int k2 = c0 + cc;
+        const V h = hartley_pair(res[idx], res[((n - k1) & (n - 1)) * C + cc]);
+        const Ts sig = n2c0 * ((Ts)tb.lap[n + k1] + (Ts)tb.lap[n + k2]) + n2d;
+        const Ts inv = (k1 == 0 && k2 == 0 && delta == 0.0) ? (Ts)0 : (Ts)1 / sig;
+        V hs;
+        hs.x = h.x * inv;
+        hs.y = h.y * inv;
+        ax.add(h.x, hs.x);
+        ay.add(h.y, hs.y);
+        oth[idx] = hs;
+    }
+    if (rho_part) {
+        const double sx = block_sum(ax.value(), red);
+        const double sy = block_sum(ay.value(), red);
+        if (tid == 0) { rho_part[0] = sx; rho_part[1] = sy; }
+    } else {
+        __syncthreads();
+    }
+    // second column pass: transform `oth` (its partner buffer is `res`)
+    V* res2 = smem_fft<V, true>(oth, res, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
+    for (int idx = tid; idx < n * C; idx += nthr) {
+        const int k1 = idx / C, cc = idx - k1 * C;
+        T[d.node_off + ((int64_t)k1 << d.log2n) + c0 + cc] =
+            hartley_pair(res2[idx], res2[((n - k1) & (n - 1)) * C + cc]);
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_fused_C(const Ctx c) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    const int blk = blockIdx.x;
+    const int b = find_real(c.startC, c.batch, blk);
+    if (c.st[b].phase == PH_DONE) return;
+    const RDesc d = c.desc[b];
+    const int C = d.tC;
+    V* F0 = reinterpret_cast<V*>(smem_raw);
+    V* F1 = F0 + d.n * C;
+    col_transform_tile<V>(static_cast<V*>(c.T), d, (blk - c.startC[b]) * C, C, F0, F1, c.tb,
+                          c.delta, red, c.partC + 2 * (int64_t)blk);
+}
+
+// ------------------------------------------------------ control kernel --
+__device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
+
+__global__ void k_control(const Ctx c) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= c.batch) return;
+    const int b = w;
+    RState& s = c.st[b];
+    if (s.phase == PH_DONE) return;
+    const int ts0 = c.startS[b], tsn = c.startS[b + 1] - ts0;
+    const int tu0 = c.startU[b], tun = c.startU[b + 1] - tu0;
+    const int tc0 = c.startC[b], tcn = c.startC[b + 1] - tc0;
+    double pS[2], pU[2], pC[2];
+    for (int k = 0; k < 2; ++k) {
+        pS[k] = warp_sum_array(c.partS + 2 * (int64_t)ts0 + k, tsn, 2);
+        pU[k] = warp_sum_array(c.partU + 2 * (int64_t)tu0 + k, tun, 2);
+        pC[k] = warp_sum_array(c.partC + 2 * (int64_t)tc0 + k, tcn, 2);
+    }
+    if ((threadIdx.x & 31) != 0) return;
+    if (s.phase == PH_ITER) {
+        bool any_active = false;
+        for (int k = 0; k < 2; ++k) {
+            if (!s.active[k]) { s.alpha[k] = 0.0; s.beta[k] = 0.0; continue; }
+            const double alpha = s.rho[k] / pS[k];
+            const double rn = sqrt(pU[k]);
+            if (bad(alpha) || bad(rn) || bad(pC[k])) {
+                s.status = RVE_ENAN;
+                s.phase = PH_DONE;
+                atomicAdd(c.ndone, 1);
+                return;
+            }
+            s.alpha[k] = alpha;
+            s.iters[k] += 1;
+            if (rn <= s.target[k] || s.iters[k] >= c.max_iter) {
+                s.active[k] = 0;       // frozen; alpha still pending for x
+                s.beta[k] = 0.0;
+                if (s.iters[k] >= c.max_iter && rn > s.target[k]) s.final_pass = 1;
+            } else {
+                s.beta[k] = pC[k] / s.rho[k];
+                s.rho[k] = pC[k];
+                any_active = true;
+            }
+        }
+        s.parity ^= 1;
+        if (!any_active) s.phase = PH_REFINE;
+        return;
+    }
+    // REFINE: true residual of the accumulated solution
+    s.refinements += 1;
+    bool all_done = true;
+    for (int k = 0; k < 2; ++k) {
+        const double rn = sqrt(pS[k]);
+        if (bad(rn)) {
+            s.status = RVE_ENAN;
+            s.phase = PH_DONE;
+            atomicAdd(c.ndone, 1);
+            return;
+        }
+        if (s.refinements == 1) s.fnorm[k] = rn;
+        const bool conv = (s.refinements == 1) ? (rn == 0.0) : (rn <= c.tol * s.fnorm[k]);
+        s.relres[k] = s.fnorm[k] > 0.0 ? rn / s.fnorm[k] : 0.0;
+        s.alpha[k] = 0.0;
+        s.beta[k] = 0.0;
+        if (conv || s.cdone[k]) {
+            s.cdone[k] = 1;
+            s.active[k] = 0;
+            s.s[k] = 0.0;
+            continue;
+        }
+        all_done = false;
+        s.s[k] = rn;
+        s.active[k] = 1;
+        const double want = 0.5 * c.tol * s.fnorm[k] / rn;   // enough for the outer tolerance
+        s.target[k] = fmin(0.5, fmax(c.inner_tol, want));
+        s.rho[k] = pC[k];
+        if (s.iters[k] >= c.max_iter) s.final_pass = 1;
+    }
+    if (all_done || s.final_pass) {
+        if (!all_done) s.status = RVE_ENOCONV;
+        s.phase = PH_DONE;
+        atomicAdd(c.ndone, 1);
+        return;
+    }
+    s.phase = PH_ITER;
+}
+
+__global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = gid; k < nodes; k += stride) {
+        c.u[k] = make_double2(0.0, 0.0);
+        if (vbytes == 16) {
+            static_cast<double2*>(c.X)[k] = make_double2(0.0, 0.0);
+            static_cast<double2*>(c.P0)[k] = make_double2(0.0, 0.0);
+            static_cast<double2*>(c.P1)[k] = make_double2(0.0, 0.0);
+        } else {
+            static_cast<float2*>(c.X)[k] = make_float2(0.f, 0.f);
+            static_cast<float2*>(c.P0)[k] = make_float2(0.f, 0.f);
+            static_cast<float2*>(c.P1)[k] = make_float2(0.f, 0.f);
+        }
+    }
+    for (int64_t b = gid; b < c.batch; b += stride) {
+        RState z = {};
+        z.phase = PH_REFINE;
+        z.status = RVE_OK;
+        c.st[b] = z;
+    }
+    if (gid == 0) *c.ndone = 0;
+}
+
+__global__ void k_report(const Ctx c, rve_solve_info* info) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= c.batch) return;
+    const RState s = c.st[b];
+    rve_solve_info r;
+    r.iters[0] = s.iters[0];
+    r.iters[1] = s.iters[1];
+    r.status = (s.phase == PH_DONE) ? s.status : RVE_ENOCONV;
+    r.refinements = s.refinements;
+    r.relres[0] = s.relres[0];
+    r.relres[1] = s.relres[1];
+    info[b] = r;
+}
+
+// --------------------------------------------------------------- host --
+static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double* coef, double* u,
+                    const rve_solve_opts& o) {
+    char* w = static_cast<char*>(ws);
+    Ctx c;
+    c.batch = p.batch;
+    c.desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
+    c.startS = reinterpret_cast<const int32_t*>(w + p.o_startS);
+    c.startU = reinterpret_cast<const int32_t*>(w + p.o_startU);
+    c.startC = reinterpret_cast<const int32_t*>(w + p.o_startC);
+    c.st = reinterpret_cast<RState*>(w + p.o_state);
+    c.partS = reinterpret_cast<double*>(w + p.o_partS);
+    c.partU = reinterpret_cast<double*>(w + p.o_partU);
+    c.partC = reinterpret_cast<double*>(w + p.o_partC);
+    c.tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
+    c.tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
+    c.tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
+    c.cs.mask = mask;
+    c.cs.coef = coef;
+    c.u = reinterpret_cast<double2*>(u);
+    c.X = w + p.o_X;
+    c.R = w + p.o_R;
+    c.Q = w + p.o_Q;
+    c.T = w + p.o_T;
+    c.P0 = w + p.o_P0;
+    c.P1 = w + p.o_P1;
+    c.tol = o.tol;
+    c.inner_tol = (p.precision == RVE_MIXED) ? o.inner_tol : 0.5 * o.tol;
+    c.delta = o.delta;
+    c.max_iter = o.max_iter;
+    c.ndone = reinterpret_cast<int*>(w + p.o_ctl);
+    return c;
+}
+
+rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    cudaError_t e = cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(RDesc) * p.batch,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + p.o_startS, p.startS.data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + p.o_startU, p.startU.data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + p.o_startC, p.startC.data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + p.o_startA, p.startA.data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return RVE_ECUDA;
+    const int total = 2 << p.max_log2n;
+    k_tables<<<(total + 255) / 256, 256, 0, s>>>(reinterpret_cast<double2*>(w + p.o_tw64),
+                                                 reinterpret_cast<float2*>(w + p.o_tw32),
+                                                 reinterpret_cast<double*>(w + p.o_lap), total);
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+template <typename V, int SCHEME>
+static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s) {
+    k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
+    k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
+    k_fused_C<V><<<p.tilesC, 256, p.smemC, s>>>(c);
+    k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+template <typename V, int SCHEME>
+static cudaError_t set_smem_attrs(const Plan& p) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_S<V, SCHEME>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smemS);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused_U<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.smemU);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused_C<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.smemC);
+    return e;
+}
+
+template <typename V, int SCHEME>
+static rve_status fused_loop(const Plan& p, const Ctx& c, const rve_solve_opts& o,
+                             cudaStream_t s) {
+    if (set_smem_attrs<V, SCHEME>(p) != cudaSuccess) return RVE_ECUDA;
+    // bound on pipeline steps: every cycle costs one REFINE step
+    const int64_t max_steps = 2LL * o.max_iter + 64;
+    const int every = o.check_every > 0 ? o.check_every : 8;
+    int host_done = 0;
+    for (int64_t g = 0; g < max_steps; ++g) {
+        if (fused_step<V, SCHEME>(p, c, s) != cudaSuccess) return RVE_ECUDA;
+        if ((g + 1) % every == 0) {
+            if (cudaMemcpyAsync(&host_done, c.ndone, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return RVE_ECUDA;
+            if (host_done >= p.batch) break;
+        }
+    }
+    return RVE_OK;
+}
+
+rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                           const rve_solve_opts& o, double* u, rve_solve_info* info,
+                           cudaStream_t s) {
+    rve_status st = upload_plan(p, ws, s);
+    if (st != RVE_OK) return st;
+    Ctx c = make_ctx(p, ws, mask, coef, u, o);
+    k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
+    if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
+    if (p.precision == RVE_MIXED) {
+        st = (p.scheme == RVE_Q1_LUMPED) ? fused_loop<float2, 1>(p, c, o, s)
+                                         : fused_loop<float2, 0>(p, c, o, s);
+    } else {
+        st = (p.scheme == RVE_Q1_LUMPED) ? fused_loop<double2, 1>(p, c, o, s)
+                                         : fused_loop<double2, 0>(p, c, o, s);
+    }
+    if (st != RVE_OK) return st;
+    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+// --------------------------------------------------- preconditioner apply --
+template <typename V>
+__global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ desc,
+                                                     const int32_t* __restrict__ startU, int batch,
+                                                     Tables tb, const V* __restrict__ in,
+                                                     V* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int blk = blockIdx.x;
+    const int b = find_real(startU, batch, blk);
+    const RDesc d = desc[b];
+    const int n = d.n, G = d.tU;
+    const int row0 = (blk - startU[b]) * G;
+    V* F0 = reinterpret_cast<V*>(smem_raw);
+    V* F1 = F0 + G * n;
+    V* H = F1 + G * n;
+    rows_hartley_to_smem<V>(in, d, row0, G, F0, F1, H, tb);
+    for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x)
+        out[d.node_off + ((int64_t)row0 << d.log2n) + idx] = H[idx];
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_col_hartley(const RDesc* __restrict__ desc,
+                                                     const int32_t* __restrict__ startC, int batch,
+                                                     Tables tb, double delta, V* __restrict__ T) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    const int blk = blockIdx.x;
+    const int b = find_real(startC, batch, blk);
+    const RDesc d = desc[b];
+    const int C = d.tC;
+    V* F0 = reinterpret_cast<V*>(smem_raw);
+    V* F1 = F0 + d.n * C;
+    col_transform_tile<V>(T, d, (blk - startC[b]) * C, C, F0, F1, tb, delta, red, nullptr);
+}
+
+template <typename V>
+static cudaError_t precond_apply_t(const Plan& p, void* ws, double delta, const V* x, V* y,
+                                   V* tmp, cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
+    const int32_t* startU = reinterpret_cast<const int32_t*>(w + p.o_startU);
+    const int32_t* startC = reinterpret_cast<const int32_t*>(w + p.o_startC);
+    Tables tb;
+    tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
+    tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
+    tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
+    const size_t smem_row = p.smemU / 2 * 3;   // F0, F1 and the output rows
+    cudaError_t e = cudaFuncSetAttribute(k_row_hartley<V>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_col_hartley<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p.smemC);
+    if (e != cudaSuccess) return e;
+    k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, x, tmp);
+    k_col_hartley<V><<<p.tilesC, 256, p.smemC, s>>>(desc, startC, p.batch, tb, delta, tmp);
+    k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, tmp, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision, const void* x,
+                           void* y, cudaStream_t s) {
+    if (upload_plan(p, ws, s) != RVE_OK) return cudaErrorUnknown;
+    char* w = static_cast<char*>(ws);
+    if (precision == RVE_FP64)
+        return precond_apply_t<double2>(p, ws, delta, static_cast<const double2*>(x),
+                                        static_cast<double2*>(y),
+                                        reinterpret_cast<double2*>(w + p.o_T), s);
+    return precond_apply_t<float2>(p, ws, delta, static_cast<const float2*>(x),
+                                   static_cast<float2*>(y), reinterpret_cast<float2*>(w + p.o_T), s);
+}
+
+}  // namespace rve

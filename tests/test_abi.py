@@ -1,0 +1,68 @@
+"""librve loads and exports every symbol include/rve.h declares; host-only
+argument validation (no GPU needed: these calls launch nothing)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rve.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(rve_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def librve():
+    from paper_1903_12227_gb300 import build, rve
+    build.build()
+    return rve.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("rve_gen_field", "rve_solve_correctors", "rve_a_hom", "rve_a_hom_backward",
+                     "rve_workspace_size", "rve_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(librve):
+    for name in _declared_functions():
+        assert hasattr(librve, name), f"librve.so does not export {name}"
+
+
+def test_struct_sizes_match_header(librve):
+    from paper_1903_12227_gb300 import rve
+    assert ctypes.sizeof(rve.Realization) == 48
+    assert ctypes.sizeof(rve.SolveInfo) == 32
+
+
+def test_host_validation_without_gpu(librve):
+    from paper_1903_12227_gb300 import rve, workloads
+    ok = rve.Batch([workloads.realization(4, 8, 10.0, 0, 0)])
+    assert librve.rve_nodes(ok.ptr, 1) == 32 * 32
+    assert librve.rve_mask_words(ok.ptr, 1) == 32
+    assert librve.rve_workspace_size(ok.ptr, 1, None) > 0
+    # n not a power of two, n too small, non-positive coefficient
+    for bad in (workloads.realization(3, 16, 10.0, 0, 0), workloads.realization(1, 8, 10.0, 0, 0),
+                dict(workloads.realization(4, 8, 10.0, 0, 0), a_matrix=0.0),
+                dict(workloads.realization(4, 8, 10.0, 0, 0), incl_cells=64)):
+        b = rve.Batch([bad])
+        assert librve.rve_workspace_size(b.ptr, 1, None) == 0
+        assert librve.rve_gen_field(b.ptr, 1, None, None) == rve.RVE_EINVAL
+    assert librve.rve_gen_field(ok.ptr, 0, None, None) == rve.RVE_EINVAL
+    opts = rve.make_opts(precision=rve.MIXED, path=rve.PATH_PLAIN)
+    assert librve.rve_workspace_size(ok.ptr, 1, ctypes.byref(opts)) == 0
+    assert b"RVE_OK" in librve.rve_status_string(0)
+
+
+def test_uneven_batch_sizes_add_up(librve):
+    from paper_1903_12227_gb300 import rve, workloads
+    ds = workloads.config_batch("uneven_4096", seed=3, count=40)
+    b = rve.Batch(ds)
+    assert librve.rve_nodes(b.ptr, b.count) == sum((d["L"] * d["m0"]) ** 2 for d in ds)

@@ -1,0 +1,302 @@
+"""GPU parity: every step of the CUDA path through the C ABI against the FP64
+CPU oracle on the same seeded inputs.
+
+Tolerances: integer work (the field) bit-exact; FP64 kernels 1e-12 relative
+(rounding order only); A_hom of the FP64 solve 1e-10 relative per entry
+(relative to max(|a11|, |a22|)); mixed precision 1e-7 on the same measure.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1903_12227_gb300 import rve, workloads
+
+pytestmark = pytest.mark.gpu
+
+CUDA = torch.device("cuda", 0)
+
+
+def _rel_err_A(A, ref):
+    scale = max(abs(ref[0, 0]), abs(ref[1, 1]))
+    return np.abs(np.asarray(A) - ref).max() / scale
+
+
+def _coef_np(d, mask):
+    return np.where(mask, d["a_incl"], d["a_matrix"]).astype(np.float64)
+
+
+def _pack(arrs):
+    return torch.tensor(np.concatenate([a.reshape(-1, *a.shape[2:]) if a.ndim > 2 else a.reshape(-1)
+                                        for a in arrs]), device=CUDA)
+
+
+def _u_oracle_to_nodes(u):   # [2, n, n] -> [n*n, 2]
+    return np.stack([u[0].ravel(), u[1].ravel()], axis=1)
+
+
+# ------------------------------------------------------------------ field --
+FIELD_CASES = [
+    [workloads.realization(4, 8, 10.0, 0, 0)],                          # 32^2, 11 inclusions
+    [workloads.realization(32, 16, 10.0, 5, k) for k in range(3)],     # 512^2, 717 inclusions
+    workloads.config_batch("uneven_4096", seed=1, count=24),            # uneven sizes
+    [workloads.realization(8, 8, 100.0, 2, 7, side_units=5.0)],         # s = 40 > 32: multi-word rows
+    [dict(workloads.realization(4, 8, 10.0, 0, 0), n_incl=0)],          # empty field
+    [dict(workloads.realization(4, 8, 10.0, 0, 0), incl_cells=32, n_incl=1)],   # s = n: full cover
+    [workloads.realization(256, 8, 100.0, 0, 0)],                       # 2048^2, 45875 inclusions
+]
+
+
+@pytest.mark.parametrize("case", range(len(FIELD_CASES)))
+def test_gen_field_bit_exact(case):
+    ds = FIELD_CASES[case]
+    mask = rve.gen_field(ds, device=CUDA)
+    torch.cuda.synchronize()
+    got = rve.unpack_mask(mask, ds)
+    for d, m in zip(ds, got):
+        np.testing.assert_array_equal(m, oracle.gen_field(d).astype(bool))
+
+
+# ------------------------------------------------------- rhs / stiffness --
+def _setup(ds):
+    mask = rve.gen_field(ds, device=CUDA)
+    masks = rve.unpack_mask(mask, ds)
+    coefs = [_coef_np(d, m) for d, m in zip(ds, masks)]
+    return mask, coefs
+
+
+SMALL = [workloads.realization(4, 8, 10.0, 3, k) for k in range(2)] + \
+    [workloads.realization(8, 8, 100.0, 3, 9)]
+
+
+@pytest.mark.parametrize("use_coef", [False, True])
+def test_rhs_matches_oracle(use_coef):
+    mask, coefs = _setup(SMALL)
+    coef_t = torch.tensor(np.concatenate([c.ravel() for c in coefs]), device=CUDA)
+    f = rve.rhs(SMALL, mask=None if use_coef else mask, coef=coef_t if use_coef else None)
+    f = f.cpu().numpy()
+    off = 0
+    for d, c in zip(SMALL, coefs):
+        n = c.shape[0]
+        ref = oracle.rhs(c, 1.0 / d["m0"])
+        got = f[off:off + n * n].reshape(n, n, 2)
+        assert np.abs(got[..., 0] - ref[0]).max() < 1e-14
+        assert np.abs(got[..., 1] - ref[1]).max() < 1e-14
+        off += n * n
+
+
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_stiffness_matches_oracle_csr(scheme):
+    mask, coefs = _setup(SMALL)
+    g = np.random.default_rng(1)
+    xs = [g.standard_normal((c.shape[0] ** 2, 2)) for c in coefs]
+    x = torch.tensor(np.concatenate(xs), device=CUDA)
+    y64 = rve.apply_stiffness(SMALL, x, mask=mask, scheme=scheme).cpu().numpy()
+    y32 = rve.apply_stiffness(SMALL, x.float(), mask=mask, scheme=scheme).cpu().numpy()
+    off = 0
+    for d, c, xx in zip(SMALL, coefs, xs):
+        n = c.shape[0]
+        csr = oracle.assemble(c, 1.0 / d["m0"], scheme)
+        for k in range(2):
+            ref = oracle.spmv(csr, xx[:, k])
+            sc = np.abs(ref).max()
+            assert np.abs(y64[off:off + n * n, k] - ref).max() < 1e-13 * sc
+            assert np.abs(y32[off:off + n * n, k] - ref).max() < 5e-6 * sc
+        off += n * n
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.25])
+def test_precond_matches_oracle(delta):
+    ds = [workloads.realization(4, 8, 10.0, 0, 0), workloads.realization(16, 8, 100.0, 0, 1),
+          workloads.realization(64, 8, 10.0, 0, 2), workloads.realization(8, 8, 10.0, 0, 3)]
+    g = np.random.default_rng(2)
+    xs = []
+    for d in ds:
+        n = d["L"] * d["m0"]
+        r = g.standard_normal((n * n, 2))
+        if delta == 0.0:
+            r -= r.mean(axis=0)
+        xs.append(r)
+    x = torch.tensor(np.concatenate(xs), device=CUDA)
+    z64 = rve.apply_precond(ds, x, delta=delta).cpu().numpy()
+    z32 = rve.apply_precond(ds, x.float(), delta=delta).cpu().numpy()
+    off = 0
+    for d, r in zip(ds, xs):
+        n = d["L"] * d["m0"]
+        c0 = 0.5 * (d["a_matrix"] + d["a_incl"])
+        for k in range(2):
+            ref = oracle.precond(r[:, k].reshape(n, n), c0, delta).ravel()
+            sc = np.abs(ref).max()
+            assert np.abs(z64[off:off + n * n, k] - ref).max() < 1e-12 * sc
+            assert np.abs(z32[off:off + n * n, k] - ref).max() < 2e-5 * sc
+        off += n * n
+
+
+# ---------------------------------------------------------- A_hom kernels --
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_a_hom_and_backward_kernels_on_oracle_correctors(scheme):
+    ds = SMALL
+    mask, coefs = _setup(ds)
+    refs = [oracle.solve_coef(c, d["L"], d["m0"], 0.5 * (d["a_matrix"] + d["a_incl"]),
+                              scheme=scheme, tol=1e-13) for d, c in zip(ds, coefs)]
+    u = torch.tensor(np.concatenate([_u_oracle_to_nodes(r["u"]) for r in refs]), device=CUDA)
+    A, Af = rve.a_hom(ds, u, mask=mask, scheme=scheme, want_flux=True)
+    G = np.array([[[0.7, -0.3], [0.2, 1.1]]] * len(ds))
+    grad = rve.a_hom_backward(ds, u, torch.tensor(G, device=CUDA), scheme=scheme).cpu().numpy()
+    off = 0
+    for k, (d, c, r) in enumerate(zip(ds, coefs, refs)):
+        Ae, Afl = oracle.a_hom(c, r["u"], 1.0 / d["m0"], d["L"], scheme)
+        assert _rel_err_A(A[k].cpu().numpy(), Ae) < 1e-12
+        assert _rel_err_A(Af[k].cpu().numpy(), Afl) < 1e-12
+        n = c.shape[0]
+        gref = oracle.a_hom_grad(r["u"], G[k], 1.0 / d["m0"], d["L"], scheme)
+        assert np.abs(grad[off:off + n * n].reshape(n, n) - gref).max() < 1e-12 * np.abs(gref).max()
+        off += n * n
+
+
+# -------------------------------------------------------------- solvers --
+def _solve_and_hom(ds, opts, mask=None):
+    if mask is None:
+        mask = rve.gen_field(ds, device=CUDA)
+    u, info = rve.solve(ds, mask=mask, opts=opts)
+    A = rve.a_hom(ds, u, mask=mask, scheme=opts.scheme).cpu().numpy()
+    return mask, u, A, rve.info_to_dicts(info, len(ds))
+
+
+SOLVE_CASES = {
+    "single_L4": [workloads.realization(4, 8, 10.0, 0, 0)],
+    "mixed_sizes": [workloads.realization(4, 8, 10.0, 1, 0), workloads.realization(16, 8, 100.0, 1, 1),
+                    workloads.realization(8, 8, 10.0, 1, 2), workloads.realization(4, 16, 100.0, 1, 3)],
+}
+
+
+@pytest.mark.parametrize("case", sorted(SOLVE_CASES))
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+@pytest.mark.parametrize("precision,path,bound", [(rve.FP64, rve.PATH_FUSED, 1e-10),
+                                                  (rve.MIXED, rve.PATH_FUSED, 1e-7),
+                                                  (rve.FP64, rve.PATH_PLAIN, 1e-10)])
+def test_solve_matches_oracle(case, scheme, precision, path, bound):
+    ds = SOLVE_CASES[case]
+    tol = 1e-12 if precision == rve.FP64 else 1e-10
+    opts = rve.make_opts(scheme=scheme, precision=precision, path=path, tol=tol)
+    mask, u, A, info = _solve_and_hom(ds, opts)
+    un = u.cpu().numpy()
+    off = 0
+    for k, d in enumerate(ds):
+        ref = oracle.solve_realization(d, scheme=scheme, tol=1e-13)
+        assert info[k]["status"] == rve.RVE_OK, info[k]
+        assert max(info[k]["relres"]) <= tol * 1.0001
+        assert _rel_err_A(A[k], ref["A_energy"]) < bound, (A[k], ref["A_energy"])
+        n = d["L"] * d["m0"]
+        for c in range(2):
+            ug = un[off:off + n * n, c]
+            ug = ug - ug.mean()
+            sc = np.abs(ref["u"][c]).max()
+            assert np.abs(ug - ref["u"][c].ravel()).max() < (1e-8 if precision == rve.FP64 else 1e-6) * sc
+        # iteration counts close to the oracle's (rounding order differs)
+        if precision == rve.FP64:
+            for c in range(2):
+                assert abs(info[k]["iters"][c] - ref["iters"][c]) <= 3
+        off += n * n
+
+
+def test_full_size_plain_L32_fp64_and_mixed():
+    # the benchmark's workload size (512^2 nodes), one realization each way
+    d = workloads.realization(32, 16, 10.0, 0, 0)
+    ref = oracle.solve_realization(d, tol=1e-12, want_u=False)
+    for precision, bound in ((rve.FP64, 1e-10), (rve.MIXED, 1e-7)):
+        opts = rve.make_opts(precision=precision, tol=1e-10)
+        _, _, A, info = _solve_and_hom([d], opts)
+        assert info[0]["status"] == rve.RVE_OK
+        assert _rel_err_A(A[0], ref["A_energy"]) < bound
+
+
+def test_large_2048_properties():
+    # 2048^2 nodes: f sums to zero, A annihilates constants, symmetry
+    d = workloads.realization(256, 8, 100.0, 0, 0)
+    mask = rve.gen_field([d], device=CUDA)
+    f = rve.rhs([d], mask=mask)
+    assert abs(f[:, 0].sum().item()) < 1e-9 and abs(f[:, 1].sum().item()) < 1e-9
+    ones = torch.ones(2048 * 2048, 2, dtype=torch.float64, device=CUDA)
+    y = rve.apply_stiffness([d], ones, mask=mask)
+    assert y.abs().max().item() < 1e-12
+    g = torch.randn(2048 * 2048, 2, dtype=torch.float64, device=CUDA)
+    h = torch.randn(2048 * 2048, 2, dtype=torch.float64, device=CUDA)
+    lhs = (g * rve.apply_stiffness([d], h, mask=mask)).sum(0)
+    rhs_ = (h * rve.apply_stiffness([d], g, mask=mask)).sum(0)
+    assert torch.allclose(lhs, rhs_, rtol=1e-10)
+
+
+# ------------------------------------------------------------ edge cases --
+def test_constant_field_gives_cI_and_zero_iterations():
+    for d in (dict(workloads.realization(4, 8, 10.0, 0, 0), n_incl=0),
+              dict(workloads.realization(4, 8, 10.0, 0, 0), incl_cells=32, n_incl=1),
+              dict(workloads.realization(8, 8, 1.0, 0, 0))):
+        for precision in (rve.FP64, rve.MIXED):
+            _, u, A, info = _solve_and_hom([d], rve.make_opts(precision=precision))
+            mask = oracle.gen_field(d)
+            a = d["a_incl"] if mask.all() else d["a_matrix"]
+            if d["a_incl"] == d["a_matrix"] or mask.all() or not mask.any():
+                assert np.abs(A[0] - a * np.eye(2)).max() < 1e-14
+                assert info[0]["iters"] == (0, 0)
+                assert u.abs().max().item() == 0.0
+
+
+def test_max_iter_reports_no_convergence():
+    d = workloads.realization(8, 8, 100.0, 0, 0)
+    for precision in (rve.FP64, rve.MIXED):
+        _, _, _, info = _solve_and_hom([d], rve.make_opts(precision=precision, max_iter=2))
+        assert info[0]["status"] == rve.RVE_ENOCONV
+    _, _, _, info = _solve_and_hom([d], rve.make_opts(path=rve.PATH_PLAIN, max_iter=2))
+    assert info[0]["status"] == rve.RVE_ENOCONV
+
+
+def test_invalid_arguments_rejected_before_launch():
+    d = workloads.realization(4, 8, 10.0, 0, 0)
+    with pytest.raises(rve.RveError):
+        rve.solve([d], mask=rve.gen_field([d], device=CUDA), opts=rve.make_opts(precision=7))
+    with pytest.raises(rve.RveError):
+        rve.gen_field([dict(d, m0=6)], device=CUDA)
+
+
+def test_homogenize_host_matches_device_path():
+    ds = [workloads.realization(4, 8, 10.0, 4, k) for k in range(5)]
+    opts = rve.make_opts(precision=rve.MIXED)
+    A_host, info = rve.homogenize_host(ds, opts, device=CUDA)
+    _, _, A_dev, _ = _solve_and_hom(ds, opts)
+    np.testing.assert_array_equal(A_host, A_dev)
+
+
+def test_repeat_runs_bit_identical():
+    ds = SOLVE_CASES["mixed_sizes"]
+    opts = rve.make_opts(precision=rve.MIXED)
+    _, u1, A1, _ = _solve_and_hom(ds, opts)
+    _, u2, A2, _ = _solve_and_hom(ds, opts)
+    np.testing.assert_array_equal(A1, A2)
+    assert torch.equal(u1, u2)
+
+
+# --------------------------------------------------------------- adjoint --
+def test_autograd_matches_central_differences():
+    d = workloads.realization(4, 8, 10.0, 6, 0)
+    mask = oracle.gen_field(d)
+    coef = torch.tensor(_coef_np(d, mask).ravel(), device=CUDA, requires_grad=True)
+    opts = rve.make_opts(tol=1e-13)
+    A = rve.AHom.apply(coef, [d], opts)
+    G = torch.tensor([[[0.6, -0.2], [0.4, 1.3]]], dtype=torch.float64, device=CUDA)
+    (A * G).sum().backward()
+    g = coef.grad.cpu().numpy()
+    cells = workloads.fd_cells(32, 8, seed=6, index=0)
+    eps = 1e-6
+    base = coef.detach().clone()
+    for c1, c2 in cells:
+        k = c1 * 32 + c2
+        cp, cm = base.clone(), base.clone()
+        cp[k] += eps
+        cm[k] -= eps
+        fp = (rve.AHom.apply(cp, [d], opts) * G).sum().item()
+        fm = (rve.AHom.apply(cm, [d], opts) * G).sum().item()
+        fd = (fp - fm) / (2 * eps)
+        assert abs(fd - g[k]) < 1e-6 * max(abs(g).max(), 1e-12) + 1e-9
+    # Euler identity: sum_c a_c dA_ij/da_c = A_ij (1-homogeneity)
+    assert abs((g * base.cpu().numpy()).sum() - (A * G).sum().item()) < 1e-11
