@@ -116,8 +116,11 @@ typedef struct {
     int32_t iters[2];     /* CG iterations (operator applications) per corrector */
     int32_t status;       /* rve_status                                           */
     int32_t refinements;  /* FP64 true-residual evaluations                       */
+    int32_t steps;        /* fused pipeline steps spent iterating (both correctors
+                             advance together; plain path: CG iterations)         */
+    int32_t reserved;
     double relres[2];     /* last FP64 true relative residual per corrector       */
-} rve_solve_info;
+} rve_solve_info;         /* 40 bytes */
 
 /* Human-readable name of a status code (static string). */
 const char* rve_status_string(int32_t status);
@@ -210,6 +213,18 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
                                const rve_solve_opts* opts, double* A_host,
                                rve_solve_info* info_host, void* ws, size_t ws_bytes,
                                void* stream);
+
+/* Diagnostics for benchmarks (process-wide, not thread-safe).
+ * rve_profile_enable(1): the fused solver brackets every launch of its four
+ * pipeline kernels with CUDA events on the caller's stream and accumulates
+ * their durations.  rve_profile_read(ms[4], launches[4]) returns the totals
+ * per kernel -- 0 stencil pass, 1 update + row transform, 2 column
+ * transform, 3 control -- and resets them; it returns 4.
+ * rve_launch_count() returns the number of kernels the library launched
+ * since the previous call. */
+void rve_profile_enable(int32_t on);
+int32_t rve_profile_read(double* ms, int64_t* launches);
+int64_t rve_launch_count(void);
 
 #ifdef __cplusplus
 }

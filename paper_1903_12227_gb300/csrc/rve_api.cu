@@ -357,6 +357,7 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
     double* A = reinterpret_cast<double*>(w + oa);
     rve_solve_info* info = reinterpret_cast<rve_solve_info*>(w + oi);
     if (launch_gen_field(p, nullptr, mask, s) != cudaSuccess) return RVE_ECUDA;
+    note_launch();   // the mask clear
     st = rve_solve_correctors(r_host, batch, mask, nullptr, &o, u, info, w + ow, p.total, stream);
     if (st != RVE_OK) return st;
     st = rve_a_hom(r_host, batch, mask, nullptr, o.scheme, u, A, nullptr, w + ow, p.total, stream);
@@ -370,5 +371,17 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
         return RVE_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
+
+void rve_profile_enable(int32_t on) { profile_enable(on != 0); }
+
+int32_t rve_profile_read(double* ms, int64_t* launches) {
+    long long l[4];
+    const int k = profile_read(ms, l);
+    if (launches)
+        for (int j = 0; j < 4; ++j) launches[j] = (int64_t)l[j];
+    return k;
+}
+
+int64_t rve_launch_count(void) { return (int64_t)g_launches.exchange(0); }
 
 }  // extern "C"

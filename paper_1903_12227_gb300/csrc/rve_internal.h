@@ -9,9 +9,15 @@
 
 #include "rve.h"
 
+#include <atomic>
+
 namespace rve {
 
 struct RDesc;
+
+// Kernel launches issued by the library (diagnostics).
+extern std::atomic<long long> g_launches;
+inline void note_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Solver phases of one realization (fused pipeline).
 enum : int32_t { PH_REFINE = 0, PH_ITER = 1, PH_DONE = 2 };
@@ -23,7 +29,7 @@ struct RState {
     int32_t iters[2];
     int32_t active[2];   // corrector still iterating in the current cycle
     int32_t cdone[2];    // corrector met the outer tolerance
-    int32_t final_pass, pad;
+    int32_t final_pass, steps;   // steps: pipeline steps spent in ITER
     double fnorm[2];     // ||f_c||
     double s[2];         // scale of the current inner system (||r64|| at restart)
     double rho[2];       // r.z of the current residual
@@ -83,6 +89,8 @@ rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const 
                            cudaStream_t s);
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                          int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
+void profile_enable(bool on);
+int profile_read(double* ms, long long* launches);
 cudaError_t launch_backward(const Plan& p, void* ws, int scheme, const double* u,
                             const double* gradA, double* grad_coef, cudaStream_t s);
 

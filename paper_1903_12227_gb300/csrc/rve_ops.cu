@@ -225,6 +225,7 @@ static cudaError_t for_chunks(const Plan& p, UnitsFn units, LaunchFn fn) {
         for (int k = ch.count + 1; k <= CHUNK; ++k) ch.start[k] = ch.start[ch.count];
         cudaError_t e = fn(ch, b0);
         if (e != cudaSuccess) return e;
+        note_launch();
     }
     return cudaSuccess;
 }
@@ -299,6 +300,7 @@ cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const do
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_a_hom_final<<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    note_launch(2);
     return cudaGetLastError();
 }
 

@@ -204,6 +204,8 @@ __global__ void k_pl_report(const PlainScal* sc, rve_solve_info* info, int b) {
     r.iters[1] = sc->iters[1];
     r.status = sc->status;
     r.refinements = 1;
+    r.steps = max(sc->iters[0], sc->iters[1]);
+    r.reserved = 0;
     r.relres[0] = sc->relres[0];
     r.relres[1] = sc->relres[1];
     info[b] = r;
@@ -317,6 +319,7 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
         k_pl_dot<<<nb, PL_THREADS, 0, s>>>(desc, b, r, z, part);
         k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_BETA, o.tol, o.max_iter);
         k_pl_xpby<<<nb, PL_THREADS, 0, s>>>(desc, b, sc, z, pp);
+        note_launch(13);
         if ((it + 1) % every == 0 || it == 0) {
             if (cudaMemcpyAsync(&hsc, sc, sizeof(PlainScal), cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess ||
@@ -328,6 +331,7 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
     k_pl_resid<SCHEME><<<nb, PL_THREADS, 0, s>>>(desc, b, cs, u, part);
     k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_RELRES, o.tol, o.max_iter);
     k_pl_report<<<1, 1, 0, s>>>(sc, info, b);
+    note_launch(14);   // set-up, final residual and report
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 

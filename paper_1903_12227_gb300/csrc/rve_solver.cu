@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -382,6 +383,7 @@ __global__ void k_control(const Ctx c) {
     }
     if ((threadIdx.x & 31) != 0) return;
     if (s.phase == PH_ITER) {
+        s.steps += 1;
         bool any_active = false;
         for (int k = 0; k < 2; ++k) {
             if (!s.active[k]) { s.alpha[k] = 0.0; s.beta[k] = 0.0; continue; }
@@ -481,12 +483,55 @@ __global__ void k_report(const Ctx c, rve_solve_info* info) {
     r.iters[1] = s.iters[1];
     r.status = (s.phase == PH_DONE) ? s.status : RVE_ENOCONV;
     r.refinements = s.refinements;
+    r.steps = s.steps;
+    r.reserved = 0;
     r.relres[0] = s.relres[0];
     r.relres[1] = s.relres[1];
     info[b] = r;
 }
 
 // --------------------------------------------------------------- host --
+std::atomic<long long> g_launches{0};
+
+// Per-kernel event timing of the fused pipeline (diagnostics).
+struct Profiler {
+    bool on = false;
+    double ms[4] = {0, 0, 0, 0};
+    long long launches[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev;    // 5 events per recorded step
+    int used = 0;                   // steps recorded since the last harvest
+    void ensure(int steps) {
+        while ((int)ev.size() < 5 * steps) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            ev.push_back(e);
+        }
+    }
+    void harvest() {   // stream already synchronised
+        for (int k = 0; k < used; ++k)
+            for (int j = 0; j < 4; ++j) {
+                float t = 0.f;
+                if (cudaEventElapsedTime(&t, ev[5 * k + j], ev[5 * k + j + 1]) == cudaSuccess) {
+                    ms[j] += t;
+                    launches[j] += 1;
+                }
+            }
+        used = 0;
+    }
+};
+static Profiler g_prof;
+
+void profile_enable(bool on) { g_prof.on = on; }
+int profile_read(double* ms, long long* launches) {
+    for (int j = 0; j < 4; ++j) {
+        if (ms) ms[j] = g_prof.ms[j];
+        if (launches) launches[j] = g_prof.launches[j];
+        g_prof.ms[j] = 0.0;
+        g_prof.launches[j] = 0;
+    }
+    return 4;
+}
+
 static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double* coef, double* u,
                     const rve_solve_opts& o) {
     char* w = static_cast<char*>(ws);
@@ -545,11 +590,17 @@ rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
 }
 
 template <typename V, int SCHEME>
-static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s) {
+static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaEvent_t* ev) {
+    if (ev) cudaEventRecord(ev[0], s);
     k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
+    if (ev) cudaEventRecord(ev[1], s);
     k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
+    if (ev) cudaEventRecord(ev[2], s);
     k_fused_C<V><<<p.tilesC, 256, p.smemC, s>>>(c);
+    if (ev) cudaEventRecord(ev[3], s);
     k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
+    if (ev) cudaEventRecord(ev[4], s);
+    note_launch(4);
     return cudaGetLastError();
 }
 
@@ -574,15 +625,26 @@ static rve_status fused_loop(const Plan& p, const Ctx& c, const rve_solve_opts& 
     const int64_t max_steps = 2LL * o.max_iter + 64;
     const int every = o.check_every > 0 ? o.check_every : 8;
     int host_done = 0;
+    if (g_prof.on) {
+        g_prof.ensure(every);
+        g_prof.used = 0;
+    }
     for (int64_t g = 0; g < max_steps; ++g) {
-        if (fused_step<V, SCHEME>(p, c, s) != cudaSuccess) return RVE_ECUDA;
+        cudaEvent_t* ev = nullptr;
+        if (g_prof.on && (int)g_prof.ev.size() >= 5 * every) ev = &g_prof.ev[5 * g_prof.used++];
+        if (fused_step<V, SCHEME>(p, c, s, ev) != cudaSuccess) return RVE_ECUDA;
         if ((g + 1) % every == 0) {
             if (cudaMemcpyAsync(&host_done, c.ndone, sizeof(int), cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return RVE_ECUDA;
+            if (g_prof.on) g_prof.harvest();
             if (host_done >= p.batch) break;
         }
+    }
+    if (g_prof.on) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return RVE_ECUDA;
+        g_prof.harvest();
     }
     return RVE_OK;
 }
@@ -594,6 +656,7 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
     if (st != RVE_OK) return st;
     Ctx c = make_ctx(p, ws, mask, coef, u, o);
     k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
+    note_launch(2);   // tables + init
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     if (p.precision == RVE_MIXED) {
         st = (p.scheme == RVE_Q1_LUMPED) ? fused_loop<float2, 1>(p, c, o, s)
@@ -604,6 +667,7 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
     }
     if (st != RVE_OK) return st;
     k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
@@ -663,6 +727,7 @@ static cudaError_t precond_apply_t(const Plan& p, void* ws, double delta, const 
     k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, x, tmp);
     k_col_hartley<V><<<p.tilesC, 256, p.smemC, s>>>(desc, startC, p.batch, tb, delta, tmp);
     k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, tmp, y);
+    note_launch(3);
     return cudaGetLastError();
 }
 

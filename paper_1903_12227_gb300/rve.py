@@ -47,7 +47,8 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32 * 2), ("status", ctypes.c_int32),
-                ("refinements", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
+                ("refinements", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
 
 
 INFO_BYTES = ctypes.sizeof(SolveInfo)
@@ -95,6 +96,12 @@ def lib() -> ctypes.CDLL:
         L.rve_homogenize_workspace_size.argtypes = [vp, i32, vp]
         L.rve_homogenize_host.restype = i32
         L.rve_homogenize_host.argtypes = [vp, i32, vp, vp, vp, vp, sz, vp]
+        L.rve_profile_enable.restype = None
+        L.rve_profile_enable.argtypes = [i32]
+        L.rve_profile_read.restype = i32
+        L.rve_profile_read.argtypes = [vp, vp]
+        L.rve_launch_count.restype = i64
+        L.rve_launch_count.argtypes = []
         _lib = L
     return _lib
 
@@ -222,8 +229,12 @@ def workspace_size(batch, opts: SolveOpts | None = None) -> int:
 def info_to_dicts(info: torch.Tensor, count: int) -> list:
     raw = info.cpu().numpy().tobytes()
     arr = (SolveInfo * count).from_buffer_copy(raw)
-    return [{"iters": (a.iters[0], a.iters[1]), "status": a.status,
-             "refinements": a.refinements, "relres": (a.relres[0], a.relres[1])} for a in arr]
+    return [_info_dict(a) for a in arr]
+
+
+def _info_dict(a: SolveInfo) -> dict:
+    return {"iters": (a.iters[0], a.iters[1]), "status": a.status, "refinements": a.refinements,
+            "steps": a.steps, "relres": (a.relres[0], a.relres[1])}
 
 
 def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u=None,
@@ -291,9 +302,24 @@ def homogenize_host(batch, opts: SolveOpts | None = None, ws=None, stream=None, 
                                     A.ctypes.data_as(ctypes.c_void_p),
                                     ctypes.cast(info, ctypes.c_void_p), _ptr(ws), ws.numel(),
                                     _stream(stream)), "rve_homogenize_host")
-    return A.reshape(b.count, 2, 2), [{"iters": (i.iters[0], i.iters[1]), "status": i.status,
-                                       "refinements": i.refinements,
-                                       "relres": (i.relres[0], i.relres[1])} for i in info]
+    return A.reshape(b.count, 2, 2), [_info_dict(i) for i in info]
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().rve_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    import numpy as np
+    ms = np.zeros(4)
+    ln = np.zeros(4, dtype=np.int64)
+    lib().rve_profile_read(ms.ctypes.data_as(ctypes.c_void_p), ln.ctypes.data_as(ctypes.c_void_p))
+    names = ("stencil", "update_row", "column", "control")
+    return {k: {"ms": float(ms[i]), "launches": int(ln[i])} for i, k in enumerate(names)}
+
+
+def launch_count() -> int:
+    return int(lib().rve_launch_count())
 
 
 def unpack_mask(mask: torch.Tensor, batch) -> list:

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(librve):
 def test_struct_sizes_match_header(librve):
     from paper_1903_12227_gb300 import rve
     assert ctypes.sizeof(rve.Realization) == 48
-    assert ctypes.sizeof(rve.SolveInfo) == 32
+    assert ctypes.sizeof(rve.SolveInfo) == 40
 
 
 def test_host_validation_without_gpu(librve):
