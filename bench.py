@@ -1,0 +1,402 @@
+"""Benchmark: RVE realizations per second (both correctors + A_hom each).
+
+Workload (the method at scale): L = 32 unit cells per axis, h = 1/16
+(512 x 512 nodes, 262,144 unknowns per corrector), contrast 10, 717 square
+inclusions of side 1 (density 0.7), PCG to a true relative residual of 1e-10,
+seeded synthetic realizations (seed 0, indices 0..999 cycled).  One step =
+field generation + both corrector solves + A_hom for a batch of B
+realizations through the C ABI, mixed precision (FP32 stencil / transforms /
+vectors, FP64 dots, true-residual refinement and A_hom).  The per-step
+working set (~2 GB) is far larger than L2.
+
+Also reported: the FP64 fused path and the plain FP64 path (one realization
+at a time, unfused kernels) on a small sample; the oracle on the host cores;
+the end-to-end number through rve_homogenize_host (host descriptors in, host
+A out); the roofline of the dominant kernel from live CUDA-event timing.
+
+    python bench.py [--gpus N --steps K --warmup W --batch B] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RVE realizations/s (2 correctors each) at ≤1e-7 A_hom rel. error; HBM % of peak"
+UNIT = "realizations/s"
+WORKLOAD = dict(name="plain_L32", L=32, m0=16, contrast=10.0, tol=1e-10, realizations=1000)
+CONFIG_DESC = ("L=32, h=1/16 (512x512 nodes, 262144 unknowns per corrector), contrast 10, "
+               "717 inclusions of side 1 (density 0.7), PCG tol 1e-10 on the true residual")
+
+# Algorithmic bytes per node (both correctors, float2 = 8 B per node pair) of
+# the fused pipeline kernels, per launch: S reads t, p_old, x and writes
+# p_new, q, x; in REFINE it reads u (16 B), x, p and writes q.  U reads r, q
+# and writes r, t; in REFINE it reads x, p, u, q and writes u, x, r, t.
+# C reads and writes t.  The coefficient bitmask adds 1/8 B per node.
+BYTES_PER_NODE = {
+    "stencil": {"iter": 6 * 8 + 0.125, "refine": 16 + 8 + 8 + 8 + 0.125},
+    "update_row": {"iter": 4 * 8, "refine": 8 + 8 + 16 + 8 + 16 + 8 + 8 + 8},
+    "column": {"iter": 2 * 8, "refine": 2 * 8},
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=125)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison arms")
+    return ap.parse_args()
+
+
+def descs(start: int, count: int):
+    from paper_1903_12227_gb300 import workloads
+    return [workloads.realization(WORKLOAD["L"], WORKLOAD["m0"], WORKLOAD["contrast"], 0,
+                                  (start + k) % WORKLOAD["realizations"]) for k in range(count)]
+
+
+# ----------------------------------------------------------------- clocks --
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+def cpu_oracle_rate(count: int, threads: int = 0):
+    """Oracle (as it stands) on the host cores: realizations/s, threads, A."""
+    import oracle
+    ds = descs(0, count)
+    t0 = time.perf_counter()
+    A, it, used = oracle.solve_batch(ds, tol=WORKLOAD["tol"], threads=threads)
+    dt = time.perf_counter() - t0
+    return count / dt, used, A, dt
+
+
+def run_reference(args):
+    """The oracle arm: each step solves one realization per host thread."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_step = cores
+    times = []
+    used = cores
+    for k in range(args.warmup + args.steps):
+        ds = descs(k * per_step, per_step)
+        t0 = time.perf_counter()
+        _, _, used = oracle.solve_batch(ds, tol=WORKLOAD["tol"], threads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"{WORKLOAD['name']}: {CONFIG_DESC}",
+                      "realizations_per_step": per_step},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                            "sample": f"{per_step} realizations per step (one per host thread)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm --
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1903_12227_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """Per-node DRAM traffic of `kernel` from the committed ncu summary, if it
+    was measured on the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash():
+        return None
+    return rec.get("bytes_per_node", {}).get(kernel)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1903_12227_gb300 import rve
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    B = args.batch
+    opts = rve.make_opts(precision=rve.MIXED, tol=WORKLOAD["tol"])
+    # each rank owns its own realization indices (weak scaling, no collective
+    # on the data path)
+    base = rank * B * (args.steps + args.warmup)
+    probe = rve.Batch(descs(0, B))
+    ws = rve.workspace(rve.workspace_size(probe, opts), dev)
+    mask = torch.empty(probe.words, dtype=torch.int32, device=dev)
+    u = torch.empty(probe.nodes, 2, dtype=torch.float64, device=dev)
+    info = torch.empty(B * rve.INFO_BYTES, dtype=torch.uint8, device=dev)
+    nb_hom = rve.workspace_size(probe, rve.make_opts())
+    ws_hom = ws if ws.numel() >= nb_hom else rve.workspace(nb_hom, dev)
+    A_out = torch.empty(B, 4, dtype=torch.float64, device=dev)
+    L = rve.lib()
+
+    def step(k: int):
+        b = rve.Batch(descs(base + k * B, B))
+        rve.check(L.rve_gen_field(b.ptr, b.count, rve._ptr(mask), rve._stream(stream)))
+        rve.check(L.rve_solve_correctors(b.ptr, b.count, rve._ptr(mask), None,
+                                         rve.ctypes.byref(opts), rve._ptr(u), rve._ptr(info),
+                                         rve._ptr(ws), ws.numel(), rve._stream(stream)))
+        rve.check(L.rve_a_hom(b.ptr, b.count, rve._ptr(mask), None, opts.scheme, rve._ptr(u),
+                              rve._ptr(A_out), None, rve._ptr(ws_hom), ws_hom.numel(),
+                              rve._stream(stream)))
+        return b
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    rve.launch_count()
+    rve.profile_enable(True)
+    rve.profile_read()
+    clocks = Clocks(local)
+    clocks.start()
+    infos, As = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+        infos.append(info.clone())
+        As.append(A_out.clone())
+    ev1.record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = rve.profile_read()
+    rve.profile_enable(False)
+    launches = rve.launch_count()
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_real = B * args.steps * world
+    value = total_real / (elapsed_ms / 1e3)
+
+    info_d = [d for t in infos for d in rve.info_to_dicts(t, B)]
+    A_all = torch.cat(As).cpu().numpy().reshape(-1, 2, 2)
+    statuses = sorted({d["status"] for d in info_d})
+    steps_iter = sum(d["steps"] for d in info_d)
+    refines = sum(d["refinements"] for d in info_d)
+    nodes = 512 * 512
+
+    # roofline of the dominant fused kernel (live CUDA-event timing)
+    kinds = ("stencil", "update_row", "column")
+    dom = max(kinds, key=lambda k: prof[k]["ms"])
+    bpn = BYTES_PER_NODE[dom]
+    alg_bytes = nodes * (steps_iter * bpn["iter"] + refines * bpn["refine"])
+    launches_dom = max(prof[dom]["launches"], 1)
+    avg_launch_s = prof[dom]["ms"] / 1e3 / launches_dom
+    bytes_per_launch = alg_bytes / launches_dom
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tr = ncu_traffic(dom)
+    traffic = None if tr is None else tr * nodes * (steps_iter + refines) / launches_dom
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": avg_launch_s * 1e6,
+                "time_share": {k: prof[k]["ms"] / max(sum(prof[j]["ms"] for j in prof), 1e-9)
+                               for k in prof}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 vectors + f64 dots/refinement/A_hom (mixed)", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD['name']}: {CONFIG_DESC}", "batch_per_gpu": B,
+                      "realizations_per_step": B * world, "l2": "inputs larger than L2 "
+                      "(~2 GB working set per step, 129 MB L2)", "precision": "mixed"},
+           "roofline": roofline, "gpu_launches": launches,
+           "clocks": clk,
+           "solver": {"statuses": statuses, "mean_steps": steps_iter / len(info_d),
+                      "mean_iters": float(np.mean([max(d["iters"]) for d in info_d])),
+                      "mean_refinements": refines / len(info_d),
+                      "max_relres": float(max(max(d["relres"]) for d in info_d))},
+           "a_hom_stats": {"mean": A_all.mean(axis=0).tolist(),
+                           "var": A_all.var(axis=0, ddof=1).tolist(), "count": len(A_all)},
+           "wall_s": wall}
+
+    A16 = None
+    if rank == 0 and not args.no_extras:
+        ex = extras(args, rve, torch, np, dev, stream)
+        A16 = ex.pop("_A16")
+        out.update(ex)
+        if "fp64_plain" in out:
+            out["speedup_vs_fp64_plain"] = value / out["fp64_plain"]["value"]
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, A_cpu, dt = cpu_oracle_rate(min(os.cpu_count() or 1, 32))
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{len(A_cpu)} realizations (indices 0..{len(A_cpu) - 1}) "
+                                         f"of the same workload, one per host thread ({dt:.1f} s)"}
+        if A16 is not None:
+            # mixed-precision A_hom against the oracle on the same realizations
+            k = min(len(A_cpu), len(A16))
+            sc = np.maximum(np.abs(A_cpu[:k, 0, 0]), np.abs(A_cpu[:k, 1, 1]))
+            out["a_hom_max_rel_err_vs_oracle"] = float(
+                (np.abs(A16[:k] - A_cpu[:k]).max(axis=(1, 2)) / sc).max())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extras(args, rve, torch, np, dev, stream):
+    """e2e through the host-buffer ABI call, and the FP64 comparison arms."""
+    out = {}
+    B = args.batch
+    opts = rve.make_opts(precision=rve.MIXED, tol=WORKLOAD["tol"])
+    b0 = rve.Batch(descs(0, B))
+    ws_h = rve.workspace(rve.lib().rve_homogenize_workspace_size(b0.ptr, b0.count,
+                                                                 rve.ctypes.byref(opts)), dev)
+    rve.homogenize_host(b0, opts, ws=ws_h)   # warm
+    torch.cuda.synchronize()
+    n_e2e = 2
+    t0 = time.perf_counter()
+    A_ref = None
+    for k in range(n_e2e):
+        A_ref, _ = rve.homogenize_host(descs(B * (k + 1), B), opts, ws=ws_h)
+    dt = time.perf_counter() - t0
+    out["e2e"] = {"value": n_e2e * B / dt, "unit": UNIT,
+                  "h2d_bytes_per_step": B * 48, "d2h_bytes_per_step": B * (32 + 40),
+                  "api": "rve_homogenize_host (host descriptors in, host A_hom out)"}
+    del ws_h
+    # FP64 fused and plain FP64 paths on a small sample
+    for name, o, cnt in (("fp64_fused", rve.make_opts(precision=rve.FP64, tol=WORKLOAD["tol"]), 16),
+                         ("fp64_plain", rve.make_opts(precision=rve.FP64, path=rve.PATH_PLAIN,
+                                                      tol=WORKLOAD["tol"]), 4)):
+        ds = descs(0, cnt)
+        mask = rve.gen_field(ds, device=dev)
+        ws = rve.workspace(rve.workspace_size(ds, o), dev)
+        rve.solve(ds, mask=mask, opts=o, ws=ws)   # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mask = rve.gen_field(ds, device=dev)
+        u, info = rve.solve(ds, mask=mask, opts=o, ws=ws)
+        A = rve.a_hom(ds, u, mask=mask)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"value": cnt / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                     "sample": f"{cnt} realizations",
+                     "mean_iters": float(np.mean([max(d["iters"]) for d in rve.info_to_dicts(info, cnt)]))}
+        if name == "fp64_fused":
+            fp64_A = A.cpu().numpy()
+        del ws
+    # accuracy of mixed vs FP64 (GPU) on the same 16 realizations
+    m16 = rve.gen_field(descs(0, 16), device=dev)
+    u16, _ = rve.solve(descs(0, 16), mask=m16, opts=opts)
+    A16 = rve.a_hom(descs(0, 16), u16, mask=m16).cpu().numpy()
+    sc = np.maximum(np.abs(fp64_A[:, 0, 0]), np.abs(fp64_A[:, 1, 1]))
+    out["a_hom_max_rel_err_mixed_vs_fp64"] = float((np.abs(A16 - fp64_A).max(axis=(1, 2)) / sc).max())
+    out["_A16"] = A16
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
