@@ -61,7 +61,9 @@ typedef enum {
     RVE_ENAN = 3,       /* NaN/Inf met in a reduction                        */
     RVE_ETIMEOUT = 4,   /* a bounded device-side wait gave up               */
     RVE_ECUDA = 5,      /* a CUDA call failed                               */
-    RVE_ENOMEM = 6      /* workspace smaller than rve_workspace_size()      */
+    RVE_ENOMEM = 6,     /* workspace smaller than rve_workspace_size()      */
+    RVE_ESCRATCH = 7    /* request larger than the fixed scratch of
+                           rve_a_hom_noalloc (RVE_NOALLOC_MAX_NODES)         */
 } rve_status;
 
 typedef enum {
@@ -213,6 +215,27 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
                                const rve_solve_opts* opts, double* A_host,
                                rve_solve_info* info_host, void* ws, size_t ws_bytes,
                                void* stream);
+
+/* Allocation-free variant of rve_a_hom, for callers that cannot allocate
+ * device memory: programs whose device memory is all owned by their own pool
+ * allocator, and latency-critical loops that cannot afford cudaMalloc /
+ * cudaFree (which may synchronise the device).  It takes no workspace.  The
+ * paper has no counterpart; results equal rve_a_hom's (same sums, same
+ * order).
+ * Scratch: a fixed library-owned device array of 1 MiB (8 partial sums per
+ * 1024 nodes) that every GPU loading the library holds until exit; requests
+ * above RVE_NOALLOC_MAX_NODES nodes in total return RVE_ESCRATCH before
+ * anything is launched.  The first call on a device does a one-time set-up
+ * (it looks up the array's device address with that device current): make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents; each call writes every partial it reads,
+ * so nothing needs clearing, but calls that overlap on the GPU (other streams
+ * or host threads) race on it and must be serialised by the caller.
+ * Arguments as rve_a_hom. */
+#define RVE_NOALLOC_MAX_NODES (1LL << 24)
+rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                             const double* coef, int32_t scheme, const double* u,
+                             double* A, double* A_flux, void* stream);
 
 /* Diagnostics for benchmarks (process-wide, not thread-safe).
  * rve_profile_enable(1): the fused solver brackets every launch of its four

@@ -187,6 +187,9 @@ const char* rve_status_string(int32_t status) {
         case RVE_ETIMEOUT: return "RVE_ETIMEOUT: a bounded device-side wait gave up";
         case RVE_ECUDA: return "RVE_ECUDA: a CUDA call failed";
         case RVE_ENOMEM: return "RVE_ENOMEM: workspace too small";
+        case RVE_ESCRATCH:
+            return "RVE_ESCRATCH: more nodes than the fixed scratch of rve_a_hom_noalloc holds "
+                   "(RVE_NOALLOC_MAX_NODES)";
         default: return "unknown rve_status";
     }
 }

@@ -21,7 +21,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librve.so")
 
-RVE_OK, RVE_EINVAL, RVE_ENOCONV, RVE_ENAN, RVE_ETIMEOUT, RVE_ECUDA, RVE_ENOMEM = range(7)
+RVE_OK, RVE_EINVAL, RVE_ENOCONV, RVE_ENAN, RVE_ETIMEOUT, RVE_ECUDA, RVE_ENOMEM, RVE_ESCRATCH = range(8)
+NOALLOC_MAX_NODES = 1 << 24
 FP64, MIXED = 0, 1
 CONSISTENT, LUMPED = 0, 1
 PATH_FUSED, PATH_PLAIN, PATH_PERSISTENT = 0, 1, 2
