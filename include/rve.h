@@ -107,7 +107,8 @@ typedef struct {
     double delta;        /* preconditioner shift; 0 = drop the constant mode*/
     double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-5)*/
     int32_t tile_rows;   /* stencil tile height, 0 = tuned default          */
-    int32_t col_tile;    /* columns per transform tile, 0 = tuned default   */
+    int32_t col_tile;    /* threads of a column-transform block (power of
+                            two, 32..1024); 0 = 512, or 1024 when n > 512  */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
     int32_t timeout_ms;  /* persistent path: bound on each grid-wide wait
                             (0 = 2000 ms)                                   */

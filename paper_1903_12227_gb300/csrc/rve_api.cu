@@ -43,18 +43,20 @@ static rve_solve_opts defaults(const rve_solve_opts* o) {
     return r;
 }
 
-static void default_tiles(int n, size_t vb, const rve_solve_opts& o, Tiles& t) {
+// Tile geometry of one realization.  Row kernels use 256 threads, n/8 per
+// row, so tU = 2048/n rows per block.  The stencil tile keeps tS + 2 padded
+// rows in shared memory: the largest power of two <= 8 whose tile fits
+// 110 KB (two blocks per SM; at least 1).  Column blocks use blockC
+// threads, n/8 per column.
+static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
+    const size_t seq = (size_t)seq_stride(n);
     t.tU = std::min(n, 2048 / n);
-    if (vb == 8) t.tS = (n >= 2048) ? 4 : 8;
-    else t.tS = (n >= 2048) ? 2 : (n >= 1024 ? 4 : 8);
-    int tc = (int)(65536 / (2 * (size_t)n * vb));
-    int c = 1;
-    while (c * 2 <= tc) c *= 2;
-    t.tC = std::max(c, vb == 8 ? 4 : 2);
+    t.tS = 8;
+    while (t.tS > 1 && ((size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4) > 112640)
+        t.tS >>= 1;
+    t.tC = std::min(n, blockC * 8 / n);
     if (o.tile_rows > 0) t.tS = o.tile_rows;
-    if (o.col_tile > 0) t.tC = o.col_tile;
     t.tS = std::min(t.tS, n);
-    t.tC = std::min(t.tC, n);
 }
 
 rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
@@ -83,6 +85,13 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.max_log2n = 5;
     p.smemS = p.smemU = p.smemC = 0;
     int64_t maxnb = 0;
+    int maxn = 0;
+    for (int b = 0; b < batch; ++b) {
+        const int64_t nn = (int64_t)r[b].L * r[b].m0;
+        if (nn > 0 && nn <= MAX_N) maxn = std::max(maxn, (int)nn);
+    }
+    p.blockC = (maxn > 512) ? 1024 : 512;
+    if (o.col_tile > 0) p.blockC = std::min(1024, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
@@ -95,8 +104,9 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             !(x.a_incl > 0.0))
             return RVE_EINVAL;
         Tiles t;
-        default_tiles(n, p.vbytes, o, t);
-        if (!pow2(t.tS) || !pow2(t.tC) || n % t.tS || n % t.tC) return RVE_EINVAL;
+        default_tiles(n, p.vbytes, p.blockC, o, t);
+        if (!pow2(t.tS) || !pow2(t.tC) || n % t.tS || n % t.tC || t.tC * (n / 8) > p.blockC)
+            return RVE_EINVAL;
         RDesc& d = p.desc[b];
         std::memset(&d, 0, sizeof(d));
         d.n = n;
@@ -124,13 +134,12 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         p.startA[b + 1] = p.startA[b] + (int32_t)(((int64_t)n * n) / 1024);
         maxnb = std::max<int64_t>(maxnb, ((int64_t)n * n) / 1024);
         const size_t vb = p.vbytes;
-        p.smemS = std::max(p.smemS, ((size_t)(t.tS + 2) * n + 2 * (size_t)t.tU * n) * vb);
-        p.smemU = std::max(p.smemU, 2 * (size_t)t.tU * n * vb);
-        p.smemC = std::max(p.smemC, 2 * (size_t)t.tC * n * vb);
+        const size_t seq = (size_t)seq_stride(n);
+        p.smemS = std::max(p.smemS, (size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4);
+        p.smemU = std::max(p.smemU, (size_t)t.tU * seq * vb);
+        p.smemC = std::max(p.smemC, (size_t)t.tC * seq * vb);
     }
-    // the plain path and the standalone preconditioner run FP64 transforms
-    // with the same row geometry: keep their shared memory within bounds too
-    if (p.smemS > MAX_SMEM || p.smemU * 3 / 2 > MAX_SMEM || p.smemC > MAX_SMEM) return RVE_EINVAL;
+    if (p.smemS > MAX_SMEM || p.smemU > MAX_SMEM || p.smemC > MAX_SMEM) return RVE_EINVAL;
     p.tilesS = p.startS[batch];
     p.tilesU = p.startU[batch];
     p.tilesC = p.startC[batch];

@@ -7,8 +7,9 @@
 //   inner product reaches FP64-class accuracy without FP64 arithmetic per
 //   element; partial sums leave the thread as double;
 // * deterministic warp / block reductions (fixed tree order);
-// * a shared-memory Stockham FFT of length n = 2^p (radix 8, then 4 or 2)
-//   used for the separable transforms of the preconditioner;
+// * a register-resident Stockham FFT of length n = 2^p (radix 8, then 4 or
+//   2) with one padded shared-memory buffer per sequence, used for the
+//   separable transforms of the preconditioner;
 // * the Hartley "pair" post-processing: the complex DFT Z of a + i b (a, b
 //   real) gives the Hartley transforms of a and b, because
 //   H_a(k) = Re A_k - Im A_k with A_k = (Z_k + conj Z_{-k}) / 2, and the
@@ -138,75 +139,89 @@ template <typename V> __device__ __forceinline__ void dft8(V* u) {
     u[3] = cadd(e3, t3); u[7] = csub(e3, t3);
 }
 
-// -------------------------------------------------------- Stockham FFT --
-// Forward DFT (unnormalised) of length n = 2^log2n on `nseq` sequences in
-// shared memory.  Element i of sequence q is A[q*seqstride + i*stride].
-// B is a second buffer of the same shape (ping-pong).  tw[m] =
-// exp(-2 pi i m / n), m < n.  SEQ_FAST picks the work-to-thread mapping:
-// consecutive threads on consecutive sequences (columns stored side by side)
-// or on consecutive butterflies (rows).  Called by all threads of the block
-// (tid in [0, nthr)); contains barriers.  Returns the buffer holding the
-// result (A or B).
-template <typename V, bool SEQ_FAST>
-__device__ V* smem_fft(V* A, V* B, int log2n, int stride, int seqstride, int nseq,
-                       const V* __restrict__ tw, int tid, int nthr) {
-    const int n = 1 << log2n;
-    int log2Ns = 0;
-    int rem = log2n;
-    while (rem > 0) {
-        const int lr = rem >= 3 ? 3 : rem;     // radix 8, then a 4 or 2 tail
-        const int log2units = log2n - lr;      // butterflies per sequence
-        const int units = 1 << log2units;
-        const int total = units * nseq;
+// ------------------------------------------------ register Stockham FFT --
+// Shared-memory index with one spare slot every 16 elements, so that the
+// stride-8 output pattern of a radix-8 stage spreads over the banks.
+__host__ __device__ __forceinline__ int pidx(int x) { return x + (x >> 4); }
+
+// Distance between consecutive sequences in shared memory: the padded length
+// rounded up to 4 (mod 16) elements, so that sequences side by side (columns,
+// or the short rows of small grids) start on different banks.
+__host__ __device__ __forceinline__ int seq_stride(int n) {
+    const int p = n + (n >> 4);
+    return p + ((4 - (p & 15)) & 15);
+}
+
+// Forward DFT (unnormalised) of one sequence of length n = 2^log2n >= 32,
+// cooperatively by T = n/8 threads (t in [0, T)).  On entry thread t holds
+// v[m] = x[t + m T], m = 0..7 -- exactly the inputs of its butterflies in
+// every Stockham stage (one radix-8 butterfly, or two radix-4, or four
+// radix-2), so each stage reads its inputs from registers or from `buf`,
+// writes its outputs to `buf` (one padded buffer of n elements, see pidx)
+// and a barrier separates stages.  On return buf holds X in natural order and
+// the block has synchronised.  Threads with active == false only take part
+// in the barriers.  tw[m] = exp(-2 pi i m/n).
+template <typename V>
+__device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
+                                        const V* __restrict__ tw, bool active) {
+    const int T = 1 << (log2n - 3);
+    int log2Ns = 0, rem = log2n;
+#pragma unroll 1
+    while (true) {
+        const int lr = rem >= 3 ? 3 : rem;
         const int Ns = 1 << log2Ns;
-        const int twshift = log2n - log2Ns - lr;   // m = r*k << twshift
-        for (int w = tid; w < total; w += nthr) {
-            int q, j;
-            if (SEQ_FAST) { q = w % nseq; j = w / nseq; }
-            else { q = w >> log2units; j = w & (units - 1); }
-            const V* in = A + (int64_t)q * seqstride;
-            V* out = B + (int64_t)q * seqstride;
-            const int k = j & (Ns - 1);
-            const int base = ((j - k) << lr) + k;
+        const int twshift = log2n - log2Ns - lr;
+        __syncthreads();   // earlier readers of buf are done
+        if (active) {
             if (lr == 3) {
-                V u[8];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) u[r] = in[(j + r * units) * stride];
+                const int k = t & (Ns - 1);
                 if (Ns > 1) {
 #pragma unroll
-                    for (int r = 1; r < 8; ++r) u[r] = cmul(u[r], tw[(r * k) << twshift]);
+                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[(r * k) << twshift]);
                 }
-                dft8(u);
+                dft8(v);
+                const int base = ((t - k) << 3) + k;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) out[(base + r * Ns) * stride] = u[r];
+                for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns)] = v[r];
             } else if (lr == 2) {
-                V u0 = in[j * stride], u1 = in[(j + units) * stride];
-                V u2 = in[(j + 2 * units) * stride], u3 = in[(j + 3 * units) * stride];
-                if (Ns > 1) {
-                    u1 = cmul(u1, tw[k << twshift]);
-                    u2 = cmul(u2, tw[(2 * k) << twshift]);
-                    u3 = cmul(u3, tw[(3 * k) << twshift]);
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int j = t + b * T, k = j & (Ns - 1);
+                    V a0 = v[b], a1 = v[b + 2], a2 = v[b + 4], a3 = v[b + 6];
+                    if (Ns > 1) {
+                        a1 = cmul(a1, tw[k << twshift]);
+                        a2 = cmul(a2, tw[(2 * k) << twshift]);
+                        a3 = cmul(a3, tw[(3 * k) << twshift]);
+                    }
+                    dft4(a0, a1, a2, a3);
+                    const int base = ((j - k) << 2) + k;
+                    buf[pidx(base)] = a0;
+                    buf[pidx(base + Ns)] = a1;
+                    buf[pidx(base + 2 * Ns)] = a2;
+                    buf[pidx(base + 3 * Ns)] = a3;
                 }
-                dft4(u0, u1, u2, u3);
-                out[base * stride] = u0;
-                out[(base + Ns) * stride] = u1;
-                out[(base + 2 * Ns) * stride] = u2;
-                out[(base + 3 * Ns) * stride] = u3;
             } else {
-                V u0 = in[j * stride], u1 = in[(j + units) * stride];
-                if (Ns > 1) u1 = cmul(u1, tw[k << twshift]);
-                dft2(u0, u1);
-                out[base * stride] = u0;
-                out[(base + Ns) * stride] = u1;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int j = t + b * T, k = j & (Ns - 1);
+                    V a0 = v[b], a1 = v[b + 4];
+                    if (Ns > 1) a1 = cmul(a1, tw[k << twshift]);
+                    dft2(a0, a1);
+                    const int base = ((j - k) << 1) + k;
+                    buf[pidx(base)] = a0;
+                    buf[pidx(base + Ns)] = a1;
+                }
             }
         }
         __syncthreads();
-        V* t = A; A = B; B = t;
         log2Ns += lr;
         rem -= lr;
+        if (rem == 0) break;
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = buf[pidx(t + m * T)];
+        }
     }
-    (void)n;
-    return A;
 }
 
 // Hartley pair from the DFT Z of (a + i b): returns (H_a(k), H_b(k)).

@@ -58,6 +58,7 @@ struct Plan {
     std::vector<int32_t> startS, startU, startC, startA;
     int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0;
     size_t smemS = 0, smemU = 0, smemC = 0;
+    int blockC = 512;               // threads of a column-transform block
     // workspace offsets (bytes)
     size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
     size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0;
@@ -79,6 +80,11 @@ cudaError_t launch_rhs(const Plan& p, void* ws, const uint32_t* mask, const doub
                        double* f, cudaStream_t s);
 cudaError_t launch_stiffness(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                              int scheme, int precision, const void* x, void* y, cudaStream_t s);
+// Row, column(+scale), row transform passes for realizations
+// [b_first, b_first + b_count): y = B^{-1} x, tmp a scratch vector.
+template <typename V>
+cudaError_t precond_passes(const Plan& p, void* ws, double delta, const V* x, V* y, V* tmp,
+                           int b_first, int b_count, cudaStream_t s);
 cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision, const void* x,
                            void* y, cudaStream_t s);
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,

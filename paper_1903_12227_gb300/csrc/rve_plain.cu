@@ -211,70 +211,6 @@ __global__ void k_pl_report(const PlainScal* sc, rve_solve_info* info, int b) {
     info[b] = r;
 }
 
-// Preconditioner passes of one realization (tiles of realization b only).
-template <typename V>
-__global__ void __launch_bounds__(256) k_pl_row(const RDesc* desc, int b, Tables tb,
-                                                const V* __restrict__ in, V* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RDesc d = desc[b];
-    const int n = d.n, G = d.tU;
-    const int row0 = blockIdx.x * G;
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + G * n;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int idx = tid; idx < G * n; idx += nthr)
-        F0[idx] = in[d.node_off + ((int64_t)row0 << d.log2n) + idx];
-    __syncthreads();
-    V* res = smem_fft<V, false>(F0, F1, d.log2n, 1, n, G, twiddles<V>(tb, n), tid, nthr);
-    for (int idx = tid; idx < G * n; idx += nthr) {
-        const int q = idx >> d.log2n, k = idx & (n - 1);
-        const V* z = res + q * n;
-        out[d.node_off + ((int64_t)row0 << d.log2n) + idx] = hartley_pair(z[k], z[(n - k) & (n - 1)]);
-    }
-}
-
-template <typename V>
-__global__ void __launch_bounds__(256) k_pl_col(const RDesc* desc, int b, Tables tb, double delta,
-                                                V* __restrict__ T) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
-    const RDesc d = desc[b];
-    const int C = d.tC;
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + d.n * C;
-    // column pass, scale, column pass (the transform-domain r.z is not used
-    // here: the plain path forms r.z with its own dot kernel)
-    const int c0 = blockIdx.x * C;
-    const int n = d.n, tid = threadIdx.x, nthr = blockDim.x;
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int i = idx / C, cc = idx - i * C;
-        F0[idx] = T[d.node_off + ((int64_t)i << d.log2n) + c0 + cc];
-    }
-    __syncthreads();
-    V* res = smem_fft<V, true>(F0, F1, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
-    V* oth = (res == F0) ? F1 : F0;
-    const double n2 = (double)n * (double)n;
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int k1 = idx / C, cc = idx - k1 * C;
-        const int k2 = c0 + cc;
-        const V h = hartley_pair(res[idx], res[((n - k1) & (n - 1)) * C + cc]);
-        const double sig = n2 * (d.c0 * (tb.lap[n + k1] + tb.lap[n + k2]) + delta);
-        const double inv = (k1 == 0 && k2 == 0 && delta == 0.0) ? 0.0 : 1.0 / sig;
-        V hs;
-        hs.x = h.x * inv;
-        hs.y = h.y * inv;
-        oth[idx] = hs;
-    }
-    __syncthreads();
-    V* res2 = smem_fft<V, true>(oth, res, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int k1 = idx / C, cc = idx - k1 * C;
-        T[d.node_off + ((int64_t)k1 << d.log2n) + c0 + cc] =
-            hartley_pair(res2[idx], res2[((n - k1) & (n - 1)) * C + cc]);
-    }
-    (void)red;
-}
-
 template <int SCHEME>
 static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* u,
                             const rve_solve_opts& o, rve_solve_info* info, cudaStream_t s) {
@@ -292,13 +228,8 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
     double* part = reinterpret_cast<double*>(w + p.o_partS);
     PlainScal* sc = reinterpret_cast<PlainScal*>(w + p.o_state);
     const int nb = (int)(((int64_t)d.n * d.n) / PL_NODES);
-    const int rowsU = d.n / d.tU, colsC = d.n / d.tC;
-    const size_t smem_row = (size_t)2 * d.tU * d.n * sizeof(double2);
-    const size_t smem_col = (size_t)2 * d.tC * d.n * sizeof(double2);
     auto precond = [&](const double2* in, double2* out) {
-        k_pl_row<double2><<<rowsU, 256, smem_row, s>>>(desc, b, tb, in, t);
-        k_pl_col<double2><<<colsC, 256, smem_col, s>>>(desc, b, tb, o.delta, t);
-        k_pl_row<double2><<<rowsU, 256, smem_row, s>>>(desc, b, tb, t, out);
+        precond_passes<double2>(p, w, o.delta, in, out, t, b, 1, s);
     };
     k_pl_init<<<nb, PL_THREADS, 0, s>>>(desc, b, cs, u, r, part);
     k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_FNORM, o.tol, o.max_iter);
@@ -319,7 +250,7 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
         k_pl_dot<<<nb, PL_THREADS, 0, s>>>(desc, b, r, z, part);
         k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_BETA, o.tol, o.max_iter);
         k_pl_xpby<<<nb, PL_THREADS, 0, s>>>(desc, b, sc, z, pp);
-        note_launch(13);
+        note_launch(10);
         if ((it + 1) % every == 0 || it == 0) {
             if (cudaMemcpyAsync(&hsc, sc, sizeof(PlainScal), cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess ||
@@ -341,13 +272,6 @@ rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const 
     rve_status st = upload_plan(p, ws, s);
     if (st != RVE_OK) return st;
     char* w = static_cast<char*>(ws);
-    // the plan is an FP64 plan (vbytes 16): smemU / smemC are the largest
-    // row / column tiles of the batch
-    if (cudaFuncSetAttribute(k_pl_row<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p.smemU) != cudaSuccess ||
-        cudaFuncSetAttribute(k_pl_col<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p.smemC) != cudaSuccess)
-        return RVE_ECUDA;
     CoefSrc cs{mask, coef};
     double2* uu = reinterpret_cast<double2*>(u);
     for (int b = 0; b < p.batch; ++b) {

@@ -78,30 +78,7 @@ __global__ void k_tables(double2* tw64, float2* tw32, double* lap, int total) {
     lap[idx] = 4.0 * s1 * s1;
 }
 
-// ---------------------------------------------------- row Hartley helper --
-// Loads `g` rows (global row indices row0 .. row0+g-1, wrapped) of `in` into
-// F0, transforms them along the row and writes the Hartley pair of each row
-// into out_smem (row-major, n per row).  256 threads.
-template <typename V>
-__device__ void rows_hartley_to_smem(const V* __restrict__ in, const RDesc& d, int row0, int g,
-                                     V* F0, V* F1, V* out_smem, const Tables& tb) {
-    const int n = d.n, tid = threadIdx.x, nthr = blockDim.x;
-    for (int idx = tid; idx < g * n; idx += nthr) {
-        const int q = idx >> d.log2n, j = idx & (n - 1);
-        const int row = (row0 + q) & (n - 1);
-        F0[idx] = in[d.node_off + ((int64_t)row << d.log2n) + j];
-    }
-    __syncthreads();
-    V* res = smem_fft<V, false>(F0, F1, d.log2n, 1, n, g, twiddles<V>(tb, n), tid, nthr);
-    for (int idx = tid; idx < g * n; idx += nthr) {
-        const int q = idx >> d.log2n, k = idx & (n - 1);
-        const V* z = res + q * n;
-        out_smem[idx] = hartley_pair(z[k], z[(n - k) & (n - 1)]);
-    }
-    __syncthreads();
-}
-
-// ----------------------------------------------------------- S kernel --
+// ---------------------------------------------------------- row helpers --
 template <typename V>
 __device__ __forceinline__ V axpy2(V y, double ax, double ay, V x) {
     typedef typename ScalarOf<V>::T T;
@@ -111,6 +88,24 @@ __device__ __forceinline__ V axpy2(V y, double ax, double ay, V x) {
     return r;
 }
 
+template <typename V>
+__device__ __forceinline__ int64_t node_of(const RDesc& d, int row, int col) {
+    return d.node_off + ((int64_t)row << d.log2n) + col;
+}
+
+// Thread layout of the row kernels: 256 threads, T = n/8 per row, so
+// 256/T rows per group; qq = row within the group, t = thread within row.
+struct RowLayout {
+    int T, qq, t, G;
+    __device__ __forceinline__ RowLayout(const RDesc& d) {
+        T = d.n >> 3;
+        G = blockDim.x / T;
+        qq = threadIdx.x / T;
+        t = threadIdx.x - qq * T;
+    }
+};
+
+// ----------------------------------------------------------- S kernel --
 template <typename V>
 __device__ __forceinline__ double2 refine_w(const Ctx& c, const RDesc& d, const RState& s, int i,
                                             int j, const V* P) {
@@ -122,8 +117,23 @@ __device__ __forceinline__ double2 refine_w(const Ctx& c, const RDesc& d, const 
                         uu.y + s.s[1] * (xx.y + s.alpha[1] * pp.y));
 }
 
+// Cell value from the shared-memory mask rows of the tile (cell rows
+// r0-1 .. r0+TR-1 stored at mrow 0 .. TR) or from the coefficient array.
+struct TileCoef {
+    const uint32_t* mrows;   // shared, (TR+1) x (n/32) words, or null
+    int wpr;                 // words per row
+    __device__ __forceinline__ double cell(const CoefSrc& cs, const RDesc& d, int mrow, int c1,
+                                           int c2) const {
+        if (mrows) {
+            const uint32_t w = mrows[mrow * wpr + (c2 >> 5)];
+            return ((w >> (c2 & 31)) & 1u) ? d.a_incl : d.a_matrix;
+        }
+        return cs.cell(d, c1 & (d.n - 1), c2);
+    }
+};
+
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256) k_fused_S(const Ctx c) {
+__global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[8];
     const int tile = blockIdx.x;
@@ -138,11 +148,10 @@ __global__ void __launch_bounds__(256) k_fused_S(const Ctx c) {
     V* Pnew = static_cast<V*>(s.parity ? c.P0 : c.P1);
     V* X = static_cast<V*>(c.X);
     V* Q = static_cast<V*>(c.Q);
-    DotAcc<double> a64x, a64y;   // REFINE: exact FP64 |r64|^2
     typedef typename ScalarOf<V>::T T;
-    DotAcc<T> ax, ay;            // ITER: p.q
 
     if (phase == PH_REFINE) {
+        DotAcc<double> a64x, a64y;   // exact FP64 |r64|^2
         for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
             const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
             const Cells4 a = cells_at(c.cs, d, i, j);
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(256) k_fused_S(const Ctx c) {
                 refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
                 refine_w(c, d, s, i + 1, j + 1, Pold));
             const double2 r64 = make_double2(f.x - Aw.x, f.y - Aw.y);
-            Q[d.node_off + ((int64_t)i << d.log2n) + j] = from_d2<V>(r64);
+            Q[node_of<V>(d, i, j)] = from_d2<V>(r64);
             a64x.add(r64.x, r64.x);
             a64y.add(r64.y, r64.y);
         }
@@ -168,43 +177,77 @@ __global__ void __launch_bounds__(256) k_fused_S(const Ctx c) {
     }
 
     // ---- ITER ----
-    const int G = d.tU;                       // rows per transform group
-    V* Pt = reinterpret_cast<V*>(smem_raw);  // (TR+2) x n: z, then p_new
-    V* F0 = Pt + (TR + 2) * n;
-    V* F1 = F0 + G * n;
-    for (int g0 = 0; g0 < TR + 2; g0 += G) {
-        const int g = min(G, TR + 2 - g0);
-        rows_hartley_to_smem<V>(static_cast<const V*>(c.T), d, r0 - 1 + g0, g, F0, F1,
-                                Pt + g0 * n, c.tb);
+    const int SEQ = seq_stride(n);
+    V* Pt = reinterpret_cast<V*>(smem_raw);            // (TR+2) padded rows
+    uint32_t* mrows = reinterpret_cast<uint32_t*>(Pt + (TR + 2) * SEQ);
+    const int wpr = n >> 5;
+    TileCoef tc{c.cs.coef ? nullptr : mrows, wpr};
+    if (!c.cs.coef) {
+        for (int w = threadIdx.x; w < (TR + 1) * wpr; w += blockDim.x) {
+            const int mr = w / wpr, col = w - mr * wpr;
+            const int row = (r0 - 1 + mr) & (n - 1);
+            mrows[w] = __ldg(c.cs.mask + d.word_off + (((int64_t)row << d.log2n) >> 5) + col);
+        }
     }
+    const RowLayout L(d);
     const double bx = s.beta[0], by = s.beta[1];
     const double alx = s.alpha[0], aly = s.alpha[1];
-    for (int idx = threadIdx.x; idx < (TR + 2) * n; idx += blockDim.x) {
-        const int q = idx >> d.log2n, j = idx & (n - 1);
+    const V* Tin = static_cast<const V*>(c.T);
+    const V* tw = twiddles<V>(c.tb, n);
+    for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
+        const int q = g0 + L.qq;
+        const bool active = q < TR + 2;
         const int row = (r0 - 1 + q) & (n - 1);
-        const int64_t node = d.node_off + ((int64_t)row << d.log2n) + j;
-        const V po = Pold[node];
-        const V pn = axpy2(Pt[idx], bx, by, po);
-        Pt[idx] = pn;
-        if (q >= 1 && q <= TR) {
-            Pnew[node] = pn;
-            X[node] = axpy2(X[node], alx, aly, po);
+        V v[8];
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = Tin[node_of<V>(d, row, L.t + m * L.T)];
+        }
+        V* buf = Pt + (active ? q : 0) * SEQ;
+        fft_reg(v, buf, d.log2n, L.t, tw, active);
+        V pn[8];
+        if (active) {
+            const bool own = (q >= 1 && q <= TR);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int k = L.t + m * L.T;
+                const V z = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
+                const int64_t node = node_of<V>(d, row, k);
+                const V po = Pold[node];
+                pn[m] = axpy2(z, bx, by, po);
+                if (own) {
+                    Pnew[node] = pn[m];
+                    X[node] = axpy2(X[node], alx, aly, po);
+                }
+            }
+        }
+        __syncthreads();   // partner reads of this group are done
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) buf[pidx(L.t + m * L.T)] = pn[m];
         }
     }
     __syncthreads();
+    DotAcc<T> ax, ay;   // p.q
     for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
         const int q = idx >> d.log2n, j = idx & (n - 1);
         const int i = r0 + q;
         const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-        const V* up = Pt + q * n;          // row i-1
-        const V* mid = up + n;             // row i
-        const V* dn = mid + n;             // row i+1
-        const Cells4 a = cells_at(c.cs, d, i, j);
-        const V qv = stencil_apply<SCHEME, V>(a, up[jm], up[j], up[jp], mid[jm], mid[j], mid[jp],
-                                              dn[jm], dn[j], dn[jp]);
-        Q[d.node_off + ((int64_t)i << d.log2n) + j] = qv;
-        ax.add(mid[j].x, qv.x);
-        ay.add(mid[j].y, qv.y);
+        const V* up = Pt + q * SEQ;         // row i-1
+        const V* mid = up + SEQ;            // row i
+        const V* dn = mid + SEQ;            // row i+1
+        Cells4 a;
+        a.mm = tc.cell(c.cs, d, q, i - 1, jm);
+        a.m0 = tc.cell(c.cs, d, q, i - 1, j);
+        a.z0m = tc.cell(c.cs, d, q + 1, i, jm);
+        a.z00 = tc.cell(c.cs, d, q + 1, i, j);
+        const V pc = mid[pidx(j)];
+        const V qv = stencil_apply<SCHEME, V>(a, up[pidx(jm)], up[pidx(j)], up[pidx(jp)],
+                                              mid[pidx(jm)], pc, mid[pidx(jp)], dn[pidx(jm)],
+                                              dn[pidx(j)], dn[pidx(jp)]);
+        Q[node_of<V>(d, i, j)] = qv;
+        ax.add(pc.x, qv.x);
+        ay.add(pc.y, qv.y);
     }
     const double sx = block_sum(ax.value(), red);
     const double sy = block_sum(ay.value(), red);
@@ -226,6 +269,23 @@ __device__ __forceinline__ void reduce_pair(const double* part, int t0, int nt, 
     __syncthreads();
 }
 
+// Row Hartley pass of the rows held in registers (v[m] = row value at
+// t + m T) into `out` (global), through the row's shared buffer.
+template <typename V>
+__device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d, int row,
+                                                  const RowLayout& L, const V* tw, bool active,
+                                                  V* __restrict__ out) {
+    fft_reg(v, buf, d.log2n, L.t, tw, active);
+    if (active) {
+        const int n = d.n;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int k = L.t + m * L.T;
+            out[node_of<V>(d, row, k)] = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
+        }
+    }
+}
+
 template <typename V>
 __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -237,26 +297,32 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
     const int phase = s.phase;
     if (phase == PH_DONE) return;
     const RDesc d = c.desc[b];
-    const int n = d.n, G = d.tU;
-    const int row0 = (blk - c.startU[b]) * G;
+    const int n = d.n;
+    const RowLayout L(d);
+    const int G = d.tU;
+    const int row = (blk - c.startU[b]) * G + L.qq;
+    const bool active = L.qq < G;
     typedef typename ScalarOf<V>::T T;
     V* R = static_cast<V*>(c.R);
     V* X = static_cast<V*>(c.X);
-    const V* Q = static_cast<const V*>(c.Q);
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + G * n;
+    const V* Qv = static_cast<const V*>(c.Q);
+    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(n);
     reduce_pair(c.partS, c.startS[b], c.startS[b + 1] - c.startS[b], sc);
     DotAcc<T> ax, ay;
+    V v[8];
     if (phase == PH_ITER) {
         const double alx = s.active[0] ? s.rho[0] / sc[0] : 0.0;
         const double aly = s.active[1] ? s.rho[1] / sc[1] : 0.0;
-        for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
-            const int64_t node = d.node_off + ((int64_t)row0 << d.log2n) + idx;
-            const V rr = axpy2(R[node], -alx, -aly, Q[node]);
-            R[node] = rr;
-            F0[idx] = rr;
-            ax.add(rr.x, rr.x);
-            ay.add(rr.y, rr.y);
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
+                const V rr = axpy2(R[node], -alx, -aly, Qv[node]);
+                R[node] = rr;
+                v[m] = rr;
+                ax.add(rr.x, rr.x);
+                ay.add(rr.y, rr.y);
+            }
         }
     } else {   // REFINE
         const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
@@ -265,21 +331,24 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
         const bool cx = first ? (nx == 0.0) : (nx <= c.tol * s.fnorm[0]);
         const bool cy = first ? (ny == 0.0) : (ny <= c.tol * s.fnorm[1]);
         const double ix = cx ? 0.0 : 1.0 / nx, iy = cy ? 0.0 : 1.0 / ny;
-        for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
-            const int64_t node = d.node_off + ((int64_t)row0 << d.log2n) + idx;
-            const double2 xx = to_d2(X[node]);
-            const double2 pp = to_d2(Pold[node]);
-            double2 uu = c.u[node];
-            uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
-            uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
-            c.u[node] = uu;
-            X[node] = from_d2<V>(make_double2(0.0, 0.0));
-            const double2 q = to_d2(Q[node]);
-            const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
-            R[node] = rr;
-            F0[idx] = rr;
-            ax.add(rr.x, rr.x);
-            ay.add(rr.y, rr.y);
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
+                const double2 xx = to_d2(X[node]);
+                const double2 pp = to_d2(Pold[node]);
+                double2 uu = c.u[node];
+                uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
+                uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
+                c.u[node] = uu;
+                X[node] = from_d2<V>(make_double2(0.0, 0.0));
+                const double2 q = to_d2(Qv[node]);
+                const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
+                R[node] = rr;
+                v[m] = rr;
+                ax.add(rr.x, rr.x);
+                ay.add(rr.y, rr.y);
+            }
         }
     }
     const double sx = block_sum(ax.value(), red);
@@ -288,79 +357,78 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
         c.partU[2 * (int64_t)blk] = sx;
         c.partU[2 * (int64_t)blk + 1] = sy;
     }
-    __syncthreads();
-    // row Hartley of r -> t
-    V* res = smem_fft<V, false>(F0, F1, d.log2n, 1, n, G, twiddles<V>(c.tb, n), threadIdx.x,
-                                blockDim.x);
-    V* Tv = static_cast<V*>(c.T);
-    for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x) {
-        const int q = idx >> d.log2n, k = idx & (n - 1);
-        const V* z = res + q * n;
-        Tv[d.node_off + ((int64_t)(row0 + q) << d.log2n) + k] = hartley_pair(z[k], z[(n - k) & (n - 1)]);
-    }
+    row_hartley_store(v, buf, d, row, L, twiddles<V>(c.tb, n), active, static_cast<V*>(c.T));
 }
 
 // ----------------------------------------------------------- C kernel --
 // Column Hartley pass, diagonal scale 1/(n^2 sigma), partial rho, column
-// Hartley pass; in place on t.  `rho_part` may be null (plain path).
+// Hartley pass; in place on t.  Block of C*T threads (T = n/8), thread
+// (t, c) with c fastest so that global accesses are row segments of C
+// elements.  `rho_part` may be null.
 template <typename V>
-__device__ void col_transform_tile(V* T, const RDesc& d, int c0, int C, V* F0, V* F1,
+__device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
                                    const Tables& tb, double delta, double* red,
                                    double* rho_part) {
     typedef typename ScalarOf<V>::T Ts;
-    const int n = d.n, tid = threadIdx.x, nthr = blockDim.x;
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int i = idx / C, cc = idx - i * C;
-        F0[idx] = T[d.node_off + ((int64_t)i << d.log2n) + c0 + cc];
+    const int n = d.n, C = d.tC, T = n >> 3;
+    const int tid = threadIdx.x;
+    const int t = tid / C, cc = tid - (tid / C) * C;
+    const bool active = t < T;
+    const int SEQ = seq_stride(n);
+    V* buf = smem + (active ? cc : 0) * SEQ;
+    const V* tw = twiddles<V>(tb, n);
+    V v[8];
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
     }
-    __syncthreads();
-    V* res = smem_fft<V, true>(F0, F1, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
-    V* oth = (res == F0) ? F1 : F0;
+    fft_reg(v, buf, d.log2n, t, tw, active);
     const double n2 = (double)n * (double)n;
     const Ts n2c0 = (Ts)(n2 * d.c0), n2d = (Ts)(n2 * delta);
+    const int k2 = c0 + cc;
     DotAcc<Ts> ax, ay;
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int k1 = idx / C, cc = idx - k1 * C;
-        const int k2 = c0 + cc;
-        const V h = hartley_pair(res[idx], res[((n - k1) & (n - 1)) * C + cc]);
-        const Ts sig = n2c0 * ((Ts)tb.lap[n + k1] + (Ts)tb.lap[n + k2]) + n2d;
-        const Ts inv = (k1 == 0 && k2 == 0 && delta == 0.0) ? (Ts)0 : (Ts)1 / sig;
-        V hs;
-        hs.x = h.x * inv;
-        hs.y = h.y * inv;
-        ax.add(h.x, hs.x);
-        ay.add(h.y, hs.y);
-        oth[idx] = hs;
+    if (active) {
+        const Ts lap2 = (Ts)tb.lap[n + k2];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int k1 = t + m * T;
+            const V h = hartley_pair(buf[pidx(k1)], buf[pidx((n - k1) & (n - 1))]);
+            const Ts sig = n2c0 * ((Ts)tb.lap[n + k1] + lap2) + n2d;
+            const Ts inv = (k1 == 0 && k2 == 0 && delta == 0.0) ? (Ts)0 : (Ts)1 / sig;
+            V hs;
+            hs.x = h.x * inv;
+            hs.y = h.y * inv;
+            ax.add(h.x, hs.x);
+            ay.add(h.y, hs.y);
+            v[m] = hs;
+        }
+    }
+    fft_reg(v, buf, d.log2n, t, tw, active);   // its first barrier orders the reads above
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int k1 = t + m * T;
+            Tg[node_of<V>(d, k1, c0 + cc)] = hartley_pair(buf[pidx(k1)], buf[pidx((n - k1) & (n - 1))]);
+        }
     }
     if (rho_part) {
         const double sx = block_sum(ax.value(), red);
         const double sy = block_sum(ay.value(), red);
         if (tid == 0) { rho_part[0] = sx; rho_part[1] = sy; }
-    } else {
-        __syncthreads();
-    }
-    // second column pass: transform `oth` (its partner buffer is `res`)
-    V* res2 = smem_fft<V, true>(oth, res, d.log2n, C, 1, C, twiddles<V>(tb, n), tid, nthr);
-    for (int idx = tid; idx < n * C; idx += nthr) {
-        const int k1 = idx / C, cc = idx - k1 * C;
-        T[d.node_off + ((int64_t)k1 << d.log2n) + c0 + cc] =
-            hartley_pair(res2[idx], res2[((n - k1) & (n - 1)) * C + cc]);
     }
 }
 
 template <typename V>
-__global__ void __launch_bounds__(256) k_fused_C(const Ctx c) {
+__global__ void __launch_bounds__(1024) k_fused_C(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
+    __shared__ double red[32];
     const int blk = blockIdx.x;
     const int b = find_real(c.startC, c.batch, blk);
     if (c.st[b].phase == PH_DONE) return;
     const RDesc d = c.desc[b];
-    const int C = d.tC;
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + d.n * C;
-    col_transform_tile<V>(static_cast<V*>(c.T), d, (blk - c.startC[b]) * C, C, F0, F1, c.tb,
-                          c.delta, red, c.partC + 2 * (int64_t)blk);
+    col_transform_tile<V>(static_cast<V*>(c.T), d, (blk - c.startC[b]) * d.tC,
+                          reinterpret_cast<V*>(smem_raw), c.tb, c.delta, red,
+                          c.partC + 2 * (int64_t)blk);
 }
 
 // ------------------------------------------------------ control kernel --
@@ -596,7 +664,7 @@ static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaE
     if (ev) cudaEventRecord(ev[1], s);
     k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
     if (ev) cudaEventRecord(ev[2], s);
-    k_fused_C<V><<<p.tilesC, 256, p.smemC, s>>>(c);
+    k_fused_C<V><<<p.tilesC, p.blockC, p.smemC, s>>>(c);
     if (ev) cudaEventRecord(ev[3], s);
     k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
     if (ev) cudaEventRecord(ev[4], s);
@@ -672,43 +740,48 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
 }
 
 // --------------------------------------------------- preconditioner apply --
+// Standalone transform passes (rve_apply_precond and the plain path): row
+// Hartley of `in` into `out`, and the column pair with the scale in place.
+// Tiles tile0 .. tile0 + gridDim.x - 1 of the batch's row / column tiling.
 template <typename V>
 __global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ desc,
                                                      const int32_t* __restrict__ startU, int batch,
-                                                     Tables tb, const V* __restrict__ in,
+                                                     int tile0, Tables tb, const V* __restrict__ in,
                                                      V* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int blk = blockIdx.x;
+    const int blk = blockIdx.x + tile0;
     const int b = find_real(startU, batch, blk);
     const RDesc d = desc[b];
-    const int n = d.n, G = d.tU;
-    const int row0 = (blk - startU[b]) * G;
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + G * n;
-    V* H = F1 + G * n;
-    rows_hartley_to_smem<V>(in, d, row0, G, F0, F1, H, tb);
-    for (int idx = threadIdx.x; idx < G * n; idx += blockDim.x)
-        out[d.node_off + ((int64_t)row0 << d.log2n) + idx] = H[idx];
+    const RowLayout L(d);
+    const int G = d.tU;
+    const int row = (blk - startU[b]) * G + L.qq;
+    const bool active = L.qq < G;
+    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(d.n);
+    V v[8];
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = in[node_of<V>(d, row, L.t + m * L.T)];
+    }
+    row_hartley_store(v, buf, d, row, L, twiddles<V>(tb, d.n), active, out);
 }
 
 template <typename V>
-__global__ void __launch_bounds__(256) k_col_hartley(const RDesc* __restrict__ desc,
-                                                     const int32_t* __restrict__ startC, int batch,
-                                                     Tables tb, double delta, V* __restrict__ T) {
+__global__ void __launch_bounds__(1024) k_col_hartley(const RDesc* __restrict__ desc,
+                                                      const int32_t* __restrict__ startC, int batch,
+                                                      int tile0, Tables tb, double delta,
+                                                      V* __restrict__ T) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
-    const int blk = blockIdx.x;
+    __shared__ double red[32];
+    const int blk = blockIdx.x + tile0;
     const int b = find_real(startC, batch, blk);
     const RDesc d = desc[b];
-    const int C = d.tC;
-    V* F0 = reinterpret_cast<V*>(smem_raw);
-    V* F1 = F0 + d.n * C;
-    col_transform_tile<V>(T, d, (blk - startC[b]) * C, C, F0, F1, tb, delta, red, nullptr);
+    col_transform_tile<V>(T, d, (blk - startC[b]) * d.tC, reinterpret_cast<V*>(smem_raw), tb,
+                          delta, red, nullptr);
 }
 
 template <typename V>
-static cudaError_t precond_apply_t(const Plan& p, void* ws, double delta, const V* x, V* y,
-                                   V* tmp, cudaStream_t s) {
+cudaError_t precond_passes(const Plan& p, void* ws, double delta, const V* x, V* y, V* tmp,
+                           int b_first, int b_count, cudaStream_t s) {
     char* w = static_cast<char*>(ws);
     const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
     const int32_t* startU = reinterpret_cast<const int32_t*>(w + p.o_startU);
@@ -717,30 +790,37 @@ static cudaError_t precond_apply_t(const Plan& p, void* ws, double delta, const 
     tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
     tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
     tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
-    const size_t smem_row = p.smemU / 2 * 3;   // F0, F1 and the output rows
     cudaError_t e = cudaFuncSetAttribute(k_row_hartley<V>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smemU);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_col_hartley<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)p.smemC);
     if (e != cudaSuccess) return e;
-    k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, x, tmp);
-    k_col_hartley<V><<<p.tilesC, 256, p.smemC, s>>>(desc, startC, p.batch, tb, delta, tmp);
-    k_row_hartley<V><<<p.tilesU, 256, smem_row, s>>>(desc, startU, p.batch, tb, tmp, y);
+    const int u0 = p.startU[b_first], un = p.startU[b_first + b_count] - u0;
+    const int c0 = p.startC[b_first], cn = p.startC[b_first + b_count] - c0;
+    k_row_hartley<V><<<un, 256, p.smemU, s>>>(desc, startU, p.batch, u0, tb, x, tmp);
+    k_col_hartley<V><<<cn, p.blockC, p.smemC, s>>>(desc, startC, p.batch, c0, tb, delta, tmp);
+    k_row_hartley<V><<<un, 256, p.smemU, s>>>(desc, startU, p.batch, u0, tb, tmp, y);
     note_launch(3);
     return cudaGetLastError();
 }
+
+template cudaError_t precond_passes<double2>(const Plan&, void*, double, const double2*, double2*,
+                                             double2*, int, int, cudaStream_t);
+template cudaError_t precond_passes<float2>(const Plan&, void*, double, const float2*, float2*,
+                                            float2*, int, int, cudaStream_t);
 
 cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision, const void* x,
                            void* y, cudaStream_t s) {
     if (upload_plan(p, ws, s) != RVE_OK) return cudaErrorUnknown;
     char* w = static_cast<char*>(ws);
     if (precision == RVE_FP64)
-        return precond_apply_t<double2>(p, ws, delta, static_cast<const double2*>(x),
-                                        static_cast<double2*>(y),
-                                        reinterpret_cast<double2*>(w + p.o_T), s);
-    return precond_apply_t<float2>(p, ws, delta, static_cast<const float2*>(x),
-                                   static_cast<float2*>(y), reinterpret_cast<float2*>(w + p.o_T), s);
+        return precond_passes<double2>(p, ws, delta, static_cast<const double2*>(x),
+                                       static_cast<double2*>(y),
+                                       reinterpret_cast<double2*>(w + p.o_T), 0, p.batch, s);
+    return precond_passes<float2>(p, ws, delta, static_cast<const float2*>(x),
+                                  static_cast<float2*>(y), reinterpret_cast<float2*>(w + p.o_T), 0,
+                                  p.batch, s);
 }
 
 }  // namespace rve
