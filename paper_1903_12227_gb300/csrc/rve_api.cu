@@ -160,6 +160,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_tw64 = take(sizeof(double2) * tab);
     p.o_tw32 = take(sizeof(float2) * tab);
     p.o_lap = take(sizeof(double) * tab);
+    p.o_lap32 = take(sizeof(float) * tab);
     p.o_state = take(sizeof(RState) * batch);
     p.o_partS = take(sizeof(double) * 2 * (size_t)std::max<int64_t>(p.tilesS, maxnb));
     p.o_partU = take(sizeof(double) * 2 * (size_t)p.tilesU);

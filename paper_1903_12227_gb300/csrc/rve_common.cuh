@@ -70,8 +70,12 @@ struct CoefSrc {
     }
 };
 
-// The four cells around node (i,j) with periodic wrap.
-struct Cells4 { double mm, m0, z0m, z00; };
+// The four cells around node (i,j) with periodic wrap, in arithmetic type T.
+template <typename T> struct CellsT { T mm, m0, z0m, z00; };
+typedef CellsT<double> Cells4;
+template <typename T> __device__ __forceinline__ CellsT<T> cells_as(const Cells4& a) {
+    return CellsT<T>{(T)a.mm, (T)a.m0, (T)a.z0m, (T)a.z00};
+}
 
 __device__ __forceinline__ Cells4 cells_at(const CoefSrc& cs, const RDesc& d, int i, int j) {
     const int im = (i - 1) & (d.n - 1), jm = (j - 1) & (d.n - 1);
@@ -94,11 +98,11 @@ template <> struct Weights<1> {   // trapezoid-lumped (paper's I-hat)
 // q(i,j) = (A p)(i,j) for both correctors (V = float2 or double2), with the
 // nine neighbours supplied by the caller.  T is the arithmetic type.
 template <int SCHEME, typename V>
-__device__ __forceinline__ V stencil_apply(const Cells4& a, V pmm, V pm0, V pmp, V p0m, V p00,
-                                           V p0p, V ppm, V pp0, V ppp) {
+__device__ __forceinline__ V stencil_apply(const CellsT<typename ScalarOf<V>::T>& a, V pmm, V pm0,
+                                           V pmp, V p0m, V p00, V p0p, V ppm, V pp0, V ppp) {
     typedef typename ScalarOf<V>::T T;
     const T w0 = (T)Weights<SCHEME>::w0, w1 = (T)Weights<SCHEME>::w1;
-    const T amm = (T)a.mm, am0 = (T)a.m0, a0m = (T)a.z0m, a00 = (T)a.z00;
+    const T amm = a.mm, am0 = a.m0, a0m = a.z0m, a00 = a.z00;
     const T cc = (T)2 * w0 * ((amm + am0) + (a0m + a00));
     const T e = w1 - w0;
     const T en = e * (amm + am0);   // edge to (i-1, j)
@@ -136,7 +140,11 @@ struct Tables {
     const double2* __restrict__ tw64;   // exp(-2 pi i m/n)
     const float2* __restrict__ tw32;
     const double* __restrict__ lap;     // 4 sin^2(pi m/n)
+    const float* __restrict__ lap32;
 };
+template <typename T> __device__ __forceinline__ const T* lap_table(const Tables& tb, int n);
+template <> __device__ __forceinline__ const double* lap_table<double>(const Tables& tb, int n) { return tb.lap + n; }
+template <> __device__ __forceinline__ const float* lap_table<float>(const Tables& tb, int n) { return tb.lap32 + n; }
 template <typename V> __device__ __forceinline__ const V* twiddles(const Tables& tb, int n);
 template <> __device__ __forceinline__ const double2* twiddles<double2>(const Tables& tb, int n) { return tb.tw64 + n; }
 template <> __device__ __forceinline__ const float2* twiddles<float2>(const Tables& tb, int n) { return tb.tw32 + n; }

@@ -85,7 +85,7 @@ __global__ void k_stiffness(const __grid_constant__ DescChunk ch, CoefSrc cs,
     const RDesc& d = ch.d[b];
     const int64_t node = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
     const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
-    const Cells4 a = cells_at(cs, d, i, j);
+    const CellsT<typename ScalarOf<V>::T> a = cells_as<typename ScalarOf<V>::T>(cells_at(cs, d, i, j));
     y[d.node_off + node] = stencil_apply<SCHEME, V>(
         a, ldv(x, d, i - 1, j - 1), ldv(x, d, i - 1, j), ldv(x, d, i - 1, j + 1),
         ldv(x, d, i, j - 1), ldv(x, d, i, j), ldv(x, d, i, j + 1),

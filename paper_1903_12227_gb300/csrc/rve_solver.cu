@@ -65,7 +65,7 @@ struct Ctx {
 // ------------------------------------------------------------- tables --
 // tw64[n + m] = exp(-2 pi i m / n), lap[n + m] = 4 sin^2(pi m / n) for every
 // n = 2^p <= 2^maxlog; computed with sincospi/sinpi.
-__global__ void k_tables(double2* tw64, float2* tw32, double* lap, int total) {
+__global__ void k_tables(double2* tw64, float2* tw32, double* lap, float* lap32, int total) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < 2 || idx >= total) return;
     const int p = 31 - __clz(idx);
@@ -76,15 +76,18 @@ __global__ void k_tables(double2* tw64, float2* tw32, double* lap, int total) {
     tw32[idx] = make_float2((float)cs, (float)sn);
     const double s1 = sinpi((double)m / (double)n);
     lap[idx] = 4.0 * s1 * s1;
+    lap32[idx] = (float)(4.0 * s1 * s1);
 }
 
 // ---------------------------------------------------------- row helpers --
+// y + (ax, ay) * x componentwise; the scalars are already in the vector's
+// type (no per-element conversion: on GB300 conversions from double run on
+// the slow FP64 pipe).
 template <typename V>
-__device__ __forceinline__ V axpy2(V y, double ax, double ay, V x) {
-    typedef typename ScalarOf<V>::T T;
+__device__ __forceinline__ V axpy2(V y, typename ScalarOf<V>::T ax, typename ScalarOf<V>::T ay, V x) {
     V r;
-    r.x = y.x + (T)ax * x.x;
-    r.y = y.y + (T)ay * x.y;
+    r.x = y.x + ax * x.x;
+    r.y = y.y + ay * x.y;
     return r;
 }
 
@@ -119,16 +122,18 @@ __device__ __forceinline__ double2 refine_w(const Ctx& c, const RDesc& d, const 
 
 // Cell value from the shared-memory mask rows of the tile (cell rows
 // r0-1 .. r0+TR-1 stored at mrow 0 .. TR) or from the coefficient array.
+template <typename T>
 struct TileCoef {
     const uint32_t* mrows;   // shared, (TR+1) x (n/32) words, or null
     int wpr;                 // words per row
-    __device__ __forceinline__ double cell(const CoefSrc& cs, const RDesc& d, int mrow, int c1,
-                                           int c2) const {
+    T a_incl, a_matrix;      // the two values in the arithmetic type
+    __device__ __forceinline__ T cell(const CoefSrc& cs, const RDesc& d, int mrow, int c1,
+                                      int c2) const {
         if (mrows) {
             const uint32_t w = mrows[mrow * wpr + (c2 >> 5)];
-            return ((w >> (c2 & 31)) & 1u) ? d.a_incl : d.a_matrix;
+            return ((w >> (c2 & 31)) & 1u) ? a_incl : a_matrix;
         }
-        return cs.cell(d, c1 & (d.n - 1), c2);
+        return (T)cs.cell(d, c1 & (d.n - 1), c2);
     }
 };
 
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
     V* Pt = reinterpret_cast<V*>(smem_raw);            // (TR+2) padded rows
     uint32_t* mrows = reinterpret_cast<uint32_t*>(Pt + (TR + 2) * SEQ);
     const int wpr = n >> 5;
-    TileCoef tc{c.cs.coef ? nullptr : mrows, wpr};
+    const TileCoef<T> tc{c.cs.coef ? nullptr : mrows, wpr, (T)d.a_incl, (T)d.a_matrix};
     if (!c.cs.coef) {
         for (int w = threadIdx.x; w < (TR + 1) * wpr; w += blockDim.x) {
             const int mr = w / wpr, col = w - mr * wpr;
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
         }
     }
     const RowLayout L(d);
-    const double bx = s.beta[0], by = s.beta[1];
-    const double alx = s.alpha[0], aly = s.alpha[1];
+    const T bx = (T)s.beta[0], by = (T)s.beta[1];
+    const T alx = (T)s.alpha[0], aly = (T)s.alpha[1];
     const V* Tin = static_cast<const V*>(c.T);
     const V* tw = twiddles<V>(c.tb, n);
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
         const V* up = Pt + q * SEQ;         // row i-1
         const V* mid = up + SEQ;            // row i
         const V* dn = mid + SEQ;            // row i+1
-        Cells4 a;
+        CellsT<T> a;
         a.mm = tc.cell(c.cs, d, q, i - 1, jm);
         a.m0 = tc.cell(c.cs, d, q, i - 1, j);
         a.z0m = tc.cell(c.cs, d, q + 1, i, jm);
@@ -311,8 +316,8 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
     DotAcc<T> ax, ay;
     V v[8];
     if (phase == PH_ITER) {
-        const double alx = s.active[0] ? s.rho[0] / sc[0] : 0.0;
-        const double aly = s.active[1] ? s.rho[1] / sc[1] : 0.0;
+        const T alx = (T)(s.active[0] ? s.rho[0] / sc[0] : 0.0);
+        const T aly = (T)(s.active[1] ? s.rho[1] / sc[1] : 0.0);
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -385,16 +390,18 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
     fft_reg(v, buf, d.log2n, t, tw, active);
     const double n2 = (double)n * (double)n;
     const Ts n2c0 = (Ts)(n2 * d.c0), n2d = (Ts)(n2 * delta);
+    const bool drop0 = (delta == 0.0);
     const int k2 = c0 + cc;
+    const Ts* lap = lap_table<Ts>(tb, n);
     DotAcc<Ts> ax, ay;
     if (active) {
-        const Ts lap2 = (Ts)tb.lap[n + k2];
+        const Ts lap2 = lap[k2];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int k1 = t + m * T;
             const V h = hartley_pair(buf[pidx(k1)], buf[pidx((n - k1) & (n - 1))]);
-            const Ts sig = n2c0 * ((Ts)tb.lap[n + k1] + lap2) + n2d;
-            const Ts inv = (k1 == 0 && k2 == 0 && delta == 0.0) ? (Ts)0 : (Ts)1 / sig;
+            const Ts sig = n2c0 * (lap[k1] + lap2) + n2d;
+            const Ts inv = (k1 == 0 && k2 == 0 && drop0) ? (Ts)0 : (Ts)1 / sig;
             V hs;
             hs.x = h.x * inv;
             hs.y = h.y * inv;
@@ -616,6 +623,7 @@ static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double*
     c.tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
     c.tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
     c.tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
+    c.tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
     c.cs.mask = mask;
     c.cs.coef = coef;
     c.u = reinterpret_cast<double2*>(u);
@@ -653,7 +661,8 @@ rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
     const int total = 2 << p.max_log2n;
     k_tables<<<(total + 255) / 256, 256, 0, s>>>(reinterpret_cast<double2*>(w + p.o_tw64),
                                                  reinterpret_cast<float2*>(w + p.o_tw32),
-                                                 reinterpret_cast<double*>(w + p.o_lap), total);
+                                                 reinterpret_cast<double*>(w + p.o_lap),
+                                                 reinterpret_cast<float*>(w + p.o_lap32), total);
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
@@ -790,6 +799,7 @@ cudaError_t precond_passes(const Plan& p, void* ws, double delta, const V* x, V*
     tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
     tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
     tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
+    tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
     cudaError_t e = cudaFuncSetAttribute(k_row_hartley<V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smemU);
     if (e == cudaSuccess)
