@@ -95,6 +95,65 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return r;
 }
 
+// Block sums of two dot-product accumulators; (sx, sy) valid in thread 0.
+// FP64 data: double tree.  FP32 data: the whole tree stays in double-float
+// (TwoSum on (hi, lo) pairs, fixed xor-butterfly order) and only thread 0
+// converts to double, so the block issues a handful of FP64 instructions
+// instead of a few per thread (GB300's FP64 pipe is ~1/64 of FP32).
+// `scratch` holds 64 floats / 32 doubles.  Contains barriers; ends with one.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float oh, float ol) {
+    const float t = hi + oh;
+    const float bv = t - hi;
+    const float e = (hi - (t - bv)) + (oh - bv);
+    hi = t;
+    lo = lo + ol + e;
+}
+
+__device__ __forceinline__ void df_warp(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        df_add(hi, lo, oh, ol);
+    }
+}
+
+__device__ __forceinline__ void block_sum2(const DotAcc<float>& ax, const DotAcc<float>& ay,
+                                           void* scratch, double& sx, double& sy) {
+    float* sh = static_cast<float*>(scratch);   // [32][4]
+    float xh = ax.hi, xl = ax.lo, yh = ay.hi, yl = ay.lo;
+    df_warp(xh, xl);
+    df_warp(yh, yl);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        sh[4 * wid + 0] = xh; sh[4 * wid + 1] = xl;
+        sh[4 * wid + 2] = yh; sh[4 * wid + 3] = yl;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        xh = lane < nw ? sh[4 * lane + 0] : 0.f;
+        xl = lane < nw ? sh[4 * lane + 1] : 0.f;
+        yh = lane < nw ? sh[4 * lane + 2] : 0.f;
+        yl = lane < nw ? sh[4 * lane + 3] : 0.f;
+        df_warp(xh, xl);
+        df_warp(yh, yl);
+        if (lane == 0) {
+            sx = (double)xh + (double)xl;
+            sy = (double)yh + (double)yl;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_sum2(const DotAcc<double>& ax, const DotAcc<double>& ay,
+                                           void* scratch, double& sx, double& sy) {
+    double* sh = static_cast<double*>(scratch);   // [32]
+    const double a = block_sum(ax.value(), sh);
+    const double b = block_sum(ay.value(), sh);
+    if (threadIdx.x == 0) { sx = a; sy = b; }
+}
+
 // Fixed-order sum of `count` doubles at src[k*stride] by one warp; every
 // lane gets the result.
 __device__ __forceinline__ double warp_sum_array(const double* __restrict__ src, int count,

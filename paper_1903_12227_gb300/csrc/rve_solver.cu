@@ -138,9 +138,10 @@ struct TileCoef {
 };
 
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 4 : 2) k_fused_S(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
+    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
+    __shared__ typename ScalarOf<V>::T bsc[6];
     const int tile = blockIdx.x;
     const int b = find_real(c.startS, c.batch, tile);
     const RState& s = c.st[b];
@@ -182,11 +183,19 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
     }
 
     // ---- ITER ----
+    // scalars of this step, converted once (thread 0) to the vector type
+    if (threadIdx.x == 0) {
+        bsc[0] = (T)s.beta[0];
+        bsc[1] = (T)s.beta[1];
+        bsc[2] = (T)s.alpha[0];
+        bsc[3] = (T)s.alpha[1];
+        bsc[4] = (T)d.a_incl;
+        bsc[5] = (T)d.a_matrix;
+    }
     const int SEQ = seq_stride(n);
     V* Pt = reinterpret_cast<V*>(smem_raw);            // (TR+2) padded rows
     uint32_t* mrows = reinterpret_cast<uint32_t*>(Pt + (TR + 2) * SEQ);
     const int wpr = n >> 5;
-    const TileCoef<T> tc{c.cs.coef ? nullptr : mrows, wpr, (T)d.a_incl, (T)d.a_matrix};
     if (!c.cs.coef) {
         for (int w = threadIdx.x; w < (TR + 1) * wpr; w += blockDim.x) {
             const int mr = w / wpr, col = w - mr * wpr;
@@ -194,9 +203,11 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
             mrows[w] = __ldg(c.cs.mask + d.word_off + (((int64_t)row << d.log2n) >> 5) + col);
         }
     }
+    __syncthreads();
+    const TileCoef<T> tc{c.cs.coef ? nullptr : mrows, wpr, bsc[4], bsc[5]};
     const RowLayout L(d);
-    const T bx = (T)s.beta[0], by = (T)s.beta[1];
-    const T alx = (T)s.alpha[0], aly = (T)s.alpha[1];
+    const T bx = bsc[0], by = bsc[1];
+    const T alx = bsc[2], aly = bsc[3];
     const V* Tin = static_cast<const V*>(c.T);
     const V* tw = twiddles<V>(c.tb, n);
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
@@ -254,8 +265,8 @@ __global__ void __launch_bounds__(256, 4) k_fused_S(const Ctx c) {
         ax.add(pc.x, qv.x);
         ay.add(pc.y, qv.y);
     }
-    const double sx = block_sum(ax.value(), red);
-    const double sy = block_sum(ay.value(), red);
+    double sx = 0.0, sy = 0.0;
+    block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {
         c.partS[2 * (int64_t)tile] = sx;
         c.partS[2 * (int64_t)tile + 1] = sy;
@@ -294,8 +305,9 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
 template <typename V>
 __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
+    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
     __shared__ double sc[2];
+    __shared__ typename ScalarOf<V>::T usc[2];
     const int blk = blockIdx.x;
     const int b = find_real(c.startU, c.batch, blk);
     const RState& s = c.st[b];
@@ -316,8 +328,13 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
     DotAcc<T> ax, ay;
     V v[8];
     if (phase == PH_ITER) {
-        const T alx = (T)(s.active[0] ? s.rho[0] / sc[0] : 0.0);
-        const T aly = (T)(s.active[1] ? s.rho[1] / sc[1] : 0.0);
+        // alpha = rho / p.q, formed once per block (thread 0) in FP64
+        if (threadIdx.x == 0) {
+            usc[0] = (T)(s.active[0] ? s.rho[0] / sc[0] : 0.0);
+            usc[1] = (T)(s.active[1] ? s.rho[1] / sc[1] : 0.0);
+        }
+        __syncthreads();
+        const T alx = usc[0], aly = usc[1];
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -356,8 +373,8 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
             }
         }
     }
-    const double sx = block_sum(ax.value(), red);
-    const double sy = block_sum(ay.value(), red);
+    double sx = 0.0, sy = 0.0;
+    block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {
         c.partU[2 * (int64_t)blk] = sx;
         c.partU[2 * (int64_t)blk + 1] = sy;
@@ -375,6 +392,12 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
                                    const Tables& tb, double delta, double* red,
                                    double* rho_part) {
     typedef typename ScalarOf<V>::T Ts;
+    __shared__ Ts csc[2];
+    if (threadIdx.x == 0) {
+        const double n2 = (double)d.n * (double)d.n;
+        csc[0] = (Ts)(n2 * d.c0);
+        csc[1] = (Ts)(n2 * delta);
+    }
     const int n = d.n, C = d.tC, T = n >> 3;
     const int tid = threadIdx.x;
     const int t = tid / C, cc = tid - (tid / C) * C;
@@ -387,10 +410,9 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
     }
-    fft_reg(v, buf, d.log2n, t, tw, active);
-    const double n2 = (double)n * (double)n;
-    const Ts n2c0 = (Ts)(n2 * d.c0), n2d = (Ts)(n2 * delta);
-    const bool drop0 = (delta == 0.0);
+    fft_reg(v, buf, d.log2n, t, tw, active);   // ends with a barrier: csc is visible
+    const Ts n2c0 = csc[0], n2d = csc[1];
+    const bool drop0 = (n2d == (Ts)0);
     const int k2 = c0 + cc;
     const Ts* lap = lap_table<Ts>(tb, n);
     DotAcc<Ts> ax, ay;
@@ -419,8 +441,8 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
         }
     }
     if (rho_part) {
-        const double sx = block_sum(ax.value(), red);
-        const double sy = block_sum(ay.value(), red);
+        double sx = 0.0, sy = 0.0;
+        block_sum2(ax, ay, red, sx, sy);
         if (tid == 0) { rho_part[0] = sx; rho_part[1] = sy; }
     }
 }
@@ -428,7 +450,7 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 template <typename V>
 __global__ void __launch_bounds__(1024) k_fused_C(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
     const int blk = blockIdx.x;
     const int b = find_real(c.startC, c.batch, blk);
     if (c.st[b].phase == PH_DONE) return;
@@ -780,7 +802,7 @@ __global__ void __launch_bounds__(1024) k_col_hartley(const RDesc* __restrict__ 
                                                       int tile0, Tables tb, double delta,
                                                       V* __restrict__ T) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
     const int blk = blockIdx.x + tile0;
     const int b = find_real(startC, batch, blk);
     const RDesc d = desc[b];
