@@ -137,16 +137,57 @@ struct TileCoef {
     }
 };
 
+// REFINE step: r64 = f - A(u + s (x + alpha p)) in FP64 for the tile's rows,
+// stored (rounded to the vector type) in q, partial |r64|^2 into partS.
+// Launched every step next to k_fused_S; blocks of realizations that are
+// not refining return at once.
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 4 : 2) k_fused_S(const Ctx c) {
+__global__ void __launch_bounds__(256) k_fused_R(const Ctx c) {
+    __shared__ double red[64];
+    const int tile = blockIdx.x;
+    const int b = find_real(c.startS, c.batch, tile);
+    const RState& s = c.st[b];
+    if (s.phase != PH_REFINE) return;
+    const RDesc d = c.desc[b];
+    const int n = d.n, TR = d.tS;
+    const int r0 = (tile - c.startS[b]) * TR;
+    const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+    V* Q = static_cast<V*>(c.Q);
+    DotAcc<double> a64x, a64y;   // exact FP64 |r64|^2
+    for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
+        const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
+        const Cells4 a = cells_at(c.cs, d, i, j);
+        const double2 f = rhs_at(a, d.h);
+        const double2 Aw = stencil_apply<SCHEME, double2>(
+            a, refine_w(c, d, s, i - 1, j - 1, Pold), refine_w(c, d, s, i - 1, j, Pold),
+            refine_w(c, d, s, i - 1, j + 1, Pold), refine_w(c, d, s, i, j - 1, Pold),
+            refine_w(c, d, s, i, j, Pold), refine_w(c, d, s, i, j + 1, Pold),
+            refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
+            refine_w(c, d, s, i + 1, j + 1, Pold));
+        const double2 r64 = make_double2(f.x - Aw.x, f.y - Aw.y);
+        Q[node_of<V>(d, i, j)] = from_d2<V>(r64);
+        a64x.add(r64.x, r64.x);
+        a64y.add(r64.y, r64.y);
+    }
+    double sx = 0.0, sy = 0.0;
+    block_sum2(a64x, a64y, red, sx, sy);
+    if (threadIdx.x == 0) {
+        c.partS[2 * (int64_t)tile] = sx;
+        c.partS[2 * (int64_t)tile + 1] = sy;
+    }
+}
+
+// ITER step: inverse row Hartley of t on the tile + halo rows (z),
+// p_new = z + beta p_old, x += alpha p_old (own rows), q = A p_new, p.q.
+template <typename V, int SCHEME>
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
+    __shared__ double red[64];   // block_sum2 scratch
     __shared__ typename ScalarOf<V>::T bsc[6];
     const int tile = blockIdx.x;
     const int b = find_real(c.startS, c.batch, tile);
     const RState& s = c.st[b];
-    const int phase = s.phase;
-    if (phase == PH_DONE) return;
+    if (s.phase != PH_ITER) return;
     const RDesc d = c.desc[b];
     const int n = d.n, TR = d.tS;
     const int r0 = (tile - c.startS[b]) * TR;
@@ -155,32 +196,6 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 4 : 2) k_fused_S(const C
     V* X = static_cast<V*>(c.X);
     V* Q = static_cast<V*>(c.Q);
     typedef typename ScalarOf<V>::T T;
-
-    if (phase == PH_REFINE) {
-        DotAcc<double> a64x, a64y;   // exact FP64 |r64|^2
-        for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
-            const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
-            const Cells4 a = cells_at(c.cs, d, i, j);
-            const double2 f = rhs_at(a, d.h);
-            const double2 Aw = stencil_apply<SCHEME, double2>(
-                a, refine_w(c, d, s, i - 1, j - 1, Pold), refine_w(c, d, s, i - 1, j, Pold),
-                refine_w(c, d, s, i - 1, j + 1, Pold), refine_w(c, d, s, i, j - 1, Pold),
-                refine_w(c, d, s, i, j, Pold), refine_w(c, d, s, i, j + 1, Pold),
-                refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
-                refine_w(c, d, s, i + 1, j + 1, Pold));
-            const double2 r64 = make_double2(f.x - Aw.x, f.y - Aw.y);
-            Q[node_of<V>(d, i, j)] = from_d2<V>(r64);
-            a64x.add(r64.x, r64.x);
-            a64y.add(r64.y, r64.y);
-        }
-        const double sx = block_sum(a64x.value(), red);
-        const double sy = block_sum(a64y.value(), red);
-        if (threadIdx.x == 0) {
-            c.partS[2 * (int64_t)tile] = sx;
-            c.partS[2 * (int64_t)tile + 1] = sy;
-        }
-        return;
-    }
 
     // ---- ITER ----
     // scalars of this step, converted once (thread 0) to the vector type
@@ -224,16 +239,31 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 4 : 2) k_fused_S(const C
         V pn[8];
         if (active) {
             const bool own = (q >= 1 && q <= TR);
+            // in two halves of four: the global loads of a half first, then
+            // its stores (the compiler cannot prove Pold, Pnew and X
+            // distinct, so a load after a store would wait for it)
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int k = L.t + m * L.T;
-                const V z = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
-                const int64_t node = node_of<V>(d, row, k);
-                const V po = Pold[node];
-                pn[m] = axpy2(z, bx, by, po);
+            for (int h = 0; h < 8; h += 4) {
+                V po[4], xo[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) po[m] = Pold[node_of<V>(d, row, L.t + (h + m) * L.T)];
                 if (own) {
-                    Pnew[node] = pn[m];
-                    X[node] = axpy2(X[node], alx, aly, po);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) xo[m] = X[node_of<V>(d, row, L.t + (h + m) * L.T)];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int k = L.t + (h + m) * L.T;
+                    const V z = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
+                    pn[h + m] = axpy2(z, bx, by, po[m]);
+                }
+                if (own) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int64_t node = node_of<V>(d, row, L.t + (h + m) * L.T);
+                        Pnew[node] = pn[h + m];
+                        X[node] = axpy2(xo[m], alx, aly, po[m]);
+                    }
                 }
             }
         }
@@ -336,11 +366,17 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
         __syncthreads();
         const T alx = usc[0], aly = usc[1];
         if (active) {
+            V qv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {   // loads first, stores after
+                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
+                v[m] = R[node];
+                qv[m] = Qv[node];
+            }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
-                const V rr = axpy2(R[node], -alx, -aly, Qv[node]);
-                R[node] = rr;
+                const V rr = axpy2(v[m], -alx, -aly, qv[m]);
+                R[node_of<V>(d, row, L.t + m * L.T)] = rr;
                 v[m] = rr;
                 ax.add(rr.x, rr.x);
                 ay.add(rr.y, rr.y);
@@ -691,6 +727,7 @@ rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
 template <typename V, int SCHEME>
 static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
+    k_fused_R<V, SCHEME><<<p.tilesS, 256, 0, s>>>(c);
     k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
     if (ev) cudaEventRecord(ev[1], s);
     k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
@@ -699,7 +736,7 @@ static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaE
     if (ev) cudaEventRecord(ev[3], s);
     k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
     if (ev) cudaEventRecord(ev[4], s);
-    note_launch(4);
+    note_launch(5);
     return cudaGetLastError();
 }
 
