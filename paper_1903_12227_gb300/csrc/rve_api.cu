@@ -90,8 +90,10 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         const int64_t nn = (int64_t)r[b].L * r[b].m0;
         if (nn > 0 && nn <= MAX_N) maxn = std::max(maxn, (int)nn);
     }
-    p.blockC = (maxn > 512) ? 1024 : 512;
-    if (o.col_tile > 0) p.blockC = std::min(1024, std::max(32, o.col_tile));
+    // column blocks: 1024 threads for large FP32 grids; FP64 stays at 512
+    // (more registers per thread for the double-precision transform)
+    p.blockC = (maxn > 512 && p.vbytes == 8) ? 1024 : 512;
+    if (o.col_tile > 0) p.blockC = std::min(p.vbytes == 8 ? 1024 : 512, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;

@@ -211,16 +211,24 @@ __host__ __device__ __forceinline__ int seq_stride(int n) {
     return p + ((4 - (p & 15)) & 15);
 }
 
+// Where the last Stockham stage leaves the transform.
+enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
+
 // Forward DFT (unnormalised) of one sequence of length n = 2^log2n >= 32,
 // cooperatively by T = n/8 threads (t in [0, T)).  On entry thread t holds
 // v[m] = x[t + m T], m = 0..7 -- exactly the inputs of its butterflies in
 // every Stockham stage (one radix-8 butterfly, or two radix-4, or four
 // radix-2), so each stage reads its inputs from registers or from `buf`,
 // writes its outputs to `buf` (one padded buffer of n elements, see pidx)
-// and a barrier separates stages.  On return buf holds X in natural order and
-// the block has synchronised.  Threads with active == false only take part
-// in the barriers.  tw[m] = exp(-2 pi i m/n).
-template <typename V>
+// and a barrier separates stages.  The outputs of the last stage fall on the
+// same positions t + m T, so they can stay in registers:
+//   FFT_TO_SMEM: buf holds X in natural order, then a barrier;
+//   FFT_TO_REGS: v[m] = X[t + m T], buf untouched by the last stage, no
+//                trailing barrier;
+//   FFT_TO_BOTH: both, then a barrier.
+// Threads with active == false only take part in the barriers.
+// tw[m] = exp(-2 pi i m/n).
+template <int FINAL, typename V>
 __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                                         const V* __restrict__ tw, bool active) {
     const int T = 1 << (log2n - 3);
@@ -230,6 +238,9 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
         const int lr = rem >= 3 ? 3 : rem;
         const int Ns = 1 << log2Ns;
         const int twshift = log2n - log2Ns - lr;
+        const bool last = (rem == lr);
+        const bool to_smem = !last || FINAL != FFT_TO_REGS;
+        const bool to_regs = last && FINAL != FFT_TO_SMEM;
         __syncthreads();   // earlier readers of buf are done
         if (active) {
             if (lr == 3) {
@@ -238,11 +249,14 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
 #pragma unroll
                     for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[(r * k) << twshift]);
                 }
-                dft8(v);
-                const int base = ((t - k) << 3) + k;
+                dft8(v);   // outputs stay in v[r]: the last stage's slots
+                if (to_smem) {
+                    const int base = ((t - k) << 3) + k;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns)] = v[r];
+                    for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns)] = v[r];
+                }
             } else if (lr == 2) {
+                V o[8];
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const int j = t + b * T, k = j & (Ns - 1);
@@ -253,29 +267,47 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                         a3 = cmul(a3, tw[(3 * k) << twshift]);
                     }
                     dft4(a0, a1, a2, a3);
-                    const int base = ((j - k) << 2) + k;
-                    buf[pidx(base)] = a0;
-                    buf[pidx(base + Ns)] = a1;
-                    buf[pidx(base + 2 * Ns)] = a2;
-                    buf[pidx(base + 3 * Ns)] = a3;
+                    o[b] = a0; o[b + 2] = a1; o[b + 4] = a2; o[b + 6] = a3;
+                    if (to_smem) {
+                        const int base = ((j - k) << 2) + k;
+                        buf[pidx(base)] = a0;
+                        buf[pidx(base + Ns)] = a1;
+                        buf[pidx(base + 2 * Ns)] = a2;
+                        buf[pidx(base + 3 * Ns)] = a3;
+                    }
+                }
+                if (to_regs) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) v[m] = o[m];
                 }
             } else {
+                V o[8];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const int j = t + b * T, k = j & (Ns - 1);
                     V a0 = v[b], a1 = v[b + 4];
                     if (Ns > 1) a1 = cmul(a1, tw[k << twshift]);
                     dft2(a0, a1);
-                    const int base = ((j - k) << 1) + k;
-                    buf[pidx(base)] = a0;
-                    buf[pidx(base + Ns)] = a1;
+                    o[b] = a0; o[b + 4] = a1;
+                    if (to_smem) {
+                        const int base = ((j - k) << 1) + k;
+                        buf[pidx(base)] = a0;
+                        buf[pidx(base + Ns)] = a1;
+                    }
+                }
+                if (to_regs) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) v[m] = o[m];
                 }
             }
         }
-        __syncthreads();
         log2Ns += lr;
         rem -= lr;
-        if (rem == 0) break;
+        if (last) {
+            if (FINAL != FFT_TO_REGS) __syncthreads();
+            break;
+        }
+        __syncthreads();
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) v[m] = buf[pidx(t + m * T)];

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const C
             for (int m = 0; m < 8; ++m) v[m] = Tin[node_of<V>(d, row, L.t + m * L.T)];
         }
         V* buf = Pt + (active ? q : 0) * SEQ;
-        fft_reg(v, buf, d.log2n, L.t, tw, active);
+        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
         V pn[8];
         if (active) {
             const bool own = (q >= 1 && q <= TR);
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const C
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int k = L.t + (h + m) * L.T;
-                    const V z = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
+                    const V z = hartley_pair(v[h + m], buf[pidx((n - k) & (n - 1))]);
                     pn[h + m] = axpy2(z, bx, by, po[m]);
                 }
                 if (own) {
@@ -321,13 +321,13 @@ template <typename V>
 __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d, int row,
                                                   const RowLayout& L, const V* tw, bool active,
                                                   V* __restrict__ out) {
-    fft_reg(v, buf, d.log2n, L.t, tw, active);
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
     if (active) {
         const int n = d.n;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int k = L.t + m * L.T;
-            out[node_of<V>(d, row, k)] = hartley_pair(buf[pidx(k)], buf[pidx((n - k) & (n - 1))]);
+            out[node_of<V>(d, row, k)] = hartley_pair(v[m], buf[pidx((n - k) & (n - 1))]);
         }
     }
 }
@@ -419,10 +419,18 @@ __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
 }
 
 // ----------------------------------------------------------- C kernel --
-// Column Hartley pass, diagonal scale 1/(n^2 sigma), partial rho, column
-// Hartley pass; in place on t.  Block of C*T threads (T = n/8), thread
-// (t, c) with c fastest so that global accesses are row segments of C
-// elements.  `rho_part` may be null.
+// Column pass on t (already row-Hartley transformed).  For each row
+// frequency k2 the column operator is the real symmetric circulant with
+// symbol 1/(n^2 sigma(., k2)) (sigma is even in k1), so it is applied to the
+// pair (a, b) = (t_1, t_2) of a column as one complex FFT, a real scale and
+// one inverse complex FFT (conj-FFT-conj); the outputs of the inverse stay
+// in registers and go straight to global memory.  The corrector parts of
+// rho are split with the mirror row: A = (Z_k + conj Z_-k)/2 is the DFT of
+// a, B = (Z_k - conj Z_-k)/2i that of b, and rho_c = sum s |A|^2 (resp.
+// |B|^2) with s = 1/(n^2 sigma) (Parseval; the row Hartley pass is
+// orthogonal up to n).  Block of C*T threads (T = n/8), thread (t, c) with c
+// fastest so that global accesses are row segments of C elements.
+// `rho_part` may be null.
 template <typename V>
 __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
                                    const Tables& tb, double delta, double* red,
@@ -446,7 +454,7 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
     }
-    fft_reg(v, buf, d.log2n, t, tw, active);   // ends with a barrier: csc is visible
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, tw, active);   // barrier: csc visible
     const Ts n2c0 = csc[0], n2d = csc[1];
     const bool drop0 = (n2d == (Ts)0);
     const int k2 = c0 + cc;
@@ -454,26 +462,30 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
     DotAcc<Ts> ax, ay;
     if (active) {
         const Ts lap2 = lap[k2];
+        const Ts q4 = (Ts)0.25;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int k1 = t + m * T;
-            const V h = hartley_pair(buf[pidx(k1)], buf[pidx((n - k1) & (n - 1))]);
+            const V z = v[m];
+            const V zm = buf[pidx((n - k1) & (n - 1))];
             const Ts sig = n2c0 * (lap[k1] + lap2) + n2d;
             const Ts inv = (k1 == 0 && k2 == 0 && drop0) ? (Ts)0 : (Ts)1 / sig;
-            V hs;
-            hs.x = h.x * inv;
-            hs.y = h.y * inv;
-            ax.add(h.x, hs.x);
-            ay.add(h.y, hs.y);
-            v[m] = hs;
+            const Ts w = q4 * inv;
+            const Ts apx = z.x + zm.x, apy = z.y - zm.y;   // 2 A
+            const Ts amx = z.x - zm.x, amy = z.y + zm.y;   // 2 i B
+            ax.add(apx * w, apx);
+            ax.add(apy * w, apy);
+            ay.add(amx * w, amx);
+            ay.add(amy * w, amy);
+            v[m] = mk<V>(z.x * inv, -(z.y * inv));        // conj(s Z)
         }
     }
-    fft_reg(v, buf, d.log2n, t, tw, active);   // its first barrier orders the reads above
+    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, tw, active);   // its first barrier ends the reads
     if (active) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int k1 = t + m * T;
-            Tg[node_of<V>(d, k1, c0 + cc)] = hartley_pair(buf[pidx(k1)], buf[pidx((n - k1) & (n - 1))]);
+            const V o = v[m];
+            Tg[node_of<V>(d, t + m * T, c0 + cc)] = mk<V>(o.x, -o.y);
         }
     }
     if (rho_part) {
@@ -484,7 +496,7 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 }
 
 template <typename V>
-__global__ void __launch_bounds__(1024) k_fused_C(const Ctx c) {
+__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const Ctx c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
     const int blk = blockIdx.x;
@@ -834,7 +846,7 @@ __global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ d
 }
 
 template <typename V>
-__global__ void __launch_bounds__(1024) k_col_hartley(const RDesc* __restrict__ desc,
+__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_col_hartley(const RDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ startC, int batch,
                                                       int tile0, Tables tb, double delta,
                                                       V* __restrict__ T) {
