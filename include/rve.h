@@ -110,8 +110,8 @@ typedef struct {
     int32_t col_tile;    /* threads of a column-transform block (power of
                             two, 32..1024); 0 = 512, or 1024 when n > 512  */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
-    int32_t timeout_ms;  /* persistent path: bound on each grid-wide wait
-                            (0 = 2000 ms)                                   */
+    int32_t timeout_us;  /* persistent path: bound on each grid-wide wait, in
+                            microseconds (0 = 2 s)                          */
 } rve_solve_opts;
 
 /* Per-realization solver report (device memory, one per realization). */
@@ -216,6 +216,46 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
                                const rve_solve_opts* opts, double* A_host,
                                rve_solve_info* info_host, void* ws, size_t ws_bytes,
                                void* stream);
+
+/* Plans: the whole pipeline (field, both correctors on the persistent path,
+ * A_hom) of a fixed batch, captured once into a CUDA graph and relaunched.
+ * The persistent path runs each solve as ONE cooperative launch over all
+ * realizations of the batch (sizes may differ), with grid-wide barriers
+ * between the pipeline phases; every barrier wait is bounded by
+ * opts->timeout_us, after which the launch ends and the affected
+ * realizations report RVE_ETIMEOUT (Sec. 3.4 for the solver itself).
+ * rve_plan_create: validates (host only) and lays out the workspace.
+ * rve_plan_execute: A (device double[batch][4], energy form) and info
+ * (device rve_solve_info[batch]); ws holds masks, correctors and solver
+ * state (rve_plan_workspace_size bytes).  The first call (and any call with
+ * different ws/A/info pointers) uploads the descriptors with a host
+ * synchronisation and captures the graph on `stream`; later calls only
+ * launch the graph.  rve_plan_destroy frees the host-side plan. */
+typedef struct rve_plan_s* rve_plan;
+rve_status rve_plan_create(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
+                           rve_plan* plan);
+size_t rve_plan_workspace_size(rve_plan plan);
+rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void* ws,
+                            size_t ws_bytes, void* stream);
+void rve_plan_destroy(rve_plan plan);
+
+/* Autotuner.  For every distinct grid size n of the batch, times short
+ * trial solves of up to 16 of its realizations for each candidate tile shape
+ * (stencil tile rows 1..8; column-block threads 256/512/1024 on the fused
+ * path, 256 on the persistent path) and records the fastest in the
+ * process-wide tuner table, keyed by (n, precision, persistent).  Plans and
+ * solves with opts->tile_rows == 0 and opts->col_tile == 0 then use the
+ * table.  ws: device scratch for the trials (candidates that do not fit are
+ * skipped); synchronises `stream`.  rve_tuner_save / rve_tuner_load write
+ * and read the table as text; rve_tuner_lookup returns 1 and the entry if
+ * present; rve_tuner_clear empties it. */
+rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
+                        void* ws, size_t ws_bytes, void* stream);
+rve_status rve_tuner_save(const char* path);
+rve_status rve_tuner_load(const char* path);
+int32_t rve_tuner_lookup(int32_t n, int32_t precision, int32_t persistent, int32_t* tile_rows,
+                         int32_t* block_threads);
+void rve_tuner_clear(void);
 
 /* Allocation-free variant of rve_a_hom, for callers that cannot allocate
  * device memory: programs whose device memory is all owned by their own pool

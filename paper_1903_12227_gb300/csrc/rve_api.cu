@@ -31,7 +31,7 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int MIN_N = 32, MAX_N = 2048;
 constexpr size_t MAX_SMEM = 227 * 1024;
 
-static rve_solve_opts defaults(const rve_solve_opts* o) {
+rve_solve_opts resolved_opts(const rve_solve_opts* o) {
     rve_solve_opts r;
     std::memset(&r, 0, sizeof(r));
     if (o) r = *o;
@@ -39,7 +39,7 @@ static rve_solve_opts defaults(const rve_solve_opts* o) {
     if (!(r.tol > 0.0)) r.tol = 1e-10;
     if (!(r.inner_tol > 0.0)) r.inner_tol = 1e-5;
     if (r.check_every <= 0) r.check_every = 8;
-    if (r.timeout_ms <= 0) r.timeout_ms = 2000;
+    if (r.timeout_us <= 0) r.timeout_us = 2000000;
     return r;
 }
 
@@ -54,6 +54,9 @@ static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o,
     t.tS = 8;
     while (t.tS > 1 && ((size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4) > 112640)
         t.tS >>= 1;
+    int ts_tuned = 0, bc_tuned = 0;
+    if (tuned_tiles(n, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0, &ts_tuned, &bc_tuned))
+        t.tS = ts_tuned;
     t.tC = std::min(n, blockC * 8 / n);
     if (o.tile_rows > 0) t.tS = o.tile_rows;
     t.tS = std::min(t.tS, n);
@@ -62,7 +65,7 @@ static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o,
 rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
                      Plan& p, bool need_vectors) {
     if (!r || batch <= 0 || batch > (1 << 22)) return RVE_EINVAL;
-    const rve_solve_opts o = defaults(opts);
+    const rve_solve_opts o = resolved_opts(opts);
     if (o.scheme != RVE_Q1_CONSISTENT && o.scheme != RVE_Q1_LUMPED) return RVE_EINVAL;
     if (o.precision != RVE_FP64 && o.precision != RVE_MIXED) return RVE_EINVAL;
     if (o.path != RVE_PATH_FUSED && o.path != RVE_PATH_PLAIN && o.path != RVE_PATH_PERSISTENT)
@@ -93,7 +96,15 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     // column blocks: 1024 threads for large FP32 grids; FP64 stays at 512
     // (more registers per thread for the double-precision transform)
     p.blockC = (maxn > 512 && p.vbytes == 8) ? 1024 : 512;
-    if (o.col_tile > 0) p.blockC = std::min(p.vbytes == 8 ? 1024 : 512, std::max(32, o.col_tile));
+    {
+        int ts_tuned = 0, bc_tuned = 0;
+        if (maxn > 0 && tuned_tiles(maxn, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0,
+                                    &ts_tuned, &bc_tuned))
+            p.blockC = bc_tuned;
+    }
+    if (o.path == RVE_PATH_PERSISTENT) p.blockC = 256;   // one block shape for all phases
+    if (o.col_tile > 0 && o.path != RVE_PATH_PERSISTENT)
+        p.blockC = std::min(p.vbytes == 8 ? 1024 : 512, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
@@ -258,7 +269,7 @@ rve_status rve_apply_stiffness(const rve_realization* r, int32_t batch, const ui
 
 size_t rve_workspace_size(const rve_realization* r, int32_t batch, const rve_solve_opts* opts) {
     Plan p;
-    rve_solve_opts o = defaults(opts);
+    rve_solve_opts o = resolved_opts(opts);
     if (!opts) o.precision = RVE_FP64;   // large enough for either precision
     if (make_plan(r, batch, &o, p, true) != RVE_OK) return 0;
     return p.total;
@@ -284,7 +295,7 @@ rve_status rve_apply_precond(const rve_realization* r, int32_t batch, double del
 rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const uint32_t* mask,
                                 const double* coef, const rve_solve_opts* opts, double* u,
                                 rve_solve_info* info, void* ws, size_t ws_bytes, void* stream) {
-    const rve_solve_opts o = defaults(opts);
+    const rve_solve_opts o = resolved_opts(opts);
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, true);
     if (st != RVE_OK) return st;
@@ -292,6 +303,8 @@ rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const u
     if (ws_bytes < p.total) return RVE_ENOMEM;
     if (o.path == RVE_PATH_PLAIN)
         return run_solve_plain(p, ws, mask, coef, o, u, info, as_stream(stream));
+    if (o.path == RVE_PATH_PERSISTENT)
+        return run_solve_persistent(p, ws, mask, coef, o, u, info, as_stream(stream));
     return run_solve_fused(p, ws, mask, coef, o, u, info, as_stream(stream));
 }
 
@@ -357,7 +370,7 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
                                const rve_solve_opts* opts, double* A_host,
                                rve_solve_info* info_host, void* ws, size_t ws_bytes,
                                void* stream) {
-    const rve_solve_opts o = defaults(opts);
+    const rve_solve_opts o = resolved_opts(opts);
     Plan p;
     rve_status st = make_plan(r_host, batch, &o, p, true);
     if (st != RVE_OK) return st;

@@ -59,6 +59,8 @@ struct Plan {
     int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0;
     size_t smemS = 0, smemU = 0, smemC = 0;
     int blockC = 512;               // threads of a column-transform block
+    int persist_grid = 0;           // blocks of the persistent launch (0 = not prepared)
+    size_t persist_smem = 0;
     // workspace offsets (bytes)
     size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
     size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0;
@@ -66,6 +68,13 @@ struct Plan {
     size_t o_X = 0, o_R = 0, o_Q = 0, o_T = 0, o_P0 = 0, o_P1 = 0;
     size_t total = 0;
 };
+
+// Options with the library defaults filled in.
+rve_solve_opts resolved_opts(const rve_solve_opts* o);
+// Tuned tile shape of grid size n (false if none recorded).
+bool tuned_tiles(int n, int precision, int path, int* tS, int* blockC);
+// Kernel attributes and co-resident grid size of the persistent launch.
+rve_status prepare_persistent(Plan& p);
 
 // Validates descriptors and fills plan (host only).  opts may be NULL.
 rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
@@ -90,6 +99,13 @@ cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision,
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
                            cudaStream_t s);
+rve_status run_solve_persistent(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                                const rve_solve_opts& o, double* u, rve_solve_info* info,
+                                cudaStream_t s);
+rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s);
+rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mask,
+                                    const double* coef, const rve_solve_opts& o, double* u,
+                                    rve_solve_info* info, cudaStream_t s);
 rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
                            cudaStream_t s);

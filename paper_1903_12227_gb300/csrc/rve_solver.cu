@@ -38,6 +38,10 @@
 
 namespace rve {
 
+// Control words (int32) in the workspace: [0] realizations done, then the
+// persistent kernel's grid barrier.
+enum { CTL_ARRIVE = 8, CTL_GEN = 9, CTL_ERR = 10 };
+
 struct Ctx {
     int batch;
     const RDesc* __restrict__ desc;
@@ -142,9 +146,8 @@ struct TileCoef {
 // Launched every step next to k_fused_S; blocks of realizations that are
 // not refining return at once.
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256) k_fused_R(const Ctx c) {
+__device__ void fused_R_tile(const Ctx& c, int tile) {
     __shared__ double red[64];
-    const int tile = blockIdx.x;
     const int b = find_real(c.startS, c.batch, tile);
     const RState& s = c.st[b];
     if (s.phase != PH_REFINE) return;
@@ -180,11 +183,10 @@ __global__ void __launch_bounds__(256) k_fused_R(const Ctx c) {
 // ITER step: inverse row Hartley of t on the tile + halo rows (z),
 // p_new = z + beta p_old, x += alpha p_old (own rows), q = A p_new, p.q.
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const Ctx c) {
+__device__ void fused_S_tile(const Ctx& c, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];   // block_sum2 scratch
     __shared__ typename ScalarOf<V>::T bsc[6];
-    const int tile = blockIdx.x;
     const int b = find_real(c.startS, c.batch, tile);
     const RState& s = c.st[b];
     if (s.phase != PH_ITER) return;
@@ -333,12 +335,11 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
 }
 
 template <typename V>
-__global__ void __launch_bounds__(256) k_fused_U(const Ctx c) {
+__device__ void fused_U_tile(const Ctx& c, int blk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
     __shared__ double sc[2];
     __shared__ typename ScalarOf<V>::T usc[2];
-    const int blk = blockIdx.x;
     const int b = find_real(c.startU, c.batch, blk);
     const RState& s = c.st[b];
     const int phase = s.phase;
@@ -496,10 +497,9 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 }
 
 template <typename V>
-__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const Ctx c) {
+__device__ void fused_C_tile(const Ctx& c, int blk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
-    const int blk = blockIdx.x;
     const int b = find_real(c.startC, c.batch, blk);
     if (c.st[b].phase == PH_DONE) return;
     const RDesc d = c.desc[b];
@@ -508,13 +508,25 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const C
                           c.partC + 2 * (int64_t)blk);
 }
 
+// One launch per pipeline kernel (the fused path).
+template <typename V, int SCHEME>
+__global__ void __launch_bounds__(256) k_fused_R(const Ctx c) { fused_R_tile<V, SCHEME>(c, blockIdx.x); }
+template <typename V, int SCHEME>
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const Ctx c) {
+    fused_S_tile<V, SCHEME>(c, blockIdx.x);
+}
+template <typename V>
+__global__ void __launch_bounds__(256) k_fused_U(const Ctx c) { fused_U_tile<V>(c, blockIdx.x); }
+template <typename V>
+__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const Ctx c) {
+    fused_C_tile<V>(c, blockIdx.x);
+}
+
 // ------------------------------------------------------ control kernel --
 __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
 
-__global__ void k_control(const Ctx c) {
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= c.batch) return;
-    const int b = w;
+// Control step of realization b, executed by one whole warp.
+__device__ void control_one(const Ctx& c, int b) {
     RState& s = c.st[b];
     if (s.phase == PH_DONE) return;
     const int ts0 = c.startS[b], tsn = c.startS[b + 1] - ts0;
@@ -595,6 +607,94 @@ __global__ void k_control(const Ctx c) {
     s.phase = PH_ITER;
 }
 
+__global__ void k_control(const Ctx c) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= c.batch) return;
+    control_one(c, w);
+}
+
+// ------------------------------------------------------ persistent path --
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  Every wait is bounded by
+// timeout_ns: a block that waits longer sets the error word and leaves; all
+// blocks then see the error after their own (bounded) wait and return
+// false, so the kernel always ends.
+__device__ bool grid_sync(int* ctl, unsigned nblocks, unsigned long long timeout_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int* vgen = ctl + CTL_GEN;
+        volatile int* verr = ctl + CTL_ERR;
+        const int gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(reinterpret_cast<unsigned*>(ctl + CTL_ARRIVE), 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(ctl + CTL_ARRIVE, 0);
+            __threadfence();
+            atomicAdd(ctl + CTL_GEN, 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*verr) break;
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(ctl + CTL_ERR, 1);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = (*verr == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct PersistArgs {
+    int tilesS, tilesU, tilesC;
+    long long max_steps;
+    unsigned long long timeout_ns;
+};
+
+// The whole solve in one cooperative launch: each pipeline step runs the
+// refine/stencil, update, column and control phases over all tiles of the
+// batch (any mix of sizes), separated by grid barriers, until every
+// realization is done.
+// Phases as separate (not inlined) calls, so that each keeps its own register
+// allocation inside the one persistent kernel.
+template <typename V, int SCHEME>
+__device__ __noinline__ void phase_RS(const Ctx& c, int t) {
+    fused_R_tile<V, SCHEME>(c, t);
+    fused_S_tile<V, SCHEME>(c, t);
+}
+template <typename V>
+__device__ __noinline__ void phase_U(const Ctx& c, int t) { fused_U_tile<V>(c, t); }
+template <typename V>
+__device__ __noinline__ void phase_C(const Ctx& c, int t) { fused_C_tile<V>(c, t); }
+
+template <typename V, int SCHEME>
+__global__ void __launch_bounds__(256, 2) k_persistent(const Ctx c, const PersistArgs a) {
+    const unsigned nb = gridDim.x;
+    for (long long step = 0; step < a.max_steps; ++step) {
+        for (int t = blockIdx.x; t < a.tilesS; t += nb) phase_RS<V, SCHEME>(c, t);
+        if (!grid_sync(c.ndone, nb, a.timeout_ns)) return;
+        for (int t = blockIdx.x; t < a.tilesU; t += nb) phase_U<V>(c, t);
+        if (!grid_sync(c.ndone, nb, a.timeout_ns)) return;
+        for (int t = blockIdx.x; t < a.tilesC; t += nb) phase_C<V>(c, t);
+        if (!grid_sync(c.ndone, nb, a.timeout_ns)) return;
+        const int warps = blockDim.x >> 5;
+        for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < c.batch; r += nb * warps)
+            control_one(c, r);
+        if (!grid_sync(c.ndone, nb, a.timeout_ns)) return;
+        if (*reinterpret_cast<volatile int*>(c.ndone) >= c.batch) return;
+    }
+}
+
 __global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -616,7 +716,12 @@ __global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
         z.status = RVE_OK;
         c.st[b] = z;
     }
-    if (gid == 0) *c.ndone = 0;
+    if (gid == 0) {
+        c.ndone[0] = 0;                          // realizations done
+        c.ndone[CTL_ARRIVE] = 0;                 // grid barrier arrivals
+        c.ndone[CTL_GEN] = 0;                    // grid barrier generation
+        c.ndone[CTL_ERR] = 0;                    // a bounded wait gave up
+    }
 }
 
 __global__ void k_report(const Ctx c, rve_solve_info* info) {
@@ -626,7 +731,8 @@ __global__ void k_report(const Ctx c, rve_solve_info* info) {
     rve_solve_info r;
     r.iters[0] = s.iters[0];
     r.iters[1] = s.iters[1];
-    r.status = (s.phase == PH_DONE) ? s.status : RVE_ENOCONV;
+    r.status = (s.phase == PH_DONE) ? s.status
+               : (c.ndone[CTL_ERR] ? RVE_ETIMEOUT : RVE_ENOCONV);
     r.refinements = s.refinements;
     r.steps = s.steps;
     r.reserved = 0;
@@ -795,6 +901,110 @@ static rve_status fused_loop(const Plan& p, const Ctx& c, const rve_solve_opts& 
         g_prof.harvest();
     }
     return RVE_OK;
+}
+
+template <typename V, int SCHEME>
+static rve_status persistent_prepare_t(Plan& p) {
+    const size_t smem = std::max(p.smemS, std::max(p.smemU, p.smemC));
+    if (cudaFuncSetAttribute(k_persistent<V, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return RVE_ECUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<V, SCHEME>, 256,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+        return RVE_ECUDA;
+    p.persist_grid = per_sm * sms;   // co-resident: one wave
+    p.persist_smem = smem;
+    return RVE_OK;
+}
+
+rve_status prepare_persistent(Plan& p) {
+    if (p.precision == RVE_MIXED)
+        return (p.scheme == RVE_Q1_LUMPED) ? persistent_prepare_t<float2, 1>(p)
+                                           : persistent_prepare_t<float2, 0>(p);
+    return (p.scheme == RVE_Q1_LUMPED) ? persistent_prepare_t<double2, 1>(p)
+                                       : persistent_prepare_t<double2, 0>(p);
+}
+
+template <typename V, int SCHEME>
+static rve_status persistent_launch(const Plan& p, const Ctx& c, const rve_solve_opts& o,
+                                    cudaStream_t s) {
+    if (p.persist_grid <= 0) return RVE_ECUDA;   // prepare_persistent() first
+    PersistArgs a;
+    a.tilesS = p.tilesS;
+    a.tilesU = p.tilesU;
+    a.tilesC = p.tilesC;
+    a.max_steps = 2LL * o.max_iter + 64;
+    a.timeout_ns = (unsigned long long)o.timeout_us * 1000ull;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.persist_grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = p.persist_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_persistent<V, SCHEME>, c, a);
+    note_launch();
+    return e == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+// Persistent path: descriptors must already be in the workspace (upload_plan);
+// everything after that is stream-ordered kernel launches (no host sync), so
+// the sequence can be captured in a CUDA graph.
+rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mask,
+                                    const double* coef, const rve_solve_opts& o, double* u,
+                                    rve_solve_info* info, cudaStream_t s) {
+    Ctx c = make_ctx(p, ws, mask, coef, u, o);
+    char* w = static_cast<char*>(ws);
+    const int total = 2 << p.max_log2n;
+    k_tables<<<(total + 255) / 256, 256, 0, s>>>(reinterpret_cast<double2*>(w + p.o_tw64),
+                                                 reinterpret_cast<float2*>(w + p.o_tw32),
+                                                 reinterpret_cast<double*>(w + p.o_lap),
+                                                 reinterpret_cast<float*>(w + p.o_lap32), total);
+    k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
+    note_launch(2);
+    if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
+    rve_status st;
+    if (p.precision == RVE_MIXED)
+        st = (p.scheme == RVE_Q1_LUMPED) ? persistent_launch<float2, 1>(p, c, o, s)
+                                         : persistent_launch<float2, 0>(p, c, o, s);
+    else
+        st = (p.scheme == RVE_Q1_LUMPED) ? persistent_launch<double2, 1>(p, c, o, s)
+                                         : persistent_launch<double2, 0>(p, c, o, s);
+    if (st != RVE_OK) return st;
+    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+// Uploads only the descriptors and tile tables (host -> device copies);
+// the lookup tables are filled by a kernel in the enqueued sequence.
+rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    cudaError_t e = cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(RDesc) * p.batch,
+                                    cudaMemcpyHostToDevice, s);
+    const std::vector<int32_t>* tabs[4] = {&p.startS, &p.startU, &p.startC, &p.startA};
+    const size_t offs[4] = {p.o_startS, p.o_startU, p.o_startC, p.o_startA};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(w + offs[k], tabs[k]->data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+rve_status run_solve_persistent(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                                const rve_solve_opts& o, double* u, rve_solve_info* info,
+                                cudaStream_t s) {
+    Plan q = p;
+    rve_status st = (q.persist_grid > 0) ? RVE_OK : prepare_persistent(q);
+    if (st == RVE_OK) st = upload_descriptors(q, ws, s);
+    if (st != RVE_OK) return st;
+    return enqueue_solve_persistent(q, ws, mask, coef, o, u, info, s);
 }
 
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,

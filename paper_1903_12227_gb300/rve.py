@@ -43,7 +43,7 @@ class SolveOpts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("tile_rows", ctypes.c_int32),
                 ("col_tile", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("timeout_ms", ctypes.c_int32)]
+                ("timeout_us", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -97,6 +97,24 @@ def lib() -> ctypes.CDLL:
         L.rve_homogenize_workspace_size.argtypes = [vp, i32, vp]
         L.rve_homogenize_host.restype = i32
         L.rve_homogenize_host.argtypes = [vp, i32, vp, vp, vp, vp, sz, vp]
+        L.rve_plan_create.restype = i32
+        L.rve_plan_create.argtypes = [vp, i32, vp, ctypes.POINTER(vp)]
+        L.rve_plan_workspace_size.restype = sz
+        L.rve_plan_workspace_size.argtypes = [vp]
+        L.rve_plan_execute.restype = i32
+        L.rve_plan_execute.argtypes = [vp, vp, vp, vp, sz, vp]
+        L.rve_plan_destroy.restype = None
+        L.rve_plan_destroy.argtypes = [vp]
+        L.rve_autotune.restype = i32
+        L.rve_autotune.argtypes = [vp, i32, vp, vp, sz, vp]
+        L.rve_tuner_save.restype = i32
+        L.rve_tuner_save.argtypes = [ctypes.c_char_p]
+        L.rve_tuner_load.restype = i32
+        L.rve_tuner_load.argtypes = [ctypes.c_char_p]
+        L.rve_tuner_lookup.restype = i32
+        L.rve_tuner_lookup.argtypes = [i32, i32, i32, vp, vp]
+        L.rve_tuner_clear.restype = None
+        L.rve_tuner_clear.argtypes = []
         L.rve_profile_enable.restype = None
         L.rve_profile_enable.argtypes = [i32]
         L.rve_profile_read.restype = i32
@@ -162,9 +180,9 @@ def as_batch(b) -> Batch:
 
 def make_opts(scheme=CONSISTENT, precision=FP64, path=PATH_FUSED, tol=1e-10, max_iter=0,
               delta=0.0, inner_tol=0.0, tile_rows=0, col_tile=0, check_every=0,
-              timeout_ms=0) -> SolveOpts:
+              timeout_us=0) -> SolveOpts:
     return SolveOpts(scheme, precision, path, max_iter, tol, delta, inner_tol, tile_rows,
-                     col_tile, check_every, timeout_ms)
+                     col_tile, check_every, timeout_us)
 
 
 def _dev(device):
@@ -304,6 +322,74 @@ def homogenize_host(batch, opts: SolveOpts | None = None, ws=None, stream=None, 
                                     ctypes.cast(info, ctypes.c_void_p), _ptr(ws), ws.numel(),
                                     _stream(stream)), "rve_homogenize_host")
     return A.reshape(b.count, 2, 2), [_info_dict(i) for i in info]
+
+
+class Plan:
+    """Whole pipeline of a fixed batch on the persistent path, captured once
+    into a CUDA graph (rve_plan_*).  execute() returns A [B,2,2] (device,
+    float64) and the raw info tensor; calls after the first relaunch the graph."""
+
+    def __init__(self, batch, opts: SolveOpts | None = None, device=None):
+        _require_cuda()
+        self.batch = as_batch(batch)
+        self.opts = opts or make_opts(precision=MIXED, path=PATH_PERSISTENT)
+        h = ctypes.c_void_p()
+        check(lib().rve_plan_create(self.batch.ptr, self.batch.count, ctypes.byref(self.opts),
+                                    ctypes.byref(h)), "rve_plan_create")
+        self.handle = h
+        dev = _dev(device)
+        self.ws = workspace(lib().rve_plan_workspace_size(h), dev)
+        self.A = torch.empty(self.batch.count, 4, dtype=torch.float64, device=dev)
+        self.info = torch.empty(self.batch.count * INFO_BYTES, dtype=torch.uint8, device=dev)
+
+    def execute(self, stream=None):
+        check(lib().rve_plan_execute(self.handle, _ptr(self.A), _ptr(self.info), _ptr(self.ws),
+                                     self.ws.numel(), _stream(stream)), "rve_plan_execute")
+        return self.A.view(self.batch.count, 2, 2), self.info
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rve_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(batch, opts: SolveOpts | None = None, ws_bytes: int | None = None, stream=None,
+             device=None) -> None:
+    """Time candidate tile shapes per grid size and record the fastest (rve_autotune)."""
+    _require_cuda()
+    b = as_batch(batch)
+    opts = opts or make_opts()
+    if ws_bytes is None:
+        sub = Batch(b.descs[:16])
+        ws_bytes = 4 * workspace_size(sub, make_opts(precision=FP64)) + (64 << 20)
+    ws = workspace(ws_bytes, device)
+    check(lib().rve_autotune(b.ptr, b.count, ctypes.byref(opts), _ptr(ws), ws.numel(),
+                             _stream(stream)), "rve_autotune")
+
+
+def tuner_save(path: str) -> None:
+    check(lib().rve_tuner_save(path.encode()), "rve_tuner_save")
+
+
+def tuner_load(path: str) -> None:
+    check(lib().rve_tuner_load(path.encode()), "rve_tuner_load")
+
+
+def tuner_lookup(n: int, precision: int, persistent: bool):
+    ts, bc = ctypes.c_int32(0), ctypes.c_int32(0)
+    found = lib().rve_tuner_lookup(n, precision, 1 if persistent else 0, ctypes.byref(ts),
+                                   ctypes.byref(bc))
+    return (ts.value, bc.value) if found else None
+
+
+def tuner_clear() -> None:
+    lib().rve_tuner_clear()
 
 
 def profile_enable(on: bool = True) -> None:

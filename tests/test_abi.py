@@ -66,3 +66,27 @@ def test_uneven_batch_sizes_add_up(librve):
     ds = workloads.config_batch("uneven_4096", seed=3, count=40)
     b = rve.Batch(ds)
     assert librve.rve_nodes(b.ptr, b.count) == sum((d["L"] * d["m0"]) ** 2 for d in ds)
+
+
+def test_tuner_table_save_load_roundtrip(librve, tmp_path):
+    # host-only: the tuner table is a process-wide map written/read as text
+    from paper_1903_12227_gb300 import rve
+    rve.tuner_clear()
+    assert rve.tuner_lookup(512, rve.MIXED, False) is None
+    path = tmp_path / "tune.txt"
+    path.write_text("# n precision persistent tile_rows block_threads\n512 1 0 4 1024\n64 0 1 8 256\n")
+    rve.tuner_load(str(path))
+    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 1024)
+    assert rve.tuner_lookup(64, rve.FP64, True) == (8, 256)
+    out = tmp_path / "out.txt"
+    rve.tuner_save(str(out))
+    rve.tuner_clear()
+    rve.tuner_load(str(out))
+    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 1024)
+    # the tuned shape changes the plan (tile counts, hence the partial-sum arrays)
+    from paper_1903_12227_gb300 import workloads
+    b = rve.Batch([workloads.realization(32, 16, 10.0, 0, 0)])
+    tuned = rve.workspace_size(b, rve.make_opts(precision=rve.MIXED))
+    rve.tuner_clear()
+    default = rve.workspace_size(b, rve.make_opts(precision=rve.MIXED))
+    assert tuned != default
