@@ -155,9 +155,9 @@ __device__ __forceinline__ void block_sum2(const DotAcc<double>& ax, const DotAc
 }
 
 // Fixed-order sum of `count` doubles at src[k*stride] by one warp; every
-// lane gets the result.
-__device__ __forceinline__ double warp_sum_array(const double* __restrict__ src, int count,
-                                                 int stride) {
+// lane gets the result.  Plain (coherent) loads: the persistent solver reads
+// partial sums written by other blocks earlier in the same launch.
+__device__ __forceinline__ double warp_sum_array(const double* src, int count, int stride) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
     for (int k = lane; k < count; k += 32) s += src[(int64_t)k * stride];

@@ -48,13 +48,15 @@ struct Ctx {
     const int32_t* __restrict__ startS;
     const int32_t* __restrict__ startU;
     const int32_t* __restrict__ startC;
-    RState* __restrict__ st;
-    double* __restrict__ partS;
-    double* __restrict__ partU;
-    double* __restrict__ partC;
+    // written during a solve (by other blocks of the persistent launch too):
+    // no __restrict__, so that every read is a coherent load
+    RState* st;
+    double* partS;
+    double* partU;
+    double* partC;
     Tables tb;
     CoefSrc cs;
-    double2* __restrict__ u;
+    double2* u;
     void* X;
     void* R;
     void* Q;
