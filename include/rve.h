@@ -128,6 +128,10 @@ typedef struct {
 /* Human-readable name of a status code (static string). */
 const char* rve_status_string(int32_t status);
 
+/* Description of the last CUDA failure seen by this host thread (where it
+ * happened and CUDA's error string); "" if none. */
+const char* rve_last_error(void);
+
 /* Library version: major*10000 + minor*100 + patch. */
 int32_t rve_version(void);
 
@@ -230,7 +234,9 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
  * state (rve_plan_workspace_size bytes).  The first call (and any call with
  * different ws/A/info pointers) uploads the descriptors with a host
  * synchronisation and captures the graph on `stream`; later calls only
- * launch the graph.  rve_plan_destroy frees the host-side plan. */
+ * launch the graph.  `stream` must be a created stream (not the legacy
+ * default stream, on which CUDA cannot capture; NULL gives RVE_EINVAL).
+ * rve_plan_destroy frees the host-side plan. */
 typedef struct rve_plan_s* rve_plan;
 rve_status rve_plan_create(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
                            rve_plan* plan);

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -193,6 +194,13 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     return RVE_OK;
 }
 
+static thread_local char g_last_error[256] = "";
+
+rve_status note_error(const char* where, cudaError_t e) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+    return RVE_ECUDA;
+}
+
 }  // namespace rve
 
 using namespace rve;
@@ -218,6 +226,8 @@ const char* rve_status_string(int32_t status) {
 }
 
 int32_t rve_version(void) { return 100; }
+
+const char* rve_last_error(void) { return g_last_error; }
 
 int64_t rve_mask_words(const rve_realization* r, int32_t batch) {
     Plan p;

@@ -69,6 +69,9 @@ struct Plan {
     size_t total = 0;
 };
 
+// Records "<where>: <CUDA error string>" for rve_last_error(); returns RVE_ECUDA.
+rve_status note_error(const char* where, cudaError_t e);
+
 // Options with the library defaults filled in.
 rve_solve_opts resolved_opts(const rve_solve_opts* o);
 // Tuned tile shape of grid size n (false if none recorded).

@@ -90,7 +90,8 @@ size_t rve_plan_workspace_size(rve_plan plan) { return plan ? plan->l.total : 0;
 
 rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void* ws,
                             size_t ws_bytes, void* stream) {
-    if (!plan || !A || !info || !ws) return RVE_EINVAL;
+    // a graph cannot be captured on the legacy default stream
+    if (!plan || !A || !info || !ws || !stream) return RVE_EINVAL;
     if (ws_bytes < plan->l.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!plan->exec || plan->ws != ws || plan->A != A || plan->info != info) {
@@ -106,34 +107,37 @@ rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void
         // descriptors (pageable host -> device) and kernel attributes before
         // the capture; everything captured is a kernel or a memset
         if (upload_descriptors(p, sw, s) != RVE_OK || cudaStreamSynchronize(s) != cudaSuccess)
-            return RVE_ECUDA;
-        if (prepare_persistent(plan->p) != RVE_OK) return RVE_ECUDA;
+            return note_error("plan: descriptor upload", cudaGetLastError());
+        if (prepare_persistent(plan->p) != RVE_OK)
+            return note_error("plan: persistent kernel set-up", cudaGetLastError());
         cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return RVE_ECUDA;
+        cudaError_t be = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (be != cudaSuccess) return note_error("plan: begin capture", be);
         rve_status st = RVE_OK;
         if (launch_gen_field(p, nullptr, mask, s) != cudaSuccess) st = RVE_ECUDA;
         if (st == RVE_OK) st = enqueue_solve_persistent(p, sw, mask, nullptr, plan->o, u, info, s);
         if (st == RVE_OK &&
             launch_a_hom(p, sw, mask, nullptr, p.scheme, u, A, nullptr, s) != cudaSuccess)
             st = RVE_ECUDA;
+        const cudaError_t le = cudaGetLastError();
         const cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (st != RVE_OK || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return st != RVE_OK ? st : RVE_ECUDA;
+            return note_error("plan: capture", ce != cudaSuccess ? ce : le);
         }
         const cudaError_t ie = cudaGraphInstantiate(&plan->exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) {
             plan->exec = nullptr;
-            return RVE_ECUDA;
+            return note_error("plan: instantiate", ie);
         }
         plan->ws = ws;
         plan->A = A;
         plan->info = info;
     }
     note_launch();
-    return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
+    const cudaError_t ge = cudaGraphLaunch(plan->exec, s);
+    return ge == cudaSuccess ? RVE_OK : note_error("plan: graph launch", ge);
 }
 
 void rve_plan_destroy(rve_plan plan) {

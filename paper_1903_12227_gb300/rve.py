@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.rve_status_string.restype = ctypes.c_char_p
         L.rve_status_string.argtypes = [i32]
         L.rve_version.restype = i32
+        L.rve_last_error.restype = ctypes.c_char_p
+        L.rve_last_error.argtypes = []
         L.rve_mask_words.restype = i64
         L.rve_mask_words.argtypes = [vp, i32]
         L.rve_nodes.restype = i64
@@ -128,6 +130,8 @@ def lib() -> ctypes.CDLL:
 def check(status: int, what: str = "") -> None:
     if status != RVE_OK:
         msg = lib().rve_status_string(status).decode()
+        if status == RVE_ECUDA:
+            msg += f" ({lib().rve_last_error().decode()})"
         raise RveError(f"{what}: {msg}" if what else msg)
 
 
@@ -341,10 +345,17 @@ class Plan:
         self.ws = workspace(lib().rve_plan_workspace_size(h), dev)
         self.A = torch.empty(self.batch.count, 4, dtype=torch.float64, device=dev)
         self.info = torch.empty(self.batch.count * INFO_BYTES, dtype=torch.uint8, device=dev)
+        # graphs cannot be captured on the legacy default stream: own stream
+        self.stream = torch.cuda.Stream(device=dev)
 
-    def execute(self, stream=None):
+    def execute(self):
+        """Launch (capturing on the first call) on the plan's stream; the
+        caller's current stream then waits for it."""
+        cur = torch.cuda.current_stream(self.A.device)
+        self.stream.wait_stream(cur)
         check(lib().rve_plan_execute(self.handle, _ptr(self.A), _ptr(self.info), _ptr(self.ws),
-                                     self.ws.numel(), _stream(stream)), "rve_plan_execute")
+                                     self.ws.numel(), _stream(self.stream)), "rve_plan_execute")
+        cur.wait_stream(self.stream)
         return self.A.view(self.batch.count, 2, 2), self.info
 
     def close(self):
