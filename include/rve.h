@@ -263,6 +263,20 @@ int32_t rve_tuner_lookup(int32_t n, int32_t precision, int32_t persistent, int32
                          int32_t* block_threads);
 void rve_tuner_clear(void);
 
+/* Ensemble statistics (host memory, host arithmetic, FP64, summed in
+ * index order so that results do not depend on how the realizations were
+ * distributed).  A: double[N][4] (a11, a12, a21, a22) of N >= 2
+ * realizations of RVE size L in d dimensions.  Outputs (each nullable):
+ *   mean[4]   empirical mean (Eq. "A_hom_Empir");
+ *   var[4]    unbiased sample variance of each entry;
+ *   std12     sqrt(mean a12^2) (Eq. "Var1"), stddiff sqrt(mean (a11-a22)^2)
+ *             (Eq. "Var2") -- the paper's estimators, no mean subtracted;
+ *   Q[16]     L^d/(N-1) sum_n (A_n - mean)(x)(A_n - mean), the 4x4 Kronecker
+ *             unfolding of the quartic tensor of Eq. "quartic" (row/column
+ *             order a11, a12, a21, a22). */
+rve_status rve_statistics(const double* A, int64_t N, double L, int32_t d, double* mean,
+                          double* var, double* std12, double* stddiff, double* Q);
+
 /* Allocation-free variant of rve_a_hom, for callers that cannot allocate
  * device memory: programs whose device memory is all owned by their own pool
  * allocator, and latency-critical loops that cannot afford cudaMalloc /

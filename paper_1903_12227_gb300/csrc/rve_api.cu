@@ -410,6 +410,37 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
     return cudaStreamSynchronize(s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
+rve_status rve_statistics(const double* A, int64_t N, double L, int32_t d, double* mean,
+                          double* var, double* std12, double* stddiff, double* Q) {
+    if (!A || N < 2 || !(L > 0.0) || d < 1) return RVE_EINVAL;
+    double m[4] = {0, 0, 0, 0};
+    for (int64_t k = 0; k < N; ++k)
+        for (int e = 0; e < 4; ++e) m[e] += A[4 * k + e];
+    for (int e = 0; e < 4; ++e) m[e] /= (double)N;
+    double c[16];
+    for (int e = 0; e < 16; ++e) c[e] = 0.0;
+    double s12 = 0.0, sd = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        double dev[4];
+        for (int e = 0; e < 4; ++e) dev[e] = A[4 * k + e] - m[e];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) c[4 * i + j] += dev[i] * dev[j];
+        s12 += A[4 * k + 1] * A[4 * k + 1];
+        const double df = A[4 * k + 0] - A[4 * k + 3];
+        sd += df * df;
+    }
+    const double Ld = std::pow(L, (double)d);
+    for (int e = 0; e < 4; ++e) {
+        if (mean) mean[e] = m[e];
+        if (var) var[e] = c[5 * e] / (double)(N - 1);
+    }
+    if (Q)
+        for (int e = 0; e < 16; ++e) Q[e] = Ld * c[e] / (double)(N - 1);
+    if (std12) *std12 = std::sqrt(s12 / (double)N);
+    if (stddiff) *stddiff = std::sqrt(sd / (double)N);
+    return RVE_OK;
+}
+
 void rve_profile_enable(int32_t on) { profile_enable(on != 0); }
 
 int32_t rve_profile_read(double* ms, int64_t* launches) {

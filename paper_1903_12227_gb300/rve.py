@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.rve_homogenize_workspace_size.argtypes = [vp, i32, vp]
         L.rve_homogenize_host.restype = i32
         L.rve_homogenize_host.argtypes = [vp, i32, vp, vp, vp, vp, sz, vp]
+        L.rve_statistics.restype = i32
+        L.rve_statistics.argtypes = [vp, i64, dbl, i32, vp, vp, vp, vp, vp]
         L.rve_plan_create.restype = i32
         L.rve_plan_create.argtypes = [vp, i32, vp, ctypes.POINTER(vp)]
         L.rve_plan_workspace_size.restype = sz
@@ -401,6 +403,20 @@ def tuner_lookup(n: int, precision: int, persistent: bool):
 
 def tuner_clear() -> None:
     lib().rve_tuner_clear()
+
+
+def statistics(A, L: float, d: int = 2) -> dict:
+    """Ensemble statistics of homogenized matrices A [N,2,2] (host, FP64, index order)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(-1, 4))
+    mean, var, Q = np.zeros(4), np.zeros(4), np.zeros(16)
+    s12, sd = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    vp = ctypes.c_void_p
+    check(lib().rve_statistics(a.ctypes.data_as(vp), a.shape[0], float(L), int(d),
+                               mean.ctypes.data_as(vp), var.ctypes.data_as(vp), ctypes.byref(s12),
+                               ctypes.byref(sd), Q.ctypes.data_as(vp)), "rve_statistics")
+    return {"mean": mean.reshape(2, 2), "var": var.reshape(2, 2), "std12_paper": s12.value,
+            "stddiff_paper": sd.value, "Q": Q.reshape(4, 4), "count": a.shape[0]}
 
 
 def profile_enable(on: bool = True) -> None:
