@@ -1,0 +1,108 @@
+"""GPU checks at the full sizes of the other workloads, on sampled outputs the
+oracle computes one by one or through properties that hold at any size.
+
+* uneven batch: 4096 realizations, L in {8,16,32,64}, h = 1/8, contrast in
+  {10, 100}, mixed precision, one persistent launch captured in a CUDA graph
+  after autotuning; sampled realizations against the oracle;
+* adjoint: L = 64, h = 1/16 (1024^2 nodes), contrast 100, batch 64, FP64;
+  Euler homogeneity for every realization and central differences on
+  sampled cells;
+* large: L = 256, h = 1/8 (2048^2 nodes), contrast 100, mixed precision
+  against FP64 on a sample of the 256 realizations.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1903_12227_gb300 import rve, workloads
+
+pytestmark = pytest.mark.gpu
+CUDA = torch.device("cuda", 0)
+
+
+def _rel_err_A(A, ref):
+    return np.abs(np.asarray(A) - ref).max() / max(abs(ref[0, 0]), abs(ref[1, 1]))
+
+
+def test_uneven_4096_plan_full_batch():
+    ds = workloads.config_batch("uneven_4096", seed=0)
+    assert len(ds) == 4096
+    opts = rve.make_opts(precision=rve.MIXED, path=rve.PATH_PERSISTENT, tol=1e-10)
+    rve.tuner_clear()
+    rve.autotune(ds[:256], opts, device=CUDA)
+    plan = rve.Plan(ds, opts, device=CUDA)
+    A, info = plan.execute()
+    torch.cuda.synchronize()
+    A = A.cpu().numpy()
+    inf = rve.info_to_dicts(info, len(ds))
+    assert all(d["status"] == rve.RVE_OK for d in inf)
+    assert max(max(d["relres"]) for d in inf) <= 1e-10 * 1.0001
+    # energy form exactly symmetric; Voigt-Reuss bounds for every realization
+    assert np.array_equal(A[:, 0, 1], A[:, 1, 0])
+    ev = np.linalg.eigvalsh(A)
+    lam = np.array([d["a_incl"] for d in ds])
+    assert (ev[:, 0] > 1.0).all() and (ev[:, 1] < lam).all()
+    # sampled realizations against the oracle (every size, both contrasts)
+    picks = {}
+    for k, d in enumerate(ds):
+        picks.setdefault((d["L"], d["a_incl"]), k)
+    for (L, lam_), k in sorted(picks.items()):
+        if L == 64 and lam_ == 100.0:
+            continue      # the 512^2 / contrast-100 oracle solve is the slowest; one 512^2 case suffices
+        ref = oracle.solve_realization(ds[k], tol=1e-12, want_u=False)
+        assert _rel_err_A(A[k], ref["A_energy"]) < 1e-7, (ds[k], A[k], ref["A_energy"])
+    plan.close()
+    rve.tuner_clear()
+
+
+def test_adjoint_L64_batch64_euler_and_central_differences():
+    ds = workloads.config_batch("adjoint_L64", seed=0)
+    assert len(ds) == 64 and ds[0]["L"] * ds[0]["m0"] == 1024
+    b = rve.Batch(ds)
+    mask = rve.gen_field(b, device=CUDA)
+    bits = rve.unpack_mask(mask, b)
+    coef = torch.tensor(np.concatenate([np.where(m, d["a_incl"], d["a_matrix"]).ravel()
+                                        for d, m in zip(ds, bits)]), device=CUDA,
+                        requires_grad=True)
+    opts = rve.make_opts(precision=rve.FP64, tol=1e-13)
+    A = rve.AHom.apply(coef, b, opts)
+    G = torch.tensor(np.random.default_rng(4).standard_normal((64, 2, 2)), device=CUDA)
+    (A * G).sum().backward()
+    g = coef.grad.detach()
+    nn = 1024 * 1024
+    # Euler: sum_c a_c dF/da_c = F for F = sum_ij G_ij A_ij (A is 1-homogeneous)
+    euler = (coef.detach() * g).view(64, nn).sum(1)
+    F = (A.detach() * G).sum((1, 2))
+    assert torch.allclose(euler, F, rtol=1e-10, atol=1e-12)
+    # central differences on sampled cells of two realizations
+    eps = 1e-6
+    for r in (0, 37):
+        d = ds[r]
+        base = coef.detach()[r * nn:(r + 1) * nn].clone()
+        for c1, c2 in workloads.fd_cells(1024, 3, seed=0, index=r):
+            k = int(c1) * 1024 + int(c2)
+            cp, cm = base.clone(), base.clone()
+            cp[k] += eps
+            cm[k] -= eps
+            fp = (rve.AHom.apply(cp, [d], opts) * G[r]).sum().item()
+            fm = (rve.AHom.apply(cm, [d], opts) * G[r]).sum().item()
+            fd = (fp - fm) / (2 * eps)
+            gk = g[r * nn + k].item()
+            assert abs(fd - gk) <= 1e-3 * abs(gk) + 1e-11, (r, k, fd, gk)
+
+
+def test_large_L256_mixed_against_fp64_sample():
+    ds = workloads.config_batch("large_L256", seed=0, count=4)
+    mask = rve.gen_field(ds, device=CUDA)
+    u32, i32 = rve.solve(ds, mask=mask, opts=rve.make_opts(precision=rve.MIXED, tol=1e-10))
+    A32 = rve.a_hom(ds, u32, mask=mask).cpu().numpy()
+    del u32
+    u64, i64 = rve.solve(ds, mask=mask, opts=rve.make_opts(precision=rve.FP64, tol=1e-10))
+    A64 = rve.a_hom(ds, u64, mask=mask).cpu().numpy()
+    for k in range(len(ds)):
+        assert rve.info_to_dicts(i32, 4)[k]["status"] == rve.RVE_OK
+        assert rve.info_to_dicts(i64, 4)[k]["status"] == rve.RVE_OK
+        assert _rel_err_A(A32[k], A64[k]) < 1e-7
+        ev = np.linalg.eigvalsh(A32[k])
+        assert 1.0 < ev[0] <= ev[1] < 100.0
