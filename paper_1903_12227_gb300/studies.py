@@ -64,24 +64,32 @@ def variance_study(Ls=(32, 64, 128, 256), N=256, contrast=100.0, m0=8, seed=0,
     return rows
 
 
-def paper_descs(L: int, N: int, seed: int = 0) -> list:
+def paper_descs(L: int, N: int, seed: int = 0, count: str = "fixed") -> list:
     """The paper's statistics model: m0 = 4, inclusions of side 1/2 (alpha =
-    1/4), L^2 of them, values 0.4 (matrix) and 1 (inclusions)."""
-    return [workloads.realization(L, 4, 1.0 / 0.4, seed, k, density=1.0, side_units=0.5,
-                                  a_matrix=0.4) for k in range(N)]
+    1/4), values 0.4 (matrix) and 1 (inclusions); L^2 inclusions per
+    realization (count="fixed"), or a Poisson number of mean L^2
+    (count="poisson", one reading of Sec. 2's placement)."""
+    ds = [workloads.realization(L, 4, 1.0 / 0.4, seed, k, density=1.0, side_units=0.5,
+                                a_matrix=0.4) for k in range(N)]
+    if count == "poisson":
+        g = np.random.default_rng([seed, L, 11])
+        for d, m in zip(ds, g.poisson(L * L, size=N)):
+            d["n_incl"] = int(m)
+    return ds
 
 
-def paper_study(Ls=(8, 16, 32, 64), N=10000, seed=0, batch_nodes=1 << 26) -> list:
+def paper_study(Ls=(8, 16, 32, 64), N=10000, seed=0, batch_nodes=1 << 26,
+                count: str = "fixed") -> list:
     rows = []
     opts = rve.make_opts(scheme=rve.LUMPED, precision=rve.MIXED, tol=1e-8)
     for L in Ls:
         n = 4 * L
         t0 = time.perf_counter()
-        A, infos = solve_ensemble(paper_descs(L, N, seed), opts,
+        A, infos = solve_ensemble(paper_descs(L, N, seed, count), opts,
                                   batch=max(1, batch_nodes // (n * n)))
         dt = time.perf_counter() - t0
         st = rve.statistics(A, L)
-        rows.append({"L": L, "N": N, "seconds": dt,
+        rows.append({"L": L, "N": N, "count": count, "seconds": dt,
                      "failed": sum(1 for i in infos if i["status"] != rve.RVE_OK),
                      "mean_a11": float(st["mean"][0, 0]), "mean_a22": float(st["mean"][1, 1]),
                      "mean_a12": float(st["mean"][0, 1]),
@@ -100,12 +108,14 @@ def main(argv=None):
     ap.add_argument("--Ls", type=int, nargs="+")
     ap.add_argument("--N", type=int)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--count", choices=["fixed", "poisson"], default="fixed")
     ap.add_argument("--json")
     a = ap.parse_args(argv)
     if a.study == "variance":
         rows = variance_study(Ls=tuple(a.Ls or (32, 64, 128, 256)), N=a.N or 256, seed=a.seed)
     else:
-        rows = paper_study(Ls=tuple(a.Ls or (8, 16, 32, 64)), N=a.N or 10000, seed=a.seed)
+        rows = paper_study(Ls=tuple(a.Ls or (8, 16, 32, 64)), N=a.N or 10000, seed=a.seed,
+                           count=a.count)
     txt = json.dumps({"study": a.study, "rows": rows})
     if a.json:
         with open(a.json, "w") as f:
