@@ -126,6 +126,12 @@ __device__ __forceinline__ double2 rhs_at(const Cells4& a, double h) {
     return make_double2(hh * ((a.z0m + a.z00) - (a.mm + a.m0)), hh * ((a.m0 + a.z00) - (a.mm + a.z0m)));
 }
 
+// Reciprocal of the preconditioner's symbol: the approximate hardware
+// reciprocal in FP32 (a preconditioner needs no correct rounding), exact
+// division in FP64.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
 // Conversions between the FP64 and FP32 pair types.
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }

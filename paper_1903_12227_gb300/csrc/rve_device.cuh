@@ -214,6 +214,43 @@ __host__ __device__ __forceinline__ int seq_stride(int n) {
 // Where the last Stockham stage leaves the transform.
 enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 
+// A thread's twiddle factors for every stage after the first (at most three
+// for n <= 2048): they depend only on the thread and the stage, so a kernel
+// that runs several transforms loads them once.  Slot layout per stage:
+// radix 8: w[r-1] for r = 1..7; radix 4: w[3b + r-1] for butterfly b = 0,1;
+// radix 2: w[b] for b = 0..3.
+template <typename V> struct TwCache { V w[3][7]; };
+
+template <typename V>
+__device__ __forceinline__ void load_twiddles(TwCache<V>& c, int log2n, int t,
+                                              const V* __restrict__ tw) {
+    const int T = 1 << (log2n - 3);
+    int log2Ns = 3, rem = log2n - 3, s = 0;   // the first stage is radix 8 without twiddles
+    while (rem > 0) {
+        const int lr = rem >= 3 ? 3 : rem;
+        const int Ns = 1 << log2Ns;
+        const int twshift = log2n - log2Ns - lr;
+        if (lr == 3) {
+            const int k = t & (Ns - 1);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) c.w[s][r - 1] = tw[(r * k) << twshift];
+        } else if (lr == 2) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int k = (t + b * T) & (Ns - 1);
+#pragma unroll
+                for (int r = 1; r < 4; ++r) c.w[s][3 * b + r - 1] = tw[(r * k) << twshift];
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) c.w[s][b] = tw[((t + b * T) & (Ns - 1)) << twshift];
+        }
+        log2Ns += lr;
+        rem -= lr;
+        ++s;
+    }
+}
+
 // Forward DFT (unnormalised) of one sequence of length n = 2^log2n >= 32,
 // cooperatively by T = n/8 threads (t in [0, T)).  On entry thread t holds
 // v[m] = x[t + m T], m = 0..7 -- exactly the inputs of its butterflies in
@@ -226,18 +263,17 @@ enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 //   FFT_TO_REGS: v[m] = X[t + m T], buf untouched by the last stage, no
 //                trailing barrier;
 //   FFT_TO_BOTH: both, then a barrier.
-// Threads with active == false only take part in the barriers.
-// tw[m] = exp(-2 pi i m/n).
+// Threads with active == false only take part in the barriers.  tc: the
+// thread's twiddles (load_twiddles with tw[m] = exp(-2 pi i m/n)).
 template <int FINAL, typename V>
 __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
-                                        const V* __restrict__ tw, bool active) {
+                                        const TwCache<V>& tc, bool active) {
     const int T = 1 << (log2n - 3);
-    int log2Ns = 0, rem = log2n;
+    int log2Ns = 0, rem = log2n, st = -1;
 #pragma unroll 1
     while (true) {
         const int lr = rem >= 3 ? 3 : rem;
         const int Ns = 1 << log2Ns;
-        const int twshift = log2n - log2Ns - lr;
         const bool last = (rem == lr);
         const bool to_smem = !last || FINAL != FFT_TO_REGS;
         const bool to_regs = last && FINAL != FFT_TO_SMEM;
@@ -247,7 +283,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                 const int k = t & (Ns - 1);
                 if (Ns > 1) {
 #pragma unroll
-                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[(r * k) << twshift]);
+                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tc.w[st][r - 1]);
                 }
                 dft8(v);   // outputs stay in v[r]: the last stage's slots
                 if (to_smem) {
@@ -262,9 +298,9 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                     const int j = t + b * T, k = j & (Ns - 1);
                     V a0 = v[b], a1 = v[b + 2], a2 = v[b + 4], a3 = v[b + 6];
                     if (Ns > 1) {
-                        a1 = cmul(a1, tw[k << twshift]);
-                        a2 = cmul(a2, tw[(2 * k) << twshift]);
-                        a3 = cmul(a3, tw[(3 * k) << twshift]);
+                        a1 = cmul(a1, tc.w[st][3 * b + 0]);
+                        a2 = cmul(a2, tc.w[st][3 * b + 1]);
+                        a3 = cmul(a3, tc.w[st][3 * b + 2]);
                     }
                     dft4(a0, a1, a2, a3);
                     o[b] = a0; o[b + 2] = a1; o[b + 4] = a2; o[b + 6] = a3;
@@ -286,7 +322,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                 for (int b = 0; b < 4; ++b) {
                     const int j = t + b * T, k = j & (Ns - 1);
                     V a0 = v[b], a1 = v[b + 4];
-                    if (Ns > 1) a1 = cmul(a1, tw[k << twshift]);
+                    if (Ns > 1) a1 = cmul(a1, tc.w[st][b]);
                     dft2(a0, a1);
                     o[b] = a0; o[b + 4] = a1;
                     if (to_smem) {
@@ -303,6 +339,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
         }
         log2Ns += lr;
         rem -= lr;
+        ++st;
         if (last) {
             if (FINAL != FFT_TO_REGS) __syncthreads();
             break;

@@ -228,7 +228,8 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
     const T bx = bsc[0], by = bsc[1];
     const T alx = bsc[2], aly = bsc[3];
     const V* Tin = static_cast<const V*>(c.T);
-    const V* tw = twiddles<V>(c.tb, n);
+    TwCache<V> twc;
+    load_twiddles(twc, d.log2n, L.t, twiddles<V>(c.tb, n));   // once for all row groups
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
         const int q = g0 + L.qq;
         const bool active = q < TR + 2;
@@ -239,7 +240,7 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
             for (int m = 0; m < 8; ++m) v[m] = Tin[node_of<V>(d, row, L.t + m * L.T)];
         }
         V* buf = Pt + (active ? q : 0) * SEQ;
-        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
+        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, twc, active);
         V pn[8];
         if (active) {
             const bool own = (q >= 1 && q <= TR);
@@ -325,7 +326,9 @@ template <typename V>
 __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d, int row,
                                                   const RowLayout& L, const V* tw, bool active,
                                                   V* __restrict__ out) {
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
+    TwCache<V> twc;
+    load_twiddles(twc, d.log2n, L.t, tw);
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, twc, active);
     if (active) {
         const int n = d.n;
 #pragma unroll
@@ -451,13 +454,14 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
     const bool active = t < T;
     const int SEQ = seq_stride(n);
     V* buf = smem + (active ? cc : 0) * SEQ;
-    const V* tw = twiddles<V>(tb, n);
     V v[8];
     if (active) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
     }
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, tw, active);   // barrier: csc visible
+    TwCache<V> twc;   // shared by the forward and the inverse transform
+    load_twiddles(twc, d.log2n, t < T ? t : 0, twiddles<V>(tb, n));
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, twc, active);   // barrier: csc visible
     const Ts n2c0 = csc[0], n2d = csc[1];
     const bool drop0 = (n2d == (Ts)0);
     const int k2 = c0 + cc;
@@ -472,7 +476,7 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
             const V z = v[m];
             const V zm = buf[pidx((n - k1) & (n - 1))];
             const Ts sig = n2c0 * (lap[k1] + lap2) + n2d;
-            const Ts inv = (k1 == 0 && k2 == 0 && drop0) ? (Ts)0 : (Ts)1 / sig;
+            const Ts inv = (k1 == 0 && k2 == 0 && drop0) ? (Ts)0 : fast_rcp(sig);
             const Ts w = q4 * inv;
             const Ts apx = z.x + zm.x, apy = z.y - zm.y;   // 2 A
             const Ts amx = z.x - zm.x, amy = z.y + zm.y;   // 2 i B
@@ -483,7 +487,7 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
             v[m] = mk<V>(z.x * inv, -(z.y * inv));        // conj(s Z)
         }
     }
-    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, tw, active);   // its first barrier ends the reads
+    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, twc, active);   // its first barrier ends the reads
     if (active) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
