@@ -181,6 +181,8 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_partC = take(sizeof(double) * 2 * (size_t)p.tilesC);
     p.o_partA = take(sizeof(double) * 8 * (size_t)p.tilesA);
     p.o_ctl = take(sizeof(int32_t) * 64);
+    p.o_uscal = take(sizeof(double) * 2 * (size_t)batch);
+    p.o_cnt = take(sizeof(int32_t) * (size_t)batch);
     if (need_vectors) {
         const size_t vec = (size_t)p.nodes * p.vbytes;
         p.o_X = take(vec);

@@ -2,10 +2,9 @@
 //
 // * complex helpers on float2 / double2;
 // * DotAcc: per-thread dot-product accumulators.  FP64 data accumulate in
-//   double.  FP32 data form each product exactly (fmaf error-free
-//   transformation) and sum it in a double-float (hi, lo) pair, so every
-//   inner product reaches FP64-class accuracy without FP64 arithmetic per
-//   element; partial sums leave the thread as double;
+//   double.  FP32 data: each thread sums its own <= 8 products in FP32, the
+//   block combines the thread sums in double-float and the blocks are
+//   combined in FP64 -- no long FP32 sums and no per-element FP64 work;
 // * deterministic warp / block reductions (fixed tree order);
 // * a register-resident Stockham FFT of length n = 2^p (radix 8, then 4 or
 //   2) with one padded shared-memory buffer per sequence, used for the
@@ -52,21 +51,15 @@ template <> struct DotAcc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// double-float accumulation: exact product (hi + lo), then TwoSum into
-// (s_hi, s_lo) (Knuth's TwoSum; Dekker/Ogita-Rump-Oishi error-free
-// transformations).
+// FP32 data: a thread sums only its own few (<= 8) products, with fused
+// multiply-adds in FP32; the block then combines the per-thread sums in
+// double-float (TwoSum, see block_sum2) and the blocks are combined in FP64,
+// so no sum longer than 8 terms is formed in FP32.  (hi, lo) is the
+// double-float pair of the block tree; lo stays 0 within a thread.
 template <> struct DotAcc<float> {
     float hi, lo;
     __device__ __forceinline__ DotAcc() : hi(0.f), lo(0.f) {}
-    __device__ __forceinline__ void add(float a, float b) {
-        float p = a * b;
-        float pe = fmaf(a, b, -p);        // exact: a*b = p + pe
-        float t = hi + p;
-        float bv = t - hi;
-        float e = (hi - (t - bv)) + (p - bv);  // exact: hi + p = t + e
-        hi = t;
-        lo += e + pe;
-    }
+    __device__ __forceinline__ void add(float a, float b) { hi = fmaf(a, b, hi); }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -214,43 +207,6 @@ __host__ __device__ __forceinline__ int seq_stride(int n) {
 // Where the last Stockham stage leaves the transform.
 enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 
-// A thread's twiddle factors for every stage after the first (at most three
-// for n <= 2048): they depend only on the thread and the stage, so a kernel
-// that runs several transforms loads them once.  Slot layout per stage:
-// radix 8: w[r-1] for r = 1..7; radix 4: w[3b + r-1] for butterfly b = 0,1;
-// radix 2: w[b] for b = 0..3.
-template <typename V> struct TwCache { V w[3][7]; };
-
-template <typename V>
-__device__ __forceinline__ void load_twiddles(TwCache<V>& c, int log2n, int t,
-                                              const V* __restrict__ tw) {
-    const int T = 1 << (log2n - 3);
-    int log2Ns = 3, rem = log2n - 3, s = 0;   // the first stage is radix 8 without twiddles
-    while (rem > 0) {
-        const int lr = rem >= 3 ? 3 : rem;
-        const int Ns = 1 << log2Ns;
-        const int twshift = log2n - log2Ns - lr;
-        if (lr == 3) {
-            const int k = t & (Ns - 1);
-#pragma unroll
-            for (int r = 1; r < 8; ++r) c.w[s][r - 1] = tw[(r * k) << twshift];
-        } else if (lr == 2) {
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int k = (t + b * T) & (Ns - 1);
-#pragma unroll
-                for (int r = 1; r < 4; ++r) c.w[s][3 * b + r - 1] = tw[(r * k) << twshift];
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) c.w[s][b] = tw[((t + b * T) & (Ns - 1)) << twshift];
-        }
-        log2Ns += lr;
-        rem -= lr;
-        ++s;
-    }
-}
-
 // Forward DFT (unnormalised) of one sequence of length n = 2^log2n >= 32,
 // cooperatively by T = n/8 threads (t in [0, T)).  On entry thread t holds
 // v[m] = x[t + m T], m = 0..7 -- exactly the inputs of its butterflies in
@@ -263,17 +219,18 @@ __device__ __forceinline__ void load_twiddles(TwCache<V>& c, int log2n, int t,
 //   FFT_TO_REGS: v[m] = X[t + m T], buf untouched by the last stage, no
 //                trailing barrier;
 //   FFT_TO_BOTH: both, then a barrier.
-// Threads with active == false only take part in the barriers.  tc: the
-// thread's twiddles (load_twiddles with tw[m] = exp(-2 pi i m/n)).
+// Threads with active == false only take part in the barriers.
+// tw[m] = exp(-2 pi i m/n).
 template <int FINAL, typename V>
 __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
-                                        const TwCache<V>& tc, bool active) {
+                                        const V* __restrict__ tw, bool active) {
     const int T = 1 << (log2n - 3);
-    int log2Ns = 0, rem = log2n, st = -1;
+    int log2Ns = 0, rem = log2n;
 #pragma unroll 1
     while (true) {
         const int lr = rem >= 3 ? 3 : rem;
         const int Ns = 1 << log2Ns;
+        const int twshift = log2n - log2Ns - lr;
         const bool last = (rem == lr);
         const bool to_smem = !last || FINAL != FFT_TO_REGS;
         const bool to_regs = last && FINAL != FFT_TO_SMEM;
@@ -283,7 +240,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                 const int k = t & (Ns - 1);
                 if (Ns > 1) {
 #pragma unroll
-                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tc.w[st][r - 1]);
+                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[(r * k) << twshift]);
                 }
                 dft8(v);   // outputs stay in v[r]: the last stage's slots
                 if (to_smem) {
@@ -298,9 +255,9 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                     const int j = t + b * T, k = j & (Ns - 1);
                     V a0 = v[b], a1 = v[b + 2], a2 = v[b + 4], a3 = v[b + 6];
                     if (Ns > 1) {
-                        a1 = cmul(a1, tc.w[st][3 * b + 0]);
-                        a2 = cmul(a2, tc.w[st][3 * b + 1]);
-                        a3 = cmul(a3, tc.w[st][3 * b + 2]);
+                        a1 = cmul(a1, tw[k << twshift]);
+                        a2 = cmul(a2, tw[(2 * k) << twshift]);
+                        a3 = cmul(a3, tw[(3 * k) << twshift]);
                     }
                     dft4(a0, a1, a2, a3);
                     o[b] = a0; o[b + 2] = a1; o[b + 4] = a2; o[b + 6] = a3;
@@ -322,7 +279,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                 for (int b = 0; b < 4; ++b) {
                     const int j = t + b * T, k = j & (Ns - 1);
                     V a0 = v[b], a1 = v[b + 4];
-                    if (Ns > 1) a1 = cmul(a1, tc.w[st][b]);
+                    if (Ns > 1) a1 = cmul(a1, tw[k << twshift]);
                     dft2(a0, a1);
                     o[b] = a0; o[b + 4] = a1;
                     if (to_smem) {
@@ -339,7 +296,6 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
         }
         log2Ns += lr;
         rem -= lr;
-        ++st;
         if (last) {
             if (FINAL != FFT_TO_REGS) __syncthreads();
             break;

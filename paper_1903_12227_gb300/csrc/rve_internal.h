@@ -65,6 +65,7 @@ struct Plan {
     size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
     size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0;
     size_t o_state = 0, o_partS = 0, o_partU = 0, o_partC = 0, o_partA = 0, o_ctl = 0;
+    size_t o_uscal = 0, o_cnt = 0;
     size_t o_X = 0, o_R = 0, o_Q = 0, o_T = 0, o_P0 = 0, o_P1 = 0;
     size_t total = 0;
 };

@@ -54,6 +54,8 @@ struct Ctx {
     double* partS;
     double* partU;
     double* partC;
+    double* uscal;     // [batch][2]: the update kernel's step scalars (see finish_S)
+    int* tiles_done;   // [batch]: stencil/refine blocks finished this step
     Tables tb;
     CoefSrc cs;
     double2* u;
@@ -143,6 +145,47 @@ struct TileCoef {
     }
 };
 
+// Called by every stencil/refine block after it wrote its partial sums of
+// realization b.  The block that finishes last (atomic tile counter) sums
+// all of them in tile order -- deterministic whichever block is last -- and
+// stores the update kernel's scalars: in ITER alpha = rho / p.q (0 for a
+// frozen corrector), in REFINE 1/|r64| (0 once the corrector meets the
+// tolerance).  The update kernel then starts without any FP64 work.
+__device__ void finish_S(const Ctx& c, int b, const RState& s, bool refine) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int nt = c.startS[b + 1] - c.startS[b];
+        last = (atomicAdd(c.tiles_done + b, 1) == nt - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x < 32) {
+        __threadfence();
+        const int t0 = c.startS[b], nt = c.startS[b + 1] - t0;
+        const double sx = warp_sum_array(c.partS + 2 * (int64_t)t0, nt, 2);
+        const double sy = warp_sum_array(c.partS + 2 * (int64_t)t0 + 1, nt, 2);
+        if (threadIdx.x == 0) {
+            double a0, a1;
+            if (!refine) {
+                a0 = s.active[0] ? s.rho[0] / sx : 0.0;
+                a1 = s.active[1] ? s.rho[1] / sy : 0.0;
+            } else {
+                const double nx = sqrt(sx), ny = sqrt(sy);
+                const bool first = (s.refinements == 0);
+                const bool cx = first ? (nx == 0.0) : (nx <= c.tol * s.fnorm[0]);
+                const bool cy = first ? (ny == 0.0) : (ny <= c.tol * s.fnorm[1]);
+                a0 = cx ? 0.0 : 1.0 / nx;
+                a1 = cy ? 0.0 : 1.0 / ny;
+            }
+            c.uscal[2 * b] = a0;
+            c.uscal[2 * b + 1] = a1;
+            c.tiles_done[b] = 0;   // ready for the next step
+        }
+    }
+}
+
 // REFINE step: r64 = f - A(u + s (x + alpha p)) in FP64 for the tile's rows,
 // stored (rounded to the vector type) in q, partial |r64|^2 into partS.
 // Launched every step next to k_fused_S; blocks of realizations that are
@@ -180,6 +223,7 @@ __device__ void fused_R_tile(const Ctx& c, int tile) {
         c.partS[2 * (int64_t)tile] = sx;
         c.partS[2 * (int64_t)tile + 1] = sy;
     }
+    finish_S(c, b, s, true);
 }
 
 // ITER step: inverse row Hartley of t on the tile + halo rows (z),
@@ -228,8 +272,7 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
     const T bx = bsc[0], by = bsc[1];
     const T alx = bsc[2], aly = bsc[3];
     const V* Tin = static_cast<const V*>(c.T);
-    TwCache<V> twc;
-    load_twiddles(twc, d.log2n, L.t, twiddles<V>(c.tb, n));   // once for all row groups
+    const V* tw = twiddles<V>(c.tb, n);
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
         const int q = g0 + L.qq;
         const bool active = q < TR + 2;
@@ -240,7 +283,7 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
             for (int m = 0; m < 8; ++m) v[m] = Tin[node_of<V>(d, row, L.t + m * L.T)];
         }
         V* buf = Pt + (active ? q : 0) * SEQ;
-        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, twc, active);
+        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
         V pn[8];
         if (active) {
             const bool own = (q >= 1 && q <= TR);
@@ -306,29 +349,17 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
         c.partS[2 * (int64_t)tile] = sx;
         c.partS[2 * (int64_t)tile + 1] = sy;
     }
+    finish_S(c, b, s, false);
 }
 
 // ----------------------------------------------------------- U kernel --
-// The reductions of another kernel's partials, done redundantly (and
-// identically) by every consumer block: warp 0 sums them in a fixed order.
-__device__ __forceinline__ void reduce_pair(const double* part, int t0, int nt, double* out2) {
-    if (threadIdx.x < 32) {
-        const double a = warp_sum_array(part + 2 * (int64_t)t0, nt, 2);
-        const double b = warp_sum_array(part + 2 * (int64_t)t0 + 1, nt, 2);
-        if (threadIdx.x == 0) { out2[0] = a; out2[1] = b; }
-    }
-    __syncthreads();
-}
-
 // Row Hartley pass of the rows held in registers (v[m] = row value at
 // t + m T) into `out` (global), through the row's shared buffer.
 template <typename V>
 __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d, int row,
                                                   const RowLayout& L, const V* tw, bool active,
                                                   V* __restrict__ out) {
-    TwCache<V> twc;
-    load_twiddles(twc, d.log2n, L.t, tw);
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, twc, active);
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
     if (active) {
         const int n = d.n;
 #pragma unroll
@@ -343,7 +374,6 @@ template <typename V>
 __device__ void fused_U_tile(const Ctx& c, int blk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
-    __shared__ double sc[2];
     __shared__ typename ScalarOf<V>::T usc[2];
     const int b = find_real(c.startU, c.batch, blk);
     const RState& s = c.st[b];
@@ -360,14 +390,13 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
     V* X = static_cast<V*>(c.X);
     const V* Qv = static_cast<const V*>(c.Q);
     V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(n);
-    reduce_pair(c.partS, c.startS[b], c.startS[b + 1] - c.startS[b], sc);
     DotAcc<T> ax, ay;
     V v[8];
     if (phase == PH_ITER) {
-        // alpha = rho / p.q, formed once per block (thread 0) in FP64
+        // alpha = rho / p.q, formed by the last stencil block (finish_S)
         if (threadIdx.x == 0) {
-            usc[0] = (T)(s.active[0] ? s.rho[0] / sc[0] : 0.0);
-            usc[1] = (T)(s.active[1] ? s.rho[1] / sc[1] : 0.0);
+            usc[0] = (T)c.uscal[2 * b];
+            usc[1] = (T)c.uscal[2 * b + 1];
         }
         __syncthreads();
         const T alx = usc[0], aly = usc[1];
@@ -390,11 +419,8 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
         }
     } else {   // REFINE
         const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-        const double nx = sqrt(sc[0]), ny = sqrt(sc[1]);
-        const bool first = (s.refinements == 0);
-        const bool cx = first ? (nx == 0.0) : (nx <= c.tol * s.fnorm[0]);
-        const bool cy = first ? (ny == 0.0) : (ny <= c.tol * s.fnorm[1]);
-        const double ix = cx ? 0.0 : 1.0 / nx, iy = cy ? 0.0 : 1.0 / ny;
+        // 1 / |r64| per corrector (0 once converged), from finish_S
+        const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -459,9 +485,8 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
     }
-    TwCache<V> twc;   // shared by the forward and the inverse transform
-    load_twiddles(twc, d.log2n, t < T ? t : 0, twiddles<V>(tb, n));
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, twc, active);   // barrier: csc visible
+    const V* tw = twiddles<V>(tb, n);
+    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, tw, active);   // barrier: csc visible
     const Ts n2c0 = csc[0], n2d = csc[1];
     const bool drop0 = (n2d == (Ts)0);
     const int k2 = c0 + cc;
@@ -480,14 +505,12 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
             const Ts w = q4 * inv;
             const Ts apx = z.x + zm.x, apy = z.y - zm.y;   // 2 A
             const Ts amx = z.x - zm.x, amy = z.y + zm.y;   // 2 i B
-            ax.add(apx * w, apx);
-            ax.add(apy * w, apy);
-            ay.add(amx * w, amx);
-            ay.add(amy * w, amy);
+            ax.add(w, apx * apx + apy * apy);
+            ay.add(w, amx * amx + amy * amy);
             v[m] = mk<V>(z.x * inv, -(z.y * inv));        // conj(s Z)
         }
     }
-    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, twc, active);   // its first barrier ends the reads
+    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, tw, active);   // its first barrier ends the reads
     if (active) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -721,6 +744,7 @@ __global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
         z.phase = PH_REFINE;
         z.status = RVE_OK;
         c.st[b] = z;
+        c.tiles_done[b] = 0;
     }
     if (gid == 0) {
         c.ndone[0] = 0;                          // realizations done
@@ -802,6 +826,8 @@ static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double*
     c.partS = reinterpret_cast<double*>(w + p.o_partS);
     c.partU = reinterpret_cast<double*>(w + p.o_partU);
     c.partC = reinterpret_cast<double*>(w + p.o_partC);
+    c.uscal = reinterpret_cast<double*>(w + p.o_uscal);
+    c.tiles_done = reinterpret_cast<int*>(w + p.o_cnt);
     c.tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
     c.tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
     c.tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
