@@ -106,7 +106,8 @@ typedef struct {
     double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (0=1e-10)*/
     double delta;        /* preconditioner shift; 0 = drop the constant mode*/
     double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-5)*/
-    int32_t tile_rows;   /* stencil tile height, 0 = tuned default          */
+    int32_t tile_rows;   /* stencil tile height in node rows (1..n; n need
+                            not be a multiple), 0 = tuned or default       */
     int32_t col_tile;    /* threads of a column-transform block (power of
                             two, 32..1024); 0 = 512, or 1024 when n > 512  */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
@@ -247,7 +248,7 @@ void rve_plan_destroy(rve_plan plan);
 
 /* Autotuner.  For every distinct grid size n of the batch, times short
  * trial solves of up to 16 of its realizations for each candidate tile shape
- * (stencil tile rows 1..8; column-block threads 256/512/1024 on the fused
+ * (stencil tile heights; column-block threads 256/512/1024 on the fused
  * path, 256 on the persistent path) and records the fastest in the
  * process-wide tuner table, keyed by (n, precision, persistent).  Plans and
  * solves with opts->tile_rows == 0 and opts->col_tile == 0 then use the

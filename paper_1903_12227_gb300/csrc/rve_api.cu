@@ -52,9 +52,27 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
 static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
     const size_t seq = (size_t)seq_stride(n);
     t.tU = std::min(n, 2048 / n);
-    t.tS = 8;
-    while (t.tS > 1 && ((size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4) > 112640)
-        t.tS >>= 1;
+    // stencil tile: tS own rows + 2 halo rows, transformed G = 2048/n rows
+    // at a time; choose tS + 2 a multiple of G (no idle row slots) with the
+    // tile within ~72 KB (three blocks per SM), tS <= n.  Tiles need not
+    // divide n: the last one is shorter.
+    const int G = std::max(1, 2048 / n);
+    auto smem_of = [&](int ts) {
+        return (size_t)(ts + 2) * seq * vb + (size_t)(ts + 1) * (n / 32) * 4;
+    };
+    auto pick = [&](size_t budget) {
+        int best = 1;
+        for (int k = 1; k <= 64; ++k) {
+            const int ts = std::min(k * G - 2, n);
+            if (ts < 1) continue;
+            if (smem_of(ts) > budget) break;
+            best = ts;
+            if (ts == n) break;
+        }
+        return best;
+    };
+    t.tS = pick(73728);
+    if (t.tS < 4) t.tS = pick(112640);   // large grids: fewer, taller tiles (halo <= 50 %)
     int ts_tuned = 0, bc_tuned = 0;
     if (tuned_tiles(n, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0, &ts_tuned, &bc_tuned))
         t.tS = ts_tuned;
@@ -119,7 +137,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             return RVE_EINVAL;
         Tiles t;
         default_tiles(n, p.vbytes, p.blockC, o, t);
-        if (!pow2(t.tS) || !pow2(t.tC) || n % t.tS || n % t.tC || t.tC * (n / 8) > p.blockC)
+        if (t.tS < 1 || t.tS > n || !pow2(t.tC) || n % t.tC || t.tC * (n / 8) > p.blockC)
             return RVE_EINVAL;
         RDesc& d = p.desc[b];
         std::memset(&d, 0, sizeof(d));
@@ -142,7 +160,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         p.nodes += (int64_t)n * n;
         p.words += ((int64_t)n * n) / 32;
         p.max_log2n = std::max(p.max_log2n, d.log2n);
-        p.startS[b + 1] = p.startS[b] + n / t.tS;
+        p.startS[b + 1] = p.startS[b] + (n + t.tS - 1) / t.tS;
         p.startU[b + 1] = p.startU[b] + n / t.tU;
         p.startC[b + 1] = p.startC[b] + n / t.tC;
         p.startA[b + 1] = p.startA[b] + (int32_t)(((int64_t)n * n) / 1024);

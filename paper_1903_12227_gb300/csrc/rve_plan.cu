@@ -169,7 +169,16 @@ rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve
         std::vector<rve_realization> sub;
         for (int b = 0; b < batch && (int)sub.size() < 16; ++b)
             if (r[b].L * r[b].m0 == n) sub.push_back(r[b]);
-        const std::vector<int> tss = {1, 2, 4, 8};
+        // stencil tile heights: tS + 2 a multiple of the transform group
+        // G = 2048/n (no idle row slots), plus a few small powers of two
+        std::vector<int> tss;
+        const int G = std::max(1, 2048 / n);
+        for (int k = 1; k <= 4; ++k) tss.push_back(std::min(k * G - 2, n));
+        for (int v : {2, 4, 8}) tss.push_back(v);
+        std::sort(tss.begin(), tss.end());
+        tss.erase(std::unique(tss.begin(), tss.end()), tss.end());
+        tss.erase(std::remove_if(tss.begin(), tss.end(), [&](int v) { return v < 1 || v > n; }),
+                  tss.end());
         std::vector<int> bcs = {256, 512, 1024};
         if (base.path == RVE_PATH_PERSISTENT) bcs = {256};
         float best = 1e30f;

@@ -197,12 +197,13 @@ __device__ void fused_R_tile(const Ctx& c, int tile) {
     const RState& s = c.st[b];
     if (s.phase != PH_REFINE) return;
     const RDesc d = c.desc[b];
-    const int n = d.n, TR = d.tS;
-    const int r0 = (tile - c.startS[b]) * TR;
+    const int n = d.n;
+    const int r0 = (tile - c.startS[b]) * d.tS;
+    const int rows = min(d.tS, n - r0);   // the last tile may be shorter
     const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
     V* Q = static_cast<V*>(c.Q);
     DotAcc<double> a64x, a64y;   // exact FP64 |r64|^2
-    for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
         const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
         const Cells4 a = cells_at(c.cs, d, i, j);
         const double2 f = rhs_at(a, d.h);
@@ -237,8 +238,9 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
     const RState& s = c.st[b];
     if (s.phase != PH_ITER) return;
     const RDesc d = c.desc[b];
-    const int n = d.n, TR = d.tS;
-    const int r0 = (tile - c.startS[b]) * TR;
+    const int n = d.n;
+    const int r0 = (tile - c.startS[b]) * d.tS;
+    const int TR = min(d.tS, n - r0);   // own rows (the last tile may be shorter)
     const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
     V* Pnew = static_cast<V*>(s.parity ? c.P0 : c.P1);
     V* X = static_cast<V*>(c.X);
@@ -322,26 +324,34 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
         }
     }
     __syncthreads();
+    // q = A p on the own rows: each thread walks down a column keeping the
+    // 3 x 3 neighbourhood (and the two cell columns) in registers, so a node
+    // costs three shared loads and two cell lookups
     DotAcc<T> ax, ay;   // p.q
-    for (int idx = threadIdx.x; idx < TR * n; idx += blockDim.x) {
-        const int q = idx >> d.log2n, j = idx & (n - 1);
-        const int i = r0 + q;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-        const V* up = Pt + q * SEQ;         // row i-1
-        const V* mid = up + SEQ;            // row i
-        const V* dn = mid + SEQ;            // row i+1
-        CellsT<T> a;
-        a.mm = tc.cell(c.cs, d, q, i - 1, jm);
-        a.m0 = tc.cell(c.cs, d, q, i - 1, j);
-        a.z0m = tc.cell(c.cs, d, q + 1, i, jm);
-        a.z00 = tc.cell(c.cs, d, q + 1, i, j);
-        const V pc = mid[pidx(j)];
-        const V qv = stencil_apply<SCHEME, V>(a, up[pidx(jm)], up[pidx(j)], up[pidx(jp)],
-                                              mid[pidx(jm)], pc, mid[pidx(jp)], dn[pidx(jm)],
-                                              dn[pidx(j)], dn[pidx(jp)]);
-        Q[node_of<V>(d, i, j)] = qv;
-        ax.add(pc.x, qv.x);
-        ay.add(pc.y, qv.y);
+        const int pm = pidx(jm), p0 = pidx(j), pp = pidx(jp);
+        V u0 = Pt[pm], u1 = Pt[p0], u2 = Pt[pp];                    // row r0-1
+        V m0 = Pt[SEQ + pm], m1 = Pt[SEQ + p0], m2 = Pt[SEQ + pp];  // row r0
+        T cmm = tc.cell(c.cs, d, 0, r0 - 1, jm), cm0 = tc.cell(c.cs, d, 0, r0 - 1, j);
+        for (int q = 0; q < TR; ++q) {
+            const V* dn = Pt + (q + 2) * SEQ;                         // row r0+q+1
+            const V d0 = dn[pm], d1 = dn[p0], d2 = dn[pp];
+            const T c0m = tc.cell(c.cs, d, q + 1, r0 + q, jm);
+            const T c00 = tc.cell(c.cs, d, q + 1, r0 + q, j);
+            CellsT<T> a;
+            a.mm = cmm;
+            a.m0 = cm0;
+            a.z0m = c0m;
+            a.z00 = c00;
+            const V qv = stencil_apply<SCHEME, V>(a, u0, u1, u2, m0, m1, m2, d0, d1, d2);
+            Q[node_of<V>(d, r0 + q, j)] = qv;
+            ax.add(m1.x, qv.x);
+            ay.add(m1.y, qv.y);
+            u0 = m0; u1 = m1; u2 = m2;
+            m0 = d0; m1 = d1; m2 = d2;
+            cmm = c0m; cm0 = c00;
+        }
     }
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
