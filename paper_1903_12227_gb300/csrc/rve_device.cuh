@@ -221,13 +221,19 @@ enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 //   FFT_TO_BOTH: both, then a barrier.
 // Threads with active == false only take part in the barriers.
 // tw[m] = exp(-2 pi i m/n).
-template <int FINAL, typename V>
-__device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
+// LOG2N > 0 makes the size a compile-time constant: the stages unroll and
+// every index folds to an immediate; LOG2N == 0 takes log2n at run time.
+template <int FINAL, int LOG2N = 0, typename V>
+__device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
                                         const V* __restrict__ tw, bool active) {
+    const int log2n = LOG2N ? LOG2N : log2n_rt;
     const int T = 1 << (log2n - 3);
-    int log2Ns = 0, rem = log2n;
-#pragma unroll 1
-    while (true) {
+    const int nstages = (log2n + 2) / 3;   // radix 8, then one radix-4 or -2 tail
+#pragma unroll
+    for (int stage = 0; stage < (LOG2N ? (LOG2N + 2) / 3 : 4); ++stage) {
+        if (!LOG2N && stage >= nstages) break;
+        const int log2Ns = 3 * stage;        // every earlier stage was radix 8
+        const int rem = log2n - log2Ns;
         const int lr = rem >= 3 ? 3 : rem;
         const int Ns = 1 << log2Ns;
         const int twshift = log2n - log2Ns - lr;
@@ -294,8 +300,6 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
                 }
             }
         }
-        log2Ns += lr;
-        rem -= lr;
         if (last) {
             if (FINAL != FFT_TO_REGS) __syncthreads();
             break;
@@ -307,6 +311,16 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n, int t,
         }
     }
 }
+
+// Grid size as compile-time constants (LOG2N > 0) or run-time values (0).
+template <int LOG2N> struct Sz {
+    static constexpr int log2n = LOG2N, n = 1 << LOG2N, T = (1 << LOG2N) >> 3;
+    __device__ __forceinline__ explicit Sz(int) {}
+};
+template <> struct Sz<0> {
+    int log2n, n, T;
+    __device__ __forceinline__ explicit Sz(int l) : log2n(l), n(1 << l), T((1 << l) >> 3) {}
+};
 
 // Hartley pair from the DFT Z of (a + i b): returns (H_a(k), H_b(k)).
 template <typename V> __device__ __forceinline__ V hartley_pair(V zk, V zm) {

@@ -104,17 +104,39 @@ __device__ __forceinline__ int64_t node_of(const RDesc& d, int row, int col) {
     return d.node_off + ((int64_t)row << d.log2n) + col;
 }
 
-// Thread layout of the row kernels: 256 threads, T = n/8 per row, so
-// 256/T rows per group; qq = row within the group, t = thread within row.
+// Thread layout of the row kernels: T = n/8 threads per row, so
+// blockDim/T rows per group; qq = row within the group, t = thread within
+// row.  With a compile-time size (LOG2N > 0) T and the divisions fold.
+template <int LOG2N>
 struct RowLayout {
-    int T, qq, t, G;
-    __device__ __forceinline__ RowLayout(const RDesc& d) {
-        T = d.n >> 3;
-        G = blockDim.x / T;
-        qq = threadIdx.x / T;
-        t = threadIdx.x - qq * T;
+    Sz<LOG2N> z;
+    int qq, t, G;
+    __device__ __forceinline__ explicit RowLayout(int log2n) : z(log2n) {
+        G = blockDim.x / z.T;
+        qq = threadIdx.x / z.T;
+        t = threadIdx.x - qq * z.T;
     }
 };
+
+template <int LOG2N>
+__device__ __forceinline__ int64_t node_at(const RDesc& d, const Sz<LOG2N>& z, int row, int col) {
+    return d.node_off + ((int64_t)row << z.log2n) + col;
+}
+
+// Calls body.template operator()<LOG2N>() with the realization's size as a
+// compile-time constant (n = 32 .. 2048).
+template <typename F>
+__device__ __forceinline__ void dispatch_size(int log2n, F&& body) {
+    switch (log2n) {
+        case 5: body.template operator()<5>(); break;
+        case 6: body.template operator()<6>(); break;
+        case 7: body.template operator()<7>(); break;
+        case 8: body.template operator()<8>(); break;
+        case 9: body.template operator()<9>(); break;
+        case 10: body.template operator()<10>(); break;
+        default: body.template operator()<11>(); break;
+    }
+}
 
 // ----------------------------------------------------------- S kernel --
 template <typename V>
@@ -229,16 +251,13 @@ __device__ void fused_R_tile(const Ctx& c, int tile) {
 
 // ITER step: inverse row Hartley of t on the tile + halo rows (z),
 // p_new = z + beta p_old, x += alpha p_old (own rows), q = A p_new, p.q.
-template <typename V, int SCHEME>
-__device__ void fused_S_tile(const Ctx& c, int tile) {
+template <typename V, int SCHEME, int LOG2N>
+__device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, const RState& s,
+                                             const RDesc& d, double* red,
+                                             typename ScalarOf<V>::T* bsc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[64];   // block_sum2 scratch
-    __shared__ typename ScalarOf<V>::T bsc[6];
-    const int b = find_real(c.startS, c.batch, tile);
-    const RState& s = c.st[b];
-    if (s.phase != PH_ITER) return;
-    const RDesc d = c.desc[b];
-    const int n = d.n;
+    const Sz<LOG2N> z(d.log2n);
+    const int n = z.n;
     const int r0 = (tile - c.startS[b]) * d.tS;
     const int TR = min(d.tS, n - r0);   // own rows (the last tile may be shorter)
     const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
@@ -265,12 +284,12 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
         for (int w = threadIdx.x; w < (TR + 1) * wpr; w += blockDim.x) {
             const int mr = w / wpr, col = w - mr * wpr;
             const int row = (r0 - 1 + mr) & (n - 1);
-            mrows[w] = __ldg(c.cs.mask + d.word_off + (((int64_t)row << d.log2n) >> 5) + col);
+            mrows[w] = __ldg(c.cs.mask + d.word_off + (((int64_t)row << z.log2n) >> 5) + col);
         }
     }
     __syncthreads();
     const TileCoef<T> tc{c.cs.coef ? nullptr : mrows, wpr, bsc[4], bsc[5]};
-    const RowLayout L(d);
+    const RowLayout<LOG2N> L(z.log2n);
     const T bx = bsc[0], by = bsc[1];
     const T alx = bsc[2], aly = bsc[3];
     const V* Tin = static_cast<const V*>(c.T);
@@ -282,10 +301,10 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
         V v[8];
         if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = Tin[node_of<V>(d, row, L.t + m * L.T)];
+            for (int m = 0; m < 8; ++m) v[m] = Tin[node_at(d, z, row, L.t + m * L.z.T)];
         }
         V* buf = Pt + (active ? q : 0) * SEQ;
-        fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
+        fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
         V pn[8];
         if (active) {
             const bool own = (q >= 1 && q <= TR);
@@ -296,21 +315,21 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
             for (int h = 0; h < 8; h += 4) {
                 V po[4], xo[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) po[m] = Pold[node_of<V>(d, row, L.t + (h + m) * L.T)];
+                for (int m = 0; m < 4; ++m) po[m] = Pold[node_at(d, z, row, L.t + (h + m) * L.z.T)];
                 if (own) {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) xo[m] = X[node_of<V>(d, row, L.t + (h + m) * L.T)];
+                    for (int m = 0; m < 4; ++m) xo[m] = X[node_at(d, z, row, L.t + (h + m) * L.z.T)];
                 }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const int k = L.t + (h + m) * L.T;
+                    const int k = L.t + (h + m) * L.z.T;
                     const V z = hartley_pair(v[h + m], buf[pidx((n - k) & (n - 1))]);
                     pn[h + m] = axpy2(z, bx, by, po[m]);
                 }
                 if (own) {
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
-                        const int64_t node = node_of<V>(d, row, L.t + (h + m) * L.T);
+                        const int64_t node = node_at(d, z, row, L.t + (h + m) * L.z.T);
                         Pnew[node] = pn[h + m];
                         X[node] = axpy2(xo[m], alx, aly, po[m]);
                     }
@@ -320,7 +339,7 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
         __syncthreads();   // partner reads of this group are done
         if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) buf[pidx(L.t + m * L.T)] = pn[m];
+            for (int m = 0; m < 8; ++m) buf[pidx(L.t + m * L.z.T)] = pn[m];
         }
     }
     __syncthreads();
@@ -345,7 +364,7 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
             a.z0m = c0m;
             a.z00 = c00;
             const V qv = stencil_apply<SCHEME, V>(a, u0, u1, u2, m0, m1, m2, d0, d1, d2);
-            Q[node_of<V>(d, r0 + q, j)] = qv;
+            Q[node_at(d, z, r0 + q, j)] = qv;
             ax.add(m1.x, qv.x);
             ay.add(m1.y, qv.y);
             u0 = m0; u1 = m1; u2 = m2;
@@ -362,36 +381,44 @@ __device__ void fused_S_tile(const Ctx& c, int tile) {
     finish_S(c, b, s, false);
 }
 
+template <typename V, int SCHEME>
+__device__ void fused_S_tile(const Ctx& c, int tile) {
+    __shared__ double red[64];   // block_sum2 scratch
+    __shared__ typename ScalarOf<V>::T bsc[6];
+    const int b = find_real(c.startS, c.batch, tile);
+    const RState& s = c.st[b];
+    if (s.phase != PH_ITER) return;
+    const RDesc d = c.desc[b];
+    dispatch_size(d.log2n, [&]<int LG>() { fused_S_body<V, SCHEME, LG>(c, tile, b, s, d, red, bsc); });
+}
+
 // ----------------------------------------------------------- U kernel --
 // Row Hartley pass of the rows held in registers (v[m] = row value at
 // t + m T) into `out` (global), through the row's shared buffer.
-template <typename V>
-__device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d, int row,
-                                                  const RowLayout& L, const V* tw, bool active,
+template <typename V, int LOG2N>
+__device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc& d,
+                                                  const Sz<LOG2N>& z, int row, int t,
+                                                  const V* tw, bool active,
                                                   V* __restrict__ out) {
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, L.t, tw, active);
+    fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, t, tw, active);
     if (active) {
-        const int n = d.n;
+        const int n = z.n;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int k = L.t + m * L.T;
-            out[node_of<V>(d, row, k)] = hartley_pair(v[m], buf[pidx((n - k) & (n - 1))]);
+            const int k = t + m * z.T;
+            out[node_at(d, z, row, k)] = hartley_pair(v[m], buf[pidx((n - k) & (n - 1))]);
         }
     }
 }
 
-template <typename V>
-__device__ void fused_U_tile(const Ctx& c, int blk) {
+template <typename V, int LOG2N>
+__device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const RState& s,
+                                             const RDesc& d, double* red,
+                                             typename ScalarOf<V>::T* usc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
-    __shared__ typename ScalarOf<V>::T usc[2];
-    const int b = find_real(c.startU, c.batch, blk);
-    const RState& s = c.st[b];
     const int phase = s.phase;
-    if (phase == PH_DONE) return;
-    const RDesc d = c.desc[b];
-    const int n = d.n;
-    const RowLayout L(d);
+    const RowLayout<LOG2N> L(d.log2n);
+    const Sz<LOG2N>& z = L.z;
     const int G = d.tU;
     const int row = (blk - c.startU[b]) * G + L.qq;
     const bool active = L.qq < G;
@@ -399,7 +426,7 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
     V* R = static_cast<V*>(c.R);
     V* X = static_cast<V*>(c.X);
     const V* Qv = static_cast<const V*>(c.Q);
-    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(n);
+    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(z.n);
     DotAcc<T> ax, ay;
     V v[8];
     if (phase == PH_ITER) {
@@ -414,14 +441,14 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
             V qv[8];
 #pragma unroll
             for (int m = 0; m < 8; ++m) {   // loads first, stores after
-                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
+                const int64_t node = node_at(d, z, row, L.t + m * z.T);
                 v[m] = R[node];
                 qv[m] = Qv[node];
             }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const V rr = axpy2(v[m], -alx, -aly, qv[m]);
-                R[node_of<V>(d, row, L.t + m * L.T)] = rr;
+                R[node_at(d, z, row, L.t + m * z.T)] = rr;
                 v[m] = rr;
                 ax.add(rr.x, rr.x);
                 ay.add(rr.y, rr.y);
@@ -434,7 +461,7 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const int64_t node = node_of<V>(d, row, L.t + m * L.T);
+                const int64_t node = node_at(d, z, row, L.t + m * z.T);
                 const double2 xx = to_d2(X[node]);
                 const double2 pp = to_d2(Pold[node]);
                 double2 uu = c.u[node];
@@ -457,7 +484,19 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
         c.partU[2 * (int64_t)blk] = sx;
         c.partU[2 * (int64_t)blk + 1] = sy;
     }
-    row_hartley_store(v, buf, d, row, L, twiddles<V>(c.tb, n), active, static_cast<V*>(c.T));
+    row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, twiddles<V>(c.tb, z.n), active,
+                                static_cast<V*>(c.T));
+}
+
+template <typename V>
+__device__ void fused_U_tile(const Ctx& c, int blk) {
+    __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
+    __shared__ typename ScalarOf<V>::T usc[2];
+    const int b = find_real(c.startU, c.batch, blk);
+    const RState& s = c.st[b];
+    if (s.phase == PH_DONE) return;
+    const RDesc d = c.desc[b];
+    dispatch_size(d.log2n, [&]<int LG>() { fused_U_body<V, LG>(c, blk, b, s, d, red, usc); });
 }
 
 // ----------------------------------------------------------- C kernel --
@@ -473,18 +512,19 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
 // orthogonal up to n).  Block of C*T threads (T = n/8), thread (t, c) with c
 // fastest so that global accesses are row segments of C elements.
 // `rho_part` may be null.
-template <typename V>
-__device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
-                                   const Tables& tb, double delta, double* red,
-                                   double* rho_part) {
+template <typename V, int LOG2N>
+__device__ __forceinline__ void col_transform_body(V* __restrict__ Tg, const RDesc& d, int c0,
+                                                   V* smem, const Tables& tb, double delta,
+                                                   double* red, double* rho_part,
+                                                   typename ScalarOf<V>::T* csc) {
     typedef typename ScalarOf<V>::T Ts;
-    __shared__ Ts csc[2];
     if (threadIdx.x == 0) {
         const double n2 = (double)d.n * (double)d.n;
         csc[0] = (Ts)(n2 * d.c0);
         csc[1] = (Ts)(n2 * delta);
     }
-    const int n = d.n, C = d.tC, T = n >> 3;
+    const Sz<LOG2N> z(d.log2n);
+    const int n = z.n, C = d.tC, T = z.T;
     const int tid = threadIdx.x;
     const int t = tid / C, cc = tid - (tid / C) * C;
     const bool active = t < T;
@@ -493,10 +533,10 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
     V v[8];
     if (active) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = Tg[node_of<V>(d, t + m * T, c0 + cc)];
+        for (int m = 0; m < 8; ++m) v[m] = Tg[node_at(d, z, t + m * T, c0 + cc)];
     }
     const V* tw = twiddles<V>(tb, n);
-    fft_reg<FFT_TO_BOTH>(v, buf, d.log2n, t, tw, active);   // barrier: csc visible
+    fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, t, tw, active);   // barrier: csc visible
     const Ts n2c0 = csc[0], n2d = csc[1];
     const bool drop0 = (n2d == (Ts)0);
     const int k2 = c0 + cc;
@@ -520,12 +560,12 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
             v[m] = mk<V>(z.x * inv, -(z.y * inv));        // conj(s Z)
         }
     }
-    fft_reg<FFT_TO_REGS>(v, buf, d.log2n, t, tw, active);   // its first barrier ends the reads
+    fft_reg<FFT_TO_REGS, LOG2N>(v, buf, z.log2n, t, tw, active);   // its first barrier ends the reads
     if (active) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const V o = v[m];
-            Tg[node_of<V>(d, t + m * T, c0 + cc)] = mk<V>(o.x, -o.y);
+            Tg[node_at(d, z, t + m * T, c0 + cc)] = mk<V>(o.x, -o.y);
         }
     }
     if (rho_part) {
@@ -533,6 +573,17 @@ __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V
         block_sum2(ax, ay, red, sx, sy);
         if (tid == 0) { rho_part[0] = sx; rho_part[1] = sy; }
     }
+}
+
+// Column pass of one tile (any size): dispatches to the sized body.
+template <typename V>
+__device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
+                                   const Tables& tb, double delta, double* red,
+                                   double* rho_part) {
+    __shared__ typename ScalarOf<V>::T csc[2];
+    dispatch_size(d.log2n, [&]<int LG>() {
+        col_transform_body<V, LG>(Tg, d, c0, smem, tb, delta, red, rho_part, csc);
+    });
 }
 
 template <typename V>
@@ -1084,17 +1135,19 @@ __global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ d
     const int blk = blockIdx.x + tile0;
     const int b = find_real(startU, batch, blk);
     const RDesc d = desc[b];
-    const RowLayout L(d);
-    const int G = d.tU;
-    const int row = (blk - startU[b]) * G + L.qq;
-    const bool active = L.qq < G;
-    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(d.n);
-    V v[8];
-    if (active) {
+    dispatch_size(d.log2n, [&]<int LG>() {
+        const RowLayout<LG> L(d.log2n);
+        const int G = d.tU;
+        const int row = (blk - startU[b]) * G + L.qq;
+        const bool active = L.qq < G;
+        V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(L.z.n);
+        V v[8];
+        if (active) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = in[node_of<V>(d, row, L.t + m * L.T)];
-    }
-    row_hartley_store(v, buf, d, row, L, twiddles<V>(tb, d.n), active, out);
+            for (int m = 0; m < 8; ++m) v[m] = in[node_at(d, L.z, row, L.t + m * L.z.T)];
+        }
+        row_hartley_store<V, LG>(v, buf, d, L.z, row, L.t, twiddles<V>(tb, L.z.n), active, out);
+    });
 }
 
 template <typename V>
