@@ -45,7 +45,10 @@ def needs_build() -> bool:
 
 def _compile(src: str, extra: list) -> str:
     obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
+    # the solver's size dispatch uses templated lambdas (C++20); the other
+    # units stay C++17
+    std = "-std=c++20" if src == "rve_solver.cu" else "-std=c++17"
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", std, "-Xcompiler", "-fPIC",
            "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
