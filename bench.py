@@ -37,13 +37,15 @@ CONFIG_DESC = ("L=32, h=1/16 (512x512 nodes, 262144 unknowns per corrector), con
                "717 inclusions of side 1 (density 0.7), PCG tol 1e-10 on the true residual")
 
 # Algorithmic bytes per node (both correctors, float2 = 8 B per node pair) of
-# the fused pipeline kernels, per launch: S reads t, p_old, x and writes
-# p_new, q, x; in REFINE it reads u (16 B), x, p and writes q.  U reads r, q
-# and writes r, t; in REFINE it reads x, p, u, q and writes u, x, r, t.
-# C reads and writes t.  The coefficient bitmask adds 1/8 B per node.
+# the fused pipeline kernels, per realization-step.  ITER: S reads t, p_old,
+# x and writes p_new, q, x; U reads r, q and writes r, t; C reads and writes
+# t.  REFINE: R reads u (double word, 16 B), x, p and writes q; U reads u,
+# x, p, q and writes u, x, r, t; C as in ITER.  The coefficient bitmask adds
+# 1/8 B per node to R and S.
 BYTES_PER_NODE = {
-    "stencil": {"iter": 6 * 8 + 0.125, "refine": 16 + 8 + 8 + 8 + 0.125},
-    "update_row": {"iter": 4 * 8, "refine": 8 + 8 + 16 + 8 + 16 + 8 + 8 + 8},
+    "refine": {"iter": 0.0, "refine": 16 + 8 + 8 + 8 + 0.125},
+    "stencil": {"iter": 6 * 8 + 0.125, "refine": 0.0},
+    "update_row": {"iter": 4 * 8, "refine": 16 + 8 + 8 + 8 + 16 + 8 + 8 + 8},
     "column": {"iter": 2 * 8, "refine": 2 * 8},
 }
 
@@ -276,23 +278,28 @@ def run_ours(args):
     refines = sum(d["refinements"] for d in info_d)
     nodes = 512 * 512
 
-    # roofline of the dominant fused kernel (live CUDA-event timing)
-    kinds = ("stencil", "update_row", "column")
-    dom = max(kinds, key=lambda k: prof[k]["ms"])
-    bpn = BYTES_PER_NODE[dom]
-    alg_bytes = nodes * (steps_iter * bpn["iter"] + refines * bpn["refine"])
-    launches_dom = max(prof[dom]["launches"], 1)
-    avg_launch_s = prof[dom]["ms"] / 1e3 / launches_dom
-    bytes_per_launch = alg_bytes / launches_dom
-    achieved = bytes_per_launch / avg_launch_s / 1e9
+    # roofline of the dominant fused kernel (live CUDA-event timing on the
+    # launching stream): algorithmic bytes / average launch duration
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    tr = ncu_traffic(dom)
-    traffic = None if tr is None else tr * nodes * (steps_iter + refines) / launches_dom
+
+    def kernel_rate(kind):
+        bpn = BYTES_PER_NODE[kind]
+        alg = nodes * (steps_iter * bpn["iter"] + refines * bpn["refine"])
+        nl = max(prof[kind]["launches"], 1)
+        avg_s = prof[kind]["ms"] / 1e3 / nl
+        return alg / nl, avg_s, (alg / nl) / avg_s / 1e9 if avg_s > 0 else 0.0
+
+    dom = max(("stencil", "update_row", "column"), key=lambda k: prof[k]["ms"])
+    bytes_per_launch, avg_launch_s, achieved = kernel_rate(dom)
+    tr = ncu_traffic(dom)   # per node of an ITER step
+    launches_dom = max(prof[dom]["launches"], 1)
+    traffic = None if tr is None else tr * nodes * steps_iter / launches_dom
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": avg_launch_s * 1e6,
+                "per_kernel_gbs": {k: kernel_rate(k)[2] for k in BYTES_PER_NODE},
                 "time_share": {k: prof[k]["ms"] / max(sum(prof[j]["ms"] for j in prof), 1e-9)
                                for k in prof}}
 

@@ -105,7 +105,7 @@ typedef struct {
     int32_t max_iter;    /* cap on CG iterations per corrector (0 = 20000)  */
     double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (0=1e-10)*/
     double delta;        /* preconditioner shift; 0 = drop the constant mode*/
-    double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-5)*/
+    double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-4)*/
     int32_t tile_rows;   /* stencil tile height in node rows (1..n; n need
                             not be a multiple), 0 = tuned or default       */
     int32_t col_tile;    /* threads of a column-transform block (power of
@@ -300,11 +300,12 @@ rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch, const uint
                              double* A, double* A_flux, void* stream);
 
 /* Diagnostics for benchmarks (process-wide, not thread-safe).
- * rve_profile_enable(1): the fused solver brackets every launch of its four
+ * rve_profile_enable(1): the fused solver brackets every launch of its five
  * pipeline kernels with CUDA events on the caller's stream and accumulates
- * their durations.  rve_profile_read(ms[4], launches[4]) returns the totals
- * per kernel -- 0 stencil pass, 1 update + row transform, 2 column
- * transform, 3 control -- and resets them; it returns 4.
+ * their durations.  rve_profile_read(ms[5], launches[5]) returns the totals
+ * per kernel -- 0 true-residual (refinement) pass, 1 stencil pass, 2 update
+ * + row transform, 3 column transform, 4 control -- and resets them; it
+ * returns 5.
  * rve_launch_count() returns the number of kernels the library launched
  * since the previous call. */
 void rve_profile_enable(int32_t on);

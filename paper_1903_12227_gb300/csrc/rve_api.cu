@@ -38,7 +38,7 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
     if (o) r = *o;
     if (r.max_iter <= 0) r.max_iter = 20000;
     if (!(r.tol > 0.0)) r.tol = 1e-10;
-    if (!(r.inner_tol > 0.0)) r.inner_tol = 1e-5;
+    if (!(r.inner_tol > 0.0)) r.inner_tol = 1e-4;
     if (r.check_every <= 0) r.check_every = 8;
     if (r.timeout_us <= 0) r.timeout_us = 2000000;
     return r;
@@ -464,10 +464,10 @@ rve_status rve_statistics(const double* A, int64_t N, double L, int32_t d, doubl
 void rve_profile_enable(int32_t on) { profile_enable(on != 0); }
 
 int32_t rve_profile_read(double* ms, int64_t* launches) {
-    long long l[4];
+    long long l[PROFILE_KERNELS];
     const int k = profile_read(ms, l);
     if (launches)
-        for (int j = 0; j < 4; ++j) launches[j] = (int64_t)l[j];
+        for (int j = 0; j < k; ++j) launches[j] = (int64_t)l[j];
     return k;
 }
 

@@ -157,6 +157,67 @@ __device__ __forceinline__ double warp_sum_array(const double* src, int count, i
     return warp_sum(s);
 }
 
+// ---------------------------------------------------------- double-word --
+// A value carried as the unevaluated sum hi + lo of two floats, for the
+// mixed path's true residual, which must be accurate far beyond FP32 but
+// must not run on GB300's narrow FP64 pipe.  Built from the error-free
+// transformations TwoSum (Knuth), Fast2Sum (Dekker; |a| >= |b| or a = 0) and
+// TwoProd with a fused multiply-add, combined as in Dekker (1971) and Joldes,
+// Muller & Popescu (ACM TOMS 44, 2017).  The _rn intrinsics keep the compiler
+// from contracting or reassociating any step, so every kernel that evaluates
+// the same expression gets the same bits.
+struct dword { float hi, lo; };
+
+__device__ __forceinline__ dword two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dword fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// Double-word + double-word ("sloppy" sum): absolute error O(eps^2 (|x|+|y|)),
+// which is all a residual needs (its terms cancel; the error budget is set by
+// their magnitudes, not by the result's).
+__device__ __forceinline__ dword dw_add(dword x, dword y) {
+    const dword s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+// Double-word + float.
+__device__ __forceinline__ dword dw_add(dword x, float y) {
+    const dword s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ dword dw_neg(dword x) { return {-x.hi, -x.lo}; }
+// Exact scaling by a power of two.
+__device__ __forceinline__ dword dw_scale2(dword x, float p2) { return {x.hi * p2, x.lo * p2}; }
+// Nearest double-word of a double (three FP64 instructions).
+__device__ __forceinline__ dword dw_of(double a) {
+    const float h = __double2float_rn(a);
+    return {h, __double2float_rn(a - (double)h)};
+}
+
+// Running sum  s0 + sum_k (+-) c_k w_k  of double-word products: the
+// product of the high parts is split exactly (TwoProd) and added with TwoSum;
+// the rounding errors and the cross terms gather in a float compensation
+// term (the compensated dot product "Dot2" of Ogita, Rump & Oishi, SIAM J.
+// Sci. Comput. 26, 2005, with double-word operands).  The error is
+// O(eps) |result| + O(eps^2) sum |c_k w_k|.
+struct DotDW {
+    float s, comp;
+    __device__ __forceinline__ explicit DotDW(dword s0) : s(s0.hi), comp(s0.lo) {}
+    __device__ __forceinline__ void add(dword a, float whi, float wlo) {
+        const float p = __fmul_rn(a.hi, whi);
+        const float e = __fmaf_rn(a.hi, whi, -p);
+        const float x = __fmaf_rn(a.hi, wlo, __fmaf_rn(a.lo, whi, e));
+        const dword t = two_sum(s, p);
+        s = t.hi;
+        comp = __fadd_rn(comp, __fadd_rn(t.lo, x));
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, comp); }
+};
+
 // ------------------------------------------------------------ radix DFTs --
 // Forward (exp(-2 pi i rs/R)) in-register DFTs.
 template <typename V> __device__ __forceinline__ void dft2(V& a, V& b) {

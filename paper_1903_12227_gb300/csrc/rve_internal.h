@@ -37,6 +37,9 @@ struct RState {
     double beta[2];      // direction update factor for the next stencil pass
     double target[2];    // inner-cycle relative residual target
     double relres[2];    // last true relative residual
+    double best[2];      // smallest inner residual of the cycle so far
+    int32_t stall[2];    // inner steps since it last fell below STALL_FACTOR * best
+    int32_t pad_[2];
 };
 
 // Tile geometry of one realization for the fused kernels.
@@ -115,6 +118,7 @@ rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const 
                            cudaStream_t s);
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                          int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
+constexpr int PROFILE_KERNELS = 5;   // refine, stencil, update, column, control
 void profile_enable(bool on);
 int profile_read(double* ms, long long* launches);
 cudaError_t launch_backward(const Plan& p, void* ws, int scheme, const double* u,

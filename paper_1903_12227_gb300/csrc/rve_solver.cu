@@ -208,33 +208,156 @@ __device__ void finish_S(const Ctx& c, int b, const RState& s, bool refine) {
     }
 }
 
-// REFINE step: r64 = f - A(u + s (x + alpha p)) in FP64 for the tile's rows,
-// stored (rounded to the vector type) in q, partial |r64|^2 into partS.
+// Mixed path: the FP64-accurate iterate lives in the caller's u buffer as a
+// double word per node and corrector (float4 = hi.x, hi.y, lo.x, lo.y) until
+// the solve ends (k_u_finalize).  The refine and update kernels both form
+// the new iterate w = u + s (x + alpha p) with this function -- correction
+// in FP32, added to u as a double word -- so that the residual computed for
+// w belongs to exactly the w that is stored.
+struct DWScal { float sx, sy, ax, ay; };
+__device__ __forceinline__ float4 w_new(float4 u, float2 x, float2 p, const DWScal& k) {
+    const float dx = __fmul_rn(k.sx, __fmaf_rn(k.ax, p.x, x.x));
+    const float dy = __fmul_rn(k.sy, __fmaf_rn(k.ay, p.y, x.y));
+    const dword wx = dw_add(dword{u.x, u.z}, dx);
+    const dword wy = dw_add(dword{u.y, u.w}, dy);
+    return make_float4(wx.hi, wy.hi, wx.lo, wy.lo);
+}
+
+// Double word times float: unevaluated (exact high product, error + cross term).
+__device__ __forceinline__ dword dw_mulf(dword x, float f) {
+    const float p = __fmul_rn(x.hi, f);
+    return {p, __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p))};
+}
+
+// REFINE step of the mixed path: r = f - A w for the tile's rows with
+// w = u + s (x + alpha p), in double-word arithmetic on the FP32 pipe (no
+// FP64 per node).  The stiffness and the right-hand side are scaled by
+// K = 6 (consistent) resp. 2 (lumped) so that every stencil weight is an
+// integer multiple of a cell value: K A has centre 2 K w0 (sum of the four
+// cells), edges -(sum of the two shared cells), corners -2 K w1 (shared
+// cell), and K f_1 = (K h/2)(a_0m + a_00 - a_mm - a_m0).  r_K = K f - K A w
+// is accumulated as a compensated dot product, so its absolute error is
+// O(eps_32^2) times the size of the stencil terms -- far below the outer
+// tolerance -- and r = r_K / K is rounded to FP32 (the inner iteration's
+// type).  Each thread walks down one column with a 3 x 3 window of w.
+template <int SCHEME>
+__device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, const RDesc& d) {
+    __shared__ double red[64];
+    __shared__ float sc[9];
+    const int n = d.n;
+    const int r0 = (tile - c.startS[b]) * d.tS;
+    const int rows = min(d.tS, n - r0);   // the last tile may be shorter
+    if (threadIdx.x == 0) {
+        sc[0] = (float)s.s[0];
+        sc[1] = (float)s.s[1];
+        sc[2] = (float)s.alpha[0];
+        sc[3] = (float)s.alpha[1];
+        const dword ai = dw_of(d.a_incl), am = dw_of(d.a_matrix);
+        sc[4] = ai.hi; sc[5] = ai.lo; sc[6] = am.hi; sc[7] = am.lo;
+        sc[8] = (float)d.h;   // 1/m0, a power of two: exact
+    }
+    __syncthreads();
+    const DWScal k{sc[0], sc[1], sc[2], sc[3]};
+    const dword aI{sc[4], sc[5]}, aM{sc[6], sc[7]};
+    const bool first = (s.refinements == 0);   // u = x = p = 0: r = f
+    constexpr float CEN = SCHEME == 0 ? 4.f : 2.f;      // 2 K w0
+    constexpr float COR = SCHEME == 0 ? 2.f : 0.f;      // 2 K w1
+    constexpr float KH = SCHEME == 0 ? 3.f : 1.f;       // K / 2
+    constexpr float INVK = SCHEME == 0 ? (1.f / 6.f) : 0.5f;
+    const float kh2 = KH * sc[8];   // K h / 2: exact
+    const float4* U = reinterpret_cast<const float4*>(c.u);
+    const float2* X = static_cast<const float2*>(c.X);
+    const float2* P = static_cast<const float2*>(s.parity ? c.P1 : c.P0);
+    float2* Q = static_cast<float2*>(c.Q);
+    auto wat = [&](int i, int j) -> float4 {
+        if (first) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t node = d.node_off + ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1));
+        return w_new(U[node], X[node], P[node], k);
+    };
+    auto cell = [&](int i, int j) -> dword {
+        const int64_t ci = ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1));
+        if (c.cs.coef) return dw_of(__ldg(c.cs.coef + d.node_off + ci));
+        const uint32_t w = __ldg(c.cs.mask + d.word_off + (ci >> 5));
+        return ((w >> (ci & 31)) & 1u) ? aI : aM;
+    };
+    dword nx{0.f, 0.f}, ny{0.f, 0.f};   // |r|^2, double-word per thread
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float4 a0 = wat(r0 - 1, j - 1), a1 = wat(r0 - 1, j), a2 = wat(r0 - 1, j + 1);
+        float4 b0 = wat(r0, j - 1), b1 = wat(r0, j), b2 = wat(r0, j + 1);
+        dword cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
+        for (int q = 0; q < rows; ++q) {
+            const int i = r0 + q;
+            const float4 e0 = wat(i + 1, j - 1), e1 = wat(i + 1, j), e2 = wat(i + 1, j + 1);
+            const dword c0m = cell(i, j - 1), c00 = cell(i, j);
+            const dword top = dw_add(cmm, cm0);   // cells shared with (i-1, j)
+            const dword bot = dw_add(c0m, c00);   // with (i+1, j)
+            const dword lft = dw_add(cmm, c0m);   // with (i, j-1)
+            const dword rgt = dw_add(cm0, c00);   // with (i, j+1)
+            const dword cen = dw_scale2(dw_add(top, bot), -CEN);
+            DotDW rx(dw_mulf(dw_add(bot, dw_neg(top)), kh2));
+            DotDW ry(dw_mulf(dw_add(rgt, dw_neg(lft)), kh2));
+            rx.add(cen, b1.x, b1.z); ry.add(cen, b1.y, b1.w);
+            rx.add(top, a1.x, a1.z); ry.add(top, a1.y, a1.w);
+            rx.add(bot, e1.x, e1.z); ry.add(bot, e1.y, e1.w);
+            rx.add(lft, b0.x, b0.z); ry.add(lft, b0.y, b0.w);
+            rx.add(rgt, b2.x, b2.z); ry.add(rgt, b2.y, b2.w);
+            if (COR != 0.f) {
+                const dword kmm = dw_scale2(cmm, COR), km0 = dw_scale2(cm0, COR);
+                const dword k0m = dw_scale2(c0m, COR), k00 = dw_scale2(c00, COR);
+                rx.add(kmm, a0.x, a0.z); ry.add(kmm, a0.y, a0.w);
+                rx.add(km0, a2.x, a2.z); ry.add(km0, a2.y, a2.w);
+                rx.add(k0m, e0.x, e0.z); ry.add(k0m, e0.y, e0.w);
+                rx.add(k00, e2.x, e2.z); ry.add(k00, e2.y, e2.w);
+            }
+            const float2 r = make_float2(rx.value() * INVK, ry.value() * INVK);
+            Q[d.node_off + ((int64_t)i << d.log2n) + j] = r;
+            nx = dw_add(nx, r.x * r.x);
+            ny = dw_add(ny, r.y * r.y);
+            a0 = b0; a1 = b1; a2 = b2;
+            b0 = e0; b1 = e1; b2 = e2;
+            cmm = c0m; cm0 = c00;
+        }
+    }
+    DotAcc<float> ax, ay;
+    ax.hi = nx.hi; ax.lo = nx.lo;
+    ay.hi = ny.hi; ay.lo = ny.lo;
+    double sx = 0.0, sy = 0.0;
+    block_sum2(ax, ay, red, sx, sy);
+    if (threadIdx.x == 0) {
+        c.partS[2 * (int64_t)tile] = sx;
+        c.partS[2 * (int64_t)tile + 1] = sy;
+    }
+    finish_S(c, b, s, true);
+}
+
+// REFINE step: r64 = f - A(u + s (x + alpha p)) for the tile's rows, stored
+// (rounded to the vector type) in q, partial |r64|^2 into partS -- in FP64
+// for the FP64 path, in double words for the mixed path (refine_tile_dw).
 // Launched every step next to k_fused_S; blocks of realizations that are
 // not refining return at once.
-template <typename V, int SCHEME>
-__device__ void fused_R_tile(const Ctx& c, int tile) {
+template <int SCHEME>
+__device__ void refine_tile_fp64(const Ctx& c, int tile, int b, const RState& s, const RDesc& d) {
+    typedef double2 V;
     __shared__ double red[64];
-    const int b = find_real(c.startS, c.batch, tile);
-    const RState& s = c.st[b];
-    if (s.phase != PH_REFINE) return;
-    const RDesc d = c.desc[b];
     const int n = d.n;
     const int r0 = (tile - c.startS[b]) * d.tS;
     const int rows = min(d.tS, n - r0);   // the last tile may be shorter
     const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
     V* Q = static_cast<V*>(c.Q);
+    const bool first = (s.refinements == 0);   // u = x = p = 0: r = f
     DotAcc<double> a64x, a64y;   // exact FP64 |r64|^2
     for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
         const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
         const Cells4 a = cells_at(c.cs, d, i, j);
         const double2 f = rhs_at(a, d.h);
-        const double2 Aw = stencil_apply<SCHEME, double2>(
-            a, refine_w(c, d, s, i - 1, j - 1, Pold), refine_w(c, d, s, i - 1, j, Pold),
-            refine_w(c, d, s, i - 1, j + 1, Pold), refine_w(c, d, s, i, j - 1, Pold),
-            refine_w(c, d, s, i, j, Pold), refine_w(c, d, s, i, j + 1, Pold),
-            refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
-            refine_w(c, d, s, i + 1, j + 1, Pold));
+        double2 Aw = make_double2(0.0, 0.0);
+        if (!first)
+            Aw = stencil_apply<SCHEME, double2>(
+                a, refine_w(c, d, s, i - 1, j - 1, Pold), refine_w(c, d, s, i - 1, j, Pold),
+                refine_w(c, d, s, i - 1, j + 1, Pold), refine_w(c, d, s, i, j - 1, Pold),
+                refine_w(c, d, s, i, j, Pold), refine_w(c, d, s, i, j + 1, Pold),
+                refine_w(c, d, s, i + 1, j - 1, Pold), refine_w(c, d, s, i + 1, j, Pold),
+                refine_w(c, d, s, i + 1, j + 1, Pold));
         const double2 r64 = make_double2(f.x - Aw.x, f.y - Aw.y);
         Q[node_of<V>(d, i, j)] = from_d2<V>(r64);
         a64x.add(r64.x, r64.x);
@@ -247,6 +370,18 @@ __device__ void fused_R_tile(const Ctx& c, int tile) {
         c.partS[2 * (int64_t)tile + 1] = sy;
     }
     finish_S(c, b, s, true);
+}
+
+template <typename V, int SCHEME>
+__device__ void fused_R_tile(const Ctx& c, int tile) {
+    const int b = find_real(c.startS, c.batch, tile);
+    const RState& s = c.st[b];
+    if (s.phase != PH_REFINE) return;
+    const RDesc d = c.desc[b];
+    if constexpr (sizeof(V) == 8)
+        refine_tile_dw<SCHEME>(c, tile, b, s, d);
+    else
+        refine_tile_fp64<SCHEME>(c, tile, b, s, d);
 }
 
 // ITER step: inverse row Hartley of t on the tile + halo rows (z),
@@ -454,7 +589,47 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
                 ay.add(rr.y, rr.y);
             }
         }
-    } else {   // REFINE
+    } else if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
+        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+        if (threadIdx.x == 0) {   // the same conversions as refine_tile_dw
+            usc[0] = (float)s.s[0];
+            usc[1] = (float)s.s[1];
+            usc[2] = (float)s.alpha[0];
+            usc[3] = (float)s.alpha[1];
+            usc[4] = (float)c.uscal[2 * b];       // 1 / |r| per corrector (0 once
+            usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
+        }
+        __syncthreads();
+        const DWScal k{usc[0], usc[1], usc[2], usc[3]};
+        const float ix = usc[4], iy = usc[5];
+        float4* U4 = reinterpret_cast<float4*>(c.u);
+        if (active) {
+#pragma unroll
+            for (int h = 0; h < 8; h += 4) {
+                float4 uu[4];
+                V xx[4], pp[4], qv[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {   // loads first, stores after
+                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                    uu[m] = U4[node];
+                    xx[m] = X[node];
+                    pp[m] = Pold[node];
+                    qv[m] = Qv[node];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                    U4[node] = w_new(uu[m], xx[m], pp[m], k);
+                    X[node] = mk<V>(0.f, 0.f);
+                    const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
+                    R[node] = rr;
+                    v[h + m] = rr;
+                    ax.add(rr.x, rr.x);
+                    ay.add(rr.y, rr.y);
+                }
+            }
+        }
+    } else {   // REFINE, FP64
         const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
         // 1 / |r64| per corrector (0 once converged), from finish_S
         const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
@@ -491,7 +666,7 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
 template <typename V>
 __device__ void fused_U_tile(const Ctx& c, int blk) {
     __shared__ double red[64];   // block_sum2 scratch: 4 floats per warp (<= 32 warps)
-    __shared__ typename ScalarOf<V>::T usc[2];
+    __shared__ typename ScalarOf<V>::T usc[6];
     const int b = find_real(c.startU, c.batch, blk);
     const RState& s = c.st[b];
     if (s.phase == PH_DONE) return;
@@ -615,6 +790,13 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const C
 // ------------------------------------------------------ control kernel --
 __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
 
+// Stagnation test of an inner cycle: the residual must fall below
+// STALL_FACTOR times its best value within STALL_STEPS steps.  Healthy
+// preconditioned CG here contracts by ~0.8 per step or better, so only a
+// cycle that has reached the attainable accuracy of its precision trips it.
+constexpr double STALL_FACTOR = 0.7;
+constexpr int STALL_STEPS = 30;
+
 // Control step of realization b, executed by one whole warp.
 __device__ void control_one(const Ctx& c, int b) {
     RState& s = c.st[b];
@@ -644,7 +826,17 @@ __device__ void control_one(const Ctx& c, int b) {
             }
             s.alpha[k] = alpha;
             s.iters[k] += 1;
-            if (rn <= s.target[k] || s.iters[k] >= c.max_iter) {
+            // a cycle whose residual has stopped falling (the attainable
+            // accuracy of the inner precision) ends early: the refinement
+            // step then restarts from the true residual
+            if (rn < STALL_FACTOR * s.best[k]) {
+                s.best[k] = rn;
+                s.stall[k] = 0;
+            } else {
+                s.stall[k] += 1;
+            }
+            const bool stalled = s.stall[k] >= STALL_STEPS;
+            if (rn <= s.target[k] || stalled || s.iters[k] >= c.max_iter) {
                 s.active[k] = 0;       // frozen; alpha still pending for x
                 s.beta[k] = 0.0;
                 if (s.iters[k] >= c.max_iter && rn > s.target[k]) s.final_pass = 1;
@@ -655,7 +847,7 @@ __device__ void control_one(const Ctx& c, int b) {
             }
         }
         s.parity ^= 1;
-        if (!any_active) s.phase = PH_REFINE;
+        if (!any_active) s.phase = PH_REFINE;   // every corrector ended its cycle
         return;
     }
     // REFINE: true residual of the accumulated solution
@@ -671,20 +863,38 @@ __device__ void control_one(const Ctx& c, int b) {
         }
         if (s.refinements == 1) s.fnorm[k] = rn;
         const bool conv = (s.refinements == 1) ? (rn == 0.0) : (rn <= c.tol * s.fnorm[k]);
+        const double prev = s.relres[k];
         s.relres[k] = s.fnorm[k] > 0.0 ? rn / s.fnorm[k] : 0.0;
         s.alpha[k] = 0.0;
-        s.beta[k] = 0.0;
         if (conv || s.cdone[k]) {
             s.cdone[k] = 1;
             s.active[k] = 0;
             s.s[k] = 0.0;
+            s.beta[k] = 0.0;
             continue;
         }
         all_done = false;
+        // each cycle restarts CG from the true residual (p = z): keeping
+        // the old direction across the replaced residual loses conjugacy
+        // when the FP32 recurrence has drifted (tens of percent here)
+        s.beta[k] = 0.0;
         s.s[k] = rn;
         s.active[k] = 1;
-        const double want = 0.5 * c.tol * s.fnorm[k] / rn;   // enough for the outer tolerance
-        s.target[k] = fmin(0.5, fmax(c.inner_tol, want));
+        s.best[k] = 1.0;   // the inner system starts from r / |r|
+        s.stall[k] = 0;
+        // inner target: what the outer tolerance still needs, but no less
+        // than the usual inner reduction
+        const double want = 0.5 * c.tol * s.fnorm[k] / rn;
+        double tgt = fmax(want, c.inner_tol);
+        // a cycle gains at most what the rounding of its iterate allows
+        // (about eps_inner times the condition of A on the correction): when
+        // the last cycle's true residual fell far less than it was asked
+        // to, ask the next one for no more than ten times what it achieved
+        if (s.refinements >= 2 && prev > 0.0) {
+            const double got = s.relres[k] / prev;
+            if (got > 10.0 * s.target[k]) tgt = fmax(tgt, 0.1 * got);
+        }
+        s.target[k] = fmin(0.5, tgt);
         s.rho[k] = pC[k];
         if (s.iters[k] >= c.max_iter) s.final_pass = 1;
     }
@@ -832,18 +1042,37 @@ __global__ void k_report(const Ctx c, rve_solve_info* info) {
     info[b] = r;
 }
 
+// Mixed path: the double-word iterate (float4 per node) becomes the caller's
+// FP64 solution, in place (each thread rewrites the 16 bytes it read).
+__global__ void k_u_finalize(double2* u, int64_t nodes) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nodes; k += stride) {
+        const float4 w = reinterpret_cast<const float4*>(u)[k];
+        u[k] = make_double2((double)w.x + (double)w.z, (double)w.y + (double)w.w);
+    }
+}
+
+static cudaError_t finalize_u(const Plan& p, const Ctx& c, cudaStream_t s) {
+    if (p.precision != RVE_MIXED) return cudaSuccess;
+    k_u_finalize<<<std::min<int64_t>((p.nodes + 255) / 256, 8 * 152), 256, 0, s>>>(c.u, p.nodes);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- host --
 std::atomic<long long> g_launches{0};
 
 // Per-kernel event timing of the fused pipeline (diagnostics).
+// Kernels: 0 refine, 1 stencil, 2 update + row transform, 3 column, 4 control.
 struct Profiler {
+    static constexpr int K = PROFILE_KERNELS;
     bool on = false;
-    double ms[4] = {0, 0, 0, 0};
-    long long launches[4] = {0, 0, 0, 0};
-    std::vector<cudaEvent_t> ev;    // 5 events per recorded step
+    double ms[K] = {};
+    long long launches[K] = {};
+    std::vector<cudaEvent_t> ev;    // K + 1 events per recorded step
     int used = 0;                   // steps recorded since the last harvest
     void ensure(int steps) {
-        while ((int)ev.size() < 5 * steps) {
+        while ((int)ev.size() < (K + 1) * steps) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return;
             ev.push_back(e);
@@ -851,9 +1080,10 @@ struct Profiler {
     }
     void harvest() {   // stream already synchronised
         for (int k = 0; k < used; ++k)
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < K; ++j) {
                 float t = 0.f;
-                if (cudaEventElapsedTime(&t, ev[5 * k + j], ev[5 * k + j + 1]) == cudaSuccess) {
+                if (cudaEventElapsedTime(&t, ev[(K + 1) * k + j], ev[(K + 1) * k + j + 1]) ==
+                    cudaSuccess) {
                     ms[j] += t;
                     launches[j] += 1;
                 }
@@ -865,13 +1095,13 @@ static Profiler g_prof;
 
 void profile_enable(bool on) { g_prof.on = on; }
 int profile_read(double* ms, long long* launches) {
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < Profiler::K; ++j) {
         if (ms) ms[j] = g_prof.ms[j];
         if (launches) launches[j] = g_prof.launches[j];
         g_prof.ms[j] = 0.0;
         g_prof.launches[j] = 0;
     }
-    return 4;
+    return Profiler::K;
 }
 
 static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double* coef, double* u,
@@ -939,14 +1169,15 @@ template <typename V, int SCHEME>
 static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     k_fused_R<V, SCHEME><<<p.tilesS, 256, 0, s>>>(c);
-    k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
     if (ev) cudaEventRecord(ev[1], s);
-    k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
+    k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
     if (ev) cudaEventRecord(ev[2], s);
-    k_fused_C<V><<<p.tilesC, p.blockC, p.smemC, s>>>(c);
+    k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
     if (ev) cudaEventRecord(ev[3], s);
-    k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
+    k_fused_C<V><<<p.tilesC, p.blockC, p.smemC, s>>>(c);
     if (ev) cudaEventRecord(ev[4], s);
+    k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
+    if (ev) cudaEventRecord(ev[5], s);
     note_launch(5);
     return cudaGetLastError();
 }
@@ -978,7 +1209,8 @@ static rve_status fused_loop(const Plan& p, const Ctx& c, const rve_solve_opts& 
     }
     for (int64_t g = 0; g < max_steps; ++g) {
         cudaEvent_t* ev = nullptr;
-        if (g_prof.on && (int)g_prof.ev.size() >= 5 * every) ev = &g_prof.ev[5 * g_prof.used++];
+        if (g_prof.on && (int)g_prof.ev.size() >= (Profiler::K + 1) * every)
+            ev = &g_prof.ev[(Profiler::K + 1) * g_prof.used++];
         if (fused_step<V, SCHEME>(p, c, s, ev) != cudaSuccess) return RVE_ECUDA;
         if ((g + 1) % every == 0) {
             if (cudaMemcpyAsync(&host_done, c.ndone, sizeof(int), cudaMemcpyDeviceToHost, s) !=
@@ -1071,6 +1303,7 @@ rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mas
         st = (p.scheme == RVE_Q1_LUMPED) ? persistent_launch<double2, 1>(p, c, o, s)
                                          : persistent_launch<double2, 0>(p, c, o, s);
     if (st != RVE_OK) return st;
+    if (finalize_u(p, c, s) != cudaSuccess) return RVE_ECUDA;
     k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
@@ -1117,6 +1350,7 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
                                          : fused_loop<double2, 0>(p, c, o, s);
     }
     if (st != RVE_OK) return st;
+    if (finalize_u(p, c, s) != cudaSuccess) return RVE_ECUDA;
     k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;

@@ -425,10 +425,10 @@ def profile_enable(on: bool = True) -> None:
 
 def profile_read() -> dict:
     import numpy as np
-    ms = np.zeros(4)
-    ln = np.zeros(4, dtype=np.int64)
+    ms = np.zeros(5)
+    ln = np.zeros(5, dtype=np.int64)
     lib().rve_profile_read(ms.ctypes.data_as(ctypes.c_void_p), ln.ctypes.data_as(ctypes.c_void_p))
-    names = ("stencil", "update_row", "column", "control")
+    names = ("refine", "stencil", "update_row", "column", "control")
     return {k: {"ms": float(ms[i]), "launches": int(ln[i])} for i, k in enumerate(names)}
 
 
