@@ -48,7 +48,7 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
 // row, so tU = 2048/n rows per block.  The stencil tile keeps tS + 2 padded
 // rows in shared memory: the largest power of two <= 8 whose tile fits
 // 110 KB (two blocks per SM; at least 1).  Column blocks use blockC
-// threads, n/8 per column.
+// threads, n / col_seg_rows per column.
 static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
     const size_t seq = (size_t)seq_stride(n);
     t.tU = std::min(n, 2048 / n);
@@ -76,7 +76,7 @@ static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o,
     int ts_tuned = 0, bc_tuned = 0;
     if (tuned_tiles(n, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0, &ts_tuned, &bc_tuned))
         t.tS = ts_tuned;
-    t.tC = std::min(n, blockC * 8 / n);
+    t.tC = std::min(n, blockC / (n / col_seg_rows(n, (int)vb)));
     if (o.tile_rows > 0) t.tS = o.tile_rows;
     t.tS = std::min(t.tS, n);
 }
@@ -112,18 +112,18 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         const int64_t nn = (int64_t)r[b].L * r[b].m0;
         if (nn > 0 && nn <= MAX_N) maxn = std::max(maxn, (int)nn);
     }
-    // column blocks: 1024 threads for large FP32 grids; FP64 stays at 512
-    // (more registers per thread for the double-precision transform)
-    p.blockC = (maxn > 512 && p.vbytes == 8) ? 1024 : 512;
+    // column blocks: 512 threads (a segment of up to 32 rows per thread in
+    // registers)
+    p.blockC = 512;
     {
         int ts_tuned = 0, bc_tuned = 0;
         if (maxn > 0 && tuned_tiles(maxn, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0,
                                     &ts_tuned, &bc_tuned))
-            p.blockC = bc_tuned;
+            p.blockC = std::min(512, std::max(32, bc_tuned));   // a loaded table may hold anything
     }
     if (o.path == RVE_PATH_PERSISTENT) p.blockC = 256;   // one block shape for all phases
     if (o.col_tile > 0 && o.path != RVE_PATH_PERSISTENT)
-        p.blockC = std::min(p.vbytes == 8 ? 1024 : 512, std::max(32, o.col_tile));
+        p.blockC = std::min(512, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
@@ -137,7 +137,9 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             return RVE_EINVAL;
         Tiles t;
         default_tiles(n, p.vbytes, p.blockC, o, t);
-        if (t.tS < 1 || t.tS > n || !pow2(t.tC) || n % t.tC || t.tC * (n / 8) > p.blockC)
+        const int segs = n / col_seg_rows(n, (int)p.vbytes);   // threads per column
+        if (t.tS < 1 || t.tS > n || t.tC < 1 || !pow2(t.tC) || n % t.tC ||
+            t.tC * segs > p.blockC)
             return RVE_EINVAL;
         RDesc& d = p.desc[b];
         std::memset(&d, 0, sizeof(d));
@@ -169,7 +171,9 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         const size_t seq = (size_t)seq_stride(n);
         p.smemS = std::max(p.smemS, (size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4);
         p.smemU = std::max(p.smemU, (size_t)t.tU * seq * vb);
-        p.smemC = std::max(p.smemC, (size_t)t.tC * seq * vb);
+        // segment end / start values (2 per column segment) and the
+        // singular column's sums (2 per segment)
+        p.smemC = std::max(p.smemC, (size_t)(2 * t.tC + 2) * segs * vb);
     }
     if (p.smemS > MAX_SMEM || p.smemU > MAX_SMEM || p.smemC > MAX_SMEM) return RVE_EINVAL;
     p.tilesS = p.startS[batch];
@@ -193,6 +197,8 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_tw32 = take(sizeof(float2) * tab);
     p.o_lap = take(sizeof(double) * tab);
     p.o_lap32 = take(sizeof(float) * tab);
+    p.o_rho64 = take(sizeof(double) * tab);
+    p.o_rho32 = take(sizeof(float) * tab);
     p.o_state = take(sizeof(RState) * batch);
     p.o_partS = take(sizeof(double) * 2 * (size_t)std::max<int64_t>(p.tilesS, maxnb));
     p.o_partU = take(sizeof(double) * 2 * (size_t)p.tilesU);

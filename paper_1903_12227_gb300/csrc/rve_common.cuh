@@ -147,7 +147,26 @@ struct Tables {
     const float2* __restrict__ tw32;
     const double* __restrict__ lap;     // 4 sin^2(pi m/n)
     const float* __restrict__ lap32;
+    const double* __restrict__ rho64;   // column-filter root for lambda = lap[m], delta = 0
+    const float* __restrict__ rho32;    // (1 at m = 0: the singular column)
 };
+template <typename T> __device__ __forceinline__ const T* rho_table(const Tables& tb, int n);
+template <> __device__ __forceinline__ const double* rho_table<double>(const Tables& tb, int n) { return tb.rho64 + n; }
+template <> __device__ __forceinline__ const float* rho_table<float>(const Tables& tb, int n) { return tb.rho32 + n; }
+
+// Root rho < 1 of rho + 1/rho = 2 + mu (mu > 0), the decay of the periodic
+// tridiagonal inverse; written without cancellation.
+__host__ __device__ __forceinline__ double filter_root(double mu) {
+    return 1.0 / (1.0 + 0.5 * mu + sqrt(mu * (1.0 + 0.25 * mu)));
+}
+
+// Column solve geometry: a thread holds one segment of `col_seg_rows` rows
+// of one column in registers (n/16 rows up to n = 512, then 32; at most 16
+// for FP64 pairs), so a column spans n / col_seg_rows threads.
+__host__ __device__ constexpr int col_seg_rows(int n, int vbytes) {
+    return (vbytes == 16) ? ((n <= 512 ? n / 16 : 32) < 16 ? (n <= 512 ? n / 16 : 32) : 16)
+                          : (n <= 512 ? n / 16 : 32);
+}
 template <typename T> __device__ __forceinline__ const T* lap_table(const Tables& tb, int n);
 template <> __device__ __forceinline__ const double* lap_table<double>(const Tables& tb, int n) { return tb.lap + n; }
 template <> __device__ __forceinline__ const float* lap_table<float>(const Tables& tb, int n) { return tb.lap32 + n; }

@@ -2,7 +2,7 @@
 //
 // * complex helpers on float2 / double2;
 // * DotAcc: per-thread dot-product accumulators.  FP64 data accumulate in
-//   double.  FP32 data: each thread sums its own <= 8 products in FP32, the
+//   double.  FP32 data: each thread sums its own <= 32 products in FP32, the
 //   block combines the thread sums in double-float and the blocks are
 //   combined in FP64 -- no long FP32 sums and no per-element FP64 work;
 // * deterministic warp / block reductions (fixed tree order);
@@ -51,10 +51,10 @@ template <> struct DotAcc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// FP32 data: a thread sums only its own few (<= 8) products, with fused
+// FP32 data: a thread sums only its own few (<= 32) products, with fused
 // multiply-adds in FP32; the block then combines the per-thread sums in
 // double-float (TwoSum, see block_sum2) and the blocks are combined in FP64,
-// so no sum longer than 8 terms is formed in FP32.  (hi, lo) is the
+// so no sum longer than 32 terms is formed in FP32.  (hi, lo) is the
 // double-float pair of the block tree; lo stays 0 within a thread.
 template <> struct DotAcc<float> {
     float hi, lo;

@@ -66,7 +66,7 @@ struct Plan {
     size_t persist_smem = 0;
     // workspace offsets (bytes)
     size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
-    size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0;
+    size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0, o_rho64 = 0, o_rho32 = 0;
     size_t o_state = 0, o_partS = 0, o_partU = 0, o_partC = 0, o_partA = 0, o_ctl = 0;
     size_t o_uscal = 0, o_cnt = 0;
     size_t o_X = 0, o_R = 0, o_Q = 0, o_T = 0, o_P0 = 0, o_P1 = 0;
@@ -89,6 +89,9 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
 
 // Uploads descriptors/tile tables and fills the lookup tables in ws.
 rve_status upload_plan(const Plan& plan, void* ws, cudaStream_t s);
+// Device pointers of the lookup tables in the workspace, and the kernel that fills them.
+Tables tables_of(const Plan& p, const void* ws);
+cudaError_t launch_tables(const Plan& p, void* ws, cudaStream_t s);
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_gen_field(const Plan& p, void* ws, uint32_t* mask, cudaStream_t s);

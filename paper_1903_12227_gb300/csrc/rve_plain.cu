@@ -216,11 +216,6 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
                             const rve_solve_opts& o, rve_solve_info* info, cudaStream_t s) {
     const RDesc& d = p.desc[b];
     const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
-    Tables tb;
-    tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
-    tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
-    tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
-    tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
     double2* r = reinterpret_cast<double2*>(w + p.o_R);
     double2* z = reinterpret_cast<double2*>(w + p.o_X);
     double2* pp = reinterpret_cast<double2*>(w + p.o_P0);

@@ -179,7 +179,7 @@ rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve
         tss.erase(std::unique(tss.begin(), tss.end()), tss.end());
         tss.erase(std::remove_if(tss.begin(), tss.end(), [&](int v) { return v < 1 || v > n; }),
                   tss.end());
-        std::vector<int> bcs = {256, 512, 1024};
+        std::vector<int> bcs = {256, 512};
         if (base.path == RVE_PATH_PERSISTENT) bcs = {256};
         float best = 1e30f;
         int best_ts = 0, best_bc = 0;
@@ -192,7 +192,6 @@ rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve
                 o.max_iter = 12;   // a short trial: the time is that of iteration steps
                 Plan p;
                 if (make_plan(sub.data(), (int)sub.size(), &o, p, true) != RVE_OK) continue;
-                if (bc == 1024 && p.vbytes == 16) continue;
                 const PipeLayout l = pipe_layout(p);
                 if (l.total > ws_bytes) continue;
                 char* w = static_cast<char*>(ws);

@@ -72,19 +72,44 @@ struct Ctx {
 
 // ------------------------------------------------------------- tables --
 // tw64[n + m] = exp(-2 pi i m / n), lap[n + m] = 4 sin^2(pi m / n) for every
-// n = 2^p <= 2^maxlog; computed with sincospi/sinpi.
-__global__ void k_tables(double2* tw64, float2* tw32, double* lap, float* lap32, int total) {
+// n = 2^p <= 2^maxlog, computed with sincospi/sinpi; rho[n + m] the column
+// filter root for lambda = lap[n + m] and delta = 0 (1 for the singular
+// column m = 0).
+__global__ void k_tables(Tables out, int total) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < 2 || idx >= total) return;
     const int p = 31 - __clz(idx);
     const int n = 1 << p, m = idx - n;
     double sn, cs;
     sincospi(-2.0 * (double)m / (double)n, &sn, &cs);
-    tw64[idx] = make_double2(cs, sn);
-    tw32[idx] = make_float2((float)cs, (float)sn);
+    const_cast<double2*>(out.tw64)[idx] = make_double2(cs, sn);
+    const_cast<float2*>(out.tw32)[idx] = make_float2((float)cs, (float)sn);
     const double s1 = sinpi((double)m / (double)n);
-    lap[idx] = 4.0 * s1 * s1;
-    lap32[idx] = (float)(4.0 * s1 * s1);
+    const double lam = 4.0 * s1 * s1;
+    const_cast<double*>(out.lap)[idx] = lam;
+    const_cast<float*>(out.lap32)[idx] = (float)lam;
+    const double rho = (m == 0) ? 1.0 : filter_root(lam);
+    const_cast<double*>(out.rho64)[idx] = rho;
+    const_cast<float*>(out.rho32)[idx] = (float)rho;
+}
+
+Tables tables_of(const Plan& p, const void* ws) {
+    const char* w = static_cast<const char*>(ws);
+    Tables tb;
+    tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
+    tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
+    tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
+    tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
+    tb.rho64 = reinterpret_cast<const double*>(w + p.o_rho64);
+    tb.rho32 = reinterpret_cast<const float*>(w + p.o_rho32);
+    return tb;
+}
+
+cudaError_t launch_tables(const Plan& p, void* ws, cudaStream_t s) {
+    const int total = 2 << p.max_log2n;
+    k_tables<<<(total + 255) / 256, 256, 0, s>>>(tables_of(p, ws), total);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- row helpers --
@@ -675,72 +700,192 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
 }
 
 // ----------------------------------------------------------- C kernel --
-// Column pass on t (already row-Hartley transformed).  For each row
-// frequency k2 the column operator is the real symmetric circulant with
-// symbol 1/(n^2 sigma(., k2)) (sigma is even in k1), so it is applied to the
-// pair (a, b) = (t_1, t_2) of a column as one complex FFT, a real scale and
-// one inverse complex FFT (conj-FFT-conj); the outputs of the inverse stay
-// in registers and go straight to global memory.  The corrector parts of
-// rho are split with the mirror row: A = (Z_k + conj Z_-k)/2 is the DFT of
-// a, B = (Z_k - conj Z_-k)/2i that of b, and rho_c = sum s |A|^2 (resp.
-// |B|^2) with s = 1/(n^2 sigma) (Parseval; the row Hartley pass is
-// orthogonal up to n).  Block of C*T threads (T = n/8), thread (t, c) with c
-// fastest so that global accesses are row segments of C elements.
-// `rho_part` may be null.
+// Column pass on t = row-Hartley(r).  The row transform diagonalises the
+// row factor of A_Delta, so column k2 of t is left with the periodic
+// tridiagonal system
+//     M z = t,   M = c0 (T + lambda) + delta,   lambda = 4 sin^2(pi k2 / n),
+// T the periodic second difference along the column (the fast Poisson
+// scheme of Hockney: Fourier in one direction, tridiagonal solves in the
+// other).  With rho + 1/rho = 2 + mu, mu = lambda + delta / c0,
+//     M = (c0 / rho) (1 - rho S)(1 - rho S^T),   S the cyclic shift,
+// so M^{-1} t = (rho / c0) F^T F t with the causal filter F = (1 - rho S)^{-1}
+// (y_i = t_i + rho y_{i-1}, periodic) and its transpose, the anticausal
+// filter.  The pass stores zhat = M^{-1} t / n (the row transform in the
+// stencil kernel supplies the other factor 1/n of the inverse transform)
+// and rho_c = r.z = t.zhat = (rho / (n c0)) |F t|^2.
+//
+// Each thread holds SEG consecutive rows of one column in registers: it
+// runs the filter over its segment from a zero start, the segment's end
+// value goes through shared memory, and every thread adds the periodic
+// carry-in  sum_{j=1..P} R^{j-1} e_{s-j} / (1 - R^P)  (R = rho^SEG, P
+// segments; the sum stops once R^{j-1} is negligible) times rho^{i+1}.
+// The anticausal filter runs the same way upwards.  The singular column
+// k2 = 0 with delta = 0 (rho = 1) takes the pseudo-inverse: with
+// t' = t - mean t, y = cumsum t' made mean-zero, w = reverse cumsum y made
+// mean-zero, zhat = w / (n c0), rho_c = |y|^2 / (n c0).
+// Block: C columns x P segments, thread (cc, s) with cc fastest so that the
+// global accesses of a warp are row segments of C elements.  `rho_part`
+// may be null.
 template <typename V, int LOG2N>
-__device__ __forceinline__ void col_transform_body(V* __restrict__ Tg, const RDesc& d, int c0,
-                                                   V* smem, const Tables& tb, double delta,
-                                                   double* red, double* rho_part,
-                                                   typename ScalarOf<V>::T* csc) {
+__device__ __forceinline__ void col_solve_body(V* __restrict__ Tg, const RDesc& d, int c0,
+                                               V* smem, const Tables& tb, double delta,
+                                               double* red, double* rho_part,
+                                               typename ScalarOf<V>::T* csc) {
     typedef typename ScalarOf<V>::T Ts;
-    if (threadIdx.x == 0) {
-        const double n2 = (double)d.n * (double)d.n;
-        csc[0] = (Ts)(n2 * d.c0);
-        csc[1] = (Ts)(n2 * delta);
-    }
-    const Sz<LOG2N> z(d.log2n);
-    const int n = z.n, C = d.tC, T = z.T;
+    constexpr int n = 1 << LOG2N;
+    constexpr int SEG = col_seg_rows(n, (int)sizeof(V));
+    constexpr int P = n / SEG;
+    // carry terms below this weight are dropped (far below the rounding of Ts)
+    constexpr Ts CARRY_EPS = sizeof(Ts) == 4 ? (Ts)1e-10 : (Ts)1e-19;
+    const Sz<LOG2N> z(LOG2N);
+    const int C = d.tC;
     const int tid = threadIdx.x;
-    const int t = tid / C, cc = tid - (tid / C) * C;
-    const bool active = t < T;
-    const int SEQ = seq_stride(n);
-    V* buf = smem + (active ? cc : 0) * SEQ;
-    V v[8];
-    if (active) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = Tg[node_at(d, z, t + m * T, c0 + cc)];
-    }
-    const V* tw = twiddles<V>(tb, n);
-    fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, t, tw, active);   // barrier: csc visible
-    const Ts n2c0 = csc[0], n2d = csc[1];
-    const bool drop0 = (n2d == (Ts)0);
+    const int s = tid / C, cc = tid - (tid / C) * C;
+    const bool active = s < P;
     const int k2 = c0 + cc;
-    const Ts* lap = lap_table<Ts>(tb, n);
-    DotAcc<Ts> ax, ay;
-    if (active) {
-        const Ts lap2 = lap[k2];
-        const Ts q4 = (Ts)0.25;
+    const bool zero_block = (c0 == 0 && delta == 0.0);   // block holds the singular column
+    const bool zcol = zero_block && cc == 0;
+    if (tid == 0) csc[0] = (Ts)(1.0 / ((double)n * d.c0));
+    V v[SEG];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int k1 = t + m * T;
-            const V z = v[m];
-            const V zm = buf[pidx((n - k1) & (n - 1))];
-            const Ts sig = n2c0 * (lap[k1] + lap2) + n2d;
-            const Ts inv = (k1 == 0 && k2 == 0 && drop0) ? (Ts)0 : fast_rcp(sig);
-            const Ts w = q4 * inv;
-            const Ts apx = z.x + zm.x, apy = z.y - zm.y;   // 2 A
-            const Ts amx = z.x - zm.x, amy = z.y + zm.y;   // 2 i B
-            ax.add(w, apx * apx + apy * apy);
-            ay.add(w, amx * amx + amy * amy);
-            v[m] = mk<V>(z.x * inv, -(z.y * inv));        // conj(s Z)
+    for (int i = 0; i < SEG; ++i)
+        v[i] = active ? Tg[node_at(d, z, s * SEG + i, k2)] : mk<V>((Ts)0, (Ts)0);
+    Ts rho = (Ts)1;
+    if (active && !zcol)
+        rho = (delta == 0.0) ? rho_table<Ts>(tb, n)[k2]
+                             : (Ts)filter_root(tb.lap[n + k2] + delta / d.c0);   // rare: FP64
+    V* E = smem;                  // [P][C] segment end values (causal pass)
+    V* B = smem + P * C;          // [P][C] segment start values (anticausal pass)
+    V* Zs = smem + 2 * P * C;     // [2][P] singular column: segment sums
+    // causal filter within the segment
+#pragma unroll
+    for (int i = 1; i < SEG; ++i) {
+        v[i].x += rho * v[i - 1].x;
+        v[i].y += rho * v[i - 1].y;
+    }
+    if (active) E[s * C + cc] = v[SEG - 1];
+    __syncthreads();   // also publishes csc
+    const Ts inv_nc0 = csc[0];
+    Ts R = (Ts)0, inv1mRP = (Ts)0;
+    if (active && !zcol) {
+        R = rho;
+#pragma unroll
+        for (int k = 1; k < SEG; k <<= 1) R *= R;            // rho^SEG
+        Ts RP = R;
+#pragma unroll
+        for (int k = 1; k < P; k <<= 1) RP *= RP;            // rho^n
+        inv1mRP = (Ts)1 / ((Ts)1 - RP);
+        V acc = mk<V>((Ts)0, (Ts)0);
+        Ts Rj = (Ts)1;
+        for (int j = 1; j <= P; ++j) {
+            const V e = E[((s - j) & (P - 1)) * C + cc];
+            acc.x += Rj * e.x;
+            acc.y += Rj * e.y;
+            Rj *= R;
+            if (Rj < CARRY_EPS) break;
+        }
+        const Ts cx = acc.x * inv1mRP, cy = acc.y * inv1mRP;
+        Ts pw = rho;
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            v[i].x += pw * cx;
+            v[i].y += pw * cy;
+            pw *= rho;
+        }
+    } else if (active) {   // singular column: y = cumsum(t - mean t)
+        V tot = mk<V>((Ts)0, (Ts)0), pre = mk<V>((Ts)0, (Ts)0);
+        for (int j = 0; j < P; ++j) {
+            const V e = E[j * C];
+            tot.x += e.x;
+            tot.y += e.y;
+            if (j < s) { pre.x += e.x; pre.y += e.y; }
+        }
+        const Ts mx = tot.x / (Ts)n, my = tot.y / (Ts)n;
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            const Ts k = (Ts)(s * SEG + i + 1);
+            v[i].x += pre.x - k * mx;
+            v[i].y += pre.y - k * my;
         }
     }
-    fft_reg<FFT_TO_REGS, LOG2N>(v, buf, z.log2n, t, tw, active);   // its first barrier ends the reads
-    if (active) {
+    Ts wbx = (Ts)0, wby = (Ts)0;   // singular column: mean of w
+    if (zero_block) {              // block-uniform
+        if (zcol && active) {
+            V s1 = mk<V>((Ts)0, (Ts)0), s2 = mk<V>((Ts)0, (Ts)0);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const V o = v[m];
-            Tg[node_at(d, z, t + m * T, c0 + cc)] = mk<V>(o.x, -o.y);
+            for (int i = 0; i < SEG; ++i) {
+                const Ts k = (Ts)(s * SEG + i + 1);
+                s1.x += v[i].x; s1.y += v[i].y;
+                s2.x += k * v[i].x; s2.y += k * v[i].y;
+            }
+            Zs[s] = s1;
+            Zs[P + s] = s2;
+        }
+        __syncthreads();
+        if (zcol && active) {
+            V t1 = mk<V>((Ts)0, (Ts)0), t2 = mk<V>((Ts)0, (Ts)0);
+            for (int j = 0; j < P; ++j) {
+                t1.x += Zs[j].x; t1.y += Zs[j].y;
+                t2.x += Zs[P + j].x; t2.y += Zs[P + j].y;
+            }
+            const Ts ybx = t1.x / (Ts)n, yby = t1.y / (Ts)n;
+            const Ts tri = (Ts)0.5 * (Ts)(n + 1);   // (1/n) sum_{j=1..n} j
+            wbx = t2.x / (Ts)n - ybx * tri;
+            wby = t2.y / (Ts)n - yby * tri;
+#pragma unroll
+            for (int i = 0; i < SEG; ++i) { v[i].x -= ybx; v[i].y -= yby; }
+        }
+    }
+    // rho partials: (rho / (n c0)) |F t|^2 per corrector
+    DotAcc<Ts> ax, ay;
+    if (active) {
+        Ts qx = (Ts)0, qy = (Ts)0;
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            qx += v[i].x * v[i].x;
+            qy += v[i].y * v[i].y;
+        }
+        const Ts wgt = rho * inv_nc0;
+        ax.add(wgt, qx);
+        ay.add(wgt, qy);
+    }
+    // anticausal filter within the segment
+#pragma unroll
+    for (int i = SEG - 2; i >= 0; --i) {
+        v[i].x += rho * v[i + 1].x;
+        v[i].y += rho * v[i + 1].y;
+    }
+    if (active) B[s * C + cc] = v[0];
+    __syncthreads();
+    if (active) {
+        Ts sc, wx, wy;
+        if (!zcol) {
+            V acc = mk<V>((Ts)0, (Ts)0);
+            Ts Rj = (Ts)1;
+            for (int j = 1; j <= P; ++j) {
+                const V e = B[((s + j) & (P - 1)) * C + cc];
+                acc.x += Rj * e.x;
+                acc.y += Rj * e.y;
+                Rj *= R;
+                if (Rj < (Ts)1e-18) break;
+            }
+            wx = acc.x * inv1mRP;
+            wy = acc.y * inv1mRP;
+            sc = rho * inv_nc0;
+        } else {   // w = reverse cumsum of y, then mean-zero
+            V suf = mk<V>((Ts)0, (Ts)0);
+            for (int j = s + 1; j < P; ++j) { suf.x += B[j * C].x; suf.y += B[j * C].y; }
+            wx = suf.x;
+            wy = suf.y;
+            sc = inv_nc0;
+        }
+        Ts pw = zcol ? (Ts)0 : rho;
+#pragma unroll
+        for (int i = SEG - 1; i >= 0; --i) {
+            const Ts gx = zcol ? (wx - wbx) : pw * wx;
+            const Ts gy = zcol ? (wy - wby) : pw * wy;
+            Tg[node_at(d, z, s * SEG + i, k2)] = mk<V>((v[i].x + gx) * sc, (v[i].y + gy) * sc);
+            pw *= rho;
         }
     }
     if (rho_part) {
@@ -755,9 +900,9 @@ template <typename V>
 __device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
                                    const Tables& tb, double delta, double* red,
                                    double* rho_part) {
-    __shared__ typename ScalarOf<V>::T csc[2];
+    __shared__ typename ScalarOf<V>::T csc[1];
     dispatch_size(d.log2n, [&]<int LG>() {
-        col_transform_body<V, LG>(Tg, d, c0, smem, tb, delta, red, rho_part, csc);
+        col_solve_body<V, LG>(Tg, d, c0, smem, tb, delta, red, rho_part, csc);
     });
 }
 
@@ -783,7 +928,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const C
 template <typename V>
 __global__ void __launch_bounds__(256) k_fused_U(const Ctx c) { fused_U_tile<V>(c, blockIdx.x); }
 template <typename V>
-__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_fused_C(const Ctx c) {
+__global__ void __launch_bounds__(512) k_fused_C(const Ctx c) {
     fused_C_tile<V>(c, blockIdx.x);
 }
 
@@ -1119,10 +1264,7 @@ static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double*
     c.partC = reinterpret_cast<double*>(w + p.o_partC);
     c.uscal = reinterpret_cast<double*>(w + p.o_uscal);
     c.tiles_done = reinterpret_cast<int*>(w + p.o_cnt);
-    c.tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
-    c.tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
-    c.tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
-    c.tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
+    c.tb = tables_of(p, ws);
     c.cs.mask = mask;
     c.cs.coef = coef;
     c.u = reinterpret_cast<double2*>(u);
@@ -1157,12 +1299,7 @@ rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
         e = cudaMemcpyAsync(w + p.o_startA, p.startA.data(), sizeof(int32_t) * (p.batch + 1),
                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return RVE_ECUDA;
-    const int total = 2 << p.max_log2n;
-    k_tables<<<(total + 255) / 256, 256, 0, s>>>(reinterpret_cast<double2*>(w + p.o_tw64),
-                                                 reinterpret_cast<float2*>(w + p.o_tw32),
-                                                 reinterpret_cast<double*>(w + p.o_lap),
-                                                 reinterpret_cast<float*>(w + p.o_lap32), total);
-    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+    return launch_tables(p, ws, s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
 template <typename V, int SCHEME>
@@ -1286,14 +1423,9 @@ rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mas
                                     const double* coef, const rve_solve_opts& o, double* u,
                                     rve_solve_info* info, cudaStream_t s) {
     Ctx c = make_ctx(p, ws, mask, coef, u, o);
-    char* w = static_cast<char*>(ws);
-    const int total = 2 << p.max_log2n;
-    k_tables<<<(total + 255) / 256, 256, 0, s>>>(reinterpret_cast<double2*>(w + p.o_tw64),
-                                                 reinterpret_cast<float2*>(w + p.o_tw32),
-                                                 reinterpret_cast<double*>(w + p.o_lap),
-                                                 reinterpret_cast<float*>(w + p.o_lap32), total);
+    if (launch_tables(p, ws, s) != cudaSuccess) return RVE_ECUDA;
     k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
-    note_launch(2);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     rve_status st;
     if (p.precision == RVE_MIXED)
@@ -1340,7 +1472,7 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
     if (st != RVE_OK) return st;
     Ctx c = make_ctx(p, ws, mask, coef, u, o);
     k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
-    note_launch(2);   // tables + init
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     if (p.precision == RVE_MIXED) {
         st = (p.scheme == RVE_Q1_LUMPED) ? fused_loop<float2, 1>(p, c, o, s)
@@ -1385,7 +1517,7 @@ __global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ d
 }
 
 template <typename V>
-__global__ void __launch_bounds__(sizeof(V) == 8 ? 1024 : 512) k_col_hartley(const RDesc* __restrict__ desc,
+__global__ void __launch_bounds__(512) k_col_hartley(const RDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ startC, int batch,
                                                       int tile0, Tables tb, double delta,
                                                       V* __restrict__ T) {
@@ -1405,11 +1537,7 @@ cudaError_t precond_passes(const Plan& p, void* ws, double delta, const V* x, V*
     const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
     const int32_t* startU = reinterpret_cast<const int32_t*>(w + p.o_startU);
     const int32_t* startC = reinterpret_cast<const int32_t*>(w + p.o_startC);
-    Tables tb;
-    tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
-    tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
-    tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
-    tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
+    const Tables tb = tables_of(p, ws);
     cudaError_t e = cudaFuncSetAttribute(k_row_hartley<V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smemU);
     if (e == cudaSuccess)
