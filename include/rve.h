@@ -108,21 +108,34 @@ typedef struct {
     double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-4)*/
     int32_t tile_rows;   /* stencil tile height in node rows (1..n; n need
                             not be a multiple), 0 = tuned or default       */
-    int32_t col_tile;    /* threads of a column-transform block (power of
-                            two, 32..1024); 0 = 512, or 1024 when n > 512  */
+    int32_t col_tile;    /* threads of a column-solve block (power of two,
+                            32..512); 0 = 512                               */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
     int32_t timeout_us;  /* persistent path: bound on each grid-wide wait, in
                             microseconds (0 = 2 s)                          */
+    int32_t flags;       /* RVE_FLAG_* bits                                 */
+    int32_t reserved;    /* must be 0                                       */
 } rve_solve_opts;
+
+/* rve_solve_opts.flags.  RVE_FLAG_CLUSTER: on the fused mixed-precision
+ * path, run the update and column passes of a batch of equal-size grids
+ * (n = 128..512) as one thread-block-cluster kernel (16 blocks per
+ * realization, the row transform kept in distributed shared memory instead
+ * of HBM) when the device can host such clusters.  It moves 16 fewer bytes
+ * per node and step but runs one block per SM with its phases in sequence;
+ * on GB300 it measured slower than the two separate kernels (547 vs 367 us
+ * per step for 125 grids of 512^2), so it is off by default. */
+#define RVE_FLAG_CLUSTER 1
 
 /* Per-realization solver report (device memory, one per realization). */
 typedef struct {
     int32_t iters[2];     /* CG iterations (operator applications) per corrector */
     int32_t status;       /* rve_status                                           */
-    int32_t refinements;  /* FP64 true-residual evaluations                       */
+    int32_t refinements;  /* true-residual evaluations (FP64 or double word)      */
     int32_t steps;        /* fused pipeline steps spent iterating (both correctors
                              advance together; plain path: CG iterations)         */
-    int32_t reserved;
+    int32_t kernels;      /* bit 0: the update and column passes ran as one
+                             thread-block-cluster kernel (RVE_FLAG_CLUSTER)    */
     double relres[2];     /* last FP64 true relative residual per corrector       */
 } rve_solve_info;         /* 40 bytes */
 

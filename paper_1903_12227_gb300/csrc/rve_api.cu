@@ -49,7 +49,8 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
 // rows in shared memory: the largest power of two <= 8 whose tile fits
 // 110 KB (two blocks per SM; at least 1).  Column blocks use blockC
 // threads, n / col_seg_rows per column.
-static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
+static void default_tiles(int n, size_t vb, int blockC, bool uc, const rve_solve_opts& o,
+                          Tiles& t) {
     const size_t seq = (size_t)seq_stride(n);
     t.tU = std::min(n, 2048 / n);
     // stencil tile: tS own rows + 2 halo rows, transformed G = 2048/n rows
@@ -77,6 +78,10 @@ static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o,
     if (tuned_tiles(n, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0, &ts_tuned, &bc_tuned))
         t.tS = ts_tuned;
     t.tC = std::min(n, blockC / (n / col_seg_rows(n, (int)vb)));
+    if (uc) {   // cluster kernel: block `rank` updates and solves n/16 rows / columns
+        t.tU = n / UC_CTAS;
+        t.tC = n / UC_CTAS;
+    }
     if (o.tile_rows > 0) t.tS = o.tile_rows;
     t.tS = std::min(t.tS, n);
 }
@@ -122,6 +127,29 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             p.blockC = std::min(512, std::max(32, bc_tuned));   // a loaded table may hold anything
     }
     if (o.path == RVE_PATH_PERSISTENT) p.blockC = 256;   // one block shape for all phases
+    // update + column as one cluster kernel (on request): fused mixed path,
+    // one grid size n = 128..512 for the whole batch, and a device that can
+    // host the clusters (t of one realization: n/16 rows per block in shared
+    // memory)
+    p.uc_cluster = false;
+    p.smemUC = 0;
+    {
+        const int64_t n0 = (int64_t)r[0].L * r[0].m0;
+        bool same = n0 >= 128 && n0 <= 512 && pow2((int)n0);
+        for (int b = 1; b < batch && same; ++b) same = ((int64_t)r[b].L * r[b].m0 == n0);
+        if (same && o.path == RVE_PATH_FUSED && o.precision == RVE_MIXED &&
+            (o.flags & RVE_FLAG_CLUSTER)) {
+            const int n = (int)n0;
+            const size_t rows_smem = (size_t)(n / UC_CTAS) * n * sizeof(float2);
+            const size_t rowbuf = (size_t)(UC_THREADS / (n / 8)) * seq_stride(n) * sizeof(float2);
+            const size_t colbuf = (size_t)(2 * (n / UC_CTAS) + 2) * UC_CTAS * sizeof(float2);
+            const size_t smem = rows_smem + std::max(rowbuf, colbuf);
+            if (uc_cluster_ok(ilog2(n), smem)) {
+                p.uc_cluster = true;
+                p.smemUC = smem;
+            }
+        }
+    }
     if (o.col_tile > 0 && o.path != RVE_PATH_PERSISTENT)
         p.blockC = std::min(512, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
@@ -136,10 +164,10 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             !(x.a_incl > 0.0))
             return RVE_EINVAL;
         Tiles t;
-        default_tiles(n, p.vbytes, p.blockC, o, t);
+        default_tiles(n, p.vbytes, p.blockC, p.uc_cluster, o, t);
         const int segs = n / col_seg_rows(n, (int)p.vbytes);   // threads per column
         if (t.tS < 1 || t.tS > n || t.tC < 1 || !pow2(t.tC) || n % t.tC ||
-            t.tC * segs > p.blockC)
+            t.tC * segs > (p.uc_cluster ? UC_THREADS : p.blockC))
             return RVE_EINVAL;
         RDesc& d = p.desc[b];
         std::memset(&d, 0, sizeof(d));

@@ -26,6 +26,7 @@ NOALLOC_MAX_NODES = 1 << 24
 FP64, MIXED = 0, 1
 CONSISTENT, LUMPED = 0, 1
 PATH_FUSED, PATH_PLAIN, PATH_PERSISTENT = 0, 1, 2
+FLAG_CLUSTER = 1
 
 
 class Realization(ctypes.Structure):
@@ -43,13 +44,14 @@ class SolveOpts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("tile_rows", ctypes.c_int32),
                 ("col_tile", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("timeout_us", ctypes.c_int32)]
+                ("timeout_us", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32 * 2), ("status", ctypes.c_int32),
                 ("refinements", ctypes.c_int32), ("steps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
+                ("kernels", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
 
 
 INFO_BYTES = ctypes.sizeof(SolveInfo)
@@ -186,9 +188,9 @@ def as_batch(b) -> Batch:
 
 def make_opts(scheme=CONSISTENT, precision=FP64, path=PATH_FUSED, tol=1e-10, max_iter=0,
               delta=0.0, inner_tol=0.0, tile_rows=0, col_tile=0, check_every=0,
-              timeout_us=0) -> SolveOpts:
+              timeout_us=0, flags=0) -> SolveOpts:
     return SolveOpts(scheme, precision, path, max_iter, tol, delta, inner_tol, tile_rows,
-                     col_tile, check_every, timeout_us)
+                     col_tile, check_every, timeout_us, flags, 0)
 
 
 def _dev(device):
@@ -259,7 +261,8 @@ def info_to_dicts(info: torch.Tensor, count: int) -> list:
 
 def _info_dict(a: SolveInfo) -> dict:
     return {"iters": (a.iters[0], a.iters[1]), "status": a.status, "refinements": a.refinements,
-            "steps": a.steps, "relres": (a.relres[0], a.relres[1])}
+            "steps": a.steps, "relres": (a.relres[0], a.relres[1]),
+            "cluster": bool(a.kernels & 1)}
 
 
 def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u=None,

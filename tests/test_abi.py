@@ -40,6 +40,7 @@ def test_struct_sizes_match_header(librve):
     from paper_1903_12227_gb300 import rve
     assert ctypes.sizeof(rve.Realization) == 48
     assert ctypes.sizeof(rve.SolveInfo) == 40
+    assert ctypes.sizeof(rve.SolveOpts) == 64
 
 
 def test_host_validation_without_gpu(librve):
