@@ -198,6 +198,45 @@ __device__ __forceinline__ dword dw_of(double a) {
     return {h, __double2float_rn(a - (double)h)};
 }
 
+// Double word times float: unevaluated (exact high product, error + cross term).
+__device__ __forceinline__ dword dw_mulf(dword x, float f) {
+    const float p = __fmul_rn(x.hi, f);
+    return {p, __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p))};
+}
+
+// Double word of a double from its IEEE-754 fields, with integer
+// instructions only: hi = x truncated to float's 24 significant bits
+// (exact), lo = the remaining 29 bits rounded to float, so hi + lo carries
+// 48+ bits and |lo| < ulp(hi).  |x| below 2^-126 gives (0, 0); the low part
+// of |x| below 2^-74 is dropped; |x| beyond float's range gives +-inf.
+__device__ __forceinline__ dword dw_split(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(bits >> 63) << 31;
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    if (e < 897) return {__int_as_float((int)sign), 0.f};              // zero, tiny
+    if (e > 1150) return {__int_as_float((int)(sign | 0x7F800000u | (e == 0x7FF && m ? 0x400000u : 0u))), 0.f};
+    const float hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29)));
+    const int pe = e - 948;                    // biased exponent of 2^(e - 1075)
+    float lo = 0.f;
+    if (pe >= 1) lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) * __int_as_float(pe << 23);
+    return {hi, sign ? -lo : lo};
+}
+
+// Double word times double word, unevaluated: exact product of the high
+// parts plus its error and the cross terms (the lo*lo term is below eps^2).
+__device__ __forceinline__ dword dw_mul(dword x, dword y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    return {p, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, __fmaf_rn(x.hi, y.hi, -p)))};
+}
+
+// Per-thread running double-word sum of unevaluated terms (hi, lo).
+__device__ __forceinline__ void dw_acc(dword& s, dword t) {
+    const dword u = two_sum(s.hi, t.hi);
+    s.hi = u.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(u.lo, t.lo));
+}
+
 // Running sum  s0 + sum_k (+-) c_k w_k  of double-word products: the
 // product of the high parts is split exactly (TwoProd) and added with TwoSum;
 // the rounding errors and the cross terms gather in a float compensation

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "rve_ahom.cuh"
 #include "rve_common.cuh"
 #include "rve_internal.h"
 
@@ -31,6 +32,7 @@ namespace rve {
 constexpr int NA_TILE = 1024;                       // nodes per partial-sum tile
 constexpr int NA_NP = 8;                            // partial sums per tile
 constexpr int64_t NA_MAX_TILES = RVE_NOALLOC_MAX_NODES / NA_TILE;
+static_assert(NA_TILE == AHOM_TILE && NA_NP == AHOM_NP, "tiles of rve_ahom.cuh");
 constexpr int NA_MAX_DEVICES = 64;
 
 // The fixed scratch (1 MiB).  Host code must not pass its name to a kernel:
@@ -58,74 +60,27 @@ static cudaError_t noalloc_scratch(double** out) {
     return cudaSuccess;
 }
 
-template <typename V>
-__device__ __forceinline__ V na_ld(const V* __restrict__ x, const RDesc& d, int i, int j) {
-    return x[d.node_off + ((int64_t)(i & (d.n - 1)) << d.log2n) + (j & (d.n - 1))];
-}
-
-// Partial sums of one tile (same quantities as the workspace entry point):
-//   [0] sum a_c, [1..4] f_i.u_j, [5] u_1.A u_1, [6] u_1.A u_2, [7] u_2.A u_2.
+// Partial sums of one tile and the final forms: the same cell-form
+// arithmetic as the workspace entry point (rve_ahom.cuh).
 template <int SCHEME>
 __global__ void __launch_bounds__(256) k_na_part(const __grid_constant__ DescChunk ch, CoefSrc cs,
                                                  const double2* __restrict__ u,
                                                  double* __restrict__ part) {
-    __shared__ double red[8];
+    __shared__ double red[64];
+    __shared__ float sc[5];
     const int b = find_real(ch.start, ch.count, blockIdx.x);
-    const RDesc& d = ch.d[b];
-    const int64_t base = (int64_t)(blockIdx.x - ch.start[b]) * NA_TILE;
-    double acc[NA_NP];
-#pragma unroll
-    for (int k = 0; k < NA_NP; ++k) acc[k] = 0.0;
-    for (int t = threadIdx.x; t < NA_TILE; t += blockDim.x) {
-        const int64_t node = base + t;
-        const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
-        const Cells4 a = cells_at(cs, d, i, j);
-        const double2 f = rhs_at(a, d.h);
-        const double2 q = stencil_apply<SCHEME, double2>(
-            a, na_ld(u, d, i - 1, j - 1), na_ld(u, d, i - 1, j), na_ld(u, d, i - 1, j + 1),
-            na_ld(u, d, i, j - 1), na_ld(u, d, i, j), na_ld(u, d, i, j + 1),
-            na_ld(u, d, i + 1, j - 1), na_ld(u, d, i + 1, j), na_ld(u, d, i + 1, j + 1));
-        const double2 uu = na_ld(u, d, i, j);
-        acc[0] += a.z00;
-        acc[1] = fma(f.x, uu.x, acc[1]);
-        acc[2] = fma(f.x, uu.y, acc[2]);
-        acc[3] = fma(f.y, uu.x, acc[3]);
-        acc[4] = fma(f.y, uu.y, acc[4]);
-        acc[5] = fma(uu.x, q.x, acc[5]);
-        acc[6] = fma(uu.x, q.y, acc[6]);
-        acc[7] = fma(uu.y, q.y, acc[7]);
-    }
-#pragma unroll
-    for (int k = 0; k < NA_NP; ++k) {
-        const double s = block_sum(acc[k], red);
-        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NA_NP + k] = s;
-    }
+    a_hom_tile<SCHEME>(ch.d[b], blockIdx.x - ch.start[b], cs, u, red, sc,
+                       part + (int64_t)blockIdx.x * NA_NP);
 }
 
-// One warp per realization of the chunk: fixed-order sum of its partials,
-// then the energy and flux forms (as rve_a_hom).
+// One warp per realization of the chunk.
+template <int SCHEME>
 __global__ void k_na_final(const __grid_constant__ DescChunk ch, const double* __restrict__ part,
                            double* __restrict__ A, double* __restrict__ Af) {
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= ch.count) return;
-    const RDesc& d = ch.d[b];
-    const int t0 = ch.start[b], nt = ch.start[b + 1] - ch.start[b];
-    double s[NA_NP];
-#pragma unroll
-    for (int k = 0; k < NA_NP; ++k) s[k] = warp_sum_array(part + (int64_t)t0 * NA_NP + k, nt, NA_NP);
-    if ((threadIdx.x & 31) != 0) return;
-    const double mean_a = s[0] / ((double)d.n * (double)d.n);
-    const double iv = d.inv_vol;
-    A[4 * b + 0] = mean_a - (2.0 * s[1] - s[5]) * iv;
-    A[4 * b + 1] = -(s[2] + s[3] - s[6]) * iv;
-    A[4 * b + 2] = -(s[3] + s[2] - s[6]) * iv;
-    A[4 * b + 3] = mean_a - (2.0 * s[4] - s[7]) * iv;
-    if (Af) {
-        Af[4 * b + 0] = mean_a - s[1] * iv;
-        Af[4 * b + 1] = -s[3] * iv;
-        Af[4 * b + 2] = -s[2] * iv;
-        Af[4 * b + 3] = mean_a - s[4] * iv;
-    }
+    a_hom_finish<SCHEME>(ch.d[b], part + (int64_t)ch.start[b] * NA_NP, ch.start[b + 1] - ch.start[b],
+                         A + 4 * (int64_t)b, Af ? Af + 4 * (int64_t)b : nullptr);
 }
 
 }  // namespace rve
@@ -161,7 +116,11 @@ extern "C" rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch,
         const int tiles = ch.start[ch.count];
         if (scheme == RVE_Q1_LUMPED) k_na_part<1><<<tiles, 256, 0, s>>>(ch, cs, uu, part);
         else k_na_part<0><<<tiles, 256, 0, s>>>(ch, cs, uu, part);
-        k_na_final<<<(ch.count + 7) / 8, 256, 0, s>>>(ch, part, A + 4 * (int64_t)b0,
+        if (scheme == RVE_Q1_LUMPED)
+            k_na_final<1><<<(ch.count + 7) / 8, 256, 0, s>>>(ch, part, A + 4 * (int64_t)b0,
+                                                      A_flux ? A_flux + 4 * (int64_t)b0 : nullptr);
+        else
+            k_na_final<0><<<(ch.count + 7) / 8, 256, 0, s>>>(ch, part, A + 4 * (int64_t)b0,
                                                       A_flux ? A_flux + 4 * (int64_t)b0 : nullptr);
         if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
         note_launch(2);

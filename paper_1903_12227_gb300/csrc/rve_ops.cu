@@ -4,6 +4,7 @@
 
 #include <algorithm>
 
+#include "rve_ahom.cuh"
 #include "rve_common.cuh"
 #include "rve_internal.h"
 
@@ -134,79 +135,30 @@ __global__ void k_backward(const __grid_constant__ DescChunk ch, const double2* 
 }
 
 // ---------------------------------------------------------------- A_hom --
-// Per tile of 1024 nodes: partial sums of
-//   [0] sum a_c          [1..4] F_ij = f_i . u_j   (i,j = 1,2)
-//   [5] E_11 = u_1.A u_1 [6] E_12 = u_1.A u_2      [7] E_22 = u_2.A u_2
-// (E_21 is taken equal to E_12 so that the energy form is exactly symmetric).
-constexpr int AHOM_TILE = 1024;
-constexpr int AHOM_NP = 8;
-
+// Cell-form partial sums per tile and the final reduction (rve_ahom.cuh).
 template <int SCHEME>
 __global__ void __launch_bounds__(256) k_a_hom_part(const RDesc* __restrict__ desc,
                                                     const int32_t* __restrict__ start, int batch,
                                                     CoefSrc cs, const double2* __restrict__ u,
                                                     double* __restrict__ part) {
-    __shared__ double red[8];
+    __shared__ double red[64];
+    __shared__ float sc[5];
     const int b = find_real(start, batch, blockIdx.x);
     const RDesc d = desc[b];
-    const int64_t base = (int64_t)(blockIdx.x - start[b]) * AHOM_TILE;
-    double acc[AHOM_NP];
-#pragma unroll
-    for (int k = 0; k < AHOM_NP; ++k) acc[k] = 0.0;
-    for (int t = threadIdx.x; t < AHOM_TILE; t += blockDim.x) {
-        const int64_t node = base + t;
-        const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
-        const Cells4 a = cells_at(cs, d, i, j);
-        const double2 f = rhs_at(a, d.h);
-        const double2 q = stencil_apply<SCHEME, double2>(
-            a, ldv(u, d, i - 1, j - 1), ldv(u, d, i - 1, j), ldv(u, d, i - 1, j + 1),
-            ldv(u, d, i, j - 1), ldv(u, d, i, j), ldv(u, d, i, j + 1),
-            ldv(u, d, i + 1, j - 1), ldv(u, d, i + 1, j), ldv(u, d, i + 1, j + 1));
-        const double2 uu = ldv(u, d, i, j);
-        acc[0] += a.z00;
-        acc[1] = fma(f.x, uu.x, acc[1]);
-        acc[2] = fma(f.x, uu.y, acc[2]);
-        acc[3] = fma(f.y, uu.x, acc[3]);
-        acc[4] = fma(f.y, uu.y, acc[4]);
-        acc[5] = fma(uu.x, q.x, acc[5]);
-        acc[6] = fma(uu.x, q.y, acc[6]);
-        acc[7] = fma(uu.y, q.y, acc[7]);
-    }
-#pragma unroll
-    for (int k = 0; k < AHOM_NP; ++k) {
-        const double s = block_sum(acc[k], red);
-        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * AHOM_NP + k] = s;
-    }
+    a_hom_tile<SCHEME>(d, blockIdx.x - start[b], cs, u, red, sc,
+                       part + (int64_t)blockIdx.x * AHOM_NP);
 }
 
-// One warp per realization: fixed-order sum of the tile partials, then
-//   energy a_ij = mean(a) d_ij - (F_ij + F_ji - E_ij) / L^2
-//   flux   a_ij = mean(a) d_ij - F_ji / L^2            (F_ij = f_i . u_j)
+// One warp per realization.
+template <int SCHEME>
 __global__ void k_a_hom_final(const RDesc* __restrict__ desc, const int32_t* __restrict__ start,
                               int batch, const double* __restrict__ part, double* __restrict__ A,
                               double* __restrict__ Af) {
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= batch) return;
     const RDesc d = desc[b];
-    const int t0 = start[b], nt = start[b + 1] - start[b];
-    double s[AHOM_NP];
-#pragma unroll
-    for (int k = 0; k < AHOM_NP; ++k) s[k] = warp_sum_array(part + (int64_t)t0 * AHOM_NP + k, nt, AHOM_NP);
-    if ((threadIdx.x & 31) != 0) return;
-    const double mean_a = s[0] / ((double)d.n * (double)d.n);
-    const double F11 = s[1], F12 = s[2], F21 = s[3], F22 = s[4];
-    const double E11 = s[5], E12 = s[6], E22 = s[7];
-    const double iv = d.inv_vol;
-    A[4 * b + 0] = mean_a - (2.0 * F11 - E11) * iv;
-    A[4 * b + 1] = -(F12 + F21 - E12) * iv;
-    A[4 * b + 2] = -(F21 + F12 - E12) * iv;
-    A[4 * b + 3] = mean_a - (2.0 * F22 - E22) * iv;
-    if (Af) {
-        Af[4 * b + 0] = mean_a - F11 * iv;
-        Af[4 * b + 1] = -F21 * iv;   // a_12 = -f_2.u_1 / L^2
-        Af[4 * b + 2] = -F12 * iv;   // a_21 = -f_1.u_2 / L^2
-        Af[4 * b + 3] = mean_a - F22 * iv;
-    }
+    a_hom_finish<SCHEME>(d, part + (int64_t)start[b] * AHOM_NP, start[b + 1] - start[b],
+                         A + 4 * (int64_t)b, Af ? Af + 4 * (int64_t)b : nullptr);
 }
 
 // ------------------------------------------------------------- launchers --
@@ -299,7 +251,10 @@ cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const do
         k_a_hom_part<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_a_hom_final<<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    if (scheme == RVE_Q1_LUMPED)
+        k_a_hom_final<1><<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    else
+        k_a_hom_final<0><<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
     note_launch(2);
     return cudaGetLastError();
 }

@@ -250,11 +250,6 @@ __device__ __forceinline__ float4 w_new(float4 u, float2 x, float2 p, const DWSc
     return make_float4(wx.hi, wy.hi, wx.lo, wy.lo);
 }
 
-// Double word times float: unevaluated (exact high product, error + cross term).
-__device__ __forceinline__ dword dw_mulf(dword x, float f) {
-    const float p = __fmul_rn(x.hi, f);
-    return {p, __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p))};
-}
 
 // REFINE step of the mixed path: r = f - A w for the tile's rows with
 // w = u + s (x + alpha p), in double-word arithmetic on the FP32 pipe (no
@@ -580,18 +575,26 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
                               [&](int r, int k, V val) { out[node_at(d, z, r, k)] = val; });
 }
 
-// Update + row transform of rows row0 .. row0 + rows - 1 of realization b,
-// blockDim / (n/8) rows per pass, with `rowbuf` the padded per-row scratch
-// of one pass.  ITER: r -= alpha q, |r|^2, t = row-Hartley(r).  REFINE:
+// Update + row transform of rows row0 .. row0 + rows - 1 of realization b
+// (the cluster kernel's update phase), blockDim / (n/8) rows per pass, with
+// `rowbuf` the padded per-row scratch of one pass.  ITER: r -= alpha q, |r|^2, t = row-Hartley(r).  REFINE:
 // u = w (the new iterate), x = 0, r = r64 / |r64|, |r|^2, t = row-Hartley(r).
-// t goes to out(row, k, value); the |r|^2 partials stay in (ax, ay).
+// t goes to out(row, k, value); the block's |r|^2 sums go to part[0..1].
 template <typename V, int LOG2N, typename Out>
 __device__ __forceinline__ void update_rows(const Ctx& c, int b, const RState& s,
                                             const RDesc& d, int row0, int rows, V* rowbuf,
-                                            typename ScalarOf<V>::T* usc,
-                                            DotAcc<typename ScalarOf<V>::T>& ax,
-                                            DotAcc<typename ScalarOf<V>::T>& ay, Out&& out) {
+                                            typename ScalarOf<V>::T* usc, double* red,
+                                            double* part, Out&& out) {
     typedef typename ScalarOf<V>::T T;
+    DotAcc<T> ax, ay;
+    auto flush = [&]() {   // block sums of |r|^2 into part[0..1]
+        double sx = 0.0, sy = 0.0;
+        block_sum2(ax, ay, red, sx, sy);
+        if (threadIdx.x == 0) {
+            part[0] = sx;
+            part[1] = sy;
+        }
+    };
     const int phase = s.phase;
     const RowLayout<LOG2N> L(d.log2n);
     const Sz<LOG2N>& z = L.z;
@@ -695,26 +698,127 @@ __device__ __forceinline__ void update_rows(const Ctx& c, int b, const RState& s
         }
         row_hartley_out<V, LOG2N>(v, buf, z, row, L.t, tw, active, out);
     }
+    flush();
 }
 
+// The update kernel proper (one pass of tU rows per block).  The same
+// update as update_rows, written out so that the partial sums are formed
+// before the transform and the kernel stays at ~60 registers.
 template <typename V, int LOG2N>
 __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const RState& s,
                                              const RDesc& d, double* red,
                                              typename ScalarOf<V>::T* usc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int phase = s.phase;
+    const RowLayout<LOG2N> L(d.log2n);
+    const Sz<LOG2N>& z = L.z;
+    const int G = d.tU;
+    const int row = (blk - c.startU[b]) * G + L.qq;
+    const bool active = L.qq < G;
     typedef typename ScalarOf<V>::T T;
-    const Sz<LOG2N> z(d.log2n);
-    V* T_out = static_cast<V*>(c.T);
+    V* R = static_cast<V*>(c.R);
+    V* X = static_cast<V*>(c.X);
+    const V* Qv = static_cast<const V*>(c.Q);
+    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(z.n);
     DotAcc<T> ax, ay;
-    update_rows<V, LOG2N>(c, b, s, d, (blk - c.startU[b]) * d.tU, d.tU,
-                          reinterpret_cast<V*>(smem_raw), usc, ax, ay,
-                          [&](int r, int k, V val) { T_out[node_at(d, z, r, k)] = val; });
+    V v[8];
+    if (phase == PH_ITER) {
+        // alpha = rho / p.q, formed by the last stencil block (finish_S)
+        if (threadIdx.x == 0) {
+            usc[0] = (T)c.uscal[2 * b];
+            usc[1] = (T)c.uscal[2 * b + 1];
+        }
+        __syncthreads();
+        const T alx = usc[0], aly = usc[1];
+        if (active) {
+            V qv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {   // loads first, stores after
+                const int64_t node = node_at(d, z, row, L.t + m * z.T);
+                v[m] = R[node];
+                qv[m] = Qv[node];
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const V rr = axpy2(v[m], -alx, -aly, qv[m]);
+                R[node_at(d, z, row, L.t + m * z.T)] = rr;
+                v[m] = rr;
+                ax.add(rr.x, rr.x);
+                ay.add(rr.y, rr.y);
+            }
+        }
+    } else if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
+        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+        if (threadIdx.x == 0) {   // the same conversions as refine_tile_dw
+            usc[0] = (float)s.s[0];
+            usc[1] = (float)s.s[1];
+            usc[2] = (float)s.alpha[0];
+            usc[3] = (float)s.alpha[1];
+            usc[4] = (float)c.uscal[2 * b];       // 1 / |r| per corrector (0 once
+            usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
+        }
+        __syncthreads();
+        const DWScal k{usc[0], usc[1], usc[2], usc[3]};
+        const float ix = usc[4], iy = usc[5];
+        float4* U4 = reinterpret_cast<float4*>(c.u);
+        if (active) {
+#pragma unroll
+            for (int h = 0; h < 8; h += 4) {
+                float4 uu[4];
+                V xx[4], pp[4], qv[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {   // loads first, stores after
+                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                    uu[m] = U4[node];
+                    xx[m] = X[node];
+                    pp[m] = Pold[node];
+                    qv[m] = Qv[node];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                    U4[node] = w_new(uu[m], xx[m], pp[m], k);
+                    X[node] = mk<V>(0.f, 0.f);
+                    const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
+                    R[node] = rr;
+                    v[h + m] = rr;
+                    ax.add(rr.x, rr.x);
+                    ay.add(rr.y, rr.y);
+                }
+            }
+        }
+    } else {   // REFINE, FP64
+        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+        // 1 / |r64| per corrector (0 once converged), from finish_S
+        const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int64_t node = node_at(d, z, row, L.t + m * z.T);
+                const double2 xx = to_d2(X[node]);
+                const double2 pp = to_d2(Pold[node]);
+                double2 uu = c.u[node];
+                uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
+                uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
+                c.u[node] = uu;
+                X[node] = from_d2<V>(make_double2(0.0, 0.0));
+                const double2 q = to_d2(Qv[node]);
+                const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
+                R[node] = rr;
+                v[m] = rr;
+                ax.add(rr.x, rr.x);
+                ay.add(rr.y, rr.y);
+            }
+        }
+    }
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {
         c.partU[2 * (int64_t)blk] = sx;
         c.partU[2 * (int64_t)blk + 1] = sy;
     }
+    row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, twiddles<V>(c.tb, z.n), active,
+                                static_cast<V*>(c.T));
 }
 
 template <typename V>
@@ -985,16 +1089,9 @@ __global__ void __launch_bounds__(UC_THREADS, 1) k_fused_UC(const Ctx c) {
     V* ts = reinterpret_cast<V*>(smem_raw);   // [RPC][n]: t of this block's rows
     V* scratch = ts + RPC * n;                // row buffers, then column-solve scratch
     const int row0 = rank * RPC;
-    DotAcc<float> ax, ay;
-    update_rows<V, LOG2N>(c, b, s, d, row0, RPC, scratch, usc, ax, ay,
-                          [&](int r, int k, V val) { ts[(r - row0) * n + k] = val; });
-    double sx = 0.0, sy = 0.0;
-    block_sum2(ax, ay, red, sx, sy);
-    if (threadIdx.x == 0) {
-        const int64_t tile = c.startU[b] + rank;
-        c.partU[2 * tile] = sx;
-        c.partU[2 * tile + 1] = sy;
-    }
+    update_rows<V, LOG2N>(c, b, s, d, row0, RPC, scratch, usc, red,
+                                 c.partU + 2 * (int64_t)(c.startU[b] + rank),
+                                 [&](int r, int k, V val) { ts[(r - row0) * n + k] = val; });
     cl.sync();   // t of all blocks written and visible to the cluster
     V* Tg = static_cast<V*>(c.T);
     col_solve_body<V, LOG2N>(

@@ -77,15 +77,16 @@ def test_adjoint_L64_batch64_euler_and_central_differences():
     assert torch.allclose(euler, F, rtol=1e-10, atol=1e-12)
     # central differences on sampled cells of two realizations.  A per-cell
     # derivative here is ~2e-7, so an absolute step of 1e-6 moves F by ~4e-13
-    # out of ~5 -- below the ~1e-14 relative FP64 noise of evaluating A -- and
-    # agrees only to ~10 %; a relative step of 1e-4 keeps the truncation
-    # error ~1e-8 and the round-off ~0.5 %.
+    # out of ~5 -- below the noise of evaluating A (~1e-13 relative for the
+    # double-word A_hom kernel, whose sums of f.u cancel by ~100x) -- and
+    # agrees only to ~10 %; a relative step of 1e-3 keeps the truncation
+    # error ~1e-6 and the round-off ~0.1 %.
     for r in (0, 37):
         d = ds[r]
         base = coef.detach()[r * nn:(r + 1) * nn].clone()
         for c1, c2 in workloads.fd_cells(1024, 3, seed=0, index=r):
             k = int(c1) * 1024 + int(c2)
-            eps = 1e-4 * base[k].item()
+            eps = 1e-3 * base[k].item()
             cp, cm = base.clone(), base.clone()
             cp[k] += eps
             cm[k] -= eps
