@@ -174,6 +174,14 @@ rve_status rve_apply_stiffness(const rve_realization* r, int32_t batch,
                                int32_t scheme, int32_t precision,
                                const void* x, void* y, void* stream);
 
+/* y = M x, M = M1 (x) M1 the Q1 mass matrix of the scheme (1D consistent
+ * h [1/6, 2/3, 1/6], lumped h [0, 1, 0]), periodic: turns nodal values of
+ * a load function into the Galerkin load vector of the general solve (the
+ * FEM convergence test of Sec. 3.5).  x, y: device double2 per node (two
+ * loads side by side), must not alias. */
+rve_status rve_apply_mass(const rve_realization* r, int32_t batch, int32_t scheme,
+                          const double* x, double* y, void* stream);
+
 /* y = B^{-1} x with B = c0 A_Delta + delta I (Sec. 3.4), A_Delta the
  * periodic 5-point Laplacian (Eq. "Lap_Kron"), c0 = (a_matrix + a_incl)/2
  * (Lemma "Cond_Number").  delta = 0 drops the constant mode.  Applied by
@@ -203,6 +211,19 @@ rve_status rve_solve_correctors(const rve_realization* r, int32_t batch,
                                 const rve_solve_opts* opts, double* u,
                                 rve_solve_info* info, void* ws, size_t ws_bytes,
                                 void* stream);
+
+/* A u = f for a caller's pair of load vectors per node instead of the
+ * corrector right-hand sides (the general solve of the FEM convergence test,
+ * Sec. 3.5, with a load such as sin(2 pi x) cos(6 pi y)): f is device
+ * [nodes][2] FP64 (see rve_apply_mass), and each of its two components must
+ * sum to zero over every realization (the periodic problem is solvable only
+ * then; otherwise the solve ends with RVE_ENOCONV).  Everything else --
+ * options, u (mean-zero on exit), info, workspace, paths -- as in
+ * rve_solve_correctors. */
+rve_status rve_solve_rhs(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                         const double* coef, const double* f, const rve_solve_opts* opts,
+                         double* u, rve_solve_info* info, void* ws, size_t ws_bytes,
+                         void* stream);
 
 /* Homogenized matrix of every realization from its correctors u.
  * A: energy form a_ij = (1/L^2) int (e_j + grad phi_j).a(e_i + grad phi_i)

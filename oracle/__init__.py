@@ -95,6 +95,11 @@ def lib():
         L.orc_solve_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int, dbl,
                                       vp, ctypes.c_int]
         L.orc_statistics.argtypes = [i64, vp, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
+        L.orc_mass_element.argtypes = [ctypes.c_int, dbl, vp]
+        L.orc_apply_mass.argtypes = [i64, dbl, ctypes.c_int, vp, vp]
+        L.orc_solve_load.restype = ctypes.c_int
+        L.orc_solve_load.argtypes = [i64, i64, vp, dbl, ctypes.c_int, vp, dbl, ctypes.c_int, dbl,
+                                     vp, vp]
         _lib = L
     return _lib
 
@@ -180,6 +185,35 @@ def rhs(coef: np.ndarray, h: float, scheme: int = SCHEME_CONSISTENT) -> np.ndarr
 
 
 # ---------------------------------------------------------------- solver --
+def mass_element(scheme: int, h: float) -> np.ndarray:
+    M = np.zeros(16)
+    lib().orc_mass_element(scheme, h, _p(M))
+    return M.reshape(4, 4)
+
+
+def apply_mass(x: np.ndarray, h: float, scheme: int = SCHEME_CONSISTENT) -> np.ndarray:
+    """y = M x for nodal values x[n,n] (Q1 mass matrix of the scheme, periodic)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    lib().orc_apply_mass(x.shape[0], h, scheme, _p(x), _p(y))
+    return y
+
+
+def solve_load(coef: np.ndarray, L: int, m0: int, c0: float, b: np.ndarray,
+               scheme: int = SCHEME_CONSISTENT, tol: float = 1e-12, max_iter: int = 20000,
+               delta: float = 0.0):
+    """Mean-zero u[n,n] with A u = b (b a mean-zero load vector); (u, iters, relres)."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    u = np.zeros_like(b)
+    rr = ctypes.c_double(0.0)
+    it = lib().orc_solve_load(L, m0, _p(coef), c0, scheme, _p(b), tol, max_iter, delta, _p(u),
+                              ctypes.byref(rr))
+    if it < 0:
+        raise ValueError("orc_solve_load: n must be a power of two")
+    return u, it, rr.value
+
+
 def laplacian_eig(n: int, k1: int, k2: int) -> float:
     return float(lib().orc_laplacian_eig(n, k1, k2))
 

@@ -26,7 +26,9 @@
  *   6. the derivative of the energy form with respect to each cell value;
  *   7. ensemble statistics: empirical mean (Eq. "A_hom_Empir"), the paper's
  *      standard-deviation estimators (Eqs. "Var1", "Var2") and the rescaled
- *      covariance / quartic tensor (Eq. "quartic").
+ *      covariance / quartic tensor (Eq. "quartic");
+ *   8. for a general load (the FEM convergence test of Sec. 3.5): the mass
+ *      matrix M1 (x) M1 applied cell by cell, and the solve A u = b.
  *
  * Readings of the paper that this oracle fixes (where it is silent or
  * garbled) are listed beside each function.  Everything is FP64.
@@ -525,6 +527,60 @@ int orc_solve_coef(int64_t L, int64_t m0, const double* coef, double c0,
     free(rowptr); free(colidx); free(vals); free(f);
     if (!u) free(uu);
     return 0;
+}
+
+/* Element mass matrix M1 (x) M1 in local order 00, 01, 10, 11, with the 1D
+ * mass of the scheme: consistent (h/6)[[2,1],[1,2]], lumped (h/2) I. */
+void orc_mass_element(int scheme, double h, double M[16])
+{
+    double M1[2][2];
+    if (scheme == ORC_SCHEME_LUMPED) {
+        M1[0][0] = h / 2; M1[0][1] = 0; M1[1][0] = 0; M1[1][1] = h / 2;
+    } else {
+        M1[0][0] = 2 * h / 6; M1[0][1] = h / 6; M1[1][0] = h / 6; M1[1][1] = 2 * h / 6;
+    }
+    for (int a1 = 0; a1 < 2; ++a1)
+        for (int a2 = 0; a2 < 2; ++a2)
+            for (int b1 = 0; b1 < 2; ++b1)
+                for (int b2 = 0; b2 < 2; ++b2)
+                    M[(a1 * 2 + a2) * 4 + b1 * 2 + b2] = M1[a1][b1] * M1[a2][b2];
+}
+
+/* y = M x: the global mass matrix applied cell by cell (sum over cells of
+ * P_c^T M_elem P_c x), periodic. */
+void orc_apply_mass(int64_t n, double h, int scheme, const double* x, double* y)
+{
+    double M[16];
+    orc_mass_element(scheme, h, M);
+    memset(y, 0, sizeof(double) * (size_t)(n * n));
+    for (int64_t c1 = 0; c1 < n; ++c1)
+        for (int64_t c2 = 0; c2 < n; ++c2) {
+            int64_t g[4];
+            orc_cell_nodes(n, c1, c2, g);
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) y[g[i]] += M[i * 4 + j] * x[g[j]];
+        }
+}
+
+/* A u = b for a mean-zero load vector b (assembled stiffness, PCG with the
+ * FFT preconditioner); u is returned mean-zero.  Returns the iterations,
+ * or -2 when n is not a power of two. */
+int orc_solve_load(int64_t L, int64_t m0, const double* coef, double c0, int scheme,
+                   const double* b, double tol, int max_iter, double delta, double* u,
+                   double* relres_true)
+{
+    const int64_t n = L * m0;
+    const int64_t N = n * n;
+    const double h = 1.0 / (double)m0;
+    if (n < 2 || (n & (n - 1)) != 0) return -2;
+    int64_t* rowptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    int64_t* colidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(9 * N));
+    double* vals = (double*)malloc(sizeof(double) * (size_t)(9 * N));
+    if (!rowptr || !colidx || !vals) return -1;
+    orc_assemble(n, h, coef, scheme, rowptr, colidx, vals);
+    const int it = orc_pcg(n, rowptr, colidx, vals, c0, delta, b, tol, max_iter, u, relres_true);
+    free(rowptr); free(colidx); free(vals);
+    return it;
 }
 
 int orc_solve_realization(const orc_realization* r, int scheme, double tol,

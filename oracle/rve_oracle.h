@@ -67,6 +67,15 @@ int orc_solve_realization(const orc_realization* r, int scheme, double tol,
 int orc_solve_batch(const orc_realization* r, int batch, int scheme, double tol,
                     int max_iter, double delta, orc_result* res, int threads);
 
+/* General right-hand side (Sec. 3.5, the FEM convergence test): the load
+ * vector of a nodal load through the Q1 mass matrix, and the periodic
+ * solve A u = b for a given mean-zero load vector b. */
+void orc_mass_element(int scheme, double h, double M[16]);
+void orc_apply_mass(int64_t n, double h, int scheme, const double* x, double* y);
+int orc_solve_load(int64_t L, int64_t m0, const double* coef, double c0, int scheme,
+                   const double* b, double tol, int max_iter, double delta, double* u,
+                   double* relres_true);
+
 void orc_statistics(int64_t N, const double* A, double L, int d, double* mean,
                     double* var, double* std12_paper, double* stddiff_paper,
                     double* Q);

@@ -356,9 +356,10 @@ rve_status rve_apply_precond(const rve_realization* r, int32_t batch, double del
                : RVE_ECUDA;
 }
 
-rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const uint32_t* mask,
-                                const double* coef, const rve_solve_opts* opts, double* u,
-                                rve_solve_info* info, void* ws, size_t ws_bytes, void* stream) {
+static rve_status solve_any(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                            const double* coef, const double* f, const rve_solve_opts* opts,
+                            double* u, rve_solve_info* info, void* ws, size_t ws_bytes,
+                            void* stream) {
     const rve_solve_opts o = resolved_opts(opts);
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, true);
@@ -366,10 +367,36 @@ rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const u
     if (!u || !info || !ws || (!mask && !coef)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     if (o.path == RVE_PATH_PLAIN)
-        return run_solve_plain(p, ws, mask, coef, o, u, info, as_stream(stream));
+        return run_solve_plain(p, ws, mask, coef, o, u, info, as_stream(stream), f);
     if (o.path == RVE_PATH_PERSISTENT)
-        return run_solve_persistent(p, ws, mask, coef, o, u, info, as_stream(stream));
-    return run_solve_fused(p, ws, mask, coef, o, u, info, as_stream(stream));
+        return run_solve_persistent(p, ws, mask, coef, o, u, info, as_stream(stream), f);
+    return run_solve_fused(p, ws, mask, coef, o, u, info, as_stream(stream), f);
+}
+
+rve_status rve_solve_correctors(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                                const double* coef, const rve_solve_opts* opts, double* u,
+                                rve_solve_info* info, void* ws, size_t ws_bytes, void* stream) {
+    return solve_any(r, batch, mask, coef, nullptr, opts, u, info, ws, ws_bytes, stream);
+}
+
+rve_status rve_solve_rhs(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                         const double* coef, const double* f, const rve_solve_opts* opts,
+                         double* u, rve_solve_info* info, void* ws, size_t ws_bytes,
+                         void* stream) {
+    if (!f) return RVE_EINVAL;
+    return solve_any(r, batch, mask, coef, f, opts, u, info, ws, ws_bytes, stream);
+}
+
+rve_status rve_apply_mass(const rve_realization* r, int32_t batch, int32_t scheme,
+                          const double* x, double* y, void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.scheme = scheme;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, false);
+    if (st != RVE_OK) return st;
+    if (!x || !y || x == y) return RVE_EINVAL;
+    return launch_mass(p, scheme, x, y, as_stream(stream)) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
 rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* mask,

@@ -58,10 +58,13 @@ __device__ __forceinline__ int find_real(const int32_t* start, int batch, int t)
     return lo;
 }
 
-// Cell-coefficient source: bitmask + the two values, or an explicit array.
+// Cell-coefficient source: bitmask + the two values, or an explicit array;
+// and the right-hand side: the corrector loads f_1, f_2 formed from the cells
+// (f == NULL), or a caller's load vector pair per node.
 struct CoefSrc {
     const uint32_t* __restrict__ mask;   // packed over the batch
     const double* __restrict__ coef;     // packed over the batch (or NULL)
+    const double2* __restrict__ f;       // packed load vectors (or NULL)
     __device__ __forceinline__ double cell(const RDesc& d, int c1, int c2) const {
         const int64_t c = (int64_t)c1 * d.n + c2;
         if (coef) return __ldg(coef + d.node_off + c);
@@ -124,6 +127,13 @@ __device__ __forceinline__ V stencil_apply(const CellsT<typename ScalarOf<V>::T>
 __device__ __forceinline__ double2 rhs_at(const Cells4& a, double h) {
     const double hh = 0.5 * h;
     return make_double2(hh * ((a.z0m + a.z00) - (a.mm + a.m0)), hh * ((a.m0 + a.z00) - (a.mm + a.z0m)));
+}
+
+// Right-hand side at a node: the caller's load vector, or the corrector
+// loads from the node's four cells.
+__device__ __forceinline__ double2 load_at(const CoefSrc& cs, const RDesc& d, int64_t node,
+                                           const Cells4& a) {
+    return cs.f ? cs.f[d.node_off + node] : rhs_at(a, d.h);
 }
 
 // Reciprocal of the preconditioner's symbol: the approximate hardware

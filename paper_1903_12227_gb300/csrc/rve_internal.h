@@ -113,19 +113,21 @@ cudaError_t precond_passes(const Plan& p, void* ws, double delta, const V* x, V*
                            int b_first, int b_count, cudaStream_t s);
 cudaError_t launch_precond(const Plan& p, void* ws, double delta, int precision, const void* x,
                            void* y, cudaStream_t s);
+// `f`: device [nodes][2] load vectors; NULL = the corrector right-hand sides.
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
-                           cudaStream_t s);
+                           cudaStream_t s, const double* f = nullptr);
 rve_status run_solve_persistent(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                                 const rve_solve_opts& o, double* u, rve_solve_info* info,
-                                cudaStream_t s);
+                                cudaStream_t s, const double* f = nullptr);
 rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s);
 rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mask,
                                     const double* coef, const rve_solve_opts& o, double* u,
-                                    rve_solve_info* info, cudaStream_t s);
+                                    rve_solve_info* info, cudaStream_t s, const double* f = nullptr);
 rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
-                           cudaStream_t s);
+                           cudaStream_t s, const double* f = nullptr);
+cudaError_t launch_mass(const Plan& p, int scheme, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                          int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
 constexpr int PROFILE_KERNELS = 5;   // refine, stencil, update, column, control

@@ -93,6 +93,34 @@ __global__ void k_stiffness(const __grid_constant__ DescChunk ch, CoefSrc cs,
         ldv(x, d, i + 1, j - 1), ldv(x, d, i + 1, j), ldv(x, d, i + 1, j + 1));
 }
 
+// y = M x, M = M1 (x) M1 the Q1 mass matrix (1D: consistent h [1/6, 2/3,
+// 1/6], lumped h [0, 1, 0]), periodic 9-point (resp. 1-point) stencil: the
+// load vector of a nodal load for the general-right-hand-side solve.
+template <int SCHEME>
+__global__ void k_mass(const __grid_constant__ DescChunk ch, const double2* __restrict__ x,
+                       double2* __restrict__ y) {
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t node = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
+    const double h2 = d.h * d.h;
+    double2 acc = make_double2(0.0, 0.0);
+    if (SCHEME == 1) {
+        acc = ldv(x, d, i, j);
+    } else {
+        const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double2 v = ldv(x, d, i + a - 1, j + c - 1);
+                acc.x = fma(w[a] * w[c], v.x, acc.x);
+                acc.y = fma(w[a] * w[c], v.y, acc.y);
+            }
+    }
+    y[d.node_off + node] = make_double2(h2 * acc.x, h2 * acc.y);
+}
+
 // ------------------------------------------------------------- adjoint --
 // Local element action (E v)_a for the unit-coefficient element matrix
 // E = K1 (x) M1 + M1 (x) K1, local order 00, 01, 10, 11.
@@ -221,6 +249,17 @@ cudaError_t launch_stiffness(const Plan& p, void*, const uint32_t* mask, const d
             if (scheme == RVE_Q1_LUMPED) k_stiffness<1, float2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
             else k_stiffness<0, float2><<<g, NODE_TILE, 0, s>>>(ch, cs, xx, yy);
         }
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_mass(const Plan& p, int scheme, const double* x, double* y, cudaStream_t s) {
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int) {
+        const int g = ch.start[ch.count];
+        const double2* xx = reinterpret_cast<const double2*>(x);
+        double2* yy = reinterpret_cast<double2*>(y);
+        if (scheme == RVE_Q1_LUMPED) k_mass<1><<<g, NODE_TILE, 0, s>>>(ch, xx, yy);
+        else k_mass<0><<<g, NODE_TILE, 0, s>>>(ch, xx, yy);
         return cudaGetLastError();
     });
 }

@@ -45,7 +45,7 @@ __global__ void k_pl_init(const RDesc* desc, int b, CoefSrc cs, double2* u, doub
     for (int t = threadIdx.x; t < PL_NODES; t += blockDim.x) {
         const int64_t node = (int64_t)blockIdx.x * PL_NODES + t;
         const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
-        const double2 f = rhs_at(cells_at(cs, d, i, j), d.h);
+        const double2 f = load_at(cs, d, node, cells_at(cs, d, i, j));
         r[d.node_off + node] = f;
         u[d.node_off + node] = make_double2(0.0, 0.0);
         ax.add(f.x, f.x);
@@ -132,7 +132,7 @@ __global__ void k_pl_resid(const RDesc* desc, int b, CoefSrc cs, const double2* 
         const int64_t node = (int64_t)blockIdx.x * PL_NODES + t;
         const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
         const Cells4 a = cells_at(cs, d, i, j);
-        const double2 f = rhs_at(a, d.h);
+        const double2 f = load_at(cs, d, node, a);
         const double2 Au = stencil_apply<SCHEME, double2>(
             a, ld2(u, d, i - 1, j - 1), ld2(u, d, i - 1, j),
             ld2(u, d, i - 1, j + 1), ld2(u, d, i, j - 1),
@@ -264,11 +264,11 @@ static rve_status plain_one(const Plan& p, char* w, int b, CoefSrc cs, double2* 
 
 rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
-                           cudaStream_t s) {
+                           cudaStream_t s, const double* f) {
     rve_status st = upload_plan(p, ws, s);
     if (st != RVE_OK) return st;
     char* w = static_cast<char*>(ws);
-    CoefSrc cs{mask, coef};
+    CoefSrc cs{mask, coef, reinterpret_cast<const double2*>(f)};
     double2* uu = reinterpret_cast<double2*>(u);
     for (int b = 0; b < p.batch; ++b) {
         st = (p.scheme == RVE_Q1_LUMPED) ? plain_one<1>(p, w, b, cs, uu, o, info, s)

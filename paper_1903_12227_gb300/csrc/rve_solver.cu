@@ -316,8 +316,16 @@ __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, c
             const dword lft = dw_add(cmm, c0m);   // with (i, j-1)
             const dword rgt = dw_add(cm0, c00);   // with (i, j+1)
             const dword cen = dw_scale2(dw_add(top, bot), -CEN);
-            DotDW rx(dw_mulf(dw_add(bot, dw_neg(top)), kh2));
-            DotDW ry(dw_mulf(dw_add(rgt, dw_neg(lft)), kh2));
+            dword kfx, kfy;   // K f
+            if (c.cs.f) {
+                const double2 fl = c.cs.f[d.node_off + ((int64_t)i << d.log2n) + j];
+                kfx = dw_mulf(dw_split(fl.x), 2.f * KH);
+                kfy = dw_mulf(dw_split(fl.y), 2.f * KH);
+            } else {
+                kfx = dw_mulf(dw_add(bot, dw_neg(top)), kh2);
+                kfy = dw_mulf(dw_add(rgt, dw_neg(lft)), kh2);
+            }
+            DotDW rx(kfx), ry(kfy);
             rx.add(cen, b1.x, b1.z); ry.add(cen, b1.y, b1.w);
             rx.add(top, a1.x, a1.z); ry.add(top, a1.y, a1.w);
             rx.add(bot, e1.x, e1.z); ry.add(bot, e1.y, e1.w);
@@ -371,7 +379,7 @@ __device__ void refine_tile_fp64(const Ctx& c, int tile, int b, const RState& s,
     for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
         const int i = r0 + (idx >> d.log2n), j = idx & (n - 1);
         const Cells4 a = cells_at(c.cs, d, i, j);
-        const double2 f = rhs_at(a, d.h);
+        const double2 f = load_at(c.cs, d, ((int64_t)i << d.log2n) + j, a);
         double2 Aw = make_double2(0.0, 0.0);
         if (!first)
             Aw = stencil_apply<SCHEME, double2>(
@@ -1522,7 +1530,7 @@ int profile_read(double* ms, long long* launches) {
 }
 
 static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double* coef, double* u,
-                    const rve_solve_opts& o) {
+                    const rve_solve_opts& o, const double* f = nullptr) {
     char* w = static_cast<char*>(ws);
     Ctx c;
     c.batch = p.batch;
@@ -1539,6 +1547,7 @@ static Ctx make_ctx(const Plan& p, void* ws, const uint32_t* mask, const double*
     c.tb = tables_of(p, ws);
     c.cs.mask = mask;
     c.cs.coef = coef;
+    c.cs.f = reinterpret_cast<const double2*>(f);
     c.u = reinterpret_cast<double2*>(u);
     c.X = w + p.o_X;
     c.R = w + p.o_R;
@@ -1700,8 +1709,8 @@ static rve_status persistent_launch(const Plan& p, const Ctx& c, const rve_solve
 // the sequence can be captured in a CUDA graph.
 rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mask,
                                     const double* coef, const rve_solve_opts& o, double* u,
-                                    rve_solve_info* info, cudaStream_t s) {
-    Ctx c = make_ctx(p, ws, mask, coef, u, o);
+                                    rve_solve_info* info, cudaStream_t s, const double* f) {
+    Ctx c = make_ctx(p, ws, mask, coef, u, o, f);
     if (launch_tables(p, ws, s) != cudaSuccess) return RVE_ECUDA;
     k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
     note_launch();
@@ -1736,20 +1745,20 @@ rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s) {
 
 rve_status run_solve_persistent(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                                 const rve_solve_opts& o, double* u, rve_solve_info* info,
-                                cudaStream_t s) {
+                                cudaStream_t s, const double* f) {
     Plan q = p;
     rve_status st = (q.persist_grid > 0) ? RVE_OK : prepare_persistent(q);
     if (st == RVE_OK) st = upload_descriptors(q, ws, s);
     if (st != RVE_OK) return st;
-    return enqueue_solve_persistent(q, ws, mask, coef, o, u, info, s);
+    return enqueue_solve_persistent(q, ws, mask, coef, o, u, info, s, f);
 }
 
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
-                           cudaStream_t s) {
+                           cudaStream_t s, const double* f) {
     rve_status st = upload_plan(p, ws, s);
     if (st != RVE_OK) return st;
-    Ctx c = make_ctx(p, ws, mask, coef, u, o);
+    Ctx c = make_ctx(p, ws, mask, coef, u, o, f);
     k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;

@@ -93,6 +93,10 @@ def lib() -> ctypes.CDLL:
         L.rve_workspace_size.argtypes = [vp, i32, vp]
         L.rve_solve_correctors.restype = i32
         L.rve_solve_correctors.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.rve_solve_rhs.restype = i32
+        L.rve_solve_rhs.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.rve_apply_mass.restype = i32
+        L.rve_apply_mass.argtypes = [vp, i32, i32, vp, vp, vp]
         L.rve_a_hom.restype = i32
         L.rve_a_hom.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, sz, vp]
         L.rve_a_hom_backward.restype = i32
@@ -266,8 +270,10 @@ def _info_dict(a: SolveInfo) -> dict:
 
 
 def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u=None,
-          info=None, stream=None, device=None):
-    """Correctors u [nodes, 2] float64 and the raw info tensor (Sec. 3.4, 4.1)."""
+          info=None, stream=None, device=None, f: torch.Tensor | None = None):
+    """Correctors u [nodes, 2] float64 and the raw info tensor (Sec. 3.4, 4.1).
+    With `f` (device float64 [nodes, 2], each component mean-zero per
+    realization) the two load vectors of f are solved for instead."""
     _require_cuda()
     b = as_batch(batch)
     opts = opts or make_opts()
@@ -279,10 +285,29 @@ def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u
         u = torch.empty(b.nodes, 2, dtype=torch.float64, device=dev)
     if info is None:
         info = torch.empty(b.count * INFO_BYTES, dtype=torch.uint8, device=dev)
-    check(lib().rve_solve_correctors(b.ptr, b.count, _ptr(mask), _ptr(coef), ctypes.byref(opts),
-                                     _ptr(u), _ptr(info), _ptr(ws), ws.numel(), _stream(stream)),
-          "rve_solve_correctors")
+    if f is None:
+        check(lib().rve_solve_correctors(b.ptr, b.count, _ptr(mask), _ptr(coef),
+                                         ctypes.byref(opts), _ptr(u), _ptr(info), _ptr(ws),
+                                         ws.numel(), _stream(stream)), "rve_solve_correctors")
+    else:
+        if f.dtype != torch.float64 or tuple(f.shape) != (b.nodes, 2):
+            raise ValueError("f must be float64 [nodes, 2]")
+        check(lib().rve_solve_rhs(b.ptr, b.count, _ptr(mask), _ptr(coef), _ptr(f),
+                                  ctypes.byref(opts), _ptr(u), _ptr(info), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "rve_solve_rhs")
     return u, info
+
+
+def apply_mass(batch, x: torch.Tensor, scheme=CONSISTENT, stream=None) -> torch.Tensor:
+    """y = M x (Q1 mass matrix of the scheme) for float64 [nodes, 2] nodal values."""
+    _require_cuda()
+    b = as_batch(batch)
+    if x.dtype != torch.float64:
+        raise ValueError("apply_mass takes float64 nodal values")
+    y = torch.empty_like(x)
+    check(lib().rve_apply_mass(b.ptr, b.count, scheme, _ptr(x), _ptr(y), _stream(stream)),
+          "rve_apply_mass")
+    return y
 
 
 def a_hom(batch, u: torch.Tensor, mask=None, coef=None, scheme=CONSISTENT, ws=None,

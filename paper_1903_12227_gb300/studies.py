@@ -3,6 +3,12 @@
 * ``variance``: the random error of the RVE method versus L (Sec. 4.2,
   Eq. "var"): for each L the empirical mean, variances and quartic tensor of
   A_hom over N seeded realizations; L^2 var(a_12) should be roughly constant.
+* ``fem``: the FEM approximation test of Sec. 3.5 (Table 1): one fixed
+  inclusion configuration (L^2 squares of side 2 alpha = 1, values lambda =
+  0.1 outside and 1 inside, corners on the coarsest grid) solved with the
+  load f = sin(2 pi x/L) cos(6 pi y/L) on dyadic refinements n = 64 .. 1024;
+  reported are |u_p - u_{p-1}|_2 / |u_{p-1}|_2 on the coarser grid's nodes
+  and their decay factors (the paper expects about 2 sqrt(2));
 * ``paper``: the statistics of Sec. 5 with the paper's own model parameters
   (overlap alpha = 1/4, i.e. inclusions of side 1/2; L^2 inclusions; matrix
   value 0.4 and inclusion value 1; m0 = 4; the lumped (trapezoid) scheme;
@@ -12,6 +18,7 @@
 
     python -m paper_1903_12227_gb300.studies variance --Ls 32 64 128 256 --N 256
     python -m paper_1903_12227_gb300.studies paper --Ls 8 16 32 64 --N 10000
+    python -m paper_1903_12227_gb300.studies fem --Ls 2 4 8
 """
 from __future__ import annotations
 
@@ -102,16 +109,75 @@ def paper_study(Ls=(8, 16, 32, 64), N=10000, seed=0, batch_nodes=1 << 26,
     return rows
 
 
+def fem_convergence(Ls=(2, 4, 8), ns=(64, 128, 256, 512, 1024), alpha=0.5, lam=0.1, seed=0,
+                    scheme=rve.CONSISTENT, precision=rve.FP64, tol=1e-10) -> list:
+    """Sec. 3.5: differences of solutions on dyadic refinements of one fixed
+    coefficient configuration.  The configuration is drawn on the coarsest
+    grid (L^2 corners, squares of side 2*alpha units) and refined by
+    splitting every coarse cell, so that all grids see the same geometry.
+    Loads: component 1 the paper's sin(2 pi x/L) cos(6 pi y/L), component 2
+    the transposed cos(6 pi x/L) sin(2 pi y/L); load vectors through the
+    scheme's mass matrix.  tol = 1e-10: the differences are ~1e-4 and, for
+    this smooth load, FP64 CG cannot reach much below ~1e-12 at n = 1024
+    (|A| |u| / |A u| ~ 1e4)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    n0 = min(ns)
+    for L in Ls:
+        m0c = n0 // L
+        coarse = workloads.realization(L, m0c, 1.0 / lam, seed, 0, density=1.0,
+                                       side_units=2 * alpha, a_matrix=lam)
+        mask = rve.gen_field([coarse], device=dev)
+        bits = torch.as_tensor(rve.unpack_mask(mask, [coarse])[0], device=dev)   # [n0, n0] bool
+        sols = []
+        for n in ns:
+            fct = n // n0
+            m0 = n // L
+            d = workloads.realization(L, m0, 1.0 / lam, seed, 0, density=1.0,
+                                      side_units=2 * alpha, a_matrix=lam)
+            fine = bits.repeat_interleave(fct, 0).repeat_interleave(fct, 1)
+            coef = torch.where(fine, torch.tensor(1.0, dtype=torch.float64, device=dev),
+                               torch.tensor(lam, dtype=torch.float64, device=dev)).reshape(-1)
+            x = torch.arange(n, dtype=torch.float64, device=dev) / m0
+            g1 = torch.outer(torch.sin(2 * np.pi * x / L), torch.cos(6 * np.pi * x / L))
+            g2 = torch.outer(torch.cos(6 * np.pi * x / L), torch.sin(2 * np.pi * x / L))
+            g = torch.stack([g1.reshape(-1), g2.reshape(-1)], dim=1).contiguous()
+            f = rve.apply_mass([d], g, scheme=scheme)
+            t0 = time.perf_counter()
+            u, info = rve.solve([d], coef=coef, opts=rve.make_opts(scheme=scheme, precision=precision,
+                                                                   tol=tol), f=f)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            inf = rve.info_to_dicts(info, 1)[0]
+            u = u.reshape(n, n, 2)
+            u = u - u.mean(dim=(0, 1), keepdim=True)
+            sols.append((n, u, inf, dt))
+        row = {"L": L, "ns": list(ns), "iters": [s[2]["iters"] for s in sols],
+               "status": [s[2]["status"] for s in sols], "seconds": [s[3] for s in sols],
+               "rel_diff": [], "decay": []}
+        for (na, ua, _, _), (nb, ub, _, _) in zip(sols, sols[1:]):
+            step = nb // na
+            ub_c = ub[::step, ::step]   # the fine solution at the coarse nodes
+            diff = [float((ub_c[..., c] - ua[..., c]).norm() / ua[..., c].norm()) for c in range(2)]
+            row["rel_diff"].append(diff)
+        for a, b in zip(row["rel_diff"], row["rel_diff"][1:]):
+            row["decay"].append([a[c] / b[c] for c in range(2)])
+        rows.append(row)
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["variance", "paper"])
+    ap.add_argument("study", choices=["variance", "paper", "fem"])
     ap.add_argument("--Ls", type=int, nargs="+")
     ap.add_argument("--N", type=int)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--count", choices=["fixed", "poisson"], default="fixed")
     ap.add_argument("--json")
     a = ap.parse_args(argv)
-    if a.study == "variance":
+    if a.study == "fem":
+        rows = fem_convergence(Ls=tuple(a.Ls or (2, 4, 8)), seed=a.seed)
+    elif a.study == "variance":
         rows = variance_study(Ls=tuple(a.Ls or (32, 64, 128, 256)), N=a.N or 256, seed=a.seed)
     else:
         rows = paper_study(Ls=tuple(a.Ls or (8, 16, 32, 64)), N=a.N or 10000, seed=a.seed,

@@ -202,6 +202,70 @@ def test_solve_matches_oracle(case, scheme, precision, path, bound):
         off += n * n
 
 
+# ------------------------------------------ general load (Sec. 3.5) --
+def _nodal_loads(ds):
+    """Per realization the nodal loads sin(2 pi x/L) cos(6 pi y/L) and
+    cos(2 pi x/L) sin(4 pi y/L) (both mean-zero on the torus), [nodes, 2]."""
+    out = []
+    for d in ds:
+        n, h, L = d["L"] * d["m0"], 1.0 / d["m0"], d["L"]
+        x = np.arange(n) * h
+        g1 = np.outer(np.sin(2 * np.pi * x / L), np.cos(6 * np.pi * x / L))
+        g2 = np.outer(np.cos(2 * np.pi * x / L), np.sin(4 * np.pi * x / L))
+        out.append(np.stack([g1.ravel(), g2.ravel()], axis=1))
+    return out
+
+
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_apply_mass_matches_oracle(scheme):
+    ds = [workloads.realization(4, 8, 10.0, 0, 0), workloads.realization(8, 16, 10.0, 0, 1)]
+    g = np.random.default_rng(5)
+    xs = [g.standard_normal(((d["L"] * d["m0"]) ** 2, 2)) for d in ds]
+    y = rve.apply_mass(ds, torch.tensor(np.concatenate(xs), device=CUDA), scheme=scheme).cpu().numpy()
+    off = 0
+    for d, x in zip(ds, xs):
+        n, h = d["L"] * d["m0"], 1.0 / d["m0"]
+        for c in range(2):
+            ref = oracle.apply_mass(x[:, c].reshape(n, n), h, scheme).ravel()
+            assert np.abs(y[off:off + n * n, c] - ref).max() < 1e-14 * np.abs(ref).max()
+        off += n * n
+
+
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+@pytest.mark.parametrize("precision,path,bound", [(rve.FP64, rve.PATH_FUSED, 1e-8),
+                                                  (rve.MIXED, rve.PATH_FUSED, 1e-6),
+                                                  (rve.MIXED, rve.PATH_PERSISTENT, 1e-6),
+                                                  (rve.FP64, rve.PATH_PLAIN, 1e-8)])
+def test_solve_rhs_matches_oracle(scheme, precision, path, bound):
+    # the general solve A u = M g (the paper's FEM convergence test) on
+    # mixed sizes, against the oracle's assembled solve with the same loads
+    ds = [workloads.realization(2, 16, 10.0, 3, 0), workloads.realization(4, 16, 10.0, 3, 1),
+          workloads.realization(8, 8, 100.0, 3, 2)]
+    mask, coefs = _setup(ds)
+    g = _nodal_loads(ds)
+    f = rve.apply_mass(ds, torch.tensor(np.concatenate(g), device=CUDA), scheme=scheme)
+    tol = 1e-12 if precision == rve.FP64 else 1e-10
+    opts = rve.make_opts(scheme=scheme, precision=precision, path=path, tol=tol)
+    u, info = rve.solve(ds, mask=mask, opts=opts, f=f)
+    un = u.cpu().numpy()
+    inf = rve.info_to_dicts(info, len(ds))
+    off = 0
+    # the plain path stops on the CG recurrence residual (textbook PCG, no
+    # refinement): its true residual at exit may exceed tol by a few percent
+    slack = 1.1 if path == rve.PATH_PLAIN else 1.0001
+    for k, (d, c) in enumerate(zip(ds, coefs)):
+        n, h = d["L"] * d["m0"], 1.0 / d["m0"]
+        assert inf[k]["status"] == rve.RVE_OK, inf[k]
+        assert max(inf[k]["relres"]) <= tol * slack
+        for comp in range(2):
+            b = oracle.apply_mass(g[k][:, comp].reshape(n, n), h, scheme)
+            ref, _, _ = oracle.solve_load(c, d["L"], d["m0"], 0.5 * (d["a_matrix"] + d["a_incl"]),
+                                          b, scheme=scheme, tol=1e-13)
+            ug = un[off:off + n * n, comp] - un[off:off + n * n, comp].mean()
+            assert np.abs(ug - ref.ravel()).max() < bound * np.abs(ref).max()
+        off += n * n
+
+
 @pytest.mark.parametrize("L,m0", [(8, 16), (16, 16), (32, 16)])   # n = 128, 256, 512
 @pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
 def test_cluster_update_column_kernel_matches_separate_kernels(L, m0, scheme):

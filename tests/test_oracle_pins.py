@@ -385,3 +385,89 @@ def test_workload_inclusion_counts():
     assert workloads.realization(256, 8, 100, 0, 0)["n_incl"] == 45875
     assert workloads.realization(8, 8, 10, 0, 0)["n_incl"] == 45
     assert workloads.realization(16, 8, 10, 0, 0)["n_incl"] == 179
+
+
+# ------------------------------------------------- general load (Sec. 3.5) --
+def _bilinear_basis(t1, t2):
+    """Q1 shape functions in local order 00, 01, 10, 11 at (t1, t2) in [0,1]^2."""
+    return np.array([(1 - t1) * (1 - t2), (1 - t1) * t2, t1 * (1 - t2), t1 * t2])
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_mass_element_equals_quadrature(scheme):
+    # consistent: int phi_a phi_b over the cell (2x2 Gauss is exact for these
+    # degree-2 products); lumped: the trapezoid rule in both directions
+    h = 0.25
+    M = oracle.mass_element(scheme, h)
+    pts = _gauss2() if scheme == oracle.SCHEME_CONSISTENT else [(0.0, 0.5), (1.0, 0.5)]
+    ref = np.zeros((4, 4))
+    for t1, w1 in pts:
+        for t2, w2 in pts:
+            phi = _bilinear_basis(t1, t2)
+            ref += w1 * w2 * np.outer(phi, phi) * h * h
+    np.testing.assert_allclose(M, ref, atol=1e-16)
+
+
+def _symbols(theta, h, scheme):
+    """1D stiffness and mass symbols of a Fourier mode with phase theta per node."""
+    k = (2.0 - 2.0 * np.cos(theta)) / h
+    m = h * (4.0 + 2.0 * np.cos(theta)) / 6.0 if scheme == oracle.SCHEME_CONSISTENT else h
+    return k, m
+
+
+def _mode_load(L, m0):
+    n, h = L * m0, 1.0 / m0
+    x = np.arange(n) * h
+    return np.outer(np.sin(2 * np.pi * x / L), np.cos(6 * np.pi * x / L))
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_load_solve_constant_coefficient_fourier_mode(scheme):
+    # a = c: K and M are diagonal on the torus's product Fourier modes, so the
+    # discrete solution of c K u = M g for g = sin(2 pi x/L) cos(6 pi y/L) is
+    # g times m1 m2 / (c (k1 m2 + m1 k2)) with the 1D symbols k, m
+    L, m0, c = 4, 8, 2.5
+    n, h = L * m0, 1.0 / m0
+    g = _mode_load(L, m0)
+    b = oracle.apply_mass(g, h, scheme)
+    u, it, rr = oracle.solve_load(np.full((n, n), c), L, m0, c, b, scheme=scheme, tol=1e-13)
+    k1, m1 = _symbols(2 * np.pi * h / L, h, scheme)
+    k2, m2 = _symbols(6 * np.pi * h / L, h, scheme)
+    exact = g * (m1 * m2) / (c * (k1 * m2 + m1 * k2))
+    assert rr <= 1e-13
+    assert np.abs(u - exact).max() < 1e-11 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_load_solve_second_order_convergence(scheme):
+    # constant coefficient: the nodal error against -c Lap u = g, u = g / (c |w|^2),
+    # falls by ~4 per grid halving (second-order FEM)
+    L, c = 2, 1.5
+    w2 = (2 * np.pi / L) ** 2 + (6 * np.pi / L) ** 2
+    errs = []
+    for m0 in (16, 32, 64):
+        n, h = L * m0, 1.0 / m0
+        g = _mode_load(L, m0)
+        u, _, _ = oracle.solve_load(np.full((n, n), c), L, m0, c, oracle.apply_mass(g, h, scheme),
+                                    scheme=scheme, tol=1e-13)
+        errs.append(np.abs(u - g / (c * w2)).max())
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.7 < e0 / e1 < 4.3, errs
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_load_solve_matches_dense_direct_solve(scheme):
+    # jumping coefficient on a tiny torus: PCG against a direct solve of the
+    # bordered system [A 1; 1^T 0] [u; s] = [b; 0] (mean-zero solution)
+    L, m0 = 2, 4
+    n, h = L * m0, 1.0 / m0
+    coef = _random_coef(n, 7, lo=0.1, hi=1.0)
+    b = oracle.apply_mass(_mode_load(L, m0), h, scheme)
+    A = oracle.csr_to_dense(oracle.assemble(coef, h, scheme), n * n)
+    Bord = np.zeros((n * n + 1, n * n + 1))
+    Bord[:-1, :-1] = A
+    Bord[:-1, -1] = 1.0
+    Bord[-1, :-1] = 1.0
+    ref = np.linalg.solve(Bord, np.concatenate([b.ravel(), [0.0]]))[:-1]
+    u, _, rr = oracle.solve_load(coef, L, m0, 0.55, b, scheme=scheme, tol=1e-14)
+    assert np.abs(u.ravel() - ref).max() < 1e-11 * np.abs(ref).max()
