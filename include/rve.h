@@ -109,7 +109,7 @@ typedef struct {
     int32_t tile_rows;   /* stencil tile height in node rows (1..n; n need
                             not be a multiple), 0 = tuned or default       */
     int32_t col_tile;    /* threads of a column-solve block (power of two,
-                            32..512); 0 = 512                               */
+                            32..512); 0 = 256 (mixed) or 512 (FP64)         */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
     int32_t timeout_us;  /* persistent path: bound on each grid-wide wait, in
                             microseconds (0 = 2 s)                          */
