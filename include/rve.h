@@ -182,6 +182,23 @@ rve_status rve_apply_stiffness(const rve_realization* r, int32_t batch,
 rve_status rve_apply_mass(const rve_realization* r, int32_t batch, int32_t scheme,
                           const double* x, double* y, void* stream);
 
+/* Chebyshev moments for the density of states of the stiffness matrix A
+ * (the spectral-density appendix, Eqs. "DOS", "DOS_gauss"): for every
+ * realization and each of its two start vectors v (device v[nodes][2]),
+ *   mu[b][c][k] = v_c^T T_k(A~) v_c,  A~ = (2 A - (hi + lo) I) / (hi - lo),
+ * k = 0 .. K-1, with T_k the Chebyshev polynomials; [lo, hi] must contain
+ * the spectrum of A (e.g. lo = 0, hi = 4 w0 max(4 a) by Gershgorin: 16/3
+ * a_max consistent, 8 a_max lumped).  The Gaussian-broadened density is a
+ * fixed linear combination of these moments (done on the host).  The matrix
+ * is applied matrix-free in FP64, one application per two moments.  mu:
+ * device doubles [batch][2][K]; ws: rve_cheb_workspace_size() bytes.
+ * Errors: RVE_EINVAL (K < 2, hi <= lo, missing pointers), RVE_ENOMEM. */
+size_t rve_cheb_workspace_size(const rve_realization* r, int32_t batch);
+rve_status rve_cheb_moments(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                            const double* coef, int32_t scheme, const double* v, int32_t K,
+                            double lo, double hi, double* mu, void* ws, size_t ws_bytes,
+                            void* stream);
+
 /* y = B^{-1} x with B = c0 A_Delta + delta I (Sec. 3.4), A_Delta the
  * periodic 5-point Laplacian (Eq. "Lap_Kron"), c0 = (a_matrix + a_incl)/2
  * (Lemma "Cond_Number").  delta = 0 drops the constant mode.  Applied by

@@ -214,6 +214,21 @@ def solve_load(coef: np.ndarray, L: int, m0: int, c0: float, b: np.ndarray,
     return u, it, rr.value
 
 
+def spectrum(coef: np.ndarray, h: float, scheme: int = SCHEME_CONSISTENT) -> np.ndarray:
+    """All eigenvalues (ascending) of the assembled stiffness matrix, by a
+    dense symmetric eigensolver (numpy.linalg.eigvalsh); small grids only."""
+    n = coef.shape[0]
+    return np.linalg.eigvalsh(csr_to_dense(assemble(coef, h, scheme), n * n))
+
+
+def dos_gauss(eigs: np.ndarray, t: np.ndarray, eta: float) -> np.ndarray:
+    """Gaussian-broadened density of states (1/m) sum_j g_eta(t - lambda_j)
+    (the spectral-density appendix, Eq. "DOS_gauss")."""
+    t = np.asarray(t, dtype=np.float64)
+    g = np.exp(-0.5 * ((t[:, None] - eigs[None, :]) / eta) ** 2) / (np.sqrt(2 * np.pi) * eta)
+    return g.sum(axis=1) / eigs.size
+
+
 def laplacian_eig(n: int, k1: int, k2: int) -> float:
     return float(lib().orc_laplacian_eig(n, k1, k2))
 

@@ -388,6 +388,34 @@ rve_status rve_solve_rhs(const rve_realization* r, int32_t batch, const uint32_t
     return solve_any(r, batch, mask, coef, f, opts, u, info, ws, ws_bytes, stream);
 }
 
+size_t rve_cheb_workspace_size(const rve_realization* r, int32_t batch) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    Plan p;
+    if (make_plan(r, batch, &o, p, false) != RVE_OK) return 0;
+    return cheb_workspace_size(p);
+}
+
+rve_status rve_cheb_moments(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                            const double* coef, int32_t scheme, const double* v, int32_t K,
+                            double lo, double hi, double* mu, void* ws, size_t ws_bytes,
+                            void* stream) {
+    rve_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.scheme = scheme;
+    Plan p;
+    rve_status st = make_plan(r, batch, &o, p, false);
+    if (st != RVE_OK) return st;
+    if (!v || !mu || !ws || (!mask && !coef) || K < 2 || K > (1 << 20) || !std::isfinite(lo) ||
+        !std::isfinite(hi) || !(hi > lo))
+        return RVE_EINVAL;
+    if (ws_bytes < cheb_workspace_size(p)) return RVE_ENOMEM;
+    return launch_cheb(p, ws, mask, coef, scheme, v, K, lo, hi, mu, as_stream(stream)) ==
+                   cudaSuccess
+               ? RVE_OK
+               : RVE_ECUDA;
+}
+
 rve_status rve_apply_mass(const rve_realization* r, int32_t batch, int32_t scheme,
                           const double* x, double* y, void* stream) {
     rve_solve_opts o;

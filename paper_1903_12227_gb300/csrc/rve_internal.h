@@ -128,6 +128,10 @@ rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const 
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
                            cudaStream_t s, const double* f = nullptr);
 cudaError_t launch_mass(const Plan& p, int scheme, const double* x, double* y, cudaStream_t s);
+size_t cheb_workspace_size(const Plan& p);
+cudaError_t launch_cheb(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                        int scheme, const double* v, int K, double lo, double hi, double* mu,
+                        cudaStream_t s);
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                          int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
 constexpr int PROFILE_KERNELS = 5;   // refine, stencil, update, column, control

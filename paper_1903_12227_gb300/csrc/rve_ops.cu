@@ -121,6 +121,66 @@ __global__ void k_mass(const __grid_constant__ DescChunk ch, const double2* __re
     y[d.node_off + node] = make_double2(h2 * acc.x, h2 * acc.y);
 }
 
+// --------------------------------------------------- Chebyshev moments --
+// One step of the Chebyshev recurrence of A~ = a0 A - a1 I for both start
+// vectors of every realization (the spectral-density appendix):
+//   w_{k+1} = 2 A~ w_k - w_{k-1}   (first step: w_1 = A~ w_0),
+// written over w_{k-1}; per tile of NODE_TILE nodes the partial sums
+// w_k.w_k and w_{k+1}.w_k per start vector, from which the moments follow by
+// T_2k = 2 T_k^2 - T_0 and T_{2k+1} = 2 T_{k+1} T_k - T_1 (two moments per
+// operator application).  FP64 throughout.
+template <int SCHEME>
+__global__ void __launch_bounds__(NODE_TILE) k_cheb(const __grid_constant__ DescChunk ch,
+                                                    CoefSrc cs, double a0, double a1, int first,
+                                                    const double2* __restrict__ wc,
+                                                    double2* __restrict__ wp,
+                                                    double* __restrict__ part) {
+    __shared__ double red[8];
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t node = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const int i = (int)(node >> d.log2n), j = (int)(node & (d.n - 1));
+    const Cells4 a = cells_at(cs, d, i, j);
+    const double2 Aw = stencil_apply<SCHEME, double2>(
+        a, ldv(wc, d, i - 1, j - 1), ldv(wc, d, i - 1, j), ldv(wc, d, i - 1, j + 1),
+        ldv(wc, d, i, j - 1), ldv(wc, d, i, j), ldv(wc, d, i, j + 1),
+        ldv(wc, d, i + 1, j - 1), ldv(wc, d, i + 1, j), ldv(wc, d, i + 1, j + 1));
+    const double2 w = wc[d.node_off + node];
+    double2 t = make_double2(a0 * Aw.x - a1 * w.x, a0 * Aw.y - a1 * w.y);
+    if (!first) {
+        const double2 wm = wp[d.node_off + node];
+        t = make_double2(2.0 * t.x - wm.x, 2.0 * t.y - wm.y);
+    }
+    wp[d.node_off + node] = t;
+    const double v[4] = {w.x * w.x, w.y * w.y, t.x * w.x, t.y * w.y};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double sum = block_sum(v[k], red);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 4 + k] = sum;
+    }
+}
+
+// Moments of step k from its tile partials, one warp per realization (fixed
+// order): mu[b][c][2k] and mu[b][c][2k+1] (k = 0: mu_0 = w_0.w_0, mu_1 = w_1.w_0).
+__global__ void k_cheb_moments(const __grid_constant__ DescChunk ch, const double* __restrict__ part,
+                               int k, int K, double* __restrict__ mu) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= ch.count) return;
+    const int t0 = ch.start[b], nt = ch.start[b + 1] - t0;
+    double s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] = warp_sum_array(part + (int64_t)t0 * 4 + q, nt, 4);
+    if ((threadIdx.x & 31) != 0) return;
+    for (int c = 0; c < 2; ++c) {
+        double* m = mu + ((int64_t)b * 2 + c) * K;
+        const double cc = s[c], nc = s[2 + c];
+        const double e = (k == 0) ? cc : 2.0 * cc - m[0];
+        const double o = (k == 0) ? nc : 2.0 * nc - m[1];
+        if (2 * k < K) m[2 * k] = e;
+        if (2 * k + 1 < K) m[2 * k + 1] = o;
+    }
+}
+
 // ------------------------------------------------------------- adjoint --
 // Local element action (E v)_a for the unit-coefficient element matrix
 // E = K1 (x) M1 + M1 (x) K1, local order 00, 01, 10, 11.
@@ -261,6 +321,52 @@ cudaError_t launch_mass(const Plan& p, int scheme, const double* x, double* y, c
         if (scheme == RVE_Q1_LUMPED) k_mass<1><<<g, NODE_TILE, 0, s>>>(ch, xx, yy);
         else k_mass<0><<<g, NODE_TILE, 0, s>>>(ch, xx, yy);
         return cudaGetLastError();
+    });
+}
+
+size_t cheb_workspace_size(const Plan& p) {
+    int64_t tiles = 0;   // most node tiles of any launch chunk
+    for (int b0 = 0; b0 < p.batch; b0 += CHUNK) {
+        int64_t t = 0;
+        for (int k = b0; k < std::min(p.batch, b0 + CHUNK); ++k)
+            t += ((int64_t)p.desc[k].n * p.desc[k].n) / NODE_TILE;
+        tiles = std::max(tiles, t);
+    }
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    return 2 * up(sizeof(double2) * (size_t)p.nodes) + up(sizeof(double) * 4 * (size_t)tiles);
+}
+
+cudaError_t launch_cheb(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
+                        int scheme, const double* v, int K, double lo, double hi, double* mu,
+                        cudaStream_t s) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* w = static_cast<char*>(ws);
+    double2* wa = reinterpret_cast<double2*>(w);
+    double2* wb = reinterpret_cast<double2*>(w + up(sizeof(double2) * (size_t)p.nodes));
+    double* part = reinterpret_cast<double*>(w + 2 * up(sizeof(double2) * (size_t)p.nodes));
+    cudaError_t e = cudaMemcpyAsync(wb, v, sizeof(double2) * (size_t)p.nodes,
+                                    cudaMemcpyDeviceToDevice, s);   // w_0
+    if (e != cudaSuccess) return e;
+    const double a0 = 2.0 / (hi - lo), a1 = (hi + lo) / (hi - lo);
+    CoefSrc cs{mask, coef};
+    const int steps = (K + 1) / 2;
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int first_real) {
+        const int g = ch.start[ch.count];
+        double* m = mu + (int64_t)first_real * 2 * K;
+        double2* cur = wb;    // w_k
+        double2* oth = wa;    // in: w_{k-1}, out: w_{k+1}
+        for (int k = 0; k < steps; ++k) {
+            if (scheme == RVE_Q1_LUMPED)
+                k_cheb<1><<<g, NODE_TILE, 0, s>>>(ch, cs, a0, a1, k == 0, cur, oth, part);
+            else
+                k_cheb<0><<<g, NODE_TILE, 0, s>>>(ch, cs, a0, a1, k == 0, cur, oth, part);
+            k_cheb_moments<<<(ch.count + 7) / 8, 256, 0, s>>>(ch, part, k, K, m);
+            note_launch(2);
+            const cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) return le;
+            std::swap(cur, oth);
+        }
+        return cudaSuccess;
     });
 }
 

@@ -97,6 +97,11 @@ def lib() -> ctypes.CDLL:
         L.rve_solve_rhs.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.rve_apply_mass.restype = i32
         L.rve_apply_mass.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.rve_cheb_workspace_size.restype = sz
+        L.rve_cheb_workspace_size.argtypes = [vp, i32]
+        L.rve_cheb_moments.restype = i32
+        L.rve_cheb_moments.argtypes = [vp, i32, vp, vp, i32, vp, i32, ctypes.c_double,
+                                       ctypes.c_double, vp, vp, sz, vp]
         L.rve_a_hom.restype = i32
         L.rve_a_hom.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, sz, vp]
         L.rve_a_hom_backward.restype = i32
@@ -296,6 +301,25 @@ def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u
                                   ctypes.byref(opts), _ptr(u), _ptr(info), _ptr(ws),
                                   ws.numel(), _stream(stream)), "rve_solve_rhs")
     return u, info
+
+
+def cheb_moments(batch, v: torch.Tensor, K: int, lo: float, hi: float, mask=None, coef=None,
+                 scheme=CONSISTENT, stream=None) -> torch.Tensor:
+    """mu [B, 2, K] (device float64): v_c^T T_k(A~) v_c for the two start
+    vectors per realization (rve_cheb_moments), A~ = (2A - (hi+lo)) / (hi-lo)."""
+    _require_cuda()
+    b = as_batch(batch)
+    if v.dtype != torch.float64 or tuple(v.shape) != (b.nodes, 2):
+        raise ValueError("v must be float64 [nodes, 2]")
+    nb = lib().rve_cheb_workspace_size(b.ptr, b.count)
+    if nb == 0:
+        raise RveError("rve_cheb_workspace_size: invalid batch")
+    ws = workspace(nb, v.device)
+    mu = torch.empty(b.count, 2, K, dtype=torch.float64, device=v.device)
+    check(lib().rve_cheb_moments(b.ptr, b.count, _ptr(mask), _ptr(coef), scheme, _ptr(v), int(K),
+                                 float(lo), float(hi), _ptr(mu), _ptr(ws), ws.numel(),
+                                 _stream(stream)), "rve_cheb_moments")
+    return mu
 
 
 def apply_mass(batch, x: torch.Tensor, scheme=CONSISTENT, stream=None) -> torch.Tensor:

@@ -9,6 +9,12 @@
   load f = sin(2 pi x/L) cos(6 pi y/L) on dyadic refinements n = 64 .. 1024;
   reported are |u_p - u_{p-1}|_2 / |u_{p-1}|_2 on the coarser grid's nodes
   and their decay factors (the paper expects about 2 sqrt(2));
+* ``dos``: the spectral-density appendix: Gaussian-broadened densities of
+  states of the stiffness matrix for N realizations at L = 4 and 8 (lambda =
+  0.5, alpha = 1/4, m0 = 8, the paper's lumped operator), their sample
+  averages, the spread around them, the distance between the two L (the
+  paper observes practically identical shapes) and the distance to the DOS
+  of the operator with the homogenized coefficient;
 * ``paper``: the statistics of Sec. 5 with the paper's own model parameters
   (overlap alpha = 1/4, i.e. inclusions of side 1/2; L^2 inclusions; matrix
   value 0.4 and inclusion value 1; m0 = 4; the lumped (trapezoid) scheme;
@@ -19,6 +25,7 @@
     python -m paper_1903_12227_gb300.studies variance --Ls 32 64 128 256 --N 256
     python -m paper_1903_12227_gb300.studies paper --Ls 8 16 32 64 --N 10000
     python -m paper_1903_12227_gb300.studies fem --Ls 2 4 8
+    python -m paper_1903_12227_gb300.studies dos --Ls 4 8 --N 20
 """
 from __future__ import annotations
 
@@ -166,16 +173,68 @@ def fem_convergence(Ls=(2, 4, 8), ns=(64, 128, 256, 512, 1024), alpha=0.5, lam=0
     return rows
 
 
+def dos_study(Ls=(4, 8), N=20, lam=0.5, alpha=0.25, m0=8, eta=0.05, K=512, vectors=32,
+              seed=0, scheme=rve.LUMPED) -> dict:
+    """DOS of A for N realizations per L (stochastic Chebyshev moments on the
+    GPU, Gaussian broadening eta), on a common grid t in [0, hi]."""
+    from . import spectral
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"Ls": list(Ls), "N": N, "eta": eta, "K": K, "vectors": vectors, "per_L": []}
+    hi = None
+    t = None
+    means = []
+    for L in Ls:
+        ds = [workloads.realization(L, m0, 1.0 / lam, seed, k, density=1.0, side_units=2 * alpha,
+                                    a_matrix=lam) for k in range(N)]
+        lo, hi = spectral.spectral_bounds(ds[0], scheme)
+        t = np.linspace(0.0, hi, 401)
+        dt = t[1] - t[0]
+        mask = rve.gen_field(ds, device=dev)
+        words = (L * m0) ** 2 // 32
+        phis = []
+        for k, d in enumerate(ds):
+            mk = mask[k * words:(k + 1) * words]
+            phis.append(spectral.dos(d, mk, t, eta, K=K, vectors=vectors, seed=seed * 1000 + k,
+                                     scheme=scheme))
+        phis = np.array(phis)
+        mean = phis.mean(axis=0)
+        means.append(mean)
+        # homogenized operator: constant A_hom (sample mean), lumped symbol
+        u, _ = rve.solve(ds, mask=mask, opts=rve.make_opts(scheme=scheme, precision=rve.MIXED))
+        A = rve.a_hom(ds, u, mask=mask, scheme=scheme).cpu().numpy().mean(axis=0)
+        n = L * m0
+        th = 2 * np.pi * np.arange(n) / n
+        kk = 2.0 - 2.0 * np.cos(th)
+        if scheme == rve.CONSISTENT:
+            mm = (4.0 + 2.0 * np.cos(th)) / 6.0
+            ev = (A[0, 0] * np.outer(kk, mm) + A[1, 1] * np.outer(mm, kk)).ravel()
+        else:
+            ev = (A[0, 0] * kk[:, None] + A[1, 1] * kk[None, :]).ravel()
+        g = spectral.gauss(t[:, None] - ev[None, :], eta).sum(axis=1) / ev.size
+        running = [float(np.abs(phis[:j].mean(axis=0) - mean).sum() * dt) for j in range(1, N + 1)]
+        out["per_L"].append({"L": L, "mean": mean.tolist(),
+                             "spread_L1": [float(np.abs(p - mean).sum() * dt) for p in phis],
+                             "running_mean_L1": running, "A_hom": A.tolist(),
+                             "homogenized_L1": float(np.abs(g - mean).sum() * dt)})
+    out["t"] = t.tolist()
+    if len(means) >= 2:
+        dt = t[1] - t[0]
+        out["L_pair_L1"] = float(np.abs(means[0] - means[-1]).sum() * dt)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["variance", "paper", "fem"])
+    ap.add_argument("study", choices=["variance", "paper", "fem", "dos"])
     ap.add_argument("--Ls", type=int, nargs="+")
     ap.add_argument("--N", type=int)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--count", choices=["fixed", "poisson"], default="fixed")
     ap.add_argument("--json")
     a = ap.parse_args(argv)
-    if a.study == "fem":
+    if a.study == "dos":
+        rows = dos_study(Ls=tuple(a.Ls or (4, 8)), N=a.N or 20, seed=a.seed)
+    elif a.study == "fem":
         rows = fem_convergence(Ls=tuple(a.Ls or (2, 4, 8)), seed=a.seed)
     elif a.study == "variance":
         rows = variance_study(Ls=tuple(a.Ls or (32, 64, 128, 256)), N=a.N or 256, seed=a.seed)

@@ -266,6 +266,61 @@ def test_solve_rhs_matches_oracle(scheme, precision, path, bound):
         off += n * n
 
 
+# ---------------------------------------- spectral density (appendix) --
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_cheb_moments_match_dense_recurrence(scheme):
+    from paper_1903_12227_gb300 import spectral
+    ds = [workloads.realization(4, 8, 2.0, 6, 0, a_matrix=0.5),
+          workloads.realization(8, 8, 10.0, 6, 1)]
+    mask, coefs = _setup(ds)
+    g = np.random.default_rng(8)
+    vs = [g.standard_normal(((d["L"] * d["m0"]) ** 2, 2)) for d in ds]
+    K = 64
+    los_his = [spectral.spectral_bounds(d, scheme) for d in ds]
+    lo = 0.0
+    hi = max(h for _, h in los_his)
+    mu = rve.cheb_moments(ds, torch.tensor(np.concatenate(vs), device=CUDA), K, lo, hi,
+                          mask=mask, scheme=scheme).cpu().numpy()
+    for k, (d, c, v) in enumerate(zip(ds, coefs, vs)):
+        n = d["L"] * d["m0"]
+        A = oracle.csr_to_dense(oracle.assemble(c, 1.0 / d["m0"], scheme), n * n)
+        At = (2.0 * A - (hi + lo) * np.eye(n * n)) / (hi - lo)
+        for comp in range(2):
+            x = v[:, comp]
+            w0, w1 = x, At @ x
+            ref = [x @ w0, x @ w1]
+            for _ in range(2, K):
+                w0, w1 = w1, 2.0 * (At @ w1) - w0
+                ref.append(x @ w1)
+            ref = np.array(ref)
+            assert np.abs(mu[k, comp] - ref).max() < 1e-10 * abs(ref[0])
+
+
+def test_dos_exact_trace_matches_dense_spectrum():
+    # unit start vectors e_0 .. e_{m-1} give the trace exactly, so the
+    # Chebyshev density equals the oracle's dense-spectrum density up to the
+    # (tiny) truncation of the Gaussian's expansion
+    from paper_1903_12227_gb300 import spectral
+    d = workloads.realization(4, 8, 2.0, 9, 0, density=1.0, side_units=0.5, a_matrix=0.5)
+    n = d["L"] * d["m0"]
+    m = n * n
+    mask, coefs = _setup([d])
+    lo, hi = spectral.spectral_bounds(d, rve.LUMPED)
+    pairs = m // 2
+    v = torch.zeros(pairs * m, 2, dtype=torch.float64, device=CUDA)
+    idx = torch.arange(pairs, device=CUDA)
+    v[idx * m + 2 * idx, 0] = 1.0
+    v[idx * m + 2 * idx + 1, 1] = 1.0
+    K = 400
+    mu = rve.cheb_moments([d] * pairs, v, K, lo, hi, mask=mask.repeat(pairs), scheme=rve.LUMPED)
+    tr = mu.sum(dim=(0, 1)).cpu().numpy()
+    t = np.linspace(lo, hi, 301)
+    eta = 0.1
+    phi = spectral.dos_from_moments(tr, t, lo, hi, eta, m)
+    ref = oracle.dos_gauss(oracle.spectrum(coefs[0], 1.0 / d["m0"], rve.LUMPED), t, eta)
+    assert np.abs(phi - ref).max() < 1e-6 * ref.max()
+
+
 @pytest.mark.parametrize("L,m0", [(8, 16), (16, 16), (32, 16)])   # n = 128, 256, 512
 @pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
 def test_cluster_update_column_kernel_matches_separate_kernels(L, m0, scheme):

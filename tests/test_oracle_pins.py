@@ -471,3 +471,32 @@ def test_load_solve_matches_dense_direct_solve(scheme):
     ref = np.linalg.solve(Bord, np.concatenate([b.ravel(), [0.0]]))[:-1]
     u, _, rr = oracle.solve_load(coef, L, m0, 0.55, b, scheme=scheme, tol=1e-14)
     assert np.abs(u.ravel() - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+# ------------------------------------------- spectral density (appendix) --
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_spectrum_constant_coefficient_closed_form(scheme):
+    # a = c: the eigenvalues of A are the Fourier symbols
+    # c (k(t1) m(t2) + m(t1) k(t2)), k = 2 - 2 cos t and m the 1D mass symbol
+    # over h (consistent (4 + 2 cos t)/6, lumped 1; the factors h cancel),
+    # t = 2 pi p / n
+    n, h, c = 16, 0.25, 1.7
+    ev = oracle.spectrum(np.full((n, n), c), h, scheme)
+    t = 2 * np.pi * np.arange(n) / n
+    k = 2.0 - 2.0 * np.cos(t)
+    m = (4.0 + 2.0 * np.cos(t)) / 6.0 if scheme == oracle.SCHEME_CONSISTENT else np.ones(n)
+    ref = np.sort((c * (np.outer(k, m) + np.outer(m, k))).ravel())
+    np.testing.assert_allclose(ev, ref, atol=1e-12 * ref.max())
+
+
+def test_dos_gauss_normalised_and_centred():
+    # the broadened density integrates to one and its mean is Tr(A)/m
+    n, h = 16, 0.25
+    coef = _random_coef(n, 3, lo=0.5, hi=1.0)
+    ev = oracle.spectrum(coef, h)
+    t = np.linspace(ev.min() - 1.0, ev.max() + 1.0, 4001)
+    phi = oracle.dos_gauss(ev, t, 0.05)
+    dt = t[1] - t[0]
+    assert abs(phi.sum() * dt - 1.0) < 1e-6
+    A = oracle.csr_to_dense(oracle.assemble(coef, h), n * n)
+    assert abs((t * phi).sum() * dt - np.trace(A) / (n * n)) < 1e-6
