@@ -42,6 +42,12 @@ class Result(ctypes.Structure):
                 ("iters", ctypes.c_int32 * 2)]
 
 
+class Result3(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32 * 3), ("relres_true", ctypes.c_double * 3),
+                ("A_energy", ctypes.c_double * 9), ("A_flux", ctypes.c_double * 9),
+                ("mean_a", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile rve_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
     with _lock:
@@ -96,6 +102,18 @@ def lib():
                                       vp, ctypes.c_int]
         L.orc_statistics.argtypes = [i64, vp, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
         L.orc_mass_element.argtypes = [ctypes.c_int, dbl, vp]
+        L.orc3_gen_field.argtypes = [ctypes.POINTER(Realization), vp]
+        L.orc3_element_matrix.argtypes = [ctypes.c_int, dbl, vp]
+        L.orc3_assemble.restype = i64
+        L.orc3_assemble.argtypes = [i64, dbl, vp, ctypes.c_int, vp, vp, vp]
+        L.orc3_rhs.argtypes = [i64, dbl, vp, ctypes.c_int, vp]
+        L.orc3_precond.argtypes = [i64, dbl, dbl, vp, vp]
+        L.orc3_pcg.restype = ctypes.c_int
+        L.orc3_pcg.argtypes = [i64, vp, vp, vp, dbl, dbl, vp, dbl, ctypes.c_int, vp, vp]
+        L.orc3_a_hom.argtypes = [i64, dbl, dbl, vp, ctypes.c_int, vp, vp, vp]
+        L.orc3_solve_realization.restype = ctypes.c_int
+        L.orc3_solve_realization.argtypes = [ctypes.POINTER(Realization), ctypes.c_int, dbl,
+                                             ctypes.c_int, dbl, vp, vp, ctypes.POINTER(Result3)]
         L.orc_apply_mass.argtypes = [i64, dbl, ctypes.c_int, vp, vp]
         L.orc_solve_load.restype = ctypes.c_int
         L.orc_solve_load.argtypes = [i64, i64, vp, dbl, ctypes.c_int, vp, dbl, ctypes.c_int, dbl,
@@ -227,6 +245,84 @@ def dos_gauss(eigs: np.ndarray, t: np.ndarray, eta: float) -> np.ndarray:
     t = np.asarray(t, dtype=np.float64)
     g = np.exp(-0.5 * ((t[:, None] - eigs[None, :]) / eta) ** 2) / (np.sqrt(2 * np.pi) * eta)
     return g.sum(axis=1) / eigs.size
+
+
+# ------------------------------------------------------------------ 3D --
+def gen_field3(d: dict) -> np.ndarray:
+    """Covered cells [n,n,n] (uint8) of a 3D realization (cubes)."""
+    n = int(d["L"]) * int(d["m0"])
+    mask = np.zeros((n, n, n), dtype=np.uint8)
+    lib().orc3_gen_field(ctypes.byref(_real(d)), _p(mask))
+    return mask
+
+
+def element_matrix3(scheme: int, h: float) -> np.ndarray:
+    E = np.zeros(64)
+    lib().orc3_element_matrix(scheme, h, _p(E))
+    return E.reshape(8, 8)
+
+
+def assemble3(coef: np.ndarray, h: float, scheme: int = SCHEME_CONSISTENT):
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    n = coef.shape[0]
+    N = n ** 3
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    colidx = np.zeros(27 * N, dtype=np.int64)
+    vals = np.zeros(27 * N, dtype=np.float64)
+    nnz = lib().orc3_assemble(n, h, _p(coef), scheme, _p(rowptr), _p(colidx), _p(vals))
+    return rowptr, colidx[:nnz].copy(), vals[:nnz].copy()
+
+
+def rhs3(coef: np.ndarray, h: float, scheme: int = SCHEME_CONSISTENT) -> np.ndarray:
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    n = coef.shape[0]
+    f = np.zeros((3, n, n, n))
+    lib().orc3_rhs(n, h, _p(coef), scheme, _p(f))
+    return f
+
+
+def precond3(r: np.ndarray, c0: float, delta: float = 0.0) -> np.ndarray:
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    z = np.zeros_like(r)
+    lib().orc3_precond(r.shape[0], c0, delta, _p(r), _p(z))
+    return z
+
+
+def solve_coef3(coef: np.ndarray, L: int, m0: int, c0: float, scheme: int = SCHEME_CONSISTENT,
+                tol: float = 1e-12, max_iter: int = 5000) -> dict:
+    """Three corrector solves and the 3x3 A_hom for a given cell coefficient [n,n,n]."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    n = coef.shape[0]
+    h = 1.0 / m0
+    rowptr, colidx, vals = assemble3(coef, h, scheme)
+    f = rhs3(coef, h, scheme)
+    u = np.zeros_like(f)
+    iters, rel = [], []
+    for i in range(3):
+        rr = ctypes.c_double(0.0)
+        it = lib().orc3_pcg(n, _p(rowptr), _p(colidx), _p(vals), c0, 0.0, _p(f[i]), tol, max_iter,
+                            _p(u[i]), ctypes.byref(rr))
+        iters.append(it)
+        rel.append(rr.value)
+    Ae, Af = np.zeros(9), np.zeros(9)
+    lib().orc3_a_hom(n, h, float(L), _p(coef), scheme, _p(u), _p(Ae), _p(Af))
+    return {"u": u, "iters": iters, "relres": rel, "A_energy": Ae.reshape(3, 3),
+            "A_flux": Af.reshape(3, 3)}
+
+
+def solve_realization3(d: dict, scheme: int = SCHEME_CONSISTENT, tol: float = 1e-12,
+                       max_iter: int = 5000, want_u: bool = True) -> dict:
+    n = int(d["L"]) * int(d["m0"])
+    mask = np.zeros((n, n, n), dtype=np.uint8)
+    u = np.zeros((3, n, n, n)) if want_u else None
+    res = Result3()
+    rc = lib().orc3_solve_realization(ctypes.byref(_real(d)), scheme, tol, max_iter, 0.0,
+                                      _p(mask), _p(u) if want_u else None, ctypes.byref(res))
+    if rc != 0:
+        raise MemoryError("oracle 3D solve failed")
+    return {"A_energy": np.array(res.A_energy).reshape(3, 3),
+            "A_flux": np.array(res.A_flux).reshape(3, 3), "iters": list(res.iters),
+            "relres": list(res.relres_true), "mean_a": res.mean_a, "u": u, "mask": mask}
 
 
 def laplacian_eig(n: int, k1: int, k2: int) -> float:

@@ -28,7 +28,10 @@
  *      standard-deviation estimators (Eqs. "Var1", "Var2") and the rescaled
  *      covariance / quartic tensor (Eq. "quartic");
  *   8. for a general load (the FEM convergence test of Sec. 3.5): the mass
- *      matrix M1 (x) M1 applied cell by cell, and the solve A u = b.
+ *      matrix M1 (x) M1 applied cell by cell, and the solve A u = b;
+ *   9. the 3D extension (the paper's remark that the scheme extends to 3D):
+ *      cubes, the trilinear element K1(x)M1(x)M1 + M1(x)K1(x)M1 + M1(x)M1(x)K1,
+ *      the 7-point Laplacian preconditioner, three correctors, 3x3 A_hom.
  *
  * Readings of the paper that this oracle fixes (where it is silent or
  * garbled) are listed beside each function.  Everything is FP64.
@@ -658,4 +661,299 @@ void orc_statistics(int64_t N, const double* A, double L, int d, double* mean,
             Q[4 * p + q] = scale * s;
         }
     for (int k = 0; k < 4; ++k) var[k] = Q[4 * k + k] / pow(L, (double)d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 9. The 3D extension (the paper's remark on 3D): cubes, trilinear Q1       */
+/* ------------------------------------------------------------------------ */
+/* Grid: n = L*m0 nodes per axis on the torus [0,L)^3, node (i1,i2,i3) at
+ * index (i1*n + i2)*n + i3; cell (c1,c2,c3) has lower corner node (c1,c2,c3);
+ * local corner a = 4 a1 + 2 a2 + a3 (a_k in {0,1}).  Correctors u_1..u_3
+ * stored [3][N]. */
+
+/* Covered set: N_inc cubes of side s (cells) with lower corners drawn from
+ * the counter RNG (tag 1, draws 3k, 3k+1, 3k+2 per cube), periodic wrap. */
+void orc3_gen_field(const orc_realization* r, uint8_t* mask)
+{
+    const int64_t n = (int64_t)r->L * r->m0, s = r->incl_cells;
+    memset(mask, 0, (size_t)(n * n * n));
+    const uint64_t key = orc_realization_key(r->seed, r->index);
+    for (int64_t k = 0; k < r->n_incl; ++k) {
+        int64_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            const uint64_t v = orc_draw(key, 1, 3 * (uint64_t)k + (uint64_t)a);
+            c[a] = (int64_t)(((unsigned __int128)v * (uint64_t)n) >> 64);
+        }
+        for (int64_t d1 = 0; d1 < s; ++d1)
+            for (int64_t d2 = 0; d2 < s; ++d2)
+                for (int64_t d3 = 0; d3 < s; ++d3)
+                    mask[(((c[0] + d1) % n) * n + (c[1] + d2) % n) * n + (c[2] + d3) % n] = 1;
+    }
+}
+
+/* Element matrix K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1. */
+void orc3_element_matrix(int scheme, double h, double E[64])
+{
+    double K1[2][2] = {{1.0 / h, -1.0 / h}, {-1.0 / h, 1.0 / h}};
+    double M1[2][2];
+    if (scheme == ORC_SCHEME_LUMPED) {
+        M1[0][0] = h / 2; M1[0][1] = 0; M1[1][0] = 0; M1[1][1] = h / 2;
+    } else {
+        M1[0][0] = 2 * h / 6; M1[0][1] = h / 6; M1[1][0] = h / 6; M1[1][1] = 2 * h / 6;
+    }
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) {
+            const int a1 = a >> 2, a2 = (a >> 1) & 1, a3 = a & 1;
+            const int b1 = b >> 2, b2 = (b >> 1) & 1, b3 = b & 1;
+            E[a * 8 + b] = K1[a1][b1] * M1[a2][b2] * M1[a3][b3] +
+                           M1[a1][b1] * K1[a2][b2] * M1[a3][b3] +
+                           M1[a1][b1] * M1[a2][b2] * K1[a3][b3];
+        }
+}
+
+static void orc3_cell_nodes(int64_t n, int64_t c1, int64_t c2, int64_t c3, int64_t g[8])
+{
+    for (int a = 0; a < 8; ++a) {
+        const int64_t i1 = (c1 + (a >> 2)) % n, i2 = (c2 + ((a >> 1) & 1)) % n, i3 = (c3 + (a & 1)) % n;
+        g[a] = (i1 * n + i2) * n + i3;
+    }
+}
+
+/* CSR stiffness (27 entries per row), summed over cells as in 2D. */
+int64_t orc3_assemble(int64_t n, double h, const double* coef, int scheme, int64_t* rowptr,
+                      int64_t* colidx, double* vals)
+{
+    double E[64];
+    orc3_element_matrix(scheme, h, E);
+    const int64_t N = n * n * n;
+    orc_triplet* t = (orc_triplet*)malloc(sizeof(orc_triplet) * (size_t)(64 * N));
+    int64_t nt = 0;
+    for (int64_t c1 = 0; c1 < n; ++c1)
+        for (int64_t c2 = 0; c2 < n; ++c2)
+            for (int64_t c3 = 0; c3 < n; ++c3) {
+                int64_t g[8];
+                orc3_cell_nodes(n, c1, c2, c3, g);
+                const double a = coef[(c1 * n + c2) * n + c3];
+                for (int i = 0; i < 8; ++i)
+                    for (int j = 0; j < 8; ++j) {
+                        t[nt].row = g[i];
+                        t[nt].col = g[j];
+                        t[nt].val = a * E[i * 8 + j];
+                        ++nt;
+                    }
+            }
+    qsort(t, (size_t)nt, sizeof(orc_triplet), orc_triplet_cmp);
+    int64_t nnz = 0;
+    for (int64_t r = 0; r <= N; ++r) rowptr[r] = 0;
+    for (int64_t k = 0; k < nt; ++k) {
+        if (k > 0 && t[k].row == t[k - 1].row && t[k].col == t[k - 1].col) {
+            vals[nnz - 1] += t[k].val;
+        } else {
+            colidx[nnz] = t[k].col;
+            vals[nnz] = t[k].val;
+            rowptr[t[k].row + 1] += 1;
+            ++nnz;
+        }
+    }
+    for (int64_t r = 0; r < N; ++r) rowptr[r + 1] += rowptr[r];
+    free(t);
+    return nnz;
+}
+
+/* f_i = -sum_c a_c P_c^T E xi_i, xi_i = h (corner bit of axis i). */
+void orc3_rhs(int64_t n, double h, const double* coef, int scheme, double* f)
+{
+    double E[64];
+    orc3_element_matrix(scheme, h, E);
+    const int64_t N = n * n * n;
+    memset(f, 0, sizeof(double) * 3 * (size_t)N);
+    for (int i = 0; i < 3; ++i) {
+        double Exi[8];
+        for (int r = 0; r < 8; ++r) {
+            Exi[r] = 0.0;
+            for (int c = 0; c < 8; ++c) Exi[r] += E[r * 8 + c] * h * (double)((c >> (2 - i)) & 1);
+        }
+        for (int64_t c1 = 0; c1 < n; ++c1)
+            for (int64_t c2 = 0; c2 < n; ++c2)
+                for (int64_t c3 = 0; c3 < n; ++c3) {
+                    int64_t g[8];
+                    orc3_cell_nodes(n, c1, c2, c3, g);
+                    const double a = coef[(c1 * n + c2) * n + c3];
+                    for (int r = 0; r < 8; ++r) f[i * N + g[r]] -= a * Exi[r];
+                }
+    }
+}
+
+/* z = B^{-1} r, B = c0 A_Delta + delta I with A_Delta the periodic 7-point
+ * Laplacian (eigenvalues 4 sin^2(pi k1/n) + 4 sin^2(pi k2/n) + 4
+ * sin^2(pi k3/n)); the constant mode is dropped when delta = 0. */
+void orc3_precond(int64_t n, double c0, double delta, const double* r, double* z)
+{
+    const int64_t N = n * n * n;
+    if (n < 1 || (n & (n - 1)) != 0) {
+        for (int64_t k = 0; k < N; ++k) z[k] = NAN;
+        return;
+    }
+    double* re = (double*)malloc(sizeof(double) * (size_t)N);
+    double* im = (double*)calloc((size_t)N, sizeof(double));
+    double* lr = (double*)malloc(sizeof(double) * (size_t)n);
+    double* li = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(re, r, sizeof(double) * (size_t)N);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int sign = pass == 0 ? -1 : +1;
+        for (int axis = 0; axis < 3; ++axis) {
+            const int64_t stride = axis == 0 ? n * n : (axis == 1 ? n : 1);
+            for (int64_t a = 0; a < n; ++a)
+                for (int64_t b = 0; b < n; ++b) {
+                    int64_t base;
+                    if (axis == 0) base = a * n + b;
+                    else if (axis == 1) base = a * n * n + b;
+                    else base = (a * n + b) * n;
+                    for (int64_t k = 0; k < n; ++k) { lr[k] = re[base + k * stride]; li[k] = im[base + k * stride]; }
+                    orc_fft1d(n, lr, li, sign);
+                    for (int64_t k = 0; k < n; ++k) { re[base + k * stride] = lr[k]; im[base + k * stride] = li[k]; }
+                }
+        }
+        if (pass == 0) {
+            for (int64_t k1 = 0; k1 < n; ++k1)
+                for (int64_t k2 = 0; k2 < n; ++k2)
+                    for (int64_t k3 = 0; k3 < n; ++k3) {
+                        const double s1 = sin(ORC_PI * (double)k1 / (double)n);
+                        const double s2 = sin(ORC_PI * (double)k2 / (double)n);
+                        const double s3 = sin(ORC_PI * (double)k3 / (double)n);
+                        const double sigma = c0 * 4.0 * (s1 * s1 + s2 * s2 + s3 * s3) + delta;
+                        const int64_t idx = (k1 * n + k2) * n + k3;
+                        const double inv = (k1 == 0 && k2 == 0 && k3 == 0 && delta == 0.0) ? 0.0 : 1.0 / sigma;
+                        re[idx] *= inv;
+                        im[idx] *= inv;
+                    }
+        }
+    }
+    for (int64_t k = 0; k < N; ++k) z[k] = re[k] / (double)N;
+    free(re); free(im); free(lr); free(li);
+}
+
+/* PCG as orc_pcg, on n^3 unknowns with the 3D preconditioner. */
+int orc3_pcg(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* vals,
+             double c0, double delta, const double* f, double tol, int max_iter, double* u,
+             double* relres_true)
+{
+    const int64_t N = n * n * n;
+    double* r = (double*)malloc(sizeof(double) * (size_t)N);
+    double* z = (double*)malloc(sizeof(double) * (size_t)N);
+    double* p = (double*)malloc(sizeof(double) * (size_t)N);
+    double* q = (double*)malloc(sizeof(double) * (size_t)N);
+    memset(u, 0, sizeof(double) * (size_t)N);
+    memcpy(r, f, sizeof(double) * (size_t)N);
+    const double fnorm = sqrt(orc_dot(N, f, f));
+    int it = 0;
+    if (fnorm > 0.0) {
+        orc3_precond(n, c0, delta, r, z);
+        memcpy(p, z, sizeof(double) * (size_t)N);
+        double rz = orc_dot(N, r, z);
+        while (it < max_iter) {
+            orc_spmv(N, rowptr, colidx, vals, p, q);
+            ++it;
+            const double alpha = rz / orc_dot(N, p, q);
+            for (int64_t k = 0; k < N; ++k) { u[k] += alpha * p[k]; r[k] -= alpha * q[k]; }
+            if (sqrt(orc_dot(N, r, r)) <= tol * fnorm) break;
+            orc3_precond(n, c0, delta, r, z);
+            const double rz_new = orc_dot(N, r, z);
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            for (int64_t k = 0; k < N; ++k) p[k] = z[k] + beta * p[k];
+        }
+    }
+    double mean = 0.0;
+    for (int64_t k = 0; k < N; ++k) mean += u[k];
+    mean /= (double)N;
+    for (int64_t k = 0; k < N; ++k) u[k] -= mean;
+    if (relres_true) {
+        orc_spmv(N, rowptr, colidx, vals, u, q);
+        double s = 0.0;
+        for (int64_t k = 0; k < N; ++k) s += (f[k] - q[k]) * (f[k] - q[k]);
+        *relres_true = fnorm > 0.0 ? sqrt(s) / fnorm : 0.0;
+    }
+    free(r); free(z); free(p); free(q);
+    return it;
+}
+
+/* 3x3 homogenized matrices, cell by cell: energy (1/L^3) sum_c a_c v_i^T E
+ * v_j with v_i = xi_i + P_c u_i, flux (1/L^3) sum_c a_c int_c d_j (x_i +
+ * phi_i) (the exact integral of the trilinear derivative: h^2/4 times the
+ * sum over the four cell edges along axis j of the end differences). */
+void orc3_a_hom(int64_t n, double h, double Lsize, const double* coef, int scheme,
+                const double* u, double* A_energy, double* A_flux)
+{
+    double E[64];
+    orc3_element_matrix(scheme, h, E);
+    const int64_t N = n * n * n;
+    double en[9] = {0}, fl[9] = {0};
+    for (int64_t c1 = 0; c1 < n; ++c1)
+        for (int64_t c2 = 0; c2 < n; ++c2)
+            for (int64_t c3 = 0; c3 < n; ++c3) {
+                int64_t g[8];
+                orc3_cell_nodes(n, c1, c2, c3, g);
+                const double a = coef[(c1 * n + c2) * n + c3];
+                double v[3][8];
+                for (int i = 0; i < 3; ++i)
+                    for (int k = 0; k < 8; ++k)
+                        v[i][k] = u[i * N + g[k]] + h * (double)((k >> (2 - i)) & 1);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        double s = 0.0;
+                        for (int r = 0; r < 8; ++r)
+                            for (int c = 0; c < 8; ++c) s += v[j][r] * E[r * 8 + c] * v[i][c];
+                        en[3 * i + j] += a * s;
+                        double d = 0.0;
+                        for (int k = 0; k < 8; ++k)
+                            d += ((k >> (2 - j)) & 1) ? v[i][k] : -v[i][k];
+                        fl[3 * i + j] += a * 0.25 * h * h * d;
+                    }
+            }
+    const double vol = Lsize * Lsize * Lsize;
+    for (int k = 0; k < 9; ++k) {
+        if (A_energy) A_energy[k] = en[k] / vol;
+        if (A_flux) A_flux[k] = fl[k] / vol;
+    }
+}
+
+/* Field, assembly, the three corrector solves and A_hom of one 3D
+ * realization.  u (or NULL): [3][n^3]. */
+int orc3_solve_realization(const orc_realization* r, int scheme, double tol, int max_iter,
+                           double delta, uint8_t* mask_out, double* u, orc3_result* res)
+{
+    const int64_t n = (int64_t)r->L * r->m0;
+    const int64_t N = n * n * n;
+    const double h = 1.0 / (double)r->m0;
+    if (n < 2 || (n & (n - 1)) != 0) return -2;
+    uint8_t* mask = mask_out ? mask_out : (uint8_t*)malloc((size_t)N);
+    double* coef = (double*)malloc(sizeof(double) * (size_t)N);
+    int64_t* rowptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    int64_t* colidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(27 * N));
+    double* vals = (double*)malloc(sizeof(double) * (size_t)(27 * N));
+    double* f = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* uu = u ? u : (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    if (!mask || !coef || !rowptr || !colidx || !vals || !f || !uu) return -1;
+    orc3_gen_field(r, mask);
+    double s = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        coef[k] = mask[k] ? r->a_incl : r->a_matrix;
+        s += coef[k];
+    }
+    res->mean_a = s / (double)N;
+    const double c0 = 0.5 * (r->a_matrix + r->a_incl);
+    orc3_assemble(n, h, coef, scheme, rowptr, colidx, vals);
+    orc3_rhs(n, h, coef, scheme, f);
+    for (int i = 0; i < 3; ++i) {
+        double rr = 0.0;
+        res->iters[i] = orc3_pcg(n, rowptr, colidx, vals, c0, delta, f + i * N, tol, max_iter,
+                                 uu + i * N, &rr);
+        res->relres_true[i] = rr;
+    }
+    orc3_a_hom(n, h, (double)r->L, coef, scheme, uu, res->A_energy, res->A_flux);
+    free(coef); free(rowptr); free(colidx); free(vals); free(f);
+    if (!u) free(uu);
+    if (!mask_out) free(mask);
+    return 0;
 }

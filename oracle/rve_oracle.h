@@ -76,6 +76,27 @@ int orc_solve_load(int64_t L, int64_t m0, const double* coef, double c0, int sch
                    const double* b, double tol, int max_iter, double delta, double* u,
                    double* relres_true);
 
+/* The 3D extension (cubes, trilinear Q1, 3x3 A_hom). */
+typedef struct {
+    int iters[3];
+    double relres_true[3];
+    double A_energy[9], A_flux[9];
+    double mean_a;
+} orc3_result;
+void orc3_gen_field(const orc_realization* r, uint8_t* mask);
+void orc3_element_matrix(int scheme, double h, double E[64]);
+int64_t orc3_assemble(int64_t n, double h, const double* coef, int scheme, int64_t* rowptr,
+                      int64_t* colidx, double* vals);
+void orc3_rhs(int64_t n, double h, const double* coef, int scheme, double* f);
+void orc3_precond(int64_t n, double c0, double delta, const double* r, double* z);
+int orc3_pcg(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* vals,
+             double c0, double delta, const double* f, double tol, int max_iter, double* u,
+             double* relres_true);
+void orc3_a_hom(int64_t n, double h, double Lsize, const double* coef, int scheme,
+                const double* u, double* A_energy, double* A_flux);
+int orc3_solve_realization(const orc_realization* r, int scheme, double tol, int max_iter,
+                           double delta, uint8_t* mask_out, double* u, orc3_result* res);
+
 void orc_statistics(int64_t N, const double* A, double L, int d, double* mean,
                     double* var, double* std12_paper, double* stddiff_paper,
                     double* Q);

@@ -500,3 +500,138 @@ def test_dos_gauss_normalised_and_centred():
     assert abs(phi.sum() * dt - 1.0) < 1e-6
     A = oracle.csr_to_dense(oracle.assemble(coef, h), n * n)
     assert abs((t * phi).sum() * dt - np.trace(A) / (n * n)) < 1e-6
+
+
+# ---------------------------------------------------------------- 3D --
+def _trilinear_grad(e8, t, h):
+    """Gradient of the trilinear interpolant of local values (a = 4a1+2a2+a3) at t in [0,1]^3."""
+    g = np.zeros(3)
+    for a in range(8):
+        bits = ((a >> 2) & 1, (a >> 1) & 1, a & 1)
+        for ax in range(3):
+            prod = 1.0
+            for k in range(3):
+                if k == ax:
+                    prod *= (1.0 if bits[k] else -1.0) / h
+                else:
+                    prod *= t[k] if bits[k] else (1.0 - t[k])
+            g[ax] += e8[a] * prod
+    return g
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_element_matrix3_equals_quadrature(scheme):
+    # consistent: 2-point Gauss in every direction (exact); lumped: Gauss in
+    # the derivative's direction, trapezoid in the other two
+    h = 0.5
+    E = oracle.element_matrix3(scheme, h)
+    gauss, trap = _gauss2(), [(0.0, 0.5), (1.0, 0.5)]
+    for a in range(8):
+        for b in range(8):
+            ea, eb = np.eye(8)[a], np.eye(8)[b]
+            s = 0.0
+            for ax in range(3):
+                rules = [gauss if (scheme == oracle.SCHEME_CONSISTENT or k == ax) else trap
+                         for k in range(3)]
+                for t1, w1 in rules[0]:
+                    for t2, w2 in rules[1]:
+                        for t3, w3 in rules[2]:
+                            ga = _trilinear_grad(ea, (t1, t2, t3), h)
+                            gb = _trilinear_grad(eb, (t1, t2, t3), h)
+                            s += w1 * w2 * w3 * ga[ax] * gb[ax]
+            assert abs(E[a, b] - s * h ** 3) < 1e-14
+
+
+def test_stiffness3_structure():
+    n, h = 4, 0.5
+    coef = np.random.default_rng(3).uniform(0.5, 2.0, (n, n, n))
+    A = oracle.csr_to_dense(oracle.assemble3(coef, h), n ** 3)
+    assert np.abs(A - A.T).max() < 1e-14
+    assert np.abs(A.sum(axis=1)).max() < 1e-13
+    ev = np.linalg.eigvalsh(A)
+    assert abs(ev[0]) < 1e-12 and ev[1] > 1e-6      # PSD, one-dimensional kernel
+    # the trilinear element couples edge-adjacent corners with weight 0, so
+    # the six axis neighbours drop out: 1 + 12 + 8 = 21 entries per row
+    assert all(np.count_nonzero(np.abs(A[r]) > 1e-15) == 21 for r in range(n ** 3))
+
+
+def test_field3_union_matches_predicate():
+    d = {"L": 2, "m0": 4, "incl_cells": 3, "n_incl": 5, "a_matrix": 1.0, "a_incl": 5.0,
+         "seed": 77, "index": 3}
+    n = 8
+    L = oracle.lib()
+    key = L.orc_realization_key(77, 3)
+    ref = np.zeros((n, n, n), dtype=np.uint8)
+    for k in range(5):
+        c = [(L.orc_draw(key, 1, 3 * k + a) * n) >> 64 for a in range(3)]
+        for d1 in range(3):
+            for d2 in range(3):
+                for d3 in range(3):
+                    ref[(c[0] + d1) % n, (c[1] + d2) % n, (c[2] + d3) % n] = 1
+    np.testing.assert_array_equal(oracle.gen_field3(d), ref)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_constant_coefficient3_gives_cI(scheme):
+    n, c = 8, 2.5
+    coef = np.full((n, n, n), c)
+    assert np.abs(oracle.rhs3(coef, 0.25, scheme)).max() < 1e-14
+    r = oracle.solve_coef3(coef, 2, 4, c, scheme)
+    np.testing.assert_allclose(r["A_energy"], c * np.eye(3), atol=1e-13)
+    np.testing.assert_allclose(r["A_flux"], c * np.eye(3), atol=1e-13)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_laminate3_harmonic_and_arithmetic_means(scheme):
+    # a depends on the first coordinate only: a_11 = harmonic mean, a_22 =
+    # a_33 = arithmetic mean, off-diagonals zero (exact for the Q1 scheme)
+    n = 8
+    prof = np.array([1.0, 1.0, 7.0, 7.0, 7.0, 2.0, 1.0, 3.0])
+    coef = np.broadcast_to(prof[:, None, None], (n, n, n)).copy()
+    r = oracle.solve_coef3(coef, 2, 4, 4.0, scheme, tol=1e-13)
+    harm, arith = 1.0 / np.mean(1.0 / prof), np.mean(prof)
+    ref = np.diag([harm, arith, arith])
+    np.testing.assert_allclose(r["A_energy"], ref, atol=1e-11)
+    np.testing.assert_allclose(r["A_flux"], ref, atol=1e-10)
+
+
+def test_precond3_inverts_B():
+    # B = c0 A_Delta + delta I with the periodic 7-point Laplacian, built densely
+    n, c0 = 8, 1.5
+    N = n ** 3
+    idx = np.arange(N).reshape(n, n, n)
+    Ad = np.zeros((N, N))
+    for ax in range(3):
+        for sh in (-1, 1):
+            nb = np.roll(idx, sh, axis=ax).ravel()
+            Ad[np.arange(N), nb] -= 1.0
+    Ad[np.arange(N), np.arange(N)] += 6.0
+    r = np.random.default_rng(4).standard_normal((n, n, n))
+    for delta in (0.0, 0.3):
+        rr = r - r.mean() if delta == 0.0 else r
+        z = oracle.precond3(rr, c0, delta)
+        np.testing.assert_allclose((c0 * Ad + delta * np.eye(N)) @ z.ravel(), rr.ravel(), atol=1e-11)
+
+
+def test_pcg3_matches_dense_direct_solve():
+    n, h = 4, 0.5
+    coef = np.where(np.random.default_rng(6).random((n, n, n)) < 0.4, 8.0, 1.0)
+    A = oracle.csr_to_dense(oracle.assemble3(coef, h), n ** 3)
+    f = oracle.rhs3(coef, h)
+    r = oracle.solve_coef3(coef, 2, 2, 4.5, tol=1e-14)
+    Bord = np.zeros((n ** 3 + 1, n ** 3 + 1))
+    Bord[:-1, :-1] = A
+    Bord[:-1, -1] = Bord[-1, :-1] = 1.0
+    for i in range(3):
+        ref = np.linalg.solve(Bord, np.concatenate([f[i].ravel(), [0.0]]))[:-1]
+        assert np.abs(r["u"][i].ravel() - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_voigt_reuss3_bounds():
+    d = {"L": 2, "m0": 4, "incl_cells": 4, "n_incl": 6, "a_matrix": 1.0, "a_incl": 10.0,
+         "seed": 5, "index": 0}
+    r = oracle.solve_realization3(d)
+    mask = r["mask"]
+    a = np.where(mask, 10.0, 1.0)
+    ev = np.linalg.eigvalsh(0.5 * (r["A_energy"] + r["A_energy"].T))
+    assert 1.0 / np.mean(1.0 / a) <= ev[0] and ev[-1] <= np.mean(a)
