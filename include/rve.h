@@ -350,6 +350,86 @@ rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch, const uint
                              const double* coef, int32_t scheme, const double* u,
                              double* A, double* A_flux, void* stream);
 
+/* ---------------------------------------------------------------- 3D --
+ * The 3D form of the method (Sec. 2: the setting carries over verbatim to
+ * d > 2 with a d x d diagonal coefficient; Sec. 3.2: the rank-3 Kronecker
+ * Laplacian A_Delta = A_P (x) I (x) I + I (x) A_P (x) I + I (x) I (x) A_P and
+ * Eq. "As_Kron_d"; Sec. 3.1: multilinear functions on cubes).  Realization
+ * fields as in 2D with L, m0, incl_cells, n_incl describing the torus
+ * [0,L)^3, n = L*m0 nodes per axis, n a power of two, 32 <= n <= 256, and
+ * n_incl cubes of incl_cells^3 cells whose lower corners are uniform on the
+ * nodes (draws 3k, 3k+1, 3k+2 of the realization's stream for cube k).
+ * Node (i1,i2,i3) at linear index (i1 n + i2) n + i3; cell (c1,c2,c3) has
+ * lower corner node (c1,c2,c3) and the same index.  Realizations are packed
+ * back to back (offset sum_{b'<b} n_b'^3).
+ *   mask   uint8, one byte per cell (nonzero = covered by a cube);
+ *   coef   double per cell (general values; NULL = mask and the two values);
+ *   vectors of three components (u, f, x, y): double [nodes][3].
+ * Element matrix: K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1
+ * (trilinear Q1, M1 consistent or lumped as in 2D), 27-point stencil.
+ * All device pointers; ws: rve3_workspace_size() bytes of device memory,
+ * owned by the caller, contents undefined between calls.  Every call is
+ * asynchronous on `stream` except rve3_solve_correctors, which polls the
+ * convergence flags from the host.  Errors: RVE_EINVAL (sizes outside the
+ * range, n not a power of two, non-positive or non-finite coefficients,
+ * missing pointers, unknown scheme), RVE_ENOMEM (ws too small), RVE_ECUDA. */
+typedef struct {
+    int32_t scheme;      /* rve_scheme                                      */
+    int32_t max_iter;    /* cap on CG iterations per corrector (0 = 20000)  */
+    double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (0=1e-10)*/
+    double delta;        /* preconditioner shift; 0 = drop the constant mode*/
+    int32_t check_every; /* host convergence poll period (0 = 8)            */
+    int32_t reserved;    /* must be 0                                       */
+} rve3_solve_opts;       /* 32 bytes */
+
+typedef struct {
+    int32_t iters[3];     /* PCG iterations per corrector               */
+    int32_t status;       /* rve_status (first failure of the three)    */
+    double relres[3];     /* FP64 true relative residual per corrector  */
+} rve3_solve_info;        /* 40 bytes */
+
+/* Nodes of the batch (sum of n^3), or -1 if a descriptor is invalid. */
+int64_t rve3_nodes(const rve_realization* r, int32_t batch);
+/* Workspace bytes of every rve3_* call on this batch (0 if invalid). */
+size_t rve3_workspace_size(const rve_realization* r, int32_t batch);
+/* Cube field: mask[nodes] (bytes) of every realization. */
+rve_status rve3_gen_field(const rve_realization* r, int32_t batch, uint8_t* mask,
+                          void* stream);
+/* Corrector loads f_i = -A (x_i) (the Galerkin right-hand sides of the
+ * three cell problems -div a (e_i + grad phi_i) = 0), f[nodes][3].  They do
+ * not depend on the scheme (the 1D mass rows sum to h/2 in both; `scheme`
+ * is validated only): f_i = (h^2/4) (sum of the 4 cells above the node
+ * along axis i - sum of the 4 cells below), exactly 0 where the 8 cells
+ * around a node agree. */
+rve_status rve3_rhs(const rve_realization* r, int32_t batch, const uint8_t* mask,
+                    const double* coef, int32_t scheme, double* f, void* ws,
+                    size_t ws_bytes, void* stream);
+/* y = A x (27-point stencil), x, y [nodes][3], must not alias. */
+rve_status rve3_apply_stiffness(const rve_realization* r, int32_t batch, const uint8_t* mask,
+                                const double* coef, int32_t scheme, const double* x,
+                                double* y, void* ws, size_t ws_bytes, void* stream);
+/* y = B^{-1} x, B = c0 A_Delta + delta I (c0 = (a_matrix + a_incl)/2; with
+ * delta = 0 the constant mode of each component is dropped): Hartley
+ * transforms along the two inner axes, periodic tridiagonal solves along
+ * the outer one.  x, y [nodes][3]; x is read before y is written (x may
+ * equal y). */
+rve_status rve3_apply_precond(const rve_realization* r, int32_t batch, double delta,
+                              const double* x, double* y, void* ws, size_t ws_bytes,
+                              void* stream);
+/* The three correctors by preconditioned CG (FP64) from u = 0: u[nodes][3];
+ * info[batch] (device) per realization. */
+rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const uint8_t* mask,
+                                 const double* coef, const rve3_solve_opts* opts, double* u,
+                                 rve3_solve_info* info, void* ws, size_t ws_bytes,
+                                 void* stream);
+/* 3x3 homogenized matrix per realization: A[b][3 i + j] = L^-3 sum_cells
+ * a_c v_i^T E v_j (energy form, v_i = x_i + u_i on the cell's corners) and,
+ * if A_flux is not NULL, A_flux[b][3 i + j] = L^-3 sum_cells a_c int_c
+ * d_j (x_i + u_i) (flux form).  Device doubles [batch][9]. */
+rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* mask,
+                      const double* coef, int32_t scheme, const double* u, double* A,
+                      double* A_flux, void* ws, size_t ws_bytes, void* stream);
+
 /* Diagnostics for benchmarks (process-wide, not thread-safe).
  * rve_profile_enable(1): the fused solver brackets every launch of its five
  * pipeline kernels with CUDA events on the caller's stream and accumulates
@@ -361,6 +441,12 @@ rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch, const uint
  * since the previous call. */
 void rve_profile_enable(int32_t on);
 int32_t rve_profile_read(double* ms, int64_t* launches);
+/* The same for the 3D solver (enabled by rve_profile_enable as well): every
+ * launch of rve3_solve_correctors bracketed by events, totals per kind --
+ * 0 stiffness (27-point stencil, with the p.q partials), 1 line transform
+ * (x or y Hartley pass), 2 z tridiagonal solve, 3 CG vector steps (dots,
+ * updates), 4 CG scalar steps -- reset on read; returns 5. */
+int32_t rve3_profile_read(double* ms, int64_t* launches);
 int64_t rve_launch_count(void);
 
 #ifdef __cplusplus

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librve.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["rve_api.cu", "rve_ops.cu", "rve_solver.cu", "rve_plain.cu", "rve_noalloc.cu",
-           "rve_plan.cu"]
+           "rve_plan.cu", "rve3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -58,6 +58,19 @@ __device__ __forceinline__ int find_real(const int32_t* start, int batch, int t)
     return lo;
 }
 
+// ------------------------------------------------------------ SplitMix64 --
+// Steele, Lea & Flood (OOPSLA 2014): output k (k >= 1) of the stream seeded
+// with s is mix(s + k * GAMMA).  Realization key = output (index+1) of the
+// run seed's stream; draw `ctr` under `tag` = output ((tag << 40) + ctr + 1)
+// of the key's stream.
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint32_t tag, uint64_t ctr) {
+    return sm64_mix(key + (((uint64_t)tag << 40) + ctr + 1) * 0x9E3779B97F4A7C15ull);
+}
 // Cell-coefficient source: bitmask + the two values, or an explicit array;
 // and the right-hand side: the corrector loads f_1, f_2 formed from the cells
 // (f == NULL), or a caller's load vector pair per node.

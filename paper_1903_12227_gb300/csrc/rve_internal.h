@@ -75,6 +75,30 @@ struct Plan {
     size_t total = 0;
 };
 
+// Plain FP64 PCG building blocks (rve_plain.cu), shared with the 3D solver:
+// vector kernels over the nodes of realization b (PL_NODES per block, from
+// desc[b].node_off) on corrector pairs, and the per-pair scalar steps.
+constexpr int PL_THREADS = 256;
+constexpr int PL_NODES = 1024;   // nodes per block (n^2 and n^3 are multiples of 1024)
+struct PlainScal {
+    double rho[2], alpha[2], beta[2], fnorm[2], relres[2];
+    int32_t active[2], iters[2];
+    int32_t done, status;
+};
+enum { SC_FNORM = 0, SC_RHO0, SC_ALPHA, SC_CONV, SC_BETA, SC_RELRES };
+__global__ void k_pl_dot(const RDesc* desc, int b, const double2* __restrict__ x,
+                         const double2* __restrict__ y, double* part);
+__global__ void k_pl_axpy(const RDesc* desc, int b, const PlainScal* sc, double2* __restrict__ u,
+                          double2* __restrict__ r, const double2* __restrict__ p,
+                          const double2* __restrict__ q, double* part);
+__global__ void k_pl_xpby(const RDesc* desc, int b, const PlainScal* sc,
+                          const double2* __restrict__ z, double2* __restrict__ p);
+__global__ void k_pl_scalar(PlainScal* sc, const double* part, int nb, int what, double tol,
+                            int max_iter);
+// Fills the lookup tables (twiddles, Laplacian eigenvalues, filter roots)
+// for sizes up to 2^max_log2n.
+cudaError_t fill_tables(const Tables& tb, int max_log2n, cudaStream_t s);
+
 // Records "<where>: <CUDA error string>" for rve_last_error(); returns RVE_ECUDA.
 rve_status note_error(const char* where, cudaError_t e);
 
@@ -136,6 +160,7 @@ cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const do
                          int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
 constexpr int PROFILE_KERNELS = 5;   // refine, stencil, update, column, control
 void profile_enable(bool on);
+bool profile_on();
 int profile_read(double* ms, long long* launches);
 cudaError_t launch_backward(const Plan& p, void* ws, int scheme, const double* u,
                             const double* gradA, double* grad_coef, cudaStream_t s);

@@ -10,19 +10,6 @@
 
 namespace rve {
 
-// ------------------------------------------------------------ SplitMix64 --
-// Steele, Lea & Flood (OOPSLA 2014): output k (k >= 1) of the stream seeded
-// with s is mix(s + k * GAMMA).  Realization key = output (index+1) of the
-// run seed's stream; draw `ctr` under `tag` = output ((tag << 40) + ctr + 1)
-// of the key's stream.
-__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint32_t tag, uint64_t ctr) {
-    return sm64_mix(key + (((uint64_t)tag << 40) + ctr + 1) * 0x9E3779B97F4A7C15ull);
-}
 // uniform integer below n: high word of the 128-bit product (Lemire 2019,
 // no rejection)
 __device__ __forceinline__ int uniform_below(uint64_t v, uint32_t n) {

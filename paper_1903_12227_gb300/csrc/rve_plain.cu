@@ -14,14 +14,6 @@
 
 namespace rve {
 
-constexpr int PL_THREADS = 256;
-constexpr int PL_NODES = 1024;   // nodes per block (n^2 is a multiple of 1024)
-
-struct PlainScal {
-    double rho[2], alpha[2], beta[2], fnorm[2], relres[2];
-    int32_t active[2], iters[2];
-    int32_t done, status;
-};
 
 __device__ __forceinline__ double2 ld2(const double2* x, const RDesc& d, int i, int j) {
     return x[d.node_off + ((int64_t)(i & (d.n - 1)) << d.log2n) + (j & (d.n - 1))];
@@ -147,8 +139,7 @@ __global__ void k_pl_resid(const RDesc* desc, int b, CoefSrc cs, const double2* 
 }
 
 // Scalar steps of Algorithm 9.1 (one warp): reduce `nb` partials in a fixed
-// order and apply `what`.
-enum { SC_FNORM = 0, SC_RHO0, SC_ALPHA, SC_CONV, SC_BETA, SC_RELRES };
+// order and apply `what` (SC_* in rve_internal.h).
 
 __global__ void k_pl_scalar(PlainScal* sc, const double* part, int nb, int what, double tol,
                             int max_iter) {

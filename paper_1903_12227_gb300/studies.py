@@ -31,6 +31,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -223,16 +224,86 @@ def dos_study(Ls=(4, 8), N=20, lam=0.5, alpha=0.25, m0=8, eta=0.05, K=512, vecto
     return out
 
 
+# Algorithmic bytes per node of one launch of each 3D kernel kind: the
+# stencil reads x (a pair, 16 B) and the cell byte and writes y (16 B); a
+# line pass reads and writes a pair (the last one also reads r: 48 B, so
+# 36 B on average over the four passes); the z solve reads and writes a
+# pair; the CG vector steps of one iteration move 144 B (u, r, p, q read and
+# u, r written; z, p read and p written) over two launches; the scalar
+# launches (one warp) move nothing.
+CUBE_BYTES = {"stiffness": 33.0, "lines": 36.0, "zsolve": 32.0, "vector": 72.0, "scalar": 0.0}
+
+
+def _measured_hbm():
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=4, contrast=10.0, seed=0, tol=1e-10,
+                scheme=rve.CONSISTENT) -> list:
+    """3D extension: N realizations of round(0.7 L^3) unit cubes on
+    [0,L)^3 (n = L m0 nodes per axis) per L: time per realization (field,
+    three correctors, A_hom; CUDA events), iterations, per-kernel-kind
+    launch times with their algorithmic bandwidth, and the mean and spread
+    of the diagonal of the 3x3 A_hom."""
+    import torch
+    from . import rve3
+    peak = _measured_hbm()
+    rows = []
+    for L in Ls:
+        descs = [workloads.realization3(L, m0, contrast, seed, k) for k in range(N)]
+        n = L * m0
+        nodes = n ** 3
+        rve3.homogenize(descs[:1], scheme=scheme, tol=tol)   # warm-up (module load, tables)
+        torch.cuda.synchronize()
+        rve.profile_enable(True)
+        rve3.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        A, infos = rve3.homogenize(descs, scheme=scheme, tol=tol)
+        e1.record()
+        torch.cuda.synchronize()
+        rve.profile_enable(False)
+        prof = rve3.profile_read()
+        ms = e0.elapsed_time(e1)
+        kinds = {}
+        for kind, (t, cnt) in prof.items():
+            gbs = CUBE_BYTES[kind] * nodes * cnt / (t * 1e-3) / 1e9 if t > 0 and CUBE_BYTES[kind] else None
+            kinds[kind] = {"ms": round(t, 3), "launches": cnt,
+                           "us_per_launch": round(1e3 * t / cnt, 2) if cnt else None,
+                           "GBs": round(gbs, 1) if gbs else None,
+                           "frac_of_measured": round(gbs / peak, 3) if gbs and peak else None}
+        Ad = A.diagonal(dim1=1, dim2=2).cpu().numpy()
+        rows.append({"L": L, "m0": m0, "n": n, "N": N, "contrast": contrast, "tol": tol,
+                     "ms_per_realization": round(ms / N, 3),
+                     "realizations_per_s": round(1e3 * N / ms, 3),
+                     "iters_mean": float(np.mean([np.mean(i["iters"]) for i in infos])),
+                     "max_relres": float(max(max(i["relres"]) for i in infos)),
+                     "status": sorted({i["status"] for i in infos}),
+                     "A_diag_mean": float(Ad.mean()), "A_diag_std": float(Ad.std()),
+                     "offdiag_max": float(np.abs(A.cpu().numpy() - np.einsum(
+                         "bi,ij->bij", Ad, np.eye(3))).max()),
+                     "kernels": kinds, "hbm_peak_GBs": peak})
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["variance", "paper", "fem", "dos"])
+    ap.add_argument("study", choices=["variance", "paper", "fem", "dos", "cubes"])
     ap.add_argument("--Ls", type=int, nargs="+")
     ap.add_argument("--N", type=int)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--count", choices=["fixed", "poisson"], default="fixed")
     ap.add_argument("--json")
     a = ap.parse_args(argv)
-    if a.study == "dos":
+    if a.study == "cubes":
+        rows = cubes_study(Ls=tuple(a.Ls or (2, 4, 8, 16)), N=a.N or 4, seed=a.seed)
+    elif a.study == "dos":
         rows = dos_study(Ls=tuple(a.Ls or (4, 8)), N=a.N or 20, seed=a.seed)
     elif a.study == "fem":
         rows = fem_convergence(Ls=tuple(a.Ls or (2, 4, 8)), seed=a.seed)

@@ -26,7 +26,8 @@ Configurations (all synthetic; the paper uses no dataset):
   contrast 100, 256 realizations.
 
 Inclusion count = round(0.7 L^2) (density 0.7 per unit area), inclusion side
-= one unit length = m0 grid cells.
+= one unit length = m0 grid cells.  The 3D realizations (``realization3``)
+place round(0.7 L^3) unit cubes on [0,L)^3.
 """
 from __future__ import annotations
 
@@ -42,6 +43,18 @@ def realization(L: int, m0: int, contrast: float, seed: int, index: int,
     s = int(round(side_units * m0))
     return {"L": int(L), "m0": int(m0), "incl_cells": s,
             "n_incl": int(round(density * L * L)),
+            "a_matrix": float(a_matrix), "a_incl": float(contrast) * float(a_matrix),
+            "seed": int(seed), "index": int(index)}
+
+
+def realization3(L: int, m0: int, contrast: float, seed: int, index: int,
+                 density: float = DENSITY, side_units: float = 1.0,
+                 a_matrix: float = 1.0) -> dict:
+    """Descriptor of one 3D realization on [0,L)^3: round(density L^3) cubes
+    of side side_units (the 2D recipe with areas replaced by volumes)."""
+    s = int(round(side_units * m0))
+    return {"L": int(L), "m0": int(m0), "incl_cells": s,
+            "n_incl": int(round(density * L * L * L)),
             "a_matrix": float(a_matrix), "a_incl": float(contrast) * float(a_matrix),
             "seed": int(seed), "index": int(index)}
 

@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "rve.h")
 def _declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(rve_[a-z_0-9]+)\s*\(", src)
+    names = re.findall(r"\b(rve3?_[a-z_0-9]+)\s*\(", src)
     return sorted(set(names))
 
 
@@ -27,7 +27,8 @@ def librve():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("rve_gen_field", "rve_solve_correctors", "rve_a_hom", "rve_a_hom_backward",
-                     "rve_workspace_size", "rve_status_string"):
+                     "rve_workspace_size", "rve_status_string", "rve3_solve_correctors",
+                     "rve3_a_hom"):
         assert required in names
 
 
@@ -41,6 +42,9 @@ def test_struct_sizes_match_header(librve):
     assert ctypes.sizeof(rve.Realization) == 48
     assert ctypes.sizeof(rve.SolveInfo) == 40
     assert ctypes.sizeof(rve.SolveOpts) == 64
+    from paper_1903_12227_gb300 import rve3
+    assert ctypes.sizeof(rve3.Solve3Opts) == 32
+    assert ctypes.sizeof(rve3.Solve3Info) == 40
 
 
 def test_host_validation_without_gpu(librve):
@@ -60,6 +64,33 @@ def test_host_validation_without_gpu(librve):
     opts = rve.make_opts(precision=rve.MIXED, path=rve.PATH_PLAIN)
     assert librve.rve_workspace_size(ok.ptr, 1, ctypes.byref(opts)) == 0
     assert b"RVE_OK" in librve.rve_status_string(0)
+
+
+def test_host_validation_3d_without_gpu(librve):
+    from paper_1903_12227_gb300 import rve, rve3, workloads
+    L3 = rve3.lib()
+    ds = [workloads.realization3(4, 8, 10.0, 0, 0), workloads.realization3(2, 32, 10.0, 0, 1),
+          workloads.realization3(16, 16, 10.0, 0, 2)]
+    b = rve3.Batch3(ds)
+    assert L3.rve3_nodes(b.ptr, 3) == 32 ** 3 + 64 ** 3 + 256 ** 3
+    # seven pair vectors of 16 bytes per node dominate the workspace
+    assert L3.rve3_workspace_size(b.ptr, 3) >= 7 * 16 * (32 ** 3 + 64 ** 3 + 256 ** 3)
+    for bad in (workloads.realization3(32, 16, 10.0, 0, 0),             # n = 512 > 256
+                workloads.realization3(2, 8, 10.0, 0, 0),               # n = 16 < 32
+                workloads.realization3(3, 16, 10.0, 0, 0),              # n = 48
+                dict(workloads.realization3(4, 8, 10.0, 0, 0), a_incl=float("nan")),
+                dict(workloads.realization3(4, 8, 10.0, 0, 0), incl_cells=33)):
+        bb = rve3.Batch3([bad])
+        assert L3.rve3_nodes(bb.ptr, 1) == -1
+        assert L3.rve3_workspace_size(bb.ptr, 1) == 0
+        assert L3.rve3_gen_field(bb.ptr, 1, None, None) == rve.RVE_EINVAL
+    assert L3.rve3_workspace_size(b.ptr, 0) == 0
+    # missing pointers are rejected before any launch
+    ws = ctypes.c_void_p(None)
+    assert L3.rve3_solve_correctors(b.ptr, 3, None, None, None, None, None, ws, 0, None) == rve.RVE_EINVAL
+    bad_opts = rve3.Solve3Opts(7, 0, 1e-10, 0.0, 0, 0)
+    assert L3.rve3_solve_correctors(b.ptr, 3, None, None, ctypes.byref(bad_opts), None, None, ws, 0,
+                                    None) == rve.RVE_EINVAL
 
 
 def test_uneven_batch_sizes_add_up(librve):
