@@ -375,18 +375,24 @@ rve_status rve_a_hom_noalloc(const rve_realization* r, int32_t batch, const uint
  * missing pointers, unknown scheme), RVE_ENOMEM (ws too small), RVE_ECUDA. */
 typedef struct {
     int32_t scheme;      /* rve_scheme                                      */
+    int32_t precision;   /* RVE_FP64: PCG in FP64.  RVE_MIXED: FP32 PCG
+                            cycles restarted on the FP64 true residual
+                            (iterative refinement); the stopping test is
+                            the same FP64 one                               */
     int32_t max_iter;    /* cap on CG iterations per corrector (0 = 20000)  */
+    int32_t check_every; /* host convergence poll period (0 = 8)            */
     double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (0=1e-10)*/
     double delta;        /* preconditioner shift; 0 = drop the constant mode*/
-    int32_t check_every; /* host convergence poll period (0 = 8)            */
-    int32_t reserved;    /* must be 0                                       */
-} rve3_solve_opts;       /* 32 bytes */
+    double inner_tol;    /* mixed: relative reduction per FP32 cycle (0=1e-4)*/
+} rve3_solve_opts;       /* 40 bytes */
 
 typedef struct {
-    int32_t iters[3];     /* PCG iterations per corrector               */
-    int32_t status;       /* rve_status (first failure of the three)    */
-    double relres[3];     /* FP64 true relative residual per corrector  */
-} rve3_solve_info;        /* 40 bytes */
+    int32_t iters[3];     /* PCG iterations per corrector (FP32 ones when mixed) */
+    int32_t status;       /* rve_status (first failure of the three)            */
+    int32_t refinements;  /* FP64 true residuals evaluated (both pairs)         */
+    int32_t reserved;
+    double relres[3];     /* FP64 true relative residual per corrector          */
+} rve3_solve_info;        /* 48 bytes */
 
 /* Nodes of the batch (sum of n^3), or -1 if a descriptor is invalid. */
 int64_t rve3_nodes(const rve_realization* r, int32_t batch);
@@ -416,8 +422,10 @@ rve_status rve3_apply_stiffness(const rve_realization* r, int32_t batch, const u
 rve_status rve3_apply_precond(const rve_realization* r, int32_t batch, double delta,
                               const double* x, double* y, void* ws, size_t ws_bytes,
                               void* stream);
-/* The three correctors by preconditioned CG (FP64) from u = 0: u[nodes][3];
- * info[batch] (device) per realization. */
+/* The three correctors by preconditioned CG from u = 0 (FP64 or mixed
+ * precision, opts->precision): u[nodes][3]; info[batch] (device) per
+ * realization.  With general cell values the mixed path keeps an FP32 copy
+ * of them in ws. */
 rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const uint8_t* mask,
                                  const double* coef, const rve3_solve_opts* opts, double* u,
                                  rve3_solve_info* info, void* ws, size_t ws_bytes,

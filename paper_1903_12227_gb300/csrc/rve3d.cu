@@ -1,27 +1,46 @@
-// rve3d.cu -- the 3D extension of the RVE corrector method (the paper's
-// remark that the scheme extends to 3D): cubes on the torus [0,L)^3, the
-// trilinear Q1 element K1(x)M1(x)M1 + M1(x)K1(x)M1 + M1(x)M1(x)K1, three
-// corrector problems solved by PCG with B = c0 A_Delta + delta I (A_Delta
-// the periodic 7-point Laplacian), and the 3x3 homogenized matrix.  FP64.
+// rve3d.cu -- the 3D extension of the RVE corrector method (the setting of
+// Sec. 2 carries over to d = 3; the rank-3 Kronecker Laplacian of Sec. 3.2
+// and Eq. "As_Kron_d"; multilinear functions on cubes, Sec. 3.1): cubes on
+// the torus [0,L)^3, the trilinear Q1 element K1(x)M1(x)M1 + M1(x)K1(x)M1 +
+// M1(x)M1(x)K1, three corrector problems solved by PCG with B = c0 A_Delta +
+// delta I (A_Delta the periodic 7-point Laplacian), and the 3x3 homogenized
+// matrix.
 //
 // Grid: n = L m0 nodes per axis, node (i,j,k) at ((i n + j) n + k) within
 // the realization; cell (i,j,k) has lower corner node (i,j,k); local corner
-// a = 4 a1 + 2 a2 + a3.  The three correctors travel as two pairs (double2):
-// (u_1, u_2) and (u_3, 0), so that every kernel -- the stencil, the
-// Hartley transforms (pair-packed complex FFT) and the column solve -- is
-// shared with the pair layout of the 2D path.
+// a = 4 a1 + 2 a2 + a3.  The three correctors travel as two pairs: (u_1,
+// u_2) and (u_3, 0), so that every kernel -- the stencil, the Hartley
+// transforms (pair-packed complex FFT) and the column solve -- works on the
+// pair layout of the 2D path.
+//
+// Units.  The solver's unit of work is one pair of one realization (unit
+// 2b + pair).  Every launch covers all units of one grid size (blocks map to
+// units through a list of unit ids), each unit with its own scalars and
+// flags; a unit that has finished makes its blocks return at once.  The
+// host polls the flags every few steps.
 //
 // Preconditioner: the Hartley transforms along x (contiguous lines) and y
 // (lines of stride n) diagonalise two factors of A_Delta; along z (lines of
 // stride n^2) each (kx, ky) leaves the periodic tridiagonal system
 // c0 (T + lambda(kx) + lambda(ky)) + delta, solved by the causal/anticausal
-// filter pair of the 2D column pass (rve_colsolve.cuh) with the shift
-// c0 lambda(ky) folded into delta.  B^{-1} = n^-2 Hx Hy M^-1 Hy Hx.
+// filter pair of the 2D column pass (rve_colsolve.cuh).  B^{-1} = n^-2 Hx
+// Hy M^-1 Hy Hx.
+//
+// Precision.  GB300 runs FP64 at 1/64 of the FP32 rate, and the 3D stencil
+// and transforms carry enough arithmetic per node to be bound by it.  Both
+// paths run PCG cycles (Saad, Iterative Methods for Sparse Linear Systems,
+// Algorithm 9.1) on A e = r64 / s from e = 0, s = |r64|, between FP64 true
+// residuals r64 = f - A u (iterative refinement, u += s e), until |r64| <=
+// tol |f|.  FP64: the cycle's vectors are FP64 and it runs to the outer
+// tolerance, so one cycle is textbook PCG and a second one is rare.
+// Mixed: the cycle's vectors and arithmetic are FP32 and it stops at a
+// relative reduction max(tol |f| / (2 |r64|), inner_tol).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "rve_colsolve.cuh"
@@ -31,8 +50,7 @@
 namespace rve {
 
 // ------------------------------------------------------------ element --
-// Entry (a, b) of the element matrix (local corners 4 a1 + 2 a2 + a3); the
-// loops that call it unroll, so every entry folds to a constant times 1/h.
+// Entry (a, b) of the element matrix (local corners 4 a1 + 2 a2 + a3).
 template <int SCHEME>
 __host__ __device__ __forceinline__ double e3(int a, int b, double h) {
     auto m1 = [&](int x, int y) {
@@ -45,27 +63,52 @@ __host__ __device__ __forceinline__ double e3(int a, int b, double h) {
            m1(a1, b1) * m1(a2, b2) * k1(a3, b3);
 }
 
-__device__ __forceinline__ int64_t n3(const RDesc& d, int i, int j, int k) {
-    const int m = d.n - 1;
-    return d.node_off + ((((int64_t)(i & m) << d.log2n) + (j & m)) << d.log2n) + (k & m);
+// Descriptor of one unit (a corrector pair of a realization).
+struct U3 {
+    int32_t n, log2n, pair, tC;
+    int32_t n_incl, s, pad0, pad1;
+    int64_t off;        // first node of the unit's vectors
+    int64_t cell_off;   // first cell (= node) of the realization: mask, coef, ABI vectors
+    int64_t part_off;   // first partial (doubles) of the unit
+    double am, ai, h, c0, inv_vol;
+    float am32, ai32;
+    uint64_t key;       // SplitMix64 key of the realization
+};
+
+// Blocks of a launch over the units of one grid size: block -> (unit, block
+// within the unit).
+struct Grp {
+    const U3* __restrict__ desc;
+    const int32_t* __restrict__ ids;
+    int per;            // blocks per unit
+};
+__device__ __forceinline__ int unit_of(const Grp& g, int& lb) {
+    const int q = blockIdx.x / g.per;
+    lb = blockIdx.x - q * g.per;
+    return g.ids[q];
 }
 
-// Cell values: a byte mask with the two values, or an explicit array.
-struct Cells3 {
+// Local index of node (i, j, k) (periodic) within a realization.
+__device__ __forceinline__ int l3(const U3& d, int i, int j, int k) {
+    const int m = d.n - 1;
+    return ((((i & m) << d.log2n) + (j & m)) << d.log2n) + (k & m);
+}
+
+// Cell values in the arithmetic type T: a byte mask with the two values, or
+// an explicit array.
+template <typename T> struct Cells3T {
     const uint8_t* __restrict__ mask;
-    const double* __restrict__ coef;
-    __device__ __forceinline__ double at(const RDesc& d, int i, int j, int k) const {
-        const int64_t c = n3(d, i, j, k);
-        if (coef) return coef[c];
-        return mask[c] ? d.a_incl : d.a_matrix;
-    }
+    const T* __restrict__ coef;
 };
+template <typename T> __device__ __forceinline__ T two_values(const U3& d, bool incl);
+template <> __device__ __forceinline__ double two_values<double>(const U3& d, bool incl) { return incl ? d.ai : d.am; }
+template <> __device__ __forceinline__ float two_values<float>(const U3& d, bool incl) { return incl ? d.ai32 : d.am32; }
 
 constexpr int T3 = 256;   // threads of the node kernels
 
 // --------------------------------------------------------------- field --
 // One thread per (cube, row d1, d2): sets the s cells along the third axis.
-__global__ void k3_gen_field(const RDesc d, uint8_t* __restrict__ mask) {
+__global__ void k3_gen_field(const U3 d, uint8_t* __restrict__ mask) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t rows = (int64_t)d.n_incl * d.s * d.s;
     if (gid >= rows) return;
@@ -76,54 +119,136 @@ __global__ void k3_gen_field(const RDesc d, uint8_t* __restrict__ mask) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         c[a] = (int)__umul64hi(sm64_draw(d.key, 1u, 3ull * kk + a), (uint64_t)d.n);
-    for (int d3 = 0; d3 < d.s; ++d3) mask[n3(d, c[0] + d1, c[1] + d2, c[2] + d3)] = 1;
+    for (int d3 = 0; d3 < d.s; ++d3) mask[d.cell_off + l3(d, c[0] + d1, c[1] + d2, c[2] + d3)] = 1;
 }
 
-// ------------------------------------------------- stiffness and loads --
-// y = A x for one pair: for each of the 8 cells around the node, a_c times
-// the element row of the node's local corner against the cell's corners.
-// With `part` set, also the block's partials of x.y per component (the
-// p.q of CG), two doubles per block.
-template <int SCHEME>
-__global__ void __launch_bounds__(T3) k3_stiffness(const RDesc d, Cells3 cs,
-                                                   const double2* __restrict__ x,
-                                                   double2* __restrict__ y, double* part) {
-    const int64_t node = (int64_t)blockIdx.x * T3 + threadIdx.x;
-    const int n = d.n;
-    const int i = (int)(node >> (2 * d.log2n)), j = (int)((node >> d.log2n) & (n - 1)),
-              k = (int)(node & (n - 1));
-    double2 w[27];
+// ----------------------------------------------------------- stiffness --
+// y = A x for one pair.  An entry E[a][b] of the element matrix depends only
+// on the number of axes along which the corners a and b differ (K1 and M1
+// are symmetric with equal diagonals): e_0 = 3 m0^2 / h, e_1 = (2 m0 m1 -
+// m0^2) / h, e_2 = (m1^2 - 2 m0 m1) / h, e_3 = -3 m1^2 / h with M1 = [m0 m1;
+// m1 m0].  Consistent (m0 = h/3, m1 = h/6): e_0 = h/3, e_1 = 0, e_2 = e_3 =
+// -h/12; lumped (m0 = h/2, m1 = 0): e_0 = 3h/4, e_1 = -h/4, e_2 = e_3 = 0.
+// So the assembled row of node i couples neighbour i+o (o in {-1,0,1}^3)
+// with e_{|o|} times the sum of a_c over the cells holding both nodes: all 8
+// for o = 0, 4 for a face neighbour, 2 for an edge neighbour (a pair sum
+// along the axis where o is 0), 1 for a corner neighbour.  About 60
+// arithmetic operations per node and pair instead of 144 for the 8 element
+// rows.  Neighbour addresses come from the 9 wrapped row starts.
+//   MODE_APPLY: y = A x, partials of x.y per component (the p.q of CG);
+//   MODE_RESID: y = f - A x (the true residual), partials of |y|^2.
+// Blocks of units whose flag (`done`, or `outer_done` for MODE_RESID) is
+// set return at once.
+enum { MODE_APPLY = 0, MODE_RESID = 1 };
+struct MixScal;
+__device__ __forceinline__ bool unit_skip(const MixScal* sc, int u, bool outer);
+
+template <int SCHEME, int MODE, typename V>
+__global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename ScalarOf<V>::T> cs,
+                                                   const V* __restrict__ x, V* __restrict__ y,
+                                                   const V* __restrict__ f, double* part,
+                                                   const MixScal* sc) {
+    typedef typename ScalarOf<V>::T T;
+    __shared__ double red[32];
+    int lb;
+    const int u = unit_of(g, lb);
+    if (sc && unit_skip(sc, u, MODE == MODE_RESID)) return;
+    const U3& d = g.desc[u];
+    const int local = lb * T3 + threadIdx.x;
+    const int n = d.n, m = n - 1, lg = d.log2n;
+    const int i = local >> (2 * lg), j = (local >> lg) & m, k = local & m;
+    int row[3][3];   // start of node row (i + a - 1, j + b - 1)
 #pragma unroll
-    for (int o = 0; o < 27; ++o) w[o] = x[n3(d, i + o / 9 - 1, j + (o / 3) % 3 - 1, k + o % 3 - 1)];
-    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {   // cell offset (-c1, -c2, -c3), c = 4 c1 + 2 c2 + c3
-        const int c1 = c >> 2, c2 = (c >> 1) & 1, c3 = c & 1;
-        const double a = cs.at(d, i - c1, j - c2, k - c3);
-        const int l = c;   // the node is corner (c1, c2, c3) of that cell
-        double2 s = make_double2(0.0, 0.0);
+        for (int b = 0; b < 3; ++b) row[a][b] = ((((i + a - 1) & m) << lg) + ((j + b - 1) & m)) << lg;
+    const int kk[3] = {(k - 1) & m, k, (k + 1) & m};
+    const V* xu = x + d.off;
+    auto X = [&](int o1, int o2, int o3) { return xu[row[o1 + 1][o2 + 1] + kk[o3 + 1]]; };
+    T a[8];   // a[c]: the cell at offset (-c1, -c2, -c3), c = 4 c1 + 2 c2 + c3
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int o = (((b >> 2) - c1 + 1) * 3 + (((b >> 1) & 1) - c2 + 1)) * 3 + ((b & 1) - c3 + 1);
-            const double e = e3<SCHEME>(l, b, d.h);
-            s.x = fma(e, w[o].x, s.x);
-            s.y = fma(e, w[o].y, s.y);
-        }
-        acc.x = fma(a, s.x, acc.x);
-        acc.y = fma(a, s.y, acc.y);
+    for (int c = 0; c < 8; ++c) {
+        const int idx = row[1 - (c >> 2)][1 - ((c >> 1) & 1)] + kk[1 - (c & 1)];
+        a[c] = cs.coef ? cs.coef[d.cell_off + idx] : two_values<T>(d, cs.mask[d.cell_off + idx] != 0);
     }
-    y[d.node_off + node] = acc;
+    // pair sums along each axis, indexed by the other two corner bits
+    T px[4], py[4], pz[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        px[q] = a[q] + a[4 + q];                                             // q = 2 c2 + c3
+        py[q] = a[4 * (q >> 1) + (q & 1)] + a[4 * (q >> 1) + 2 + (q & 1)];   // q = 2 c1 + c3
+        pz[q] = a[2 * q] + a[2 * q + 1];                                     // q = 2 c1 + c2
+    }
+    const T A0 = (px[0] + px[1]) + (px[2] + px[3]);
+    const T h = (T)d.h;
+    // the cell bit that a neighbour offset fixes on its axis: +1 -> 0, -1 -> 1
+    auto cb = [](int o) { return o > 0 ? 0 : 1; };
+    const V xc = X(0, 0, 0);
+    V acc;
+    if (SCHEME == RVE_Q1_CONSISTENT) {
+        T sx = 0, sy = 0;
+#pragma unroll
+        for (int e = 0; e < 12; ++e) {   // edge neighbours: o zero on one axis
+            const int zax = e >> 2, s1 = (e & 2) ? 1 : -1, s2 = (e & 1) ? 1 : -1;
+            V v;
+            T w;
+            if (zax == 0) { v = X(0, s1, s2); w = px[2 * cb(s1) + cb(s2)]; }
+            else if (zax == 1) { v = X(s1, 0, s2); w = py[2 * cb(s1) + cb(s2)]; }
+            else { v = X(s1, s2, 0); w = pz[2 * cb(s1) + cb(s2)]; }
+            sx = fma(w, v.x, sx);
+            sy = fma(w, v.y, sy);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {    // corner neighbours: one cell each
+            const int o1 = (c & 4) ? 1 : -1, o2 = (c & 2) ? 1 : -1, o3 = (c & 1) ? 1 : -1;
+            const T w = a[4 * cb(o1) + 2 * cb(o2) + cb(o3)];
+            const V v = X(o1, o2, o3);
+            sx = fma(w, v.x, sx);
+            sy = fma(w, v.y, sy);
+        }
+        const T e0 = h * (T)(1.0 / 3.0), e23 = -h * (T)(1.0 / 12.0);
+        acc.x = fma(e23, sx, e0 * A0 * xc.x);
+        acc.y = fma(e23, sy, e0 * A0 * xc.y);
+    } else {
+        T sx = 0, sy = 0;
+#pragma unroll
+        for (int fc = 0; fc < 6; ++fc) {  // face neighbours: 4 cells with the bit fixed
+            const int ax = fc >> 1, sg = (fc & 1) ? 1 : -1, v0 = cb(sg);
+            V v;
+            T w;
+            if (ax == 0) { v = X(sg, 0, 0); w = pz[2 * v0] + pz[2 * v0 + 1]; }
+            else if (ax == 1) { v = X(0, sg, 0); w = pz[v0] + pz[2 + v0]; }
+            else { v = X(0, 0, sg); w = py[v0] + py[2 + v0]; }
+            sx = fma(w, v.x, sx);
+            sy = fma(w, v.y, sy);
+        }
+        const T e0 = h * (T)0.75, e1 = -h * (T)0.25;
+        acc.x = fma(e1, sx, e0 * A0 * xc.x);
+        acc.y = fma(e1, sy, e0 * A0 * xc.y);
+    }
+    DotAcc<T> dx, dy;
+    if (MODE == MODE_RESID) {
+        const V ff = f[d.off + local];
+        acc.x = ff.x - acc.x;
+        acc.y = ff.y - acc.y;
+        dx.add(acc.x, acc.x);
+        dy.add(acc.y, acc.y);
+    } else {
+        dx.add(xc.x, acc.x);
+        dy.add(xc.y, acc.y);
+    }
+    y[d.off + local] = acc;
     if (part) {   // block-uniform
-        __shared__ double red[8];
-        const double sx = block_sum(w[13].x * acc.x, red);
-        const double sy = block_sum(w[13].y * acc.y, red);
+        double tx = 0.0, ty = 0.0;
+        block_sum2(dx, dy, red, tx, ty);
         if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = sx;
-            part[2 * blockIdx.x + 1] = sy;
+            part[d.part_off + 2 * lb] = tx;
+            part[d.part_off + 2 * lb + 1] = ty;
         }
     }
 }
 
+// -------------------------------------------------------------- loads --
 // Corrector loads f_i = -sum_c a_c P_c^T E xi_i (xi_i = h x corner bit i).
 // Every row of M1 sums to h/2 (both schemes) and every row of K1 to 0, so
 // of the three Kronecker terms only the one with K1 along axis i survives,
@@ -131,17 +256,23 @@ __global__ void __launch_bounds__(T3) k3_stiffness(const RDesc d, Cells3 cs,
 // otherwise).  Summed over the 8 cells around the node (the node is corner
 // c of the cell at offset -c):
 //     f_i = (h^2/4) (sum_{c_i = 0} a_c - sum_{c_i = 1} a_c),
-// which is exactly zero where the 8 cells agree.  Pair 0 gets (f_1, f_2),
-// pair 1 gets (f_3, 0).
-__global__ void __launch_bounds__(T3) k3_rhs(const RDesc d, Cells3 cs, int pair,
-                                             double2* __restrict__ f) {
-    const int64_t node = (int64_t)blockIdx.x * T3 + threadIdx.x;
+// which is exactly zero where the 8 cells agree.  Unit pair 0 gets (f_1,
+// f_2), pair 1 gets (f_3, 0).  Also the partials of |f|^2.
+__global__ void __launch_bounds__(T3) k3_rhs(Grp g, Cells3T<double> cs, double2* __restrict__ f,
+                                             double* part) {
+    __shared__ double red[32];
+    int lb;
+    const int u = unit_of(g, lb);
+    const U3& d = g.desc[u];
+    const int local = lb * T3 + threadIdx.x;
     const int n = d.n;
-    const int i = (int)(node >> (2 * d.log2n)), j = (int)((node >> d.log2n) & (n - 1)),
-              k = (int)(node & (n - 1));
+    const int i = local >> (2 * d.log2n), j = (local >> d.log2n) & (n - 1), k = local & (n - 1);
     double a[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = cs.at(d, i - (c >> 2), j - ((c >> 1) & 1), k - (c & 1));
+    for (int c = 0; c < 8; ++c) {
+        const int idx = l3(d, i - (c >> 2), j - ((c >> 1) & 1), k - (c & 1));
+        a[c] = cs.coef ? cs.coef[d.cell_off + idx] : two_values<double>(d, cs.mask[d.cell_off + idx] != 0);
+    }
     const double q = 0.25 * d.h * d.h;
     double v[3];
 #pragma unroll
@@ -154,22 +285,18 @@ __global__ void __launch_bounds__(T3) k3_rhs(const RDesc d, Cells3 cs, int pair,
         }
         v[ax] = q * (lo - hi);
     }
-    f[d.node_off + node] = pair == 0 ? make_double2(v[0], v[1]) : make_double2(v[2], 0.0);
-}
-
-// r = f - q (true residual) and its partial |r|^2 per component.
-__global__ void __launch_bounds__(T3) k3_resid(const RDesc d, const double2* __restrict__ f,
-                                               const double2* __restrict__ q, double2* __restrict__ r,
-                                               double* part) {
-    __shared__ double red[8];
-    const int64_t node = d.node_off + (int64_t)blockIdx.x * T3 + threadIdx.x;
-    const double2 v = make_double2(f[node].x - q[node].x, f[node].y - q[node].y);
-    r[node] = v;
-    const double sx = block_sum(v.x * v.x, red);
-    const double sy = block_sum(v.y * v.y, red);
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = sx;
-        part[2 * blockIdx.x + 1] = sy;
+    const double2 out = d.pair == 0 ? make_double2(v[0], v[1]) : make_double2(v[2], 0.0);
+    f[d.off + local] = out;
+    if (part) {
+        DotAcc<double> dx, dy;
+        dx.add(out.x, out.x);
+        dy.add(out.y, out.y);
+        double tx = 0.0, ty = 0.0;
+        block_sum2(dx, dy, red, tx, ty);
+        if (threadIdx.x == 0) {
+            part[d.part_off + 2 * lb] = tx;
+            part[d.part_off + 2 * lb + 1] = ty;
+        }
     }
 }
 
@@ -179,93 +306,118 @@ __global__ void __launch_bounds__(T3) k3_resid(const RDesc d, const double2* __r
 // AXIS 2: x lines (contiguous), threads of a line side by side; AXIS 1: y
 // lines (stride n), the lines of a block side by side so that each load
 // instruction reads consecutive nodes.  With `rd` set, also the block's
-// partials of rd.dst per component (the r.z of CG), two doubles per block.
-template <int LOG2N, int AXIS>
-__global__ void __launch_bounds__(256) k3_lines(const RDesc d, Tables tb,
-                                                const double2* src, double2* dst,
-                                                double scale, const double2* __restrict__ rd,
-                                                double* part) {
+// partials of rd.dst per component (the r.z of CG).
+template <int LOG2N, int AXIS, typename V>
+__global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, V* dst,
+                                                typename ScalarOf<V>::T scale,
+                                                const V* __restrict__ rd, double* part,
+                                                const MixScal* sc) {
+    typedef typename ScalarOf<V>::T T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
-    constexpr int n = 1 << LOG2N, T = n / 8;
-    const int G = blockDim.x / T;
+    __shared__ double red[32];
+    int lb;
+    const int u = unit_of(g, lb);
+    if (sc && unit_skip(sc, u, false)) return;
+    const U3& d = g.desc[u];
+    constexpr int n = 1 << LOG2N, TL = n / 8;
+    const int G = blockDim.x / TL;
     int q, t;
-    if (AXIS == 2) { q = threadIdx.x / T; t = threadIdx.x - q * T; }
+    if (AXIS == 2) { q = threadIdx.x / TL; t = threadIdx.x - q * TL; }
     else { t = threadIdx.x / G; q = threadIdx.x - t * G; }
-    const int64_t line = (int64_t)blockIdx.x * G + q;   // < n^2
+    const int line = lb * G + q;   // < n^2
     int64_t base, stride;
-    if (AXIS == 2) { base = d.node_off + line * n; stride = 1; }
-    else { base = d.node_off + (line / n) * (int64_t)n * n + (line % n); stride = n; }
-    double2* buf = reinterpret_cast<double2*>(smem_raw) + q * seq_stride(n);
-    double2 w[8];
+    if (AXIS == 2) { base = d.off + (int64_t)line * n; stride = 1; }
+    else { base = d.off + (int64_t)(line / n) * n * n + (line % n); stride = n; }
+    V* buf = reinterpret_cast<V*>(smem_raw) + q * seq_stride(n);
+    V w[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) w[m] = src[base + (t + m * T) * stride];
-    fft_reg<FFT_TO_BOTH, LOG2N>(w, buf, LOG2N, t, twiddles<double2>(tb, n), true);
-    double ax = 0.0, ay = 0.0;
+    for (int mm = 0; mm < 8; ++mm) w[mm] = src[base + (t + mm * TL) * stride];
+    fft_reg<FFT_TO_BOTH, LOG2N>(w, buf, LOG2N, t, twiddles<V>(tb, n), true);
+    DotAcc<T> ax, ay;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int kx = t + m * T;
-        const double2 hv = hartley_pair(w[m], buf[pidx((n - kx) & (n - 1))]);
-        const double2 o = make_double2(scale * hv.x, scale * hv.y);
+    for (int mm = 0; mm < 8; ++mm) {
+        const int kx = t + mm * TL;
+        const V hv = hartley_pair(w[mm], buf[pidx((n - kx) & (n - 1))]);
+        const V o = mk<V>(scale * hv.x, scale * hv.y);
         dst[base + (int64_t)kx * stride] = o;
         if (rd) {
-            const double2 r = rd[base + (int64_t)kx * stride];
-            ax = fma(r.x, o.x, ax);
-            ay = fma(r.y, o.y, ay);
+            const V r = rd[base + (int64_t)kx * stride];
+            ax.add(r.x, o.x);
+            ay.add(r.y, o.y);
         }
     }
     if (rd) {   // block-uniform
-        const double sx = block_sum(ax, red);
-        const double sy = block_sum(ay, red);
+        double sx = 0.0, sy = 0.0;
+        block_sum2(ax, ay, red, sx, sy);
         if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = sx;
-            part[2 * blockIdx.x + 1] = sy;
+            part[d.part_off + 2 * lb] = sx;
+            part[d.part_off + 2 * lb + 1] = sy;
         }
     }
 }
 
 // Tridiagonal solves along z for the lines (kx = c0 .. c0+C-1, ky =
 // blockIdx.y) after the x and y transforms; writes M^{-1} t / n in place.
-template <int LOG2N>
-__global__ void __launch_bounds__(512) k3_zsolve(const RDesc d, Tables tb, double delta,
-                                                 double2* __restrict__ v) {
+// The filter root of (kx, ky) solves rho + 1/rho = 2 + lambda(kx) +
+// lambda(ky) + delta / c0, evaluated in the vector's precision.
+template <typename T> __device__ __forceinline__ T filter_root_t(T mu) {
+    return (T)1 / ((T)1 + (T)0.5 * mu + sqrt(mu * ((T)1 + (T)0.25 * mu)));
+}
+template <int LOG2N, typename V>
+__global__ void __launch_bounds__(512) k3_zsolve(Grp g, Tables tb, double delta, V* __restrict__ v,
+                                                 const MixScal* sc) {
+    typedef typename ScalarOf<V>::T T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];
-    __shared__ double csc[1];
+    __shared__ T csc[1];
+    int lb;
+    const int u = unit_of(g, lb);
+    if (sc && unit_skip(sc, u, false)) return;
+    const U3& d = g.desc[u];
     constexpr int n = 1 << LOG2N;
-    const int ky = blockIdx.y, c0 = blockIdx.x * d.tC;
+    RDesc cd;          // the two fields the column solve reads
+    cd.tC = d.tC;
+    cd.c0 = d.c0;
+    const int ky = blockIdx.y, c0 = lb * d.tC;
     const double delta_eff = delta + d.c0 * tb.lap[n + ky];   // the y shift folded in
-    col_solve_body<double2, LOG2N>(
-        [&](int r, int kx) { return v[d.node_off + (((int64_t)r * n + ky) * n) + kx]; },
-        [&](int r, int kx, double2 val) { v[d.node_off + (((int64_t)r * n + ky) * n) + kx] = val; },
-        d, c0, reinterpret_cast<double2*>(smem_raw), tb, delta_eff, red, nullptr, csc);
+    const T* lapT = lap_table<T>(tb, n);
+    const T muy = lapT[ky] + (T)(delta / d.c0);
+    const bool plain = delta_eff == 0.0;   // ky = 0 and delta = 0: the 1D roots
+    V* vu = v + d.off;
+    col_solve_core<V, LOG2N>(
+        [&](int r, int kx) { return vu[((r * n + ky) * n) + kx]; },
+        [&](int r, int kx, V val) { vu[((r * n + ky) * n) + kx] = val; },
+        [&](int kx) -> T { return plain ? rho_table<T>(tb, n)[kx] : filter_root_t<T>(lapT[kx] + muy); },
+        cd, c0, reinterpret_cast<V*>(smem_raw), tb, delta_eff, red, nullptr, csc);
 }
 
 // ------------------------------------------------------------- A_hom --
 // Per tile of T3 cells, partial sums of sum a_c, the energy terms
 // a_c v_i^T E v_j (ij = 11 12 13 22 23 33) and the flux terms a_c int_c
 // d_j (x_i + phi_i) (ij = 11 12 13 21 22 23 31 32 33), v_i = xi_i + P_c u_i.
+// Launched over realizations (the pair-0 unit descriptors); u is the ABI
+// layout [nodes][3].
 constexpr int A3_NP = 16;
 template <int SCHEME>
-__global__ void __launch_bounds__(T3) k3_a_hom_part(const RDesc d, Cells3 cs,
-                                                    const double2* __restrict__ u12,
-                                                    const double2* __restrict__ u3,
+__global__ void __launch_bounds__(T3) k3_a_hom_part(Grp g, Cells3T<double> cs,
+                                                    const double* __restrict__ u3,
                                                     double* __restrict__ part) {
     __shared__ double red[8];
-    const int64_t cell = (int64_t)blockIdx.x * T3 + threadIdx.x;
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3& d = g.desc[un];
+    const int cell = lb * T3 + threadIdx.x;
     const int n = d.n;
-    const int i = (int)(cell >> (2 * d.log2n)), j = (int)((cell >> d.log2n) & (n - 1)),
-              k = (int)(cell & (n - 1));
+    const int i = cell >> (2 * d.log2n), j = (cell >> d.log2n) & (n - 1), k = cell & (n - 1);
     const double h = d.h;
-    const double a = cs.at(d, i, j, k);
+    const double a = cs.coef ? cs.coef[d.cell_off + cell] : two_values<double>(d, cs.mask[d.cell_off + cell] != 0);
     double v[3][8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        const int64_t g = n3(d, i + (b >> 2), j + ((b >> 1) & 1), k + (b & 1));
-        const double2 p = u12[g], s = u3[g];
-        v[0][b] = p.x + h * (double)(b >> 2);
-        v[1][b] = p.y + h * (double)((b >> 1) & 1);
-        v[2][b] = s.x + h * (double)(b & 1);
+        const int64_t gi = 3 * (d.cell_off + l3(d, i + (b >> 2), j + ((b >> 1) & 1), k + (b & 1)));
+        v[0][b] = u3[gi] + h * (double)(b >> 2);
+        v[1][b] = u3[gi + 1] + h * (double)((b >> 1) & 1);
+        v[2][b] = u3[gi + 2] + h * (double)(b & 1);
     }
     double Ev[3][8];
 #pragma unroll
@@ -301,58 +453,330 @@ __global__ void __launch_bounds__(T3) k3_a_hom_part(const RDesc d, Cells3 cs,
 #pragma unroll
     for (int p = 0; p < A3_NP; ++p) {
         const double s = block_sum(val[p], red);
-        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * A3_NP + p] = s;
+        if (threadIdx.x == 0) part[d.part_off + (int64_t)lb * A3_NP + p] = s;
     }
 }
 
-__global__ void k3_a_hom_final(const RDesc d, const double* __restrict__ part, int tiles,
-                               double* __restrict__ A, double* __restrict__ Af) {
+// One block per realization: fixed-order sums of its partials, then A.
+__global__ void k3_a_hom_final(Grp g, const double* __restrict__ part, double* __restrict__ A,
+                               double* __restrict__ Af) {
+    __shared__ double red[32];
+    const int un = g.ids[blockIdx.x];
+    const U3& d = g.desc[un];
+    const int b = un >> 1;
+    const int tiles = (int)(((int64_t)d.n * d.n * d.n) / T3);
     double s[A3_NP];
 #pragma unroll
-    for (int p = 0; p < A3_NP; ++p) s[p] = warp_sum_array(part + p, tiles, A3_NP);
+    for (int p = 0; p < A3_NP; ++p) {
+        double t = 0.0;
+        for (int k = threadIdx.x; k < tiles; k += blockDim.x) t += part[d.part_off + (int64_t)k * A3_NP + p];
+        s[p] = block_sum(t, red);
+    }
     if (threadIdx.x != 0) return;
     const double iv = d.inv_vol;
     const int sym[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
     for (int x = 0; x < 3; ++x)
         for (int y = 0; y < 3; ++y) {
-            A[3 * x + y] = s[sym[x][y]] * iv;
-            if (Af) Af[3 * x + y] = s[7 + 3 * x + y] * iv;
+            A[9 * (int64_t)b + 3 * x + y] = s[sym[x][y]] * iv;
+            if (Af) Af[9 * (int64_t)b + 3 * x + y] = s[7 + 3 * x + y] * iv;
         }
 }
 
-// ------------------------------------------- layout: triples <-> pairs --
-__global__ void k3_split(const RDesc d, const double* __restrict__ x3, double2* __restrict__ p12,
-                         double2* __restrict__ p3) {
-    const int64_t node = d.node_off + (int64_t)blockIdx.x * T3 + threadIdx.x;
-    p12[node] = make_double2(x3[3 * node], x3[3 * node + 1]);
-    p3[node] = make_double2(x3[3 * node + 2], 0.0);
+// ------------------------------------- layout: ABI triples <-> unit pairs --
+// Launched over units: unit pair 0 <-> components (1, 2), pair 1 <-> (3, -).
+__global__ void __launch_bounds__(T3) k3_split(Grp g, const double* __restrict__ x3,
+                                               double2* __restrict__ v) {
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3& d = g.desc[un];
+    const int local = lb * T3 + threadIdx.x;
+    const int64_t c = 3 * (d.cell_off + local);
+    v[d.off + local] = d.pair == 0 ? make_double2(x3[c], x3[c + 1]) : make_double2(x3[c + 2], 0.0);
 }
 
-__global__ void k3_join(const RDesc d, const double2* __restrict__ p12,
-                        const double2* __restrict__ p3, double* __restrict__ x3) {
-    const int64_t node = d.node_off + (int64_t)blockIdx.x * T3 + threadIdx.x;
-    x3[3 * node] = p12[node].x;
-    x3[3 * node + 1] = p12[node].y;
-    x3[3 * node + 2] = p3[node].x;
+__global__ void __launch_bounds__(T3) k3_join(Grp g, const double2* __restrict__ v,
+                                              double* __restrict__ x3) {
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3& d = g.desc[un];
+    const int local = lb * T3 + threadIdx.x;
+    const int64_t c = 3 * (d.cell_off + local);
+    const double2 w = v[d.off + local];
+    if (d.pair == 0) { x3[c] = w.x; x3[c + 1] = w.y; }
+    else x3[c + 2] = w.x;
 }
 
-__global__ void k3_report(const PlainScal* s12, const PlainScal* s3, rve3_solve_info* info) {
+// Cell values as FP32 for the mixed path's stencil.
+__global__ void k3_coef32(const double* __restrict__ coef, float* __restrict__ c32, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) c32[i] = (float)coef[i];
+}
+
+// ---------------------------------------------------------- CG cycles --
+// Solver state of one unit (device; written by k3_scalar only).
+struct MixScal {
+    double fnorm[2];    // |f_c|
+    double rn_prev[2];  // |r64_c| of the previous refinement
+    double s[2];        // scale of the cycle's system (= |r64_c|)
+    double target[2];   // relative residual target of the cycle
+    double rho[2], alpha[2], beta[2];
+    double relres[2];   // last FP64 true relative residual
+    float alpha_f[2], beta_f[2], inv_s_f[2];
+    int32_t active[2];  // the cycle still iterates on the component
+    int32_t cdone[2];   // met the outer tolerance (or f_c = 0), or failed
+    int32_t iters[2];
+    int32_t stall[2];   // consecutive refinements without a 10x reduction
+    int32_t refinements, status;
+    int32_t done;       // no component active in the cycle
+    int32_t outer_done; // every component finished
+};
+__device__ __forceinline__ bool unit_skip(const MixScal* sc, int u, bool outer) {
+    return outer ? sc[u].outer_done != 0 : sc[u].done != 0;
+}
+enum { M_FNORM = 0, M_REFINE, M_RHO0, M_ALPHA, M_CONV, M_BETA };
+constexpr int MAX_REFINE = 100;
+constexpr int MAX_STALL = 4;
+
+// The scalar steps: one block per unit reduces the unit's `nb` partial
+// pairs in a fixed order (per-thread strided sums, then the block tree) and
+// thread 0 applies `what`.  `tfac`: the cycle target is max(tfac tol |f| /
+// |r64|, inner_tol).
+struct ScalArgs {
+    double tol, inner_tol, tfac;
+    int max_iter;
+};
+__global__ void __launch_bounds__(256) k3_scalar(const int32_t* __restrict__ ids,
+                                                 const U3* __restrict__ desc, MixScal* scs,
+                                                 const double* __restrict__ part, int what,
+                                                 ScalArgs a) {
+    __shared__ double red[32];
+    const int u = ids[blockIdx.x];
+    MixScal* sc = scs + u;
+    const U3& d = desc[u];
+    if (what != M_FNORM && what != M_REFINE && sc->done) return;
+    if (what == M_REFINE && sc->outer_done) return;
+    const int64_t nodes = (int64_t)d.n * d.n * d.n;
+    int nb;
+    switch (what) {
+        case M_RHO0:
+        case M_BETA: nb = (int)(nodes / 2048); break;   // last line pass (n^2 / G blocks)
+        case M_CONV: nb = (int)(nodes / (4 * T3)); break;
+        default: nb = (int)(nodes / T3); break;
+    }
+    const double* pp = part + d.part_off;
+    double tx = 0.0, ty = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        tx += pp[2 * k];
+        ty += pp[2 * k + 1];
+    }
+    const double sx = block_sum(tx, red);
+    const double sy = block_sum(ty, red);
+    if (threadIdx.x != 0) return;
+    const double v[2] = {sx, sy};
+    switch (what) {
+        case M_FNORM:
+            for (int k = 0; k < 2; ++k) {
+                sc->fnorm[k] = sqrt(v[k]);
+                sc->cdone[k] = !(v[k] > 0.0);
+                sc->active[k] = 0;
+                sc->iters[k] = 0;
+                sc->stall[k] = 0;
+                sc->relres[k] = 0.0;
+                sc->rn_prev[k] = sc->fnorm[k];
+            }
+            sc->refinements = 0;
+            sc->status = RVE_OK;
+            sc->done = 1;
+            sc->outer_done = sc->cdone[0] && sc->cdone[1];
+            break;
+        case M_REFINE:
+            sc->refinements += 1;
+            for (int k = 0; k < 2; ++k) {
+                sc->active[k] = 0;
+                sc->alpha[k] = sc->beta[k] = 0.0;
+                sc->alpha_f[k] = sc->beta_f[k] = 0.f;
+                sc->inv_s_f[k] = 0.f;
+                if (sc->cdone[k]) continue;
+                const double rn = sqrt(v[k]);
+                sc->relres[k] = rn / sc->fnorm[k];
+                if (!isfinite(rn)) { sc->status = RVE_ENAN; sc->cdone[k] = 1; continue; }
+                if (rn <= a.tol * sc->fnorm[k]) { sc->cdone[k] = 1; continue; }
+                sc->stall[k] = (rn > 0.1 * sc->rn_prev[k]) ? sc->stall[k] + 1 : 0;
+                if (sc->iters[k] >= a.max_iter || sc->refinements > MAX_REFINE ||
+                    sc->stall[k] >= MAX_STALL) {
+                    sc->status = RVE_ENOCONV;
+                    sc->cdone[k] = 1;
+                    continue;
+                }
+                sc->rn_prev[k] = rn;
+                sc->s[k] = rn;
+                sc->inv_s_f[k] = (float)(1.0 / rn);
+                sc->target[k] = fmax(a.tfac * a.tol * sc->fnorm[k] / rn, a.inner_tol);
+                sc->active[k] = 1;
+            }
+            sc->outer_done = sc->cdone[0] && sc->cdone[1];
+            sc->done = !(sc->active[0] || sc->active[1]);
+            break;
+        case M_RHO0:
+            for (int k = 0; k < 2; ++k) sc->rho[k] = v[k];
+            break;
+        case M_ALPHA:
+            for (int k = 0; k < 2; ++k) {
+                sc->alpha[k] = sc->active[k] ? sc->rho[k] / v[k] : 0.0;
+                sc->alpha_f[k] = (float)sc->alpha[k];
+                if (sc->active[k]) sc->iters[k] += 1;
+            }
+            break;
+        case M_CONV:   // the cycle's residual starts at norm 1
+            for (int k = 0; k < 2; ++k) {
+                if (!sc->active[k]) continue;
+                const double rn = sqrt(v[k]);
+                if (!isfinite(rn)) { sc->status = RVE_ENAN; sc->active[k] = 0; sc->cdone[k] = 1; }
+                else if (rn <= sc->target[k] || sc->iters[k] >= a.max_iter) sc->active[k] = 0;
+            }
+            sc->done = !(sc->active[0] || sc->active[1]);
+            break;
+        case M_BETA:
+            for (int k = 0; k < 2; ++k) {
+                sc->beta[k] = sc->active[k] ? v[k] / sc->rho[k] : 0.0;
+                sc->beta_f[k] = (float)sc->beta[k];
+                sc->rho[k] = v[k];
+            }
+            break;
+    }
+}
+
+// The step scalars in the cycle's precision.
+template <typename T> __device__ __forceinline__ T alpha_of(const MixScal& s, int k);
+template <> __device__ __forceinline__ double alpha_of<double>(const MixScal& s, int k) { return s.alpha[k]; }
+template <> __device__ __forceinline__ float alpha_of<float>(const MixScal& s, int k) { return s.alpha_f[k]; }
+template <typename T> __device__ __forceinline__ T beta_of(const MixScal& s, int k);
+template <> __device__ __forceinline__ double beta_of<double>(const MixScal& s, int k) { return s.beta[k]; }
+template <> __device__ __forceinline__ float beta_of<float>(const MixScal& s, int k) { return s.beta_f[k]; }
+
+// Start of a cycle: r = r64 / s, e = 0, p = 0 (components not iterating: 0).
+template <typename V>
+__global__ void __launch_bounds__(T3) k3_start(Grp g, const MixScal* scs,
+                                               const double2* __restrict__ r64, V* __restrict__ r,
+                                               V* __restrict__ e, V* __restrict__ p) {
+    typedef typename ScalarOf<V>::T T;
+    int lb;
+    const int u = unit_of(g, lb);
+    const MixScal& sc = scs[u];
+    if (sc.done) return;
+    const U3& d = g.desc[u];
+    const int64_t node = d.off + lb * T3 + threadIdx.x;
+    const double2 rr = r64[node];
+    V o;
+    if (sizeof(T) == 8) {
+        o.x = (T)(sc.active[0] ? rr.x / sc.s[0] : 0.0);
+        o.y = (T)(sc.active[1] ? rr.y / sc.s[1] : 0.0);
+    } else {
+        o.x = (T)rr.x * (T)sc.inv_s_f[0];
+        o.y = (T)rr.y * (T)sc.inv_s_f[1];
+    }
+    r[node] = o;
+    e[node] = mk<V>((T)0, (T)0);
+    p[node] = mk<V>((T)0, (T)0);
+}
+
+// e += alpha p; r -= alpha q; partials |r|^2.  Four nodes per thread.
+template <typename V>
+__global__ void __launch_bounds__(T3) k3_axpy(Grp g, const MixScal* scs, V* __restrict__ e,
+                                              V* __restrict__ r, const V* __restrict__ p,
+                                              const V* __restrict__ q, double* part) {
+    typedef typename ScalarOf<V>::T T;
+    __shared__ double red[32];
+    int lb;
+    const int u = unit_of(g, lb);
+    const MixScal& sc = scs[u];
+    if (sc.done) return;
+    const U3& d = g.desc[u];
+    const T ax_ = alpha_of<T>(sc, 0), ay_ = alpha_of<T>(sc, 1);
+    DotAcc<T> sx, sy;
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+        const int64_t node = d.off + (int64_t)lb * (4 * T3) + mm * T3 + threadIdx.x;
+        const V pp = p[node], qq = q[node];
+        V ee = e[node], rr = r[node];
+        ee.x = fma(ax_, pp.x, ee.x);
+        ee.y = fma(ay_, pp.y, ee.y);
+        rr.x = fma(-ax_, qq.x, rr.x);
+        rr.y = fma(-ay_, qq.y, rr.y);
+        e[node] = ee;
+        r[node] = rr;
+        sx.add(rr.x, rr.x);
+        sy.add(rr.y, rr.y);
+    }
+    double tx = 0.0, ty = 0.0;
+    block_sum2(sx, sy, red, tx, ty);
+    if (threadIdx.x == 0) {
+        part[d.part_off + 2 * lb] = tx;
+        part[d.part_off + 2 * lb + 1] = ty;
+    }
+}
+
+// p = z + beta p.  Four nodes per thread.
+template <typename V>
+__global__ void __launch_bounds__(T3) k3_xpby(Grp g, const MixScal* scs, const V* __restrict__ z,
+                                              V* __restrict__ p) {
+    typedef typename ScalarOf<V>::T T;
+    int lb;
+    const int u = unit_of(g, lb);
+    const MixScal& sc = scs[u];
+    if (sc.done) return;
+    const U3& d = g.desc[u];
+    const T bx = beta_of<T>(sc, 0), by = beta_of<T>(sc, 1);
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+        const int64_t node = d.off + (int64_t)lb * (4 * T3) + mm * T3 + threadIdx.x;
+        const V zz = z[node], pp = p[node];
+        p[node] = mk<V>(fma(bx, pp.x, zz.x), fma(by, pp.y, zz.y));
+    }
+}
+
+// End of a cycle: u += s e (components that iterated).
+template <typename V>
+__global__ void __launch_bounds__(T3) k3_accum(Grp g, const MixScal* scs, const V* __restrict__ e,
+                                               double2* __restrict__ uv) {
+    int lb;
+    const int u = unit_of(g, lb);
+    const MixScal& sc = scs[u];
+    if (sc.outer_done) return;
+    const U3& d = g.desc[u];
+    const int64_t node = d.off + lb * T3 + threadIdx.x;
+    const double sx = sc.cdone[0] ? 0.0 : sc.s[0], sy = sc.cdone[1] ? 0.0 : sc.s[1];
+    const V ee = e[node];
+    double2 w = uv[node];
+    w.x = fma(sx, (double)ee.x, w.x);
+    w.y = fma(sy, (double)ee.y, w.y);
+    uv[node] = w;
+}
+
+// Per realization: the report of its two units.
+__global__ void k3_report(const MixScal* scs, int batch, rve3_solve_info* info) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const MixScal& s12 = scs[2 * b];
+    const MixScal& s3 = scs[2 * b + 1];
     rve3_solve_info r;
-    r.iters[0] = s12->iters[0];
-    r.iters[1] = s12->iters[1];
-    r.iters[2] = s3->iters[0];
-    r.status = s12->status != RVE_OK ? s12->status : s3->status;
-    r.relres[0] = s12->relres[0];
-    r.relres[1] = s12->relres[1];
-    r.relres[2] = s3->relres[0];
-    *info = r;
+    r.iters[0] = s12.iters[0];
+    r.iters[1] = s12.iters[1];
+    r.iters[2] = s3.iters[0];
+    r.status = s12.status != RVE_OK ? s12.status : s3.status;
+    r.refinements = s12.refinements + s3.refinements;
+    r.reserved = 0;
+    r.relres[0] = s12.relres[0];
+    r.relres[1] = s12.relres[1];
+    r.relres[2] = s3.relres[0];
+    info[b] = r;
 }
 
 // ------------------------------------------------------------ profile --
 // Event timing of every 3D launch by kind (diagnostics, enabled together
 // with the fused solver's profiler by rve_profile_enable; process-wide, not
 // thread-safe): 0 stiffness, 1 line transform (x or y), 2 z solve,
-// 3 vector steps of CG (dots, updates), 4 scalar steps (one warp each).
+// 3 vector steps of CG (dots, updates), 4 scalar steps (one block per unit).
 enum { P3_STIFF = 0, P3_LINES, P3_ZSOLVE, P3_VECTOR, P3_SCALAR, P3_K };
 struct Prof3 {
     double ms[P3_K] = {};
@@ -407,32 +831,43 @@ static void prof3_sync(cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- host --
-struct Plan3 {
-    int batch = 0;
-    std::vector<RDesc> desc;
-    int64_t nodes = 0;
-    int max_log2n = 5;
-    // workspace: descriptors, tables, two scalar blocks, partials, 7 pair vectors
-    size_t o_desc = 0, o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0, o_rho64 = 0, o_rho32 = 0;
-    size_t o_sc = 0, o_part = 0, o_vec = 0, total = 0;
-    int64_t max_nodes_one = 0;
-};
-
 constexpr int N3_MIN = 32, N3_MAX = 256;
 constexpr int Z_THREADS = 512;
+constexpr int NVEC = 8;   // unit vectors: f, u, r64, and the cycle's r, z, p, e, q
 
-static int col_tile3(int n) {   // columns of a z-solve block (FP64 segments)
+static int col_tile3(int n) {   // columns of a z-solve block (16 segments per column)
     const int P = n / col_seg_rows(n, 16);
     return std::min(n, Z_THREADS / P);
 }
 
+struct Group3 {
+    int log2n = 0;
+    int count = 0;             // units of this size
+    size_t ids_off = 0;        // into the id array: units
+    size_t rids_off = 0;       // pair-0 units (realizations)
+};
+
+struct Plan3 {
+    int batch = 0;
+    std::vector<U3> desc;      // 2 * batch units
+    std::vector<int32_t> ids;  // per group: its units, then its pair-0 units
+    std::vector<Group3> groups;
+    int64_t nodes = 0;         // realization nodes (sum n^3)
+    int64_t unit_nodes = 0;    // 2 * nodes
+    int64_t parts = 0;         // doubles of partials
+    int max_log2n = 5;
+    size_t o_desc = 0, o_ids = 0, o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0, o_rho64 = 0,
+           o_rho32 = 0, o_sc = 0, o_part = 0, o_c32 = 0, o_vec = 0, total = 0;
+};
+
 static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) {
     if (!r || batch <= 0 || batch > (1 << 16)) return RVE_EINVAL;
     p.batch = batch;
-    p.desc.assign(batch, RDesc{});
+    p.desc.assign(2 * (size_t)batch, U3{});
     p.nodes = 0;
+    p.parts = 0;
     p.max_log2n = 5;
-    p.max_nodes_one = 0;
+    std::map<int, std::vector<int32_t>> by_size;
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
@@ -444,204 +879,308 @@ static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) 
         if (!std::isfinite(x.a_matrix) || !std::isfinite(x.a_incl) || !(x.a_matrix > 0.0) ||
             !(x.a_incl > 0.0))
             return RVE_EINVAL;
-        RDesc& d = p.desc[b];
-        std::memset(&d, 0, sizeof(d));
-        d.n = n;
-        d.log2n = 31 - __builtin_clz((unsigned)n);
-        d.L = x.L;
-        d.s = x.incl_cells;
-        d.n_incl = x.n_incl;
-        d.tC = col_tile3(n);
-        d.node_off = p.nodes;
-        d.a_matrix = x.a_matrix;
-        d.a_incl = x.a_incl;
-        d.h = 1.0 / (double)x.m0;
-        d.c0 = 0.5 * (x.a_matrix + x.a_incl);
-        d.inv_vol = 1.0 / ((double)x.L * (double)x.L * (double)x.L);
-        d.key = sm64_mix(x.seed + (x.index + 1) * 0x9E3779B97F4A7C15ull);
         const int64_t nn = (int64_t)n * n * n;
+        const int64_t part_real = A3_NP * (nn / T3);   // >= 2 units x 2 x (nn / T3)
+        for (int pair = 0; pair < 2; ++pair) {
+            U3& d = p.desc[2 * b + pair];
+            std::memset(&d, 0, sizeof(d));
+            d.n = n;
+            d.log2n = 31 - __builtin_clz((unsigned)n);
+            d.pair = pair;
+            d.tC = col_tile3(n);
+            d.n_incl = x.n_incl;
+            d.s = x.incl_cells;
+            d.cell_off = p.nodes;
+            d.part_off = p.parts + pair * 2 * (nn / T3);
+            d.am = x.a_matrix;
+            d.ai = x.a_incl;
+            d.am32 = (float)x.a_matrix;
+            d.ai32 = (float)x.a_incl;
+            d.h = 1.0 / (double)x.m0;
+            d.c0 = 0.5 * (x.a_matrix + x.a_incl);
+            d.inv_vol = 1.0 / ((double)x.L * (double)x.L * (double)x.L);
+            d.key = sm64_mix(x.seed + (x.index + 1) * 0x9E3779B97F4A7C15ull);
+            d.off = 2 * p.nodes + pair * nn;
+            by_size[d.log2n].push_back(2 * b + pair);
+        }
         p.nodes += nn;
-        p.max_nodes_one = std::max(p.max_nodes_one, nn);
-        p.max_log2n = std::max(p.max_log2n, d.log2n);
+        p.parts += part_real;
+        p.max_log2n = std::max(p.max_log2n, (int)p.desc[2 * b].log2n);
+    }
+    p.unit_nodes = 2 * p.nodes;
+    p.ids.clear();
+    p.groups.clear();
+    for (auto& kv : by_size) {
+        Group3 g;
+        g.log2n = kv.first;
+        g.count = (int)kv.second.size();
+        g.ids_off = p.ids.size();
+        p.ids.insert(p.ids.end(), kv.second.begin(), kv.second.end());
+        g.rids_off = p.ids.size();
+        for (int32_t u : kv.second)
+            if ((u & 1) == 0) p.ids.push_back(u);
+        p.groups.push_back(g);
     }
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = up(off + bytes); return o; };
     const size_t tab = (size_t)2 << p.max_log2n;
-    p.o_desc = take(sizeof(RDesc) * batch);
+    p.o_desc = take(sizeof(U3) * p.desc.size());
+    p.o_ids = take(sizeof(int32_t) * p.ids.size());
     p.o_tw64 = take(sizeof(double2) * tab);
     p.o_tw32 = take(sizeof(float2) * tab);
     p.o_lap = take(sizeof(double) * tab);
     p.o_lap32 = take(sizeof(float) * tab);
     p.o_rho64 = take(sizeof(double) * tab);
     p.o_rho32 = take(sizeof(float) * tab);
-    p.o_sc = take(sizeof(PlainScal) * 2);
-    p.o_part = take(sizeof(double) * A3_NP * (size_t)(p.max_nodes_one / T3 + 1));
-    p.o_vec = take(sizeof(double2) * 7 * (size_t)p.nodes);
+    p.o_sc = take(sizeof(MixScal) * p.desc.size());
+    p.o_part = take(sizeof(double) * (size_t)p.parts);
+    p.o_c32 = take(sizeof(float) * (size_t)p.nodes);
+    p.o_vec = take(sizeof(double2) * NVEC * (size_t)p.unit_nodes);
     p.total = off;
     return RVE_OK;
 }
 
-static Tables tables3(const Plan3& p, char* w) {
-    Tables tb;
-    tb.tw64 = reinterpret_cast<const double2*>(w + p.o_tw64);
-    tb.tw32 = reinterpret_cast<const float2*>(w + p.o_tw32);
-    tb.lap = reinterpret_cast<const double*>(w + p.o_lap);
-    tb.lap32 = reinterpret_cast<const float*>(w + p.o_lap32);
-    tb.rho64 = reinterpret_cast<const double*>(w + p.o_rho64);
-    tb.rho32 = reinterpret_cast<const float*>(w + p.o_rho32);
-    return tb;
+struct Ws3 {   // device pointers into the workspace
+    const Plan3* p;
+    char* w;
+    const U3* desc() const { return reinterpret_cast<const U3*>(w + p->o_desc); }
+    const int32_t* ids() const { return reinterpret_cast<const int32_t*>(w + p->o_ids); }
+    MixScal* sc() const { return reinterpret_cast<MixScal*>(w + p->o_sc); }
+    double* part() const { return reinterpret_cast<double*>(w + p->o_part); }
+    float* c32() const { return reinterpret_cast<float*>(w + p->o_c32); }
+    template <typename V> V* vec(int k) const {   // unit vector k, 16 bytes per node reserved
+        return reinterpret_cast<V*>(w + p->o_vec + (size_t)k * 16 * (size_t)p->unit_nodes);
+    }
+    Tables tables() const {
+        Tables tb;
+        tb.tw64 = reinterpret_cast<const double2*>(w + p->o_tw64);
+        tb.tw32 = reinterpret_cast<const float2*>(w + p->o_tw32);
+        tb.lap = reinterpret_cast<const double*>(w + p->o_lap);
+        tb.lap32 = reinterpret_cast<const float*>(w + p->o_lap32);
+        tb.rho64 = reinterpret_cast<const double*>(w + p->o_rho64);
+        tb.rho32 = reinterpret_cast<const float*>(w + p->o_rho32);
+        return tb;
+    }
+    // launch over the units (or the pair-0 units) of group g, `per` blocks each
+    Grp grp(const Group3& g, int per, bool reals = false) const {
+        return Grp{desc(), ids() + (reals ? g.rids_off : g.ids_off), per};
+    }
+};
+enum { V_F = 0, V_U, V_R64, V_R, V_Z, V_P, V_E, V_Q };
+
+static unsigned nblocks(const Group3& g, int64_t per, bool reals = false) {
+    return (unsigned)((reals ? g.count / 2 : g.count) * per);
+}
+static int64_t nodes_of(const Group3& g) { return (int64_t)1 << (3 * g.log2n); }
+
+// Setup common to the entry points: descriptors, id lists and tables.
+static rve_status setup3(const Plan3& p, char* w, cudaStream_t s, bool tables) {
+    if (cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(U3) * p.desc.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w + p.o_ids, p.ids.data(), sizeof(int32_t) * p.ids.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return RVE_ECUDA;
+    if (!tables) return RVE_OK;
+    Ws3 ws{&p, w};
+    return fill_tables(ws.tables(), p.max_log2n, s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
-static double2* vec3(const Plan3& p, char* w, int k) {
-    return reinterpret_cast<double2*>(w + p.o_vec) + (size_t)k * (size_t)p.nodes;
-}
-
-static int64_t blocks3(const RDesc& d) { return ((int64_t)d.n * d.n * d.n) / T3; }
-
-// dst = B^{-1} src for one realization (one pair); src is read by the first
-// pass only (it may equal dst).  With `rd`, part receives the partials of
-// rd.dst (n^3 / 2048 blocks of two doubles).
-template <int LG>
-static cudaError_t precond3_t(const RDesc& d, const Tables& tb, double delta, const double2* src,
-                              double2* dst, const double2* rd, double* part, cudaStream_t s) {
-    constexpr int n = 1 << LG, T = n / 8;
-    const int G = 256 / T;
-    const size_t smem = (size_t)G * seq_stride(n) * sizeof(double2);
-    const unsigned lines = (unsigned)(((int64_t)n * n) / G);
-    const int P = n / col_seg_rows(n, 16);
-    const size_t zsmem = (size_t)(2 * d.tC + 2) * P * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(k3_lines<LG, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// dst = B^{-1} src for the units of group g; src is read by the first pass
+// only (it may equal dst).  With `rd`, the units' partials of rd.dst.
+template <int LG, typename V>
+static cudaError_t precond3_t(const Ws3& ws, const Group3& g, double delta, const V* src, V* dst,
+                              const V* rd, const MixScal* sc, cudaStream_t s) {
+    typedef typename ScalarOf<V>::T T;
+    constexpr int n = 1 << LG, TL = n / 8;
+    const int G = 256 / TL;
+    const size_t smem = (size_t)G * seq_stride(n) * sizeof(V);
+    const int lines = (n * n) / G;
+    const int tC = col_tile3(n);
+    const int P = n / col_seg_rows(n, (int)sizeof(V));
+    const size_t zsmem = (size_t)(2 * tC + 2) * P * sizeof(V);
+    cudaError_t e = cudaFuncSetAttribute(k3_lines<LG, 2, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k3_lines<LG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k3_lines<LG, 1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const Tables tb = ws.tables();
+    double* part = ws.part();
+    const Grp gl = ws.grp(g, lines);
+    const unsigned bl = nblocks(g, lines);
     {
         Span3 sp(s, P3_LINES);
-        k3_lines<LG, 2><<<lines, 256, smem, s>>>(d, tb, src, dst, 1.0, nullptr, nullptr);
+        k3_lines<LG, 2, V><<<bl, 256, smem, s>>>(gl, tb, src, dst, (T)1, nullptr, nullptr, sc);
     }
     {
         Span3 sp(s, P3_LINES);
-        k3_lines<LG, 1><<<lines, 256, smem, s>>>(d, tb, dst, dst, 1.0, nullptr, nullptr);
+        k3_lines<LG, 1, V><<<bl, 256, smem, s>>>(gl, tb, dst, dst, (T)1, nullptr, nullptr, sc);
     }
     {
         Span3 sp(s, P3_ZSOLVE);
-        k3_zsolve<LG><<<dim3((unsigned)(n / d.tC), (unsigned)n), Z_THREADS, zsmem, s>>>(d, tb, delta, dst);
+        k3_zsolve<LG, V><<<dim3(nblocks(g, n / tC), (unsigned)n), Z_THREADS, zsmem, s>>>(
+            ws.grp(g, n / tC), tb, delta, dst, sc);
     }
     {
         Span3 sp(s, P3_LINES);
-        k3_lines<LG, 1><<<lines, 256, smem, s>>>(d, tb, dst, dst, 1.0, nullptr, nullptr);
+        k3_lines<LG, 1, V><<<bl, 256, smem, s>>>(gl, tb, dst, dst, (T)1, nullptr, nullptr, sc);
     }
     {
         Span3 sp(s, P3_LINES);
-        k3_lines<LG, 2><<<lines, 256, smem, s>>>(d, tb, dst, dst, 1.0 / (double)n, rd, part);
+        k3_lines<LG, 2, V><<<bl, 256, smem, s>>>(gl, tb, dst, dst, (T)(1.0 / (double)n), rd, part, sc);
     }
     note_launch(5);
     return cudaGetLastError();
 }
 
-static cudaError_t precond3(const RDesc& d, const Tables& tb, double delta, const double2* src,
-                            double2* dst, cudaStream_t s, const double2* rd = nullptr,
-                            double* part = nullptr) {
-    switch (d.log2n) {
-        case 5: return precond3_t<5>(d, tb, delta, src, dst, rd, part, s);
-        case 6: return precond3_t<6>(d, tb, delta, src, dst, rd, part, s);
-        case 7: return precond3_t<7>(d, tb, delta, src, dst, rd, part, s);
-        default: return precond3_t<8>(d, tb, delta, src, dst, rd, part, s);
+template <typename V>
+static cudaError_t precond3(const Ws3& ws, const Group3& g, double delta, const V* src, V* dst,
+                            cudaStream_t s, const V* rd = nullptr, const MixScal* sc = nullptr) {
+    switch (g.log2n) {
+        case 5: return precond3_t<5, V>(ws, g, delta, src, dst, rd, sc, s);
+        case 6: return precond3_t<6, V>(ws, g, delta, src, dst, rd, sc, s);
+        case 7: return precond3_t<7, V>(ws, g, delta, src, dst, rd, sc, s);
+        default: return precond3_t<8, V>(ws, g, delta, src, dst, rd, sc, s);
     }
 }
 
-// Blocks of the last line pass (its partials): n^2 / G lines of G per block.
-static int lines_blocks(const RDesc& d) {
-    const int T = d.n / 8, G = 256 / T;
-    return (int)(((int64_t)d.n * d.n) / G);
-}
-
-static cudaError_t stiffness3(const RDesc& d, Cells3 cs, int scheme, const double2* x, double2* y,
-                              cudaStream_t s, double* part = nullptr) {
+template <int MODE, typename V>
+static cudaError_t stiffness3(const Ws3& ws, const Group3& g, Cells3T<typename ScalarOf<V>::T> cs,
+                              int scheme, const V* x, V* y, const V* f, bool partials,
+                              const MixScal* sc, cudaStream_t s) {
     Span3 sp(s, P3_STIFF);
-    if (scheme == RVE_Q1_LUMPED) k3_stiffness<1><<<(unsigned)blocks3(d), T3, 0, s>>>(d, cs, x, y, part);
-    else k3_stiffness<0><<<(unsigned)blocks3(d), T3, 0, s>>>(d, cs, x, y, part);
+    const int per = (int)(nodes_of(g) / T3);
+    const Grp gg = ws.grp(g, per);
+    double* part = partials ? ws.part() : nullptr;
+    if (scheme == RVE_Q1_LUMPED)
+        k3_stiffness<1, MODE, V><<<nblocks(g, per), T3, 0, s>>>(gg, cs, x, y, f, part, sc);
+    else
+        k3_stiffness<0, MODE, V><<<nblocks(g, per), T3, 0, s>>>(gg, cs, x, y, f, part, sc);
     note_launch();
     return cudaGetLastError();
 }
 
-// The loads are the same for both schemes (the mass rows sum to h/2 in each).
-static cudaError_t rhs3(const RDesc& d, Cells3 cs, int pair, double2* f, cudaStream_t s) {
-    k3_rhs<<<(unsigned)blocks3(d), T3, 0, s>>>(d, cs, pair, f);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// Setup common to every 3D entry point: descriptors and tables into ws.
-static rve_status setup3(const Plan3& p, char* w, cudaStream_t s) {
-    if (cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(RDesc) * p.batch,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return RVE_ECUDA;
-    return fill_tables(tables3(p, w), p.max_log2n, s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
-}
-
-// PCG (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.1)
-// for one pair of one realization: A u = f with f given, u from 0.  Per
-// iteration: q = A p with the p.q partials, the step, u and r updates with
-// |r|^2, z = B^{-1} r with the r.z partials, the new direction.
-static rve_status pcg3_pair(const Plan3& p, char* w, int b, Cells3 cs, const rve3_solve_opts& o,
-                            const double2* f, double2* u, PlainScal* sc, cudaStream_t s) {
-    const RDesc& d = p.desc[b];
-    const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
-    const Tables tb = tables3(p, w);
-    double2* r = vec3(p, w, 2);
-    double2* z = vec3(p, w, 3);
-    double2* pp = vec3(p, w, 4);
-    double2* q = vec3(p, w, 5);
-    double* part = reinterpret_cast<double*>(w + p.o_part);
-    const int nb = (int)(((int64_t)d.n * d.n * d.n) / PL_NODES);   // vector kernels
-    const int ns = (int)blocks3(d);                                  // stiffness
-    const int nl = lines_blocks(d);                                  // last line pass
-    const size_t bytes = sizeof(double2) * (size_t)d.n * d.n * d.n;
+// The correctors of every unit: cycles of PCG in the precision of V between
+// FP64 true residuals (see the head of the file).
+template <typename V>
+static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
+                              Cells3T<typename ScalarOf<V>::T> csV, const rve3_solve_opts& o,
+                              cudaStream_t s) {
+    const Ws3 ws{&p, w};
+    MixScal* sc = ws.sc();
+    double* part = ws.part();
+    double2* f = ws.vec<double2>(V_F);
+    double2* uv = ws.vec<double2>(V_U);
+    double2* r64 = ws.vec<double2>(V_R64);
+    V* r = ws.vec<V>(V_R);
+    V* z = ws.vec<V>(V_Z);
+    V* pp = ws.vec<V>(V_P);
+    V* e = ws.vec<V>(V_E);
+    V* q = ws.vec<V>(V_Q);
+    const bool fp64 = sizeof(typename ScalarOf<V>::T) == 8;
+    const ScalArgs sa{o.tol, fp64 ? 0.0 : o.inner_tol, fp64 ? 1.0 : 0.5, o.max_iter};
     auto vec_step = [&](auto&& launch) {
         Span3 sp(s, P3_VECTOR);
         launch();
     };
-    auto scalar_step = [&](auto&& launch) {
+    auto scalar = [&](const Group3& g, int what) {
         Span3 sp(s, P3_SCALAR);
-        launch();
+        k3_scalar<<<g.count, 256, 0, s>>>(ws.ids() + g.ids_off, ws.desc(), sc, part, what, sa);
+        note_launch();
     };
-    // u = 0, r = f, p = 0
-    if (cudaMemcpyAsync(r + d.node_off, f + d.node_off, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(u + d.node_off, 0, bytes, s) != cudaSuccess ||
-        cudaMemsetAsync(pp + d.node_off, 0, bytes, s) != cudaSuccess)
-        return RVE_ECUDA;
-    vec_step([&] { k_pl_dot<<<nb, PL_THREADS, 0, s>>>(desc, b, r, r, part); });
-    scalar_step([&] { k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_FNORM, o.tol, o.max_iter); });
-    if (precond3(d, tb, o.delta, r, z, s, r, part) != cudaSuccess) return RVE_ECUDA;
-    scalar_step([&] { k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nl, SC_RHO0, o.tol, o.max_iter); });
-    vec_step([&] { k_pl_xpby<<<nb, PL_THREADS, 0, s>>>(desc, b, sc, z, pp); });   // p = z
-    note_launch(4);
-    const int every = o.check_every > 0 ? o.check_every : 8;
-    PlainScal hsc;
-    for (int it = 0; it < o.max_iter; ++it) {
-        if (stiffness3(d, cs, o.scheme, pp, q, s, part) != cudaSuccess) return RVE_ECUDA;
-        scalar_step([&] { k_pl_scalar<<<1, 32, 0, s>>>(sc, part, ns, SC_ALPHA, o.tol, o.max_iter); });
-        vec_step([&] { k_pl_axpy<<<nb, PL_THREADS, 0, s>>>(desc, b, sc, u, r, pp, q, part); });
-        scalar_step([&] { k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nb, SC_CONV, o.tol, o.max_iter); });
-        if (precond3(d, tb, o.delta, r, z, s, r, part) != cudaSuccess) return RVE_ECUDA;
-        scalar_step([&] { k_pl_scalar<<<1, 32, 0, s>>>(sc, part, nl, SC_BETA, o.tol, o.max_iter); });
-        vec_step([&] { k_pl_xpby<<<nb, PL_THREADS, 0, s>>>(desc, b, sc, z, pp); });
-        note_launch(5);
-        if ((it + 1) % every == 0 || it == 0) {
-            if (cudaMemcpyAsync(&hsc, sc, sizeof(PlainScal), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return RVE_ECUDA;
-            if (profile_on()) g_prof3.harvest();
-            if (hsc.done) break;
+    auto per_group = [&](auto&& fn) -> rve_status {
+        for (const Group3& g : p.groups) {
+            const rve_status st = fn(g);
+            if (st != RVE_OK) return st;
         }
+        return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+    };
+    std::vector<MixScal> hsc(p.desc.size());
+    auto poll = [&](bool outer) -> int {   // -1 error, 1 every unit finished
+        if (cudaMemcpyAsync(hsc.data(), sc, sizeof(MixScal) * hsc.size(), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return -1;
+        if (profile_on()) g_prof3.harvest();
+        for (const MixScal& m : hsc)
+            if (!(outer ? m.outer_done : m.done)) return 0;
+        return 1;
+    };
+    rve_status st;
+    // loads with |f|^2, u = 0
+    st = per_group([&](const Group3& g) {
+        const int per = (int)(nodes_of(g) / T3);
+        vec_step([&] { k3_rhs<<<nblocks(g, per), T3, 0, s>>>(ws.grp(g, per), cs64, f, part); });
+        scalar(g, M_FNORM);
+        note_launch();
+        return RVE_OK;
+    });
+    if (st != RVE_OK) return st;
+    if (cudaMemsetAsync(uv, 0, sizeof(double2) * (size_t)p.unit_nodes, s) != cudaSuccess ||
+        cudaMemcpyAsync(r64, f, sizeof(double2) * (size_t)p.unit_nodes, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+        return RVE_ECUDA;
+    const int every = o.check_every;
+    for (int cycle = 0; cycle <= MAX_REFINE + 1; ++cycle) {
+        // FP64 true residual r64 = f - A u and the refinement step
+        st = per_group([&](const Group3& g) {
+            if (cycle > 0) {
+                if (stiffness3<MODE_RESID, double2>(ws, g, cs64, o.scheme, uv, r64, f, true, sc, s) !=
+                    cudaSuccess)
+                    return RVE_ECUDA;
+            } else {   // u = 0: r64 = f, the partials of |f|^2 are still in place
+            }
+            scalar(g, M_REFINE);
+            return RVE_OK;
+        });
+        if (st != RVE_OK) return st;
+        const int pr = poll(true);
+        if (pr < 0) return RVE_ECUDA;
+        if (pr == 1) break;
+        // a cycle: r = r64 / s, z = B^-1 r, p = z
+        st = per_group([&](const Group3& g) {
+            const int per = (int)(nodes_of(g) / T3);
+            vec_step([&] { k3_start<V><<<nblocks(g, per), T3, 0, s>>>(ws.grp(g, per), sc, r64, r, e, pp); });
+            if (precond3<V>(ws, g, o.delta, r, z, s, r, sc) != cudaSuccess) return RVE_ECUDA;
+            scalar(g, M_RHO0);
+            const int per4 = per / 4;
+            vec_step([&] { k3_xpby<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, z, pp); });
+            note_launch(2);
+            return RVE_OK;
+        });
+        if (st != RVE_OK) return st;
+        for (int it = 1;; ++it) {
+            st = per_group([&](const Group3& g) {
+                const int per = (int)(nodes_of(g) / T3), per4 = per / 4;
+                if (stiffness3<MODE_APPLY, V>(ws, g, csV, o.scheme, pp, q, nullptr, true, sc, s) !=
+                    cudaSuccess)
+                    return RVE_ECUDA;
+                scalar(g, M_ALPHA);
+                vec_step([&] {
+                    k3_axpy<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, e, r, pp, q, part);
+                });
+                scalar(g, M_CONV);
+                if (precond3<V>(ws, g, o.delta, r, z, s, r, sc) != cudaSuccess) return RVE_ECUDA;
+                scalar(g, M_BETA);
+                vec_step([&] { k3_xpby<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, z, pp); });
+                note_launch(2);
+                return RVE_OK;
+            });
+            if (st != RVE_OK) return st;
+            if (it % every == 0) {
+                const int pi = poll(false);
+                if (pi < 0) return RVE_ECUDA;
+                if (pi == 1) break;
+            }
+        }
+        st = per_group([&](const Group3& g) {
+            const int per = (int)(nodes_of(g) / T3);
+            vec_step([&] { k3_accum<V><<<nblocks(g, per), T3, 0, s>>>(ws.grp(g, per), sc, e, uv); });
+            note_launch();
+            return RVE_OK;
+        });
+        if (st != RVE_OK) return st;
     }
-    // true residual
-    if (stiffness3(d, cs, o.scheme, u, q, s) != cudaSuccess) return RVE_ECUDA;
-    k3_resid<<<(unsigned)blocks3(d), T3, 0, s>>>(d, f, q, r, part);
-    k_pl_scalar<<<1, 32, 0, s>>>(sc, part, (int)blocks3(d), SC_RELRES, o.tol, o.max_iter);
-    note_launch(2);
-    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+    return RVE_OK;
 }
 
 static rve3_solve_opts resolved3(const rve3_solve_opts* opts) {
@@ -649,9 +1188,12 @@ static rve3_solve_opts resolved3(const rve3_solve_opts* opts) {
     if (opts) o = *opts;
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (!(o.tol > 0.0)) o.tol = 1e-10;
+    if (!(o.inner_tol > 0.0)) o.inner_tol = 1e-4;
     if (o.check_every <= 0) o.check_every = 8;
     return o;
 }
+
+static bool valid_scheme(int s) { return s == RVE_Q1_CONSISTENT || s == RVE_Q1_LUMPED; }
 
 }  // namespace rve
 
@@ -676,7 +1218,8 @@ rve_status rve3_gen_field(const rve_realization* r, int32_t batch, uint8_t* mask
     if (!mask) return RVE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(mask, 0, (size_t)p.nodes, s) != cudaSuccess) return RVE_ECUDA;
-    for (const RDesc& d : p.desc) {
+    for (int b = 0; b < p.batch; ++b) {
+        const U3& d = p.desc[2 * b];
         const int64_t rows = (int64_t)d.n_incl * d.s * d.s;
         if (rows == 0) continue;
         k3_gen_field<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(d, mask);
@@ -690,18 +1233,18 @@ rve_status rve3_rhs(const rve_realization* r, int32_t batch, const uint8_t* mask
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !f || !ws || (scheme != RVE_Q1_CONSISTENT && scheme != RVE_Q1_LUMPED))
-        return RVE_EINVAL;
+    if ((!mask && !coef) || !f || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
-    Cells3 cs{mask, coef};
-    for (const RDesc& d : p.desc) {
-        if (rhs3(d, cs, 0, vec3(p, w, 0), s) != cudaSuccess ||
-            rhs3(d, cs, 1, vec3(p, w, 1), s) != cudaSuccess)
-            return RVE_ECUDA;
-        k3_join<<<(unsigned)blocks3(d), T3, 0, s>>>(d, vec3(p, w, 0), vec3(p, w, 1), f);
-        note_launch();
+    if ((st = setup3(p, w, s, false)) != RVE_OK) return st;
+    const Ws3 W{&p, w};
+    const Cells3T<double> cs{mask, coef};
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        k3_rhs<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), cs, W.vec<double2>(V_F), nullptr);
+        k3_join<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), W.vec<double2>(V_F), f);
+        note_launch(2);
     }
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
@@ -712,20 +1255,21 @@ rve_status rve3_apply_stiffness(const rve_realization* r, int32_t batch, const u
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !x || !y || x == y || !ws ||
-        (scheme != RVE_Q1_CONSISTENT && scheme != RVE_Q1_LUMPED))
-        return RVE_EINVAL;
+    if ((!mask && !coef) || !x || !y || x == y || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
-    Cells3 cs{mask, coef};
-    for (const RDesc& d : p.desc) {
-        k3_split<<<(unsigned)blocks3(d), T3, 0, s>>>(d, x, vec3(p, w, 0), vec3(p, w, 1));
+    if ((st = setup3(p, w, s, false)) != RVE_OK) return st;
+    const Ws3 W{&p, w};
+    const Cells3T<double> cs{mask, coef};
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        k3_split<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), x, W.vec<double2>(V_R));
         note_launch();
-        if (stiffness3(d, cs, scheme, vec3(p, w, 0), vec3(p, w, 2), s) != cudaSuccess ||
-            stiffness3(d, cs, scheme, vec3(p, w, 1), vec3(p, w, 3), s) != cudaSuccess)
+        if (stiffness3<MODE_APPLY, double2>(W, g, cs, scheme, W.vec<double2>(V_R), W.vec<double2>(V_Q),
+                                            nullptr, false, nullptr, s) != cudaSuccess)
             return RVE_ECUDA;
-        k3_join<<<(unsigned)blocks3(d), T3, 0, s>>>(d, vec3(p, w, 2), vec3(p, w, 3), y);
+        k3_join<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), W.vec<double2>(V_Q), y);
         note_launch();
     }
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
@@ -741,15 +1285,19 @@ rve_status rve3_apply_precond(const rve_realization* r, int32_t batch, double de
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
-    if ((st = setup3(p, w, s)) != RVE_OK) return st;
-    const Tables tb = tables3(p, w);
-    for (const RDesc& d : p.desc) {
-        k3_split<<<(unsigned)blocks3(d), T3, 0, s>>>(d, x, vec3(p, w, 0), vec3(p, w, 1));
+    if ((st = setup3(p, w, s, true)) != RVE_OK) return st;
+    const Ws3 W{&p, w};
+    double2* v = W.vec<double2>(V_R);
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        k3_split<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), x, v);
         note_launch();
-        if (precond3(d, tb, delta, vec3(p, w, 0), vec3(p, w, 0), s) != cudaSuccess ||
-            precond3(d, tb, delta, vec3(p, w, 1), vec3(p, w, 1), s) != cudaSuccess)
-            return RVE_ECUDA;
-        k3_join<<<(unsigned)blocks3(d), T3, 0, s>>>(d, vec3(p, w, 0), vec3(p, w, 1), y);
+    }
+    for (const Group3& g : p.groups)
+        if (precond3<double2>(W, g, delta, v, v, s) != cudaSuccess) return RVE_ECUDA;
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        k3_join<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), v, y);
         note_launch();
     }
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
@@ -760,8 +1308,10 @@ rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const 
                                  rve3_solve_info* info, void* ws, size_t ws_bytes,
                                  void* stream) {
     const rve3_solve_opts o = resolved3(opts);
-    if (o.scheme != RVE_Q1_CONSISTENT && o.scheme != RVE_Q1_LUMPED) return RVE_EINVAL;
-    if (!std::isfinite(o.delta) || o.delta < 0.0 || !(o.tol < 1.0)) return RVE_EINVAL;
+    if (!valid_scheme(o.scheme)) return RVE_EINVAL;
+    if (o.precision != RVE_FP64 && o.precision != RVE_MIXED) return RVE_EINVAL;
+    if (!std::isfinite(o.delta) || o.delta < 0.0 || !(o.tol < 1.0) || !(o.inner_tol < 1.0))
+        return RVE_EINVAL;
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
@@ -769,24 +1319,56 @@ rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const 
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
-    if ((st = setup3(p, w, s)) != RVE_OK) return st;
-    Cells3 cs{mask, coef};
-    PlainScal* sc = reinterpret_cast<PlainScal*>(w + p.o_sc);
-    for (int b = 0; b < p.batch; ++b) {
-        const RDesc& d = p.desc[b];
-        double2* f = vec3(p, w, 0);
-        double2* upair[2] = {vec3(p, w, 1), vec3(p, w, 6)};
-        for (int pair = 0; pair < 2; ++pair) {
-            if (rhs3(d, cs, pair, f, s) != cudaSuccess) return RVE_ECUDA;
-            if ((st = pcg3_pair(p, w, b, cs, o, f, upair[pair], sc + pair, s)) != RVE_OK) return st;
+    if ((st = setup3(p, w, s, true)) != RVE_OK) return st;
+    const Ws3 W{&p, w};
+    const Cells3T<double> cs64{mask, coef};
+    if (o.precision == RVE_MIXED) {
+        if (coef) {
+            k3_coef32<<<(unsigned)((p.nodes + 255) / 256), 256, 0, s>>>(coef, W.c32(), p.nodes);
+            note_launch();
         }
-        k3_join<<<(unsigned)blocks3(d), T3, 0, s>>>(d, upair[0], upair[1], u);
-        k3_report<<<1, 1, 0, s>>>(sc, sc + 1, info + b);
-        note_launch(2);
-        if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
+        const Cells3T<float> cs32{mask, coef ? W.c32() : nullptr};
+        st = solve_units<float2>(p, w, cs64, cs32, o, s);
+    } else {
+        st = solve_units<double2>(p, w, cs64, cs64, o, s);
     }
+    if (st != RVE_OK) return st;
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        k3_join<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), W.vec<double2>(V_U), u);
+        note_launch();
+    }
+    k3_report<<<(p.batch + 127) / 128, 128, 0, s>>>(W.sc(), p.batch, info);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     prof3_sync(s);
     return RVE_OK;
+}
+
+rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* mask,
+                      const double* coef, int32_t scheme, const double* u, double* A,
+                      double* A_flux, void* ws, size_t ws_bytes, void* stream) {
+    Plan3 p;
+    rve_status st = make_plan3(r, batch, p);
+    if (st != RVE_OK) return st;
+    if ((!mask && !coef) || !u || !A || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
+    if (ws_bytes < p.total) return RVE_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    if ((st = setup3(p, w, s, false)) != RVE_OK) return st;
+    const Ws3 W{&p, w};
+    const Cells3T<double> cs{mask, coef};
+    for (const Group3& g : p.groups) {
+        const int per = (int)(nodes_of(g) / T3);
+        const Grp gr = W.grp(g, per, true);
+        if (scheme == RVE_Q1_LUMPED)
+            k3_a_hom_part<1><<<nblocks(g, per, true), T3, 0, s>>>(gr, cs, u, W.part());
+        else
+            k3_a_hom_part<0><<<nblocks(g, per, true), T3, 0, s>>>(gr, cs, u, W.part());
+        k3_a_hom_final<<<g.count / 2, 256, 0, s>>>(W.grp(g, 1, true), W.part(), A, A_flux);
+        note_launch(2);
+    }
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
 int32_t rve3_profile_read(double* ms, int64_t* launches) {
@@ -797,36 +1379,6 @@ int32_t rve3_profile_read(double* ms, int64_t* launches) {
         g_prof3.launches[j] = 0;
     }
     return P3_K;
-}
-
-rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* mask,
-                      const double* coef, int32_t scheme, const double* u, double* A,
-                      double* A_flux, void* ws, size_t ws_bytes, void* stream) {
-    Plan3 p;
-    rve_status st = make_plan3(r, batch, p);
-    if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !u || !A || !ws ||
-        (scheme != RVE_Q1_CONSISTENT && scheme != RVE_Q1_LUMPED))
-        return RVE_EINVAL;
-    if (ws_bytes < p.total) return RVE_ENOMEM;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    char* w = static_cast<char*>(ws);
-    Cells3 cs{mask, coef};
-    double* part = reinterpret_cast<double*>(w + p.o_part);
-    for (int b = 0; b < p.batch; ++b) {
-        const RDesc& d = p.desc[b];
-        const unsigned tiles = (unsigned)blocks3(d);
-        k3_split<<<tiles, T3, 0, s>>>(d, u, vec3(p, w, 0), vec3(p, w, 1));
-        if (scheme == RVE_Q1_LUMPED)
-            k3_a_hom_part<1><<<tiles, T3, 0, s>>>(d, cs, vec3(p, w, 0), vec3(p, w, 1), part);
-        else
-            k3_a_hom_part<0><<<tiles, T3, 0, s>>>(d, cs, vec3(p, w, 0), vec3(p, w, 1), part);
-        k3_a_hom_final<<<1, 32, 0, s>>>(d, part, (int)tiles, A + 9 * (int64_t)b,
-                                        A_flux ? A_flux + 9 * (int64_t)b : nullptr);
-        note_launch(3);
-        if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
-    }
-    return RVE_OK;
 }
 
 }  // extern "C"

@@ -32,10 +32,11 @@ namespace rve {
 // mean-zero, zhat = w / (n c0), rho_c = |y|^2 / (n c0).
 // Block: C columns x P segments, thread (cc, s) with cc fastest so that the
 // global accesses of a warp are row segments of C elements.  `rho_part`
-// may be null.
-template <typename V, int LOG2N, typename Ld, typename St>
-__device__ __forceinline__ void col_solve_body(Ld&& ld, St&& st, const RDesc& d, int c0,
-                                               V* smem, const Tables& tb, double delta,
+// may be null.  rho_of(k2) gives the filter root of column k2 (not called
+// for the singular column).
+template <typename V, int LOG2N, typename Ld, typename St, typename RhoOf>
+__device__ __forceinline__ void col_solve_core(Ld&& ld, St&& st, RhoOf&& rho_of, const RDesc& d,
+                                               int c0, V* smem, const Tables& tb, double delta,
                                                double* red, double* rho_part,
                                                typename ScalarOf<V>::T* csc) {
     typedef typename ScalarOf<V>::T Ts;
@@ -58,9 +59,7 @@ __device__ __forceinline__ void col_solve_body(Ld&& ld, St&& st, const RDesc& d,
     for (int i = 0; i < SEG; ++i)
         v[i] = active ? ld(s * SEG + i, k2) : mk<V>((Ts)0, (Ts)0);
     Ts rho = (Ts)1;
-    if (active && !zcol)
-        rho = (delta == 0.0) ? rho_table<Ts>(tb, n)[k2]
-                             : (Ts)filter_root(tb.lap[n + k2] + delta / d.c0);   // rare: FP64
+    if (active && !zcol) rho = rho_of(k2);
     V* E = smem;                  // [P][C] segment end values (causal pass)
     V* B = smem + P * C;          // [P][C] segment start values (anticausal pass)
     V* Zs = smem + 2 * P * C;     // [2][P] singular column: segment sums
@@ -200,6 +199,24 @@ __device__ __forceinline__ void col_solve_body(Ld&& ld, St&& st, const RDesc& d,
         block_sum2(ax, ay, red, sx, sy);
         if (tid == 0) { rho_part[0] = sx; rho_part[1] = sy; }
     }
+}
+
+// The column pass of the 2D pipeline: the root from the table (delta = 0)
+// or, rarely, computed in FP64 for the shift delta.
+template <typename V, int LOG2N, typename Ld, typename St>
+__device__ __forceinline__ void col_solve_body(Ld&& ld, St&& st, const RDesc& d, int c0,
+                                               V* smem, const Tables& tb, double delta,
+                                               double* red, double* rho_part,
+                                               typename ScalarOf<V>::T* csc) {
+    typedef typename ScalarOf<V>::T Ts;
+    constexpr int n = 1 << LOG2N;
+    col_solve_core<V, LOG2N>(
+        ld, st,
+        [&](int k2) -> Ts {
+            return (delta == 0.0) ? rho_table<Ts>(tb, n)[k2]
+                                  : (Ts)filter_root(tb.lap[n + k2] + delta / d.c0);
+        },
+        d, c0, smem, tb, delta, red, rho_part, csc);
 }
 
 }  // namespace rve

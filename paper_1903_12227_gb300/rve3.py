@@ -18,15 +18,17 @@ from .rve import CONSISTENT, Realization, RveError, _ptr, _require_cuda, _stream
 
 
 class Solve3Opts(ctypes.Structure):
-    """rve3_solve_opts (32 bytes); zero fields take the library defaults."""
-    _fields_ = [("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+    """rve3_solve_opts (40 bytes); zero fields take the library defaults."""
+    _fields_ = [("scheme", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
-                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double)]
 
 
 class Solve3Info(ctypes.Structure):
-    """rve3_solve_info (40 bytes)."""
+    """rve3_solve_info (48 bytes)."""
     _fields_ = [("iters", ctypes.c_int32 * 3), ("status", ctypes.c_int32),
+                ("refinements", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("relres", ctypes.c_double * 3)]
 
 
@@ -91,8 +93,9 @@ def as_batch3(b) -> Batch3:
     return b if isinstance(b, Batch3) else Batch3(b)
 
 
-def make_opts3(scheme=CONSISTENT, tol=1e-10, max_iter=0, delta=0.0, check_every=0) -> Solve3Opts:
-    return Solve3Opts(scheme, max_iter, tol, delta, check_every, 0)
+def make_opts3(scheme=CONSISTENT, precision=rve.FP64, tol=1e-10, max_iter=0, delta=0.0,
+               check_every=0, inner_tol=0.0) -> Solve3Opts:
+    return Solve3Opts(scheme, precision, max_iter, check_every, tol, delta, inner_tol)
 
 
 def workspace_size3(batch) -> int:
@@ -187,7 +190,8 @@ def decode_info(info: torch.Tensor) -> list:
     out = []
     for k in range(len(raw) // INFO3_BYTES):
         s = Solve3Info.from_buffer_copy(raw[k * INFO3_BYTES:(k + 1) * INFO3_BYTES])
-        out.append({"iters": list(s.iters), "status": int(s.status), "relres": list(s.relres)})
+        out.append({"iters": list(s.iters), "status": int(s.status),
+                    "refinements": int(s.refinements), "relres": list(s.relres)})
     return out
 
 
@@ -217,12 +221,12 @@ def profile_read() -> dict:
     return {PROFILE_KINDS[j]: (ms[j], int(cnt[j])) for j in range(k)}
 
 
-def homogenize(batch, scheme=CONSISTENT, tol=1e-10, delta=0.0, stream=None):
+def homogenize(batch, scheme=CONSISTENT, tol=1e-10, delta=0.0, precision=rve.FP64, stream=None):
     """Field, correctors and A_hom of every realization: (A [batch,3,3], info list)."""
     b = as_batch3(batch)
     mask = gen_field(b, stream=stream)
     ws = _ws(b, None, mask.device)
-    u, info = solve(b, mask=mask, opts=make_opts3(scheme=scheme, tol=tol, delta=delta), ws=ws,
-                    stream=stream)
+    u, info = solve(b, mask=mask, opts=make_opts3(scheme=scheme, precision=precision, tol=tol,
+                                                  delta=delta), ws=ws, stream=stream)
     A = a_hom(b, u, mask=mask, scheme=scheme, ws=ws, stream=stream)
     return A, decode_info(info)

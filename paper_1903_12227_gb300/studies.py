@@ -230,8 +230,10 @@ def dos_study(Ls=(4, 8), N=20, lam=0.5, alpha=0.25, m0=8, eta=0.05, K=512, vecto
 # 36 B on average over the four passes); the z solve reads and writes a
 # pair; the CG vector steps of one iteration move 144 B (u, r, p, q read and
 # u, r written; z, p read and p written) over two launches; the scalar
-# launches (one warp) move nothing.
+# launches (one warp) move nothing.  FP32 vectors (the mixed path's cycles)
+# halve the vector bytes.
 CUBE_BYTES = {"stiffness": 33.0, "lines": 36.0, "zsolve": 32.0, "vector": 72.0, "scalar": 0.0}
+CUBE_BYTES_FP32 = {"stiffness": 17.0, "lines": 18.0, "zsolve": 16.0, "vector": 36.0, "scalar": 0.0}
 
 
 def _measured_hbm():
@@ -244,50 +246,66 @@ def _measured_hbm():
         return None
 
 
-def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=4, contrast=10.0, seed=0, tol=1e-10,
-                scheme=rve.CONSISTENT) -> list:
+def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=None, contrast=10.0, seed=0, tol=1e-10,
+                scheme=rve.CONSISTENT, precisions=(rve.FP64, rve.MIXED)) -> list:
     """3D extension: N realizations of round(0.7 L^3) unit cubes on
     [0,L)^3 (n = L m0 nodes per axis) per L: time per realization (field,
     three correctors, A_hom; CUDA events), iterations, per-kernel-kind
     launch times with their algorithmic bandwidth, and the mean and spread
-    of the diagonal of the 3x3 A_hom."""
+    of the diagonal of the 3x3 A_hom.  N defaults to about 64 M nodes per
+    batch (at least 2 realizations): all of a batch run in the same launches."""
     import torch
     from . import rve3
     peak = _measured_hbm()
     rows = []
-    for L in Ls:
-        descs = [workloads.realization3(L, m0, contrast, seed, k) for k in range(N)]
+    for L, prec in [(L, p) for L in Ls for p in precisions]:
         n = L * m0
+        NL = N or max(2, (64 << 20) // n ** 3)
+        descs = [workloads.realization3(L, m0, contrast, seed, k) for k in range(NL)]
         nodes = n ** 3
-        rve3.homogenize(descs[:1], scheme=scheme, tol=tol)   # warm-up (module load, tables)
+        rve3.homogenize(descs[:1], scheme=scheme, tol=tol, precision=prec)   # warm-up
         torch.cuda.synchronize()
         rve.profile_enable(True)
         rve3.profile_read()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        A, infos = rve3.homogenize(descs, scheme=scheme, tol=tol)
+        A, infos = rve3.homogenize(descs, scheme=scheme, tol=tol, precision=prec)
         e1.record()
         torch.cuda.synchronize()
         rve.profile_enable(False)
         prof = rve3.profile_read()
         ms = e0.elapsed_time(e1)
+        # a launch covers every unit (pair of a realization) of the batch, but
+        # the blocks of units that have converged return at once: scale the
+        # bytes by the fraction of unit-steps that did work (CG steps of the
+        # units over stiffness launches x units)
+        units = 2 * NL
+        unit_steps = sum(max(i["iters"][0], i["iters"][1]) + i["iters"][2] for i in infos)
+        stiff_launches = max(prof["stiffness"][1], 1)
+        active = min(1.0, unit_steps / (stiff_launches * units))
         kinds = {}
         for kind, (t, cnt) in prof.items():
-            gbs = CUBE_BYTES[kind] * nodes * cnt / (t * 1e-3) / 1e9 if t > 0 and CUBE_BYTES[kind] else None
+            # mixed: nearly every launch is an FP32 one (a few FP64 refinements)
+            per = (CUBE_BYTES if prec == rve.FP64 else CUBE_BYTES_FP32)[kind]
+            nodes_launch = units * nodes * active
+            gbs = per * nodes_launch * cnt / (t * 1e-3) / 1e9 if t > 0 and per else None
             kinds[kind] = {"ms": round(t, 3), "launches": cnt,
                            "us_per_launch": round(1e3 * t / cnt, 2) if cnt else None,
                            "GBs": round(gbs, 1) if gbs else None,
                            "frac_of_measured": round(gbs / peak, 3) if gbs and peak else None}
         Ad = A.diagonal(dim1=1, dim2=2).cpu().numpy()
-        rows.append({"L": L, "m0": m0, "n": n, "N": N, "contrast": contrast, "tol": tol,
-                     "ms_per_realization": round(ms / N, 3),
-                     "realizations_per_s": round(1e3 * N / ms, 3),
+        rows.append({"L": L, "m0": m0, "n": n, "N": NL, "contrast": contrast, "tol": tol,
+                     "precision": "fp64" if prec == rve.FP64 else "mixed",
+                     "refinements_mean": float(np.mean([i["refinements"] for i in infos])),
+                     "ms_per_realization": round(ms / NL, 3),
+                     "realizations_per_s": round(1e3 * NL / ms, 3),
                      "iters_mean": float(np.mean([np.mean(i["iters"]) for i in infos])),
                      "max_relres": float(max(max(i["relres"]) for i in infos)),
                      "status": sorted({i["status"] for i in infos}),
                      "A_diag_mean": float(Ad.mean()), "A_diag_std": float(Ad.std()),
                      "offdiag_max": float(np.abs(A.cpu().numpy() - np.einsum(
                          "bi,ij->bij", Ad, np.eye(3))).max()),
+                     "active_unit_fraction": round(active, 3),
                      "kernels": kinds, "hbm_peak_GBs": peak})
     return rows
 
@@ -300,9 +318,12 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--count", choices=["fixed", "poisson"], default="fixed")
     ap.add_argument("--json")
+    ap.add_argument("--prec", choices=["both", "fp64", "mixed"], default="both",
+                    help="cubes: which solver precision(s) to measure")
     a = ap.parse_args(argv)
     if a.study == "cubes":
-        rows = cubes_study(Ls=tuple(a.Ls or (2, 4, 8, 16)), N=a.N or 4, seed=a.seed)
+        precs = {"both": (rve.FP64, rve.MIXED), "fp64": (rve.FP64,), "mixed": (rve.MIXED,)}[a.prec]
+        rows = cubes_study(Ls=tuple(a.Ls or (2, 4, 8, 16)), N=a.N, seed=a.seed, precisions=precs)
     elif a.study == "dos":
         rows = dos_study(Ls=tuple(a.Ls or (4, 8)), N=a.N or 20, seed=a.seed)
     elif a.study == "fem":

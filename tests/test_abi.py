@@ -43,8 +43,8 @@ def test_struct_sizes_match_header(librve):
     assert ctypes.sizeof(rve.SolveInfo) == 40
     assert ctypes.sizeof(rve.SolveOpts) == 64
     from paper_1903_12227_gb300 import rve3
-    assert ctypes.sizeof(rve3.Solve3Opts) == 32
-    assert ctypes.sizeof(rve3.Solve3Info) == 40
+    assert ctypes.sizeof(rve3.Solve3Opts) == 40
+    assert ctypes.sizeof(rve3.Solve3Info) == 48
 
 
 def test_host_validation_without_gpu(librve):
@@ -88,8 +88,11 @@ def test_host_validation_3d_without_gpu(librve):
     # missing pointers are rejected before any launch
     ws = ctypes.c_void_p(None)
     assert L3.rve3_solve_correctors(b.ptr, 3, None, None, None, None, None, ws, 0, None) == rve.RVE_EINVAL
-    bad_opts = rve3.Solve3Opts(7, 0, 1e-10, 0.0, 0, 0)
+    bad_opts = rve3.make_opts3(scheme=7)
     assert L3.rve3_solve_correctors(b.ptr, 3, None, None, ctypes.byref(bad_opts), None, None, ws, 0,
+                                    None) == rve.RVE_EINVAL
+    bad_prec = rve3.make_opts3(precision=5)
+    assert L3.rve3_solve_correctors(b.ptr, 3, None, None, ctypes.byref(bad_prec), None, None, ws, 0,
                                     None) == rve.RVE_EINVAL
 
 
