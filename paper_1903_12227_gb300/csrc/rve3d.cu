@@ -65,7 +65,7 @@ __host__ __device__ __forceinline__ double e3(int a, int b, double h) {
 
 // Descriptor of one unit (a corrector pair of a realization).
 struct U3 {
-    int32_t n, log2n, pair, tC;
+    int32_t n, log2n, pair, pad2;
     int32_t n_incl, s, pad0, pad1;
     int64_t off;        // first node of the unit's vectors
     int64_t cell_off;   // first cell (= node) of the realization: mask, coef, ABI vectors
@@ -105,6 +105,37 @@ template <> __device__ __forceinline__ double two_values<double>(const U3& d, bo
 template <> __device__ __forceinline__ float two_values<float>(const U3& d, bool incl) { return incl ? d.ai32 : d.am32; }
 
 constexpr int T3 = 256;   // threads of the node kernels
+constexpr int SZ = 4;     // stencil: consecutive planes per thread
+constexpr int Z_THREADS = 512;   // z solve
+
+// Block sums of two per-thread values (x, y), valid in thread 0: an xor
+// butterfly within each warp in the values' own precision, then the warp
+// sums in FP64 in warp order (fixed order: deterministic).  A thread's
+// value sums only its own few nodes, so an FP32 tree stays short.
+// `red` holds 2 * (blockDim.x / 32) doubles.
+template <typename T>
+__device__ __forceinline__ void block_pair_sum(T x, T y, double* red, double& sx, double& sy) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[2 * wid] = (double)x;
+        red[2 * wid + 1] = (double)y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[2 * w];
+            b += red[2 * w + 1];
+        }
+        sx = a;
+        sy = b;
+    }
+}
 
 // --------------------------------------------------------------- field --
 // One thread per (cube, row d1, d2): sets the s cells along the third axis.
@@ -132,9 +163,13 @@ __global__ void k3_gen_field(const U3 d, uint8_t* __restrict__ mask) {
 // So the assembled row of node i couples neighbour i+o (o in {-1,0,1}^3)
 // with e_{|o|} times the sum of a_c over the cells holding both nodes: all 8
 // for o = 0, 4 for a face neighbour, 2 for an edge neighbour (a pair sum
-// along the axis where o is 0), 1 for a corner neighbour.  About 60
-// arithmetic operations per node and pair instead of 144 for the 8 element
-// rows.  Neighbour addresses come from the 9 wrapped row starts.
+// along the axis where o is 0), 1 for a corner neighbour: about 60
+// operations per node and pair instead of 144 for the 8 element rows.
+// A block takes SZ consecutive planes of TJ = 256 / n whole rows: it first
+// copies the planes i0-1 .. i0+SZ, rows j0-1 .. j0+TJ (whole periodic rows)
+// of x and the cell values of planes i0-1 .. i0+SZ-1, rows j0-1 .. j0+TJ-1
+// into shared memory with coalesced loads, then each thread computes its
+// SZ nodes (one (j, k), SZ planes) from there.
 //   MODE_APPLY: y = A x, partials of x.y per component (the p.q of CG);
 //   MODE_RESID: y = f - A x (the true residual), partials of |y|^2.
 // Blocks of units whose flag (`done`, or `outer_done` for MODE_RESID) is
@@ -143,104 +178,161 @@ enum { MODE_APPLY = 0, MODE_RESID = 1 };
 struct MixScal;
 __device__ __forceinline__ bool unit_skip(const MixScal* sc, int u, bool outer);
 
+// Shared memory of a stiffness block for grids of n = 2^lg.
+template <typename V>
+__host__ __device__ constexpr size_t stiff_smem(int lg) {
+    return (size_t)(SZ + 2) * ((T3 >> lg) + 2) * ((size_t)1 << lg) * sizeof(V) +
+           (size_t)(SZ + 1) * ((T3 >> lg) + 1) * ((size_t)1 << lg) * (sizeof(V) / 2);
+}
+
 template <int SCHEME, int MODE, typename V>
 __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename ScalarOf<V>::T> cs,
                                                    const V* __restrict__ x, V* __restrict__ y,
                                                    const V* __restrict__ f, double* part,
                                                    const MixScal* sc) {
     typedef typename ScalarOf<V>::T T;
-    __shared__ double red[32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
     if (sc && unit_skip(sc, u, MODE == MODE_RESID)) return;
     const U3& d = g.desc[u];
-    const int local = lb * T3 + threadIdx.x;
     const int n = d.n, m = n - 1, lg = d.log2n;
-    const int i = local >> (2 * lg), j = (local >> lg) & m, k = local & m;
-    int row[3][3];   // start of node row (i + a - 1, j + b - 1)
+    const int TJ = T3 >> lg;                          // rows of the block
+    const int first = lb * T3;                        // (plane group, j0, 0)
+    const int i0 = (first >> (2 * lg)) * SZ;
+    const int j0 = (first >> lg) & m;
+    const int jl = threadIdx.x >> lg, k = threadIdx.x & m;
+    const int RW = TJ + 2, CR = TJ + 1;               // rows of the x and cell tiles
+    V* xt = reinterpret_cast<V*>(smem_raw);                          // [SZ+2][RW][n]
+    T* ct = reinterpret_cast<T*>(xt + (SZ + 2) * RW * n);            // [SZ+1][CR][n]
+    const V* __restrict__ xu = x + d.off;
+    const T am = two_values<T>(d, false), ai = two_values<T>(d, true);
+    // thread (jl, k) copies element k of tile rows jl, jl + TJ, jl + 2 TJ (those
+    // below RW, resp. CR) of each plane: every load is issued before the
+    // first shared-memory store, so a block waits for one round trip
+    V xr[SZ + 2][3];
+    T cr[SZ + 1][2];
+    const uint8_t* __restrict__ mk8 = cs.mask + d.cell_off;
+    const T* __restrict__ cf = cs.coef ? cs.coef + d.cell_off : nullptr;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int pl = 0; pl < SZ + 2; ++pl) {
+        const int gp = ((i0 - 1 + pl) & m) << (2 * lg);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) row[a][b] = ((((i + a - 1) & m) << lg) + ((j + b - 1) & m)) << lg;
-    const int kk[3] = {(k - 1) & m, k, (k + 1) & m};
-    const V* xu = x + d.off;
-    auto X = [&](int o1, int o2, int o3) { return xu[row[o1 + 1][o2 + 1] + kk[o3 + 1]]; };
-    T a[8];   // a[c]: the cell at offset (-c1, -c2, -c3), c = 4 c1 + 2 c2 + c3
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int idx = row[1 - (c >> 2)][1 - ((c >> 1) & 1)] + kk[1 - (c & 1)];
-        a[c] = cs.coef ? cs.coef[d.cell_off + idx] : two_values<T>(d, cs.mask[d.cell_off + idx] != 0);
+        for (int q = 0; q < 3; ++q) {
+            const int rr = jl + q * TJ;
+            if (rr < RW) xr[pl][q] = xu[gp + (((j0 - 1 + rr) & m) << lg) + k];
+        }
     }
-    // pair sums along each axis, indexed by the other two corner bits
-    T px[4], py[4], pz[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        px[q] = a[q] + a[4 + q];                                             // q = 2 c2 + c3
-        py[q] = a[4 * (q >> 1) + (q & 1)] + a[4 * (q >> 1) + 2 + (q & 1)];   // q = 2 c1 + c3
-        pz[q] = a[2 * q] + a[2 * q + 1];                                     // q = 2 c1 + c2
+    for (int pl = 0; pl < SZ + 1; ++pl) {
+        const int gp = ((i0 - 1 + pl) & m) << (2 * lg);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int rr = jl + q * TJ;
+            if (rr < CR) {
+                const int idx = gp + (((j0 - 1 + rr) & m) << lg) + k;
+                cr[pl][q] = cf ? cf[idx] : (mk8[idx] ? ai : am);
+            }
+        }
     }
-    const T A0 = (px[0] + px[1]) + (px[2] + px[3]);
+#pragma unroll
+    for (int pl = 0; pl < SZ + 2; ++pl)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int rr = jl + q * TJ;
+            if (rr < RW) xt[(pl * RW + rr) * n + k] = xr[pl][q];
+        }
+#pragma unroll
+    for (int pl = 0; pl < SZ + 1; ++pl)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int rr = jl + q * TJ;
+            if (rr < CR) ct[(pl * CR + rr) * n + k] = cr[pl][q];
+        }
+    __syncthreads();
+    const int km = (k - 1) & m, kp = (k + 1) & m;
+    auto X = [&](int t, int o1, int o2, int o3) -> V {
+        const int kk = o3 < 0 ? km : (o3 == 0 ? k : kp);
+        return xt[((t + 1 + o1) * RW + (jl + 1 + o2)) * n + kk];
+    };
     const T h = (T)d.h;
     // the cell bit that a neighbour offset fixes on its axis: +1 -> 0, -1 -> 1
     auto cb = [](int o) { return o > 0 ? 0 : 1; };
-    const V xc = X(0, 0, 0);
-    V acc;
-    if (SCHEME == RVE_Q1_CONSISTENT) {
-        T sx = 0, sy = 0;
+    T dx = 0, dy = 0;
 #pragma unroll
-        for (int e = 0; e < 12; ++e) {   // edge neighbours: o zero on one axis
-            const int zax = e >> 2, s1 = (e & 2) ? 1 : -1, s2 = (e & 1) ? 1 : -1;
-            V v;
-            T w;
-            if (zax == 0) { v = X(0, s1, s2); w = px[2 * cb(s1) + cb(s2)]; }
-            else if (zax == 1) { v = X(s1, 0, s2); w = py[2 * cb(s1) + cb(s2)]; }
-            else { v = X(s1, s2, 0); w = pz[2 * cb(s1) + cb(s2)]; }
-            sx = fma(w, v.x, sx);
-            sy = fma(w, v.y, sy);
-        }
+    for (int t = 0; t < SZ; ++t) {
+        T a[8];   // a[c]: the cell at offset (-c1, -c2, -c3), c = 4 c1 + 2 c2 + c3
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {    // corner neighbours: one cell each
-            const int o1 = (c & 4) ? 1 : -1, o2 = (c & 2) ? 1 : -1, o3 = (c & 1) ? 1 : -1;
-            const T w = a[4 * cb(o1) + 2 * cb(o2) + cb(o3)];
-            const V v = X(o1, o2, o3);
-            sx = fma(w, v.x, sx);
-            sy = fma(w, v.y, sy);
-        }
-        const T e0 = h * (T)(1.0 / 3.0), e23 = -h * (T)(1.0 / 12.0);
-        acc.x = fma(e23, sx, e0 * A0 * xc.x);
-        acc.y = fma(e23, sy, e0 * A0 * xc.y);
-    } else {
-        T sx = 0, sy = 0;
+        for (int c = 0; c < 8; ++c)
+            a[c] = ct[((t + 1 - (c >> 2)) * CR + (jl + 1 - ((c >> 1) & 1))) * n + ((c & 1) ? km : k)];
+        T px[4], py[4], pz[4];   // pair sums along each axis, by the other two bits
 #pragma unroll
-        for (int fc = 0; fc < 6; ++fc) {  // face neighbours: 4 cells with the bit fixed
-            const int ax = fc >> 1, sg = (fc & 1) ? 1 : -1, v0 = cb(sg);
-            V v;
-            T w;
-            if (ax == 0) { v = X(sg, 0, 0); w = pz[2 * v0] + pz[2 * v0 + 1]; }
-            else if (ax == 1) { v = X(0, sg, 0); w = pz[v0] + pz[2 + v0]; }
-            else { v = X(0, 0, sg); w = py[v0] + py[2 + v0]; }
-            sx = fma(w, v.x, sx);
-            sy = fma(w, v.y, sy);
+        for (int q = 0; q < 4; ++q) {
+            px[q] = a[q] + a[4 + q];                                             // q = 2 c2 + c3
+            py[q] = a[4 * (q >> 1) + (q & 1)] + a[4 * (q >> 1) + 2 + (q & 1)];   // q = 2 c1 + c3
+            pz[q] = a[2 * q] + a[2 * q + 1];                                     // q = 2 c1 + c2
         }
-        const T e0 = h * (T)0.75, e1 = -h * (T)0.25;
-        acc.x = fma(e1, sx, e0 * A0 * xc.x);
-        acc.y = fma(e1, sy, e0 * A0 * xc.y);
+        const T A0 = (px[0] + px[1]) + (px[2] + px[3]);
+        const V xc = X(t, 0, 0, 0);
+        V acc;
+        if (SCHEME == RVE_Q1_CONSISTENT) {
+            T sx = 0, sy = 0;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) {   // edge neighbours: o zero on one axis
+                const int zax = e >> 2, s1 = (e & 2) ? 1 : -1, s2 = (e & 1) ? 1 : -1;
+                V v;
+                T wgt;
+                if (zax == 0) { v = X(t, 0, s1, s2); wgt = px[2 * cb(s1) + cb(s2)]; }
+                else if (zax == 1) { v = X(t, s1, 0, s2); wgt = py[2 * cb(s1) + cb(s2)]; }
+                else { v = X(t, s1, s2, 0); wgt = pz[2 * cb(s1) + cb(s2)]; }
+                sx = fma(wgt, v.x, sx);
+                sy = fma(wgt, v.y, sy);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {    // corner neighbours: one cell each
+                const int o1 = (c & 4) ? 1 : -1, o2 = (c & 2) ? 1 : -1, o3 = (c & 1) ? 1 : -1;
+                const T wgt = a[4 * cb(o1) + 2 * cb(o2) + cb(o3)];
+                const V v = X(t, o1, o2, o3);
+                sx = fma(wgt, v.x, sx);
+                sy = fma(wgt, v.y, sy);
+            }
+            const T e0 = h * (T)(1.0 / 3.0), e23 = -h * (T)(1.0 / 12.0);
+            acc.x = fma(e23, sx, e0 * A0 * xc.x);
+            acc.y = fma(e23, sy, e0 * A0 * xc.y);
+        } else {
+            T sx = 0, sy = 0;
+#pragma unroll
+            for (int fc = 0; fc < 6; ++fc) {  // face neighbours: 4 cells with the bit fixed
+                const int ax = fc >> 1, sg = (fc & 1) ? 1 : -1, v0 = cb(sg);
+                V v;
+                T wgt;
+                if (ax == 0) { v = X(t, sg, 0, 0); wgt = pz[2 * v0] + pz[2 * v0 + 1]; }
+                else if (ax == 1) { v = X(t, 0, sg, 0); wgt = pz[v0] + pz[2 + v0]; }
+                else { v = X(t, 0, 0, sg); wgt = py[v0] + py[2 + v0]; }
+                sx = fma(wgt, v.x, sx);
+                sy = fma(wgt, v.y, sy);
+            }
+            const T e0 = h * (T)0.75, e1 = -h * (T)0.25;
+            acc.x = fma(e1, sx, e0 * A0 * xc.x);
+            acc.y = fma(e1, sy, e0 * A0 * xc.y);
+        }
+        const int64_t node = d.off + ((int64_t)(i0 + t) << (2 * lg)) + ((j0 + jl) << lg) + k;
+        if (MODE == MODE_RESID) {
+            const V ff = f[node];
+            acc.x = ff.x - acc.x;
+            acc.y = ff.y - acc.y;
+            dx = fma(acc.x, acc.x, dx);
+            dy = fma(acc.y, acc.y, dy);
+        } else {
+            dx = fma(xc.x, acc.x, dx);
+            dy = fma(xc.y, acc.y, dy);
+        }
+        y[node] = acc;
     }
-    DotAcc<T> dx, dy;
-    if (MODE == MODE_RESID) {
-        const V ff = f[d.off + local];
-        acc.x = ff.x - acc.x;
-        acc.y = ff.y - acc.y;
-        dx.add(acc.x, acc.x);
-        dy.add(acc.y, acc.y);
-    } else {
-        dx.add(xc.x, acc.x);
-        dy.add(xc.y, acc.y);
-    }
-    y[d.off + local] = acc;
     if (part) {   // block-uniform
         double tx = 0.0, ty = 0.0;
-        block_sum2(dx, dy, red, tx, ty);
+        block_pair_sum(dx, dy, red, tx, ty);
         if (threadIdx.x == 0) {
             part[d.part_off + 2 * lb] = tx;
             part[d.part_off + 2 * lb + 1] = ty;
@@ -303,10 +395,13 @@ __global__ void __launch_bounds__(T3) k3_rhs(Grp g, Cells3T<double> cs, double2*
 // ------------------------------------------------------ preconditioner --
 // Hartley transform of lines of n nodes (pair-packed complex FFT, register
 // Stockham, see rve_device.cuh): dst = scale H src (src may equal dst).
-// AXIS 2: x lines (contiguous), threads of a line side by side; AXIS 1: y
-// lines (stride n), the lines of a block side by side so that each load
-// instruction reads consecutive nodes.  With `rd` set, also the block's
-// partials of rd.dst per component (the r.z of CG).
+// AXIS 2: x lines (contiguous), threads of a line side by side, one padded
+// buffer per line; AXIS 1: y lines (stride n), the G lines of a block side
+// by side so that each load instruction reads consecutive nodes, and their
+// buffers interleaved element by element so that the lanes of a warp (G
+// consecutive lines at the same element) touch consecutive words.  With
+// `rd` set, also the block's partials of rd.dst per component (the r.z of
+// CG).
 template <int LOG2N, int AXIS, typename V>
 __global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, V* dst,
                                                 typename ScalarOf<V>::T scale,
@@ -314,13 +409,13 @@ __global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, 
                                                 const MixScal* sc) {
     typedef typename ScalarOf<V>::T T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
     if (sc && unit_skip(sc, u, false)) return;
     const U3& d = g.desc[u];
-    constexpr int n = 1 << LOG2N, TL = n / 8;
-    const int G = blockDim.x / TL;
+    constexpr int n = 1 << LOG2N, TL = n / 8, G = 256 / TL;
+    constexpr int BS = AXIS == 2 ? 1 : G;
     int q, t;
     if (AXIS == 2) { q = threadIdx.x / TL; t = threadIdx.x - q * TL; }
     else { t = threadIdx.x / G; q = threadIdx.x - t * G; }
@@ -328,27 +423,27 @@ __global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, 
     int64_t base, stride;
     if (AXIS == 2) { base = d.off + (int64_t)line * n; stride = 1; }
     else { base = d.off + (int64_t)(line / n) * n * n + (line % n); stride = n; }
-    V* buf = reinterpret_cast<V*>(smem_raw) + q * seq_stride(n);
+    V* buf = reinterpret_cast<V*>(smem_raw) + (AXIS == 2 ? q * seq_stride(n) : q);
     V w[8];
 #pragma unroll
     for (int mm = 0; mm < 8; ++mm) w[mm] = src[base + (t + mm * TL) * stride];
-    fft_reg<FFT_TO_BOTH, LOG2N>(w, buf, LOG2N, t, twiddles<V>(tb, n), true);
-    DotAcc<T> ax, ay;
+    fft_reg<FFT_TO_BOTH, LOG2N, BS>(w, buf, LOG2N, t, twiddles<V>(tb, n), true);
+    T ax = 0, ay = 0;
 #pragma unroll
     for (int mm = 0; mm < 8; ++mm) {
         const int kx = t + mm * TL;
-        const V hv = hartley_pair(w[mm], buf[pidx((n - kx) & (n - 1))]);
+        const V hv = hartley_pair(w[mm], buf[pidx((n - kx) & (n - 1)) * BS]);
         const V o = mk<V>(scale * hv.x, scale * hv.y);
         dst[base + (int64_t)kx * stride] = o;
         if (rd) {
             const V r = rd[base + (int64_t)kx * stride];
-            ax.add(r.x, o.x);
-            ay.add(r.y, o.y);
+            ax = fma(r.x, o.x, ax);
+            ay = fma(r.y, o.y, ay);
         }
     }
     if (rd) {   // block-uniform
         double sx = 0.0, sy = 0.0;
-        block_sum2(ax, ay, red, sx, sy);
+        block_pair_sum(ax, ay, red, sx, sy);
         if (threadIdx.x == 0) {
             part[d.part_off + 2 * lb] = sx;
             part[d.part_off + 2 * lb + 1] = sy;
@@ -356,16 +451,21 @@ __global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, 
     }
 }
 
-// Tridiagonal solves along z for the lines (kx = c0 .. c0+C-1, ky =
-// blockIdx.y) after the x and y transforms; writes M^{-1} t / n in place.
-// The filter root of (kx, ky) solves rho + 1/rho = 2 + lambda(kx) +
-// lambda(ky) + delta / c0, evaluated in the vector's precision.
+// Tridiagonal solves along z after the x and y transforms; writes M^{-1} t
+// / n in place.  The n^2 columns (kx, ky) of a unit are numbered kc = ky n +
+// kx, so column kc, row r sits at r n^2 + kc; a block takes ZC consecutive
+// columns (ZSEG rows per thread, ZC x n / ZSEG = 512 threads).  The filter
+// root of (kx, ky) solves rho + 1/rho = 2 + lambda(kx) + lambda(ky) + delta
+// / c0, evaluated in the vector's precision; column 0 with delta = 0 is the
+// singular one.
+constexpr int ZSEG = 16;
+template <int LOG2N> __host__ __device__ constexpr int zcols() { return Z_THREADS / ((1 << LOG2N) / ZSEG); }
 template <typename T> __device__ __forceinline__ T filter_root_t(T mu) {
     return (T)1 / ((T)1 + (T)0.5 * mu + sqrt(mu * ((T)1 + (T)0.25 * mu)));
 }
 template <int LOG2N, typename V>
-__global__ void __launch_bounds__(512) k3_zsolve(Grp g, Tables tb, double delta, V* __restrict__ v,
-                                                 const MixScal* sc) {
+__global__ void __launch_bounds__(Z_THREADS) k3_zsolve(Grp g, Tables tb, double delta,
+                                                       V* __restrict__ v, const MixScal* sc) {
     typedef typename ScalarOf<V>::T T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[64];
@@ -374,21 +474,23 @@ __global__ void __launch_bounds__(512) k3_zsolve(Grp g, Tables tb, double delta,
     const int u = unit_of(g, lb);
     if (sc && unit_skip(sc, u, false)) return;
     const U3& d = g.desc[u];
-    constexpr int n = 1 << LOG2N;
+    constexpr int n = 1 << LOG2N, NN = n * n, ZC = zcols<LOG2N>();
     RDesc cd;          // the two fields the column solve reads
-    cd.tC = d.tC;
+    cd.tC = ZC;
     cd.c0 = d.c0;
-    const int ky = blockIdx.y, c0 = lb * d.tC;
-    const double delta_eff = delta + d.c0 * tb.lap[n + ky];   // the y shift folded in
+    const int c0 = lb * ZC;
     const T* lapT = lap_table<T>(tb, n);
-    const T muy = lapT[ky] + (T)(delta / d.c0);
-    const bool plain = delta_eff == 0.0;   // ky = 0 and delta = 0: the 1D roots
+    const T dc = (T)(delta / d.c0);
     V* vu = v + d.off;
-    col_solve_core<V, LOG2N>(
-        [&](int r, int kx) { return vu[((r * n + ky) * n) + kx]; },
-        [&](int r, int kx, V val) { vu[((r * n + ky) * n) + kx] = val; },
-        [&](int kx) -> T { return plain ? rho_table<T>(tb, n)[kx] : filter_root_t<T>(lapT[kx] + muy); },
-        cd, c0, reinterpret_cast<V*>(smem_raw), tb, delta_eff, red, nullptr, csc);
+    col_solve_core<V, LOG2N, true, ZSEG>(
+        [&](int r, int kc) { return vu[r * NN + kc]; },
+        [&](int r, int kc, V val) { vu[r * NN + kc] = val; },
+        [&](int kc) -> T {
+            const int ky = kc >> LOG2N, kx = kc & (n - 1);
+            return (ky == 0 && delta == 0.0) ? rho_table<T>(tb, n)[kx]
+                                             : filter_root_t<T>(lapT[kx] + lapT[ky] + dc);
+        },
+        cd, c0, reinterpret_cast<V*>(smem_raw), tb, delta, red, nullptr, csc);
 }
 
 // ------------------------------------------------------------- A_hom --
@@ -537,9 +639,10 @@ enum { M_FNORM = 0, M_REFINE, M_RHO0, M_ALPHA, M_CONV, M_BETA };
 constexpr int MAX_REFINE = 100;
 constexpr int MAX_STALL = 4;
 
-// The scalar steps: one block per unit reduces the unit's `nb` partial
-// pairs in a fixed order (per-thread strided sums, then the block tree) and
-// thread 0 applies `what`.  `tfac`: the cycle target is max(tfac tol |f| /
+// The scalar steps: one block per unit reduces the unit's partial pairs (n^3
+// >> pshift of them: one per block of the kernel that wrote them) in a fixed
+// order (per-thread strided sums, then the block tree) and thread 0 applies
+// `what`.  `tfac`: the cycle target is max(tfac tol |f| /
 // |r64|, inner_tol).
 struct ScalArgs {
     double tol, inner_tol, tfac;
@@ -548,21 +651,14 @@ struct ScalArgs {
 __global__ void __launch_bounds__(256) k3_scalar(const int32_t* __restrict__ ids,
                                                  const U3* __restrict__ desc, MixScal* scs,
                                                  const double* __restrict__ part, int what,
-                                                 ScalArgs a) {
+                                                 int pshift, ScalArgs a) {
     __shared__ double red[32];
     const int u = ids[blockIdx.x];
     MixScal* sc = scs + u;
     const U3& d = desc[u];
     if (what != M_FNORM && what != M_REFINE && sc->done) return;
     if (what == M_REFINE && sc->outer_done) return;
-    const int64_t nodes = (int64_t)d.n * d.n * d.n;
-    int nb;
-    switch (what) {
-        case M_RHO0:
-        case M_BETA: nb = (int)(nodes / 2048); break;   // last line pass (n^2 / G blocks)
-        case M_CONV: nb = (int)(nodes / (4 * T3)); break;
-        default: nb = (int)(nodes / T3); break;
-    }
+    const int nb = (int)(((int64_t)d.n * d.n * d.n) >> pshift);   // partial pairs written
     const double* pp = part + d.part_off;
     double tx = 0.0, ty = 0.0;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
@@ -686,14 +782,14 @@ __global__ void __launch_bounds__(T3) k3_axpy(Grp g, const MixScal* scs, V* __re
                                               V* __restrict__ r, const V* __restrict__ p,
                                               const V* __restrict__ q, double* part) {
     typedef typename ScalarOf<V>::T T;
-    __shared__ double red[32];
+    __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
     const MixScal& sc = scs[u];
     if (sc.done) return;
     const U3& d = g.desc[u];
     const T ax_ = alpha_of<T>(sc, 0), ay_ = alpha_of<T>(sc, 1);
-    DotAcc<T> sx, sy;
+    T sx = 0, sy = 0;
 #pragma unroll
     for (int mm = 0; mm < 4; ++mm) {
         const int64_t node = d.off + (int64_t)lb * (4 * T3) + mm * T3 + threadIdx.x;
@@ -705,11 +801,11 @@ __global__ void __launch_bounds__(T3) k3_axpy(Grp g, const MixScal* scs, V* __re
         rr.y = fma(-ay_, qq.y, rr.y);
         e[node] = ee;
         r[node] = rr;
-        sx.add(rr.x, rr.x);
-        sy.add(rr.y, rr.y);
+        sx = fma(rr.x, rr.x, sx);
+        sy = fma(rr.y, rr.y, sy);
     }
     double tx = 0.0, ty = 0.0;
-    block_sum2(sx, sy, red, tx, ty);
+    block_pair_sum(sx, sy, red, tx, ty);
     if (threadIdx.x == 0) {
         part[d.part_off + 2 * lb] = tx;
         part[d.part_off + 2 * lb + 1] = ty;
@@ -832,13 +928,7 @@ static void prof3_sync(cudaStream_t s) {
 
 // ---------------------------------------------------------------- host --
 constexpr int N3_MIN = 32, N3_MAX = 256;
-constexpr int Z_THREADS = 512;
 constexpr int NVEC = 8;   // unit vectors: f, u, r64, and the cycle's r, z, p, e, q
-
-static int col_tile3(int n) {   // columns of a z-solve block (16 segments per column)
-    const int P = n / col_seg_rows(n, 16);
-    return std::min(n, Z_THREADS / P);
-}
 
 struct Group3 {
     int log2n = 0;
@@ -887,7 +977,6 @@ static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) 
             d.n = n;
             d.log2n = 31 - __builtin_clz((unsigned)n);
             d.pair = pair;
-            d.tC = col_tile3(n);
             d.n_incl = x.n_incl;
             d.s = x.incl_cells;
             d.cell_off = p.nodes;
@@ -996,9 +1085,8 @@ static cudaError_t precond3_t(const Ws3& ws, const Group3& g, double delta, cons
     const int G = 256 / TL;
     const size_t smem = (size_t)G * seq_stride(n) * sizeof(V);
     const int lines = (n * n) / G;
-    const int tC = col_tile3(n);
-    const int P = n / col_seg_rows(n, (int)sizeof(V));
-    const size_t zsmem = (size_t)(2 * tC + 2) * P * sizeof(V);
+    constexpr int ZC = zcols<LG>(), ZP = n / ZSEG;
+    const size_t zsmem = (size_t)(2 * ZC + 2) * ZP * sizeof(V);
     cudaError_t e = cudaFuncSetAttribute(k3_lines<LG, 2, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k3_lines<LG, 1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1017,8 +1105,8 @@ static cudaError_t precond3_t(const Ws3& ws, const Group3& g, double delta, cons
     }
     {
         Span3 sp(s, P3_ZSOLVE);
-        k3_zsolve<LG, V><<<dim3(nblocks(g, n / tC), (unsigned)n), Z_THREADS, zsmem, s>>>(
-            ws.grp(g, n / tC), tb, delta, dst, sc);
+        k3_zsolve<LG, V><<<nblocks(g, n * n / ZC), Z_THREADS, zsmem, s>>>(
+            ws.grp(g, n * n / ZC), tb, delta, dst, sc);
     }
     {
         Span3 sp(s, P3_LINES);
@@ -1047,14 +1135,15 @@ template <int MODE, typename V>
 static cudaError_t stiffness3(const Ws3& ws, const Group3& g, Cells3T<typename ScalarOf<V>::T> cs,
                               int scheme, const V* x, V* y, const V* f, bool partials,
                               const MixScal* sc, cudaStream_t s) {
-    Span3 sp(s, P3_STIFF);
-    const int per = (int)(nodes_of(g) / T3);
+    const int per = (int)(nodes_of(g) / (T3 * SZ));
     const Grp gg = ws.grp(g, per);
     double* part = partials ? ws.part() : nullptr;
-    if (scheme == RVE_Q1_LUMPED)
-        k3_stiffness<1, MODE, V><<<nblocks(g, per), T3, 0, s>>>(gg, cs, x, y, f, part, sc);
-    else
-        k3_stiffness<0, MODE, V><<<nblocks(g, per), T3, 0, s>>>(gg, cs, x, y, f, part, sc);
+    const size_t smem = stiff_smem<V>(g.log2n);
+    auto kern = scheme == RVE_Q1_LUMPED ? k3_stiffness<1, MODE, V> : k3_stiffness<0, MODE, V>;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    Span3 sp(s, P3_STIFF);
+    kern<<<nblocks(g, per), T3, smem, s>>>(gg, cs, x, y, f, part, sc);
     note_launch();
     return cudaGetLastError();
 }
@@ -1082,9 +1171,14 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
         Span3 sp(s, P3_VECTOR);
         launch();
     };
-    auto scalar = [&](const Group3& g, int what) {
+    // partial pairs per unit: n^3 >> shift (rhs: 256 nodes per block;
+    // stiffness and axpy: 1024; last line pass: 2048)
+    constexpr int SH_RHS = 8, SH_STIFF = 10, SH_AXPY = 10, SH_LINES = 11;
+    static_assert(T3 * SZ == (1 << SH_STIFF) && 4 * T3 == (1 << SH_AXPY) && T3 == (1 << SH_RHS),
+                  "partial counts");
+    auto scalar = [&](const Group3& g, int what, int shift) {
         Span3 sp(s, P3_SCALAR);
-        k3_scalar<<<g.count, 256, 0, s>>>(ws.ids() + g.ids_off, ws.desc(), sc, part, what, sa);
+        k3_scalar<<<g.count, 256, 0, s>>>(ws.ids() + g.ids_off, ws.desc(), sc, part, what, shift, sa);
         note_launch();
     };
     auto per_group = [&](auto&& fn) -> rve_status {
@@ -1110,7 +1204,7 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
     st = per_group([&](const Group3& g) {
         const int per = (int)(nodes_of(g) / T3);
         vec_step([&] { k3_rhs<<<nblocks(g, per), T3, 0, s>>>(ws.grp(g, per), cs64, f, part); });
-        scalar(g, M_FNORM);
+        scalar(g, M_FNORM, SH_RHS);
         note_launch();
         return RVE_OK;
     });
@@ -1129,7 +1223,7 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
                     return RVE_ECUDA;
             } else {   // u = 0: r64 = f, the partials of |f|^2 are still in place
             }
-            scalar(g, M_REFINE);
+            scalar(g, M_REFINE, cycle > 0 ? SH_STIFF : SH_RHS);
             return RVE_OK;
         });
         if (st != RVE_OK) return st;
@@ -1141,7 +1235,7 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
             const int per = (int)(nodes_of(g) / T3);
             vec_step([&] { k3_start<V><<<nblocks(g, per), T3, 0, s>>>(ws.grp(g, per), sc, r64, r, e, pp); });
             if (precond3<V>(ws, g, o.delta, r, z, s, r, sc) != cudaSuccess) return RVE_ECUDA;
-            scalar(g, M_RHO0);
+            scalar(g, M_RHO0, SH_LINES);
             const int per4 = per / 4;
             vec_step([&] { k3_xpby<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, z, pp); });
             note_launch(2);
@@ -1154,13 +1248,13 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
                 if (stiffness3<MODE_APPLY, V>(ws, g, csV, o.scheme, pp, q, nullptr, true, sc, s) !=
                     cudaSuccess)
                     return RVE_ECUDA;
-                scalar(g, M_ALPHA);
+                scalar(g, M_ALPHA, SH_STIFF);
                 vec_step([&] {
                     k3_axpy<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, e, r, pp, q, part);
                 });
-                scalar(g, M_CONV);
+                scalar(g, M_CONV, SH_AXPY);
                 if (precond3<V>(ws, g, o.delta, r, z, s, r, sc) != cudaSuccess) return RVE_ECUDA;
-                scalar(g, M_BETA);
+                scalar(g, M_BETA, SH_LINES);
                 vec_step([&] { k3_xpby<V><<<nblocks(g, per4), T3, 0, s>>>(ws.grp(g, per4), sc, z, pp); });
                 note_launch(2);
                 return RVE_OK;

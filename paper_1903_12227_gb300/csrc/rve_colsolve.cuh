@@ -33,15 +33,19 @@ namespace rve {
 // Block: C columns x P segments, thread (cc, s) with cc fastest so that the
 // global accesses of a warp are row segments of C elements.  `rho_part`
 // may be null.  rho_of(k2) gives the filter root of column k2 (not called
-// for the singular column).
-template <typename V, int LOG2N, typename Ld, typename St, typename RhoOf>
+// for the singular column).  UNROLL: the periodic carries sum all P segment
+// values (independent loads, no early exit) instead of stopping once the
+// weight is negligible.  SEGO > 0 sets the rows per segment (a divisor of
+// n) in place of col_seg_rows.
+template <typename V, int LOG2N, bool UNROLL = false, int SEGO = 0, typename Ld, typename St,
+          typename RhoOf>
 __device__ __forceinline__ void col_solve_core(Ld&& ld, St&& st, RhoOf&& rho_of, const RDesc& d,
                                                int c0, V* smem, const Tables& tb, double delta,
                                                double* red, double* rho_part,
                                                typename ScalarOf<V>::T* csc) {
     typedef typename ScalarOf<V>::T Ts;
     constexpr int n = 1 << LOG2N;
-    constexpr int SEG = col_seg_rows(n, (int)sizeof(V));
+    constexpr int SEG = SEGO > 0 ? SEGO : col_seg_rows(n, (int)sizeof(V));
     constexpr int P = n / SEG;
     // carry terms below this weight are dropped (far below the rounding of Ts)
     constexpr Ts CARRY_EPS = sizeof(Ts) == 4 ? (Ts)1e-10 : (Ts)1e-19;
@@ -83,12 +87,22 @@ __device__ __forceinline__ void col_solve_core(Ld&& ld, St&& st, RhoOf&& rho_of,
         inv1mRP = (Ts)1 / ((Ts)1 - RP);
         V acc = mk<V>((Ts)0, (Ts)0);
         Ts Rj = (Ts)1;
-        for (int j = 1; j <= P; ++j) {
-            const V e = E[((s - j) & (P - 1)) * C + cc];
-            acc.x += Rj * e.x;
-            acc.y += Rj * e.y;
-            Rj *= R;
-            if (Rj < CARRY_EPS) break;
+        if (UNROLL) {
+#pragma unroll
+            for (int j = 1; j <= P; ++j) {
+                const V e = E[((s - j) & (P - 1)) * C + cc];
+                acc.x += Rj * e.x;
+                acc.y += Rj * e.y;
+                Rj *= R;
+            }
+        } else {
+            for (int j = 1; j <= P; ++j) {
+                const V e = E[((s - j) & (P - 1)) * C + cc];
+                acc.x += Rj * e.x;
+                acc.y += Rj * e.y;
+                Rj *= R;
+                if (Rj < CARRY_EPS) break;
+            }
         }
         const Ts cx = acc.x * inv1mRP, cy = acc.y * inv1mRP;
         Ts pw = rho;
@@ -168,12 +182,22 @@ __device__ __forceinline__ void col_solve_core(Ld&& ld, St&& st, RhoOf&& rho_of,
         if (!zcol) {
             V acc = mk<V>((Ts)0, (Ts)0);
             Ts Rj = (Ts)1;
-            for (int j = 1; j <= P; ++j) {
-                const V e = B[((s + j) & (P - 1)) * C + cc];
-                acc.x += Rj * e.x;
-                acc.y += Rj * e.y;
-                Rj *= R;
-                if (Rj < (Ts)1e-18) break;
+            if (UNROLL) {
+#pragma unroll
+                for (int j = 1; j <= P; ++j) {
+                    const V e = B[((s + j) & (P - 1)) * C + cc];
+                    acc.x += Rj * e.x;
+                    acc.y += Rj * e.y;
+                    Rj *= R;
+                }
+            } else {
+                for (int j = 1; j <= P; ++j) {
+                    const V e = B[((s + j) & (P - 1)) * C + cc];
+                    acc.x += Rj * e.x;
+                    acc.y += Rj * e.y;
+                    Rj *= R;
+                    if (Rj < (Ts)1e-18) break;
+                }
             }
             wx = acc.x * inv1mRP;
             wy = acc.y * inv1mRP;

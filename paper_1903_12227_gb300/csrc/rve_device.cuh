@@ -323,7 +323,10 @@ enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 // tw[m] = exp(-2 pi i m/n).
 // LOG2N > 0 makes the size a compile-time constant: the stages unroll and
 // every index folds to an immediate; LOG2N == 0 takes log2n at run time.
-template <int FINAL, int LOG2N = 0, typename V>
+// BS: element x of the sequence sits at buf[pidx(x) * BS], so that BS
+// sequences can be interleaved element by element (BS consecutive lanes
+// working on BS sequences then touch consecutive words).
+template <int FINAL, int LOG2N = 0, int BS = 1, typename V>
 __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
                                         const V* __restrict__ tw, bool active) {
     const int log2n = LOG2N ? LOG2N : log2n_rt;
@@ -352,7 +355,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
                 if (to_smem) {
                     const int base = ((t - k) << 3) + k;
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns)] = v[r];
+                    for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns) * BS] = v[r];
                 }
             } else if (lr == 2) {
                 V o[8];
@@ -369,10 +372,10 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
                     o[b] = a0; o[b + 2] = a1; o[b + 4] = a2; o[b + 6] = a3;
                     if (to_smem) {
                         const int base = ((j - k) << 2) + k;
-                        buf[pidx(base)] = a0;
-                        buf[pidx(base + Ns)] = a1;
-                        buf[pidx(base + 2 * Ns)] = a2;
-                        buf[pidx(base + 3 * Ns)] = a3;
+                        buf[pidx(base) * BS] = a0;
+                        buf[pidx(base + Ns) * BS] = a1;
+                        buf[pidx(base + 2 * Ns) * BS] = a2;
+                        buf[pidx(base + 3 * Ns) * BS] = a3;
                     }
                 }
                 if (to_regs) {
@@ -390,8 +393,8 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
                     o[b] = a0; o[b + 4] = a1;
                     if (to_smem) {
                         const int base = ((j - k) << 1) + k;
-                        buf[pidx(base)] = a0;
-                        buf[pidx(base + Ns)] = a1;
+                        buf[pidx(base) * BS] = a0;
+                        buf[pidx(base + Ns) * BS] = a1;
                     }
                 }
                 if (to_regs) {
@@ -407,7 +410,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
         __syncthreads();
         if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = buf[pidx(t + m * T)];
+            for (int m = 0; m < 8; ++m) v[m] = buf[pidx(t + m * T) * BS];
         }
     }
 }
