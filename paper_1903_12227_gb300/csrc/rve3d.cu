@@ -13,11 +13,11 @@
 // transforms (pair-packed complex FFT) and the column solve -- works on the
 // pair layout of the 2D path.
 //
-// Units.  The solver's unit of work is one pair of one realization (unit
-// 2b + pair).  Every launch covers all units of one grid size (blocks map to
-// units through a list of unit ids), each unit with its own scalars and
-// flags; a unit that has finished makes its blocks return at once.  The
-// host polls the flags every few steps.
+// Units.  The solver's unit of work is one pair of one realization.  Units
+// are numbered by grid size (within a size, the pair-0 units first), and
+// every launch covers the consecutive units of one size, each unit with its
+// own scalars and flags; a unit that has finished makes its blocks return
+// at once.  The host polls the flags every few steps.
 //
 // Preconditioner: the Hartley transforms along x (contiguous lines) and y
 // (lines of stride n) diagonalise two factors of A_Delta; along z (lines of
@@ -66,7 +66,9 @@ __host__ __device__ __forceinline__ double e3(int a, int b, double h) {
 // Descriptor of one unit (a corrector pair of a realization).
 struct U3 {
     int32_t n, log2n, pair, pad2;
-    int32_t n_incl, s, pad0, pad1;
+    int32_t n_incl, s;
+    int32_t real;       // realization index
+    int32_t partner;    // the realization's other unit
     int64_t off;        // first node of the unit's vectors
     int64_t cell_off;   // first cell (= node) of the realization: mask, coef, ABI vectors
     int64_t part_off;   // first partial (doubles) of the unit
@@ -75,17 +77,16 @@ struct U3 {
     uint64_t key;       // SplitMix64 key of the realization
 };
 
-// Blocks of a launch over the units of one grid size: block -> (unit, block
-// within the unit).
+// Blocks of a launch over the units of one grid size (consecutive unit ids
+// from `first`): block -> (unit, block within the unit).
 struct Grp {
     const U3* __restrict__ desc;
-    const int32_t* __restrict__ ids;
-    int per;            // blocks per unit
+    int first;          // first unit of the launch
+    int per_log2;       // log2 of the blocks per unit
 };
 __device__ __forceinline__ int unit_of(const Grp& g, int& lb) {
-    const int q = blockIdx.x / g.per;
-    lb = blockIdx.x - q * g.per;
-    return g.ids[q];
+    lb = blockIdx.x & ((1 << g.per_log2) - 1);
+    return g.first + (blockIdx.x >> g.per_log2);
 }
 
 // Local index of node (i, j, k) (periodic) within a realization.
@@ -195,8 +196,8 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
     __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     if (sc && unit_skip(sc, u, MODE == MODE_RESID)) return;
-    const U3& d = g.desc[u];
     const int n = d.n, m = n - 1, lg = d.log2n;
     const int TJ = T3 >> lg;                          // rows of the block
     const int first = lb * T3;                        // (plane group, j0, 0)
@@ -412,8 +413,8 @@ __global__ void __launch_bounds__(256) k3_lines(Grp g, Tables tb, const V* src, 
     __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     if (sc && unit_skip(sc, u, false)) return;
-    const U3& d = g.desc[u];
     constexpr int n = 1 << LOG2N, TL = n / 8, G = 256 / TL;
     constexpr int BS = AXIS == 2 ? 1 : G;
     int q, t;
@@ -472,8 +473,8 @@ __global__ void __launch_bounds__(Z_THREADS) k3_zsolve(Grp g, Tables tb, double 
     __shared__ T csc[1];
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     if (sc && unit_skip(sc, u, false)) return;
-    const U3& d = g.desc[u];
     constexpr int n = 1 << LOG2N, NN = n * n, ZC = zcols<LOG2N>();
     RDesc cd;          // the two fields the column solve reads
     cd.tC = ZC;
@@ -563,9 +564,9 @@ __global__ void __launch_bounds__(T3) k3_a_hom_part(Grp g, Cells3T<double> cs,
 __global__ void k3_a_hom_final(Grp g, const double* __restrict__ part, double* __restrict__ A,
                                double* __restrict__ Af) {
     __shared__ double red[32];
-    const int un = g.ids[blockIdx.x];
+    const int un = g.first + blockIdx.x;
     const U3& d = g.desc[un];
-    const int b = un >> 1;
+    const int b = d.real;
     const int tiles = (int)(((int64_t)d.n * d.n * d.n) / T3);
     double s[A3_NP];
 #pragma unroll
@@ -648,12 +649,12 @@ struct ScalArgs {
     double tol, inner_tol, tfac;
     int max_iter;
 };
-__global__ void __launch_bounds__(256) k3_scalar(const int32_t* __restrict__ ids,
-                                                 const U3* __restrict__ desc, MixScal* scs,
+__global__ void __launch_bounds__(256) k3_scalar(int first, const U3* __restrict__ desc,
+                                                 MixScal* scs,
                                                  const double* __restrict__ part, int what,
                                                  int pshift, ScalArgs a) {
     __shared__ double red[32];
-    const int u = ids[blockIdx.x];
+    const int u = first + blockIdx.x;
     MixScal* sc = scs + u;
     const U3& d = desc[u];
     if (what != M_FNORM && what != M_REFINE && sc->done) return;
@@ -758,9 +759,9 @@ __global__ void __launch_bounds__(T3) k3_start(Grp g, const MixScal* scs,
     typedef typename ScalarOf<V>::T T;
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     const MixScal& sc = scs[u];
     if (sc.done) return;
-    const U3& d = g.desc[u];
     const int64_t node = d.off + lb * T3 + threadIdx.x;
     const double2 rr = r64[node];
     V o;
@@ -785,9 +786,9 @@ __global__ void __launch_bounds__(T3) k3_axpy(Grp g, const MixScal* scs, V* __re
     __shared__ double red[16];
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     const MixScal& sc = scs[u];
     if (sc.done) return;
-    const U3& d = g.desc[u];
     const T ax_ = alpha_of<T>(sc, 0), ay_ = alpha_of<T>(sc, 1);
     T sx = 0, sy = 0;
 #pragma unroll
@@ -819,9 +820,9 @@ __global__ void __launch_bounds__(T3) k3_xpby(Grp g, const MixScal* scs, const V
     typedef typename ScalarOf<V>::T T;
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     const MixScal& sc = scs[u];
     if (sc.done) return;
-    const U3& d = g.desc[u];
     const T bx = beta_of<T>(sc, 0), by = beta_of<T>(sc, 1);
 #pragma unroll
     for (int mm = 0; mm < 4; ++mm) {
@@ -837,9 +838,9 @@ __global__ void __launch_bounds__(T3) k3_accum(Grp g, const MixScal* scs, const 
                                                double2* __restrict__ uv) {
     int lb;
     const int u = unit_of(g, lb);
+    const U3 d = g.desc[u];   // issued before the flag test
     const MixScal& sc = scs[u];
     if (sc.outer_done) return;
-    const U3& d = g.desc[u];
     const int64_t node = d.off + lb * T3 + threadIdx.x;
     const double sx = sc.cdone[0] ? 0.0 : sc.s[0], sy = sc.cdone[1] ? 0.0 : sc.s[1];
     const V ee = e[node];
@@ -849,12 +850,14 @@ __global__ void __launch_bounds__(T3) k3_accum(Grp g, const MixScal* scs, const 
     uv[node] = w;
 }
 
-// Per realization: the report of its two units.
-__global__ void k3_report(const MixScal* scs, int batch, rve3_solve_info* info) {
+// Per realization: the report of its two units (u_of[b]: the pair-0 unit).
+__global__ void k3_report(const MixScal* scs, const U3* __restrict__ desc,
+                          const int32_t* __restrict__ u_of, int batch, rve3_solve_info* info) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
-    const MixScal& s12 = scs[2 * b];
-    const MixScal& s3 = scs[2 * b + 1];
+    const int u0 = u_of[b];
+    const MixScal& s12 = scs[u0];
+    const MixScal& s3 = scs[desc[u0].partner];
     rve3_solve_info r;
     r.iters[0] = s12.iters[0];
     r.iters[1] = s12.iters[1];
@@ -930,17 +933,18 @@ static void prof3_sync(cudaStream_t s) {
 constexpr int N3_MIN = 32, N3_MAX = 256;
 constexpr int NVEC = 8;   // unit vectors: f, u, r64, and the cycle's r, z, p, e, q
 
+// The units of one grid size: ids first .. first + count - 1, the pair-0
+// units (one per realization) first.
 struct Group3 {
     int log2n = 0;
-    int count = 0;             // units of this size
-    size_t ids_off = 0;        // into the id array: units
-    size_t rids_off = 0;       // pair-0 units (realizations)
+    int first = 0;
+    int count = 0;
 };
 
 struct Plan3 {
     int batch = 0;
-    std::vector<U3> desc;      // 2 * batch units
-    std::vector<int32_t> ids;  // per group: its units, then its pair-0 units
+    std::vector<U3> desc;      // 2 * batch units, grouped by size
+    std::vector<int32_t> u_of; // pair-0 unit of each realization
     std::vector<Group3> groups;
     int64_t nodes = 0;         // realization nodes (sum n^3)
     int64_t unit_nodes = 0;    // 2 * nodes
@@ -954,10 +958,12 @@ static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) 
     if (!r || batch <= 0 || batch > (1 << 16)) return RVE_EINVAL;
     p.batch = batch;
     p.desc.assign(2 * (size_t)batch, U3{});
+    p.u_of.assign(batch, 0);
     p.nodes = 0;
     p.parts = 0;
     p.max_log2n = 5;
-    std::map<int, std::vector<int32_t>> by_size;
+    std::map<int, std::vector<int32_t>> by_size;   // realizations by log2 n
+    std::vector<int64_t> cell_off(batch);
     for (int b = 0; b < batch; ++b) {
         const rve_realization& x = r[b];
         if (x.L <= 0 || x.m0 <= 0) return RVE_EINVAL;
@@ -969,53 +975,60 @@ static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) 
         if (!std::isfinite(x.a_matrix) || !std::isfinite(x.a_incl) || !(x.a_matrix > 0.0) ||
             !(x.a_incl > 0.0))
             return RVE_EINVAL;
-        const int64_t nn = (int64_t)n * n * n;
-        const int64_t part_real = A3_NP * (nn / T3);   // >= 2 units x 2 x (nn / T3)
-        for (int pair = 0; pair < 2; ++pair) {
-            U3& d = p.desc[2 * b + pair];
-            std::memset(&d, 0, sizeof(d));
-            d.n = n;
-            d.log2n = 31 - __builtin_clz((unsigned)n);
-            d.pair = pair;
-            d.n_incl = x.n_incl;
-            d.s = x.incl_cells;
-            d.cell_off = p.nodes;
-            d.part_off = p.parts + pair * 2 * (nn / T3);
-            d.am = x.a_matrix;
-            d.ai = x.a_incl;
-            d.am32 = (float)x.a_matrix;
-            d.ai32 = (float)x.a_incl;
-            d.h = 1.0 / (double)x.m0;
-            d.c0 = 0.5 * (x.a_matrix + x.a_incl);
-            d.inv_vol = 1.0 / ((double)x.L * (double)x.L * (double)x.L);
-            d.key = sm64_mix(x.seed + (x.index + 1) * 0x9E3779B97F4A7C15ull);
-            d.off = 2 * p.nodes + pair * nn;
-            by_size[d.log2n].push_back(2 * b + pair);
-        }
-        p.nodes += nn;
-        p.parts += part_real;
-        p.max_log2n = std::max(p.max_log2n, (int)p.desc[2 * b].log2n);
+        const int lg = 31 - __builtin_clz((unsigned)n);
+        by_size[lg].push_back(b);
+        cell_off[b] = p.nodes;
+        p.nodes += (int64_t)n * n * n;
+        p.max_log2n = std::max(p.max_log2n, lg);
     }
     p.unit_nodes = 2 * p.nodes;
-    p.ids.clear();
     p.groups.clear();
+    int u = 0;
+    int64_t off = 0;
     for (auto& kv : by_size) {
         Group3 g;
         g.log2n = kv.first;
-        g.count = (int)kv.second.size();
-        g.ids_off = p.ids.size();
-        p.ids.insert(p.ids.end(), kv.second.begin(), kv.second.end());
-        g.rids_off = p.ids.size();
-        for (int32_t u : kv.second)
-            if ((u & 1) == 0) p.ids.push_back(u);
+        g.first = u;
+        g.count = 2 * (int)kv.second.size();
+        const int half = (int)kv.second.size();
+        const int64_t nn = (int64_t)1 << (3 * kv.first);
+        for (int pair = 0; pair < 2; ++pair)
+            for (int q = 0; q < half; ++q) {
+                const int b = kv.second[q];
+                const rve_realization& x = r[b];
+                U3& d = p.desc[u];
+                std::memset(&d, 0, sizeof(d));
+                d.n = 1 << kv.first;
+                d.log2n = kv.first;
+                d.pair = pair;
+                d.n_incl = x.n_incl;
+                d.s = x.incl_cells;
+                d.real = b;
+                d.partner = pair == 0 ? g.first + half + q : g.first + q;
+                d.cell_off = cell_off[b];
+                d.part_off = p.parts;
+                d.am = x.a_matrix;
+                d.ai = x.a_incl;
+                d.am32 = (float)x.a_matrix;
+                d.ai32 = (float)x.a_incl;
+                d.h = 1.0 / (double)x.m0;
+                d.c0 = 0.5 * (x.a_matrix + x.a_incl);
+                d.inv_vol = 1.0 / ((double)x.L * (double)x.L * (double)x.L);
+                d.key = sm64_mix(x.seed + (x.index + 1) * 0x9E3779B97F4A7C15ull);
+                d.off = off;
+                if (pair == 0) p.u_of[b] = u;
+                off += nn;
+                p.parts += A3_NP * (nn / T3);   // enough for every kernel and for A_hom
+                ++u;
+            }
         p.groups.push_back(g);
     }
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    size_t off = 0;
-    auto take = [&](size_t bytes) { const size_t o = off; off = up(off + bytes); return o; };
+    size_t woff = 0;
+    auto take = [&](size_t bytes) { const size_t o = woff; woff = up(woff + bytes); return o; };
     const size_t tab = (size_t)2 << p.max_log2n;
     p.o_desc = take(sizeof(U3) * p.desc.size());
-    p.o_ids = take(sizeof(int32_t) * p.ids.size());
+    p.o_ids = take(sizeof(int32_t) * p.u_of.size());
     p.o_tw64 = take(sizeof(double2) * tab);
     p.o_tw32 = take(sizeof(float2) * tab);
     p.o_lap = take(sizeof(double) * tab);
@@ -1026,7 +1039,7 @@ static rve_status make_plan3(const rve_realization* r, int32_t batch, Plan3& p) 
     p.o_part = take(sizeof(double) * (size_t)p.parts);
     p.o_c32 = take(sizeof(float) * (size_t)p.nodes);
     p.o_vec = take(sizeof(double2) * NVEC * (size_t)p.unit_nodes);
-    p.total = off;
+    p.total = woff;
     return RVE_OK;
 }
 
@@ -1034,7 +1047,7 @@ struct Ws3 {   // device pointers into the workspace
     const Plan3* p;
     char* w;
     const U3* desc() const { return reinterpret_cast<const U3*>(w + p->o_desc); }
-    const int32_t* ids() const { return reinterpret_cast<const int32_t*>(w + p->o_ids); }
+    const int32_t* u_of() const { return reinterpret_cast<const int32_t*>(w + p->o_ids); }
     MixScal* sc() const { return reinterpret_cast<MixScal*>(w + p->o_sc); }
     double* part() const { return reinterpret_cast<double*>(w + p->o_part); }
     float* c32() const { return reinterpret_cast<float*>(w + p->o_c32); }
@@ -1051,9 +1064,11 @@ struct Ws3 {   // device pointers into the workspace
         tb.rho32 = reinterpret_cast<const float*>(w + p->o_rho32);
         return tb;
     }
-    // launch over the units (or the pair-0 units) of group g, `per` blocks each
+    // launch over the units (or the pair-0 units) of group g, `per` (a power
+    // of two) blocks each
     Grp grp(const Group3& g, int per, bool reals = false) const {
-        return Grp{desc(), ids() + (reals ? g.rids_off : g.ids_off), per};
+        (void)reals;   // the pair-0 units come first in the group
+        return Grp{desc(), g.first, 31 - __builtin_clz((unsigned)per)};
     }
 };
 enum { V_F = 0, V_U, V_R64, V_R, V_Z, V_P, V_E, V_Q };
@@ -1067,7 +1082,7 @@ static int64_t nodes_of(const Group3& g) { return (int64_t)1 << (3 * g.log2n); }
 static rve_status setup3(const Plan3& p, char* w, cudaStream_t s, bool tables) {
     if (cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(U3) * p.desc.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(w + p.o_ids, p.ids.data(), sizeof(int32_t) * p.ids.size(),
+        cudaMemcpyAsync(w + p.o_ids, p.u_of.data(), sizeof(int32_t) * p.u_of.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
         return RVE_ECUDA;
     if (!tables) return RVE_OK;
@@ -1178,7 +1193,7 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
                   "partial counts");
     auto scalar = [&](const Group3& g, int what, int shift) {
         Span3 sp(s, P3_SCALAR);
-        k3_scalar<<<g.count, 256, 0, s>>>(ws.ids() + g.ids_off, ws.desc(), sc, part, what, shift, sa);
+        k3_scalar<<<g.count, 256, 0, s>>>(g.first, ws.desc(), sc, part, what, shift, sa);
         note_launch();
     };
     auto per_group = [&](auto&& fn) -> rve_status {
@@ -1313,7 +1328,7 @@ rve_status rve3_gen_field(const rve_realization* r, int32_t batch, uint8_t* mask
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(mask, 0, (size_t)p.nodes, s) != cudaSuccess) return RVE_ECUDA;
     for (int b = 0; b < p.batch; ++b) {
-        const U3& d = p.desc[2 * b];
+        const U3& d = p.desc[p.u_of[b]];
         const int64_t rows = (int64_t)d.n_incl * d.s * d.s;
         if (rows == 0) continue;
         k3_gen_field<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(d, mask);
@@ -1432,7 +1447,7 @@ rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const 
         k3_join<<<nblocks(g, per), T3, 0, s>>>(W.grp(g, per), W.vec<double2>(V_U), u);
         note_launch();
     }
-    k3_report<<<(p.batch + 127) / 128, 128, 0, s>>>(W.sc(), p.batch, info);
+    k3_report<<<(p.batch + 127) / 128, 128, 0, s>>>(W.sc(), W.desc(), W.u_of(), p.batch, info);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
     prof3_sync(s);
