@@ -15,6 +15,13 @@ the end-to-end number through rve_homogenize_host (host descriptors in, host
 A out); the roofline of the dominant kernel from live CUDA-event timing.
 
     python bench.py [--gpus N --steps K --warmup W --batch B] [--impl reference]
+    python bench.py --workload cubes_L4    # the 3D extension (one JSON line too)
+
+The 3D workload (`--workload cubes_L4`): L = 4, h = 1/16 (64^3 nodes), 45
+unit cubes (density 0.7 per unit volume), contrast 10, three correctors per
+realization by the mixed-precision 3D solver to a true relative residual of
+1e-10, 3x3 A_hom; one step = field + correctors + A_hom for 256
+realizations (67 M nodes, ~17 GB of state).
 """
 from __future__ import annotations
 
@@ -57,6 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=125)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_L32", choices=["plain_L32", "cubes_L4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison arms")
     return ap.parse_args()
@@ -351,6 +359,175 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+CUBES = dict(name="cubes_L4", L=4, m0=16, contrast=10.0, tol=1e-10, batch=256)
+CUBES_METRIC = "3D RVE realizations/s (3 correctors each, mixed precision, true residual <= 1e-10)"
+CUBES_DESC = ("L=4, h=1/16 (64^3 nodes, 262144 unknowns per corrector), contrast 10, 45 unit "
+              "cubes (density 0.7), PCG tol 1e-10 on the true residual, 3x3 A_hom")
+# Algorithmic bytes per unit-node (a unit = one corrector pair of a
+# realization) of one launch of each 3D kernel kind in the mixed solve:
+# FP32 stencil 17 (x, cells, y); line pass 18 on average (16, the last of
+# four also reads r); z solve 16; vector steps 36 on average (axpy 48, xpby
+# 24); FP64 true residual 49 (u, f, cells in; r out).
+CUBES_BYTES = {"stiffness": 17.0, "lines": 18.0, "zsolve": 16.0, "vector": 36.0, "scalar": 0.0,
+               "resid64": 49.0}
+
+
+def cubes_descs(start: int, count: int):
+    from paper_1903_12227_gb300 import workloads
+    return [workloads.realization3(CUBES["L"], CUBES["m0"], CUBES["contrast"], 0, start + k)
+            for k in range(count)]
+
+
+def cpu_oracle_rate_cubes(count: int):
+    """The 3D oracle as it stands, one realization per host thread (the C
+    oracle runs with the GIL released): realizations/s, threads, A."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    ds = cubes_descs(0, count)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=count) as ex:
+        res = list(ex.map(lambda d: oracle.solve_realization3(d, tol=CUBES["tol"], want_u=False), ds))
+    dt = time.perf_counter() - t0
+    return count / dt, count, np.array([r["A_energy"] for r in res]), dt
+
+
+def run_cubes(args):
+    """The 3D extension: batches of 64^3 realizations through the rve3 C ABI."""
+    import numpy as np
+    import torch
+
+    from paper_1903_12227_gb300 import rve, rve3
+
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload cubes_L4 runs on one GPU")
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    B = args.batch if args.batch != 125 else CUBES["batch"]
+    opts = rve3.make_opts3(precision=rve.MIXED, tol=CUBES["tol"])
+    probe = rve3.Batch3(cubes_descs(0, B))
+    L3 = rve3.lib()
+    ws = rve.workspace(rve3.workspace_size3(probe), dev)
+    mask = torch.empty(probe.nodes, dtype=torch.uint8, device=dev)
+    u = torch.empty(probe.nodes, 3, dtype=torch.float64, device=dev)
+    info = torch.empty(B * rve3.INFO3_BYTES, dtype=torch.uint8, device=dev)
+    A_out = torch.empty(B, 9, dtype=torch.float64, device=dev)
+
+    def step(k: int):
+        b = rve3.Batch3(cubes_descs(k * B, B))
+        s = rve._stream(stream)
+        rve.check(L3.rve3_gen_field(b.ptr, b.count, rve._ptr(mask), s))
+        rve.check(L3.rve3_solve_correctors(b.ptr, b.count, rve._ptr(mask), None,
+                                           rve3.ctypes.byref(opts), rve._ptr(u), rve._ptr(info),
+                                           rve._ptr(ws), ws.numel(), s))
+        rve.check(L3.rve3_a_hom(b.ptr, b.count, rve._ptr(mask), None, opts.scheme, rve._ptr(u),
+                                rve._ptr(A_out), None, rve._ptr(ws), ws.numel(), s))
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    rve.launch_count()
+    rve.profile_enable(True)
+    rve3.profile_read()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    infos, As = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+        infos.append(info.clone())
+        As.append(A_out.clone())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = rve3.profile_read()
+    rve.profile_enable(False)
+    launches = rve.launch_count()
+    value = B * args.steps / (elapsed_ms / 1e3)
+    info_d = [d for t in infos for d in rve3.decode_info(t)]
+    A_all = torch.cat(As).cpu().numpy().reshape(-1, 3, 3)
+
+    # roofline of the dominant kernel kind: algorithmic bytes of the unit-
+    # nodes its launches worked on / the average CUDA-event launch time; a
+    # launch covers every unit, but blocks of converged units return at once,
+    # so the unit-nodes are the units' CG steps (FP32 stencil launches) x n^3
+    n3 = (CUBES["L"] * CUBES["m0"]) ** 3
+    unit_steps = sum(max(d["iters"][0], d["iters"][1]) + d["iters"][2] for d in info_d)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    def rate(kind, unit_nodes):
+        ms, cnt = prof[kind]
+        if cnt == 0 or ms <= 0:
+            return 0.0, 0.0, 0.0
+        per_launch = CUBES_BYTES[kind] * unit_nodes / cnt
+        avg_s = ms / 1e3 / cnt
+        return per_launch, avg_s, per_launch / avg_s / 1e9
+
+    # unit-node counts per kind: one stencil, four line passes, one z solve,
+    # two vector launches per unit CG step
+    per_kind_nodes = {"stiffness": unit_steps * n3, "lines": 4 * unit_steps * n3,
+                      "zsolve": unit_steps * n3, "vector": 2 * unit_steps * n3, "scalar": 0,
+                      "resid64": sum(max(d["refinements"] - 2, 0) for d in info_d) * n3}
+    dom = max(("stiffness", "lines", "zsolve", "vector"), key=lambda k: prof[k][0])
+    bpl, avg_s, achieved = rate(dom, per_kind_nodes[dom])
+    total_ms = max(sum(v[0] for v in prof.values()), 1e-9)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_launch": bpl,
+                "avg_launch_us": avg_s * 1e6,
+                "per_kernel_gbs": {k: rate(k, per_kind_nodes[k])[2] for k in CUBES_BYTES},
+                "time_share": {k: prof[k][0] / total_ms for k in prof}}
+    out = {"metric": CUBES_METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 vectors + f64 dots/refinement/A_hom (mixed)", "data": "synthetic",
+           "config": {"workload": f"{CUBES['name']}: {CUBES_DESC}", "batch_per_gpu": B,
+                      "l2": "inputs larger than L2 (~17 GB of state per step)",
+                      "precision": "mixed"},
+           "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+           "solver": {"statuses": sorted({d["status"] for d in info_d}),
+                      "mean_iters": float(np.mean([np.mean(d["iters"]) for d in info_d])),
+                      "mean_refinements": float(np.mean([d["refinements"] for d in info_d])),
+                      "max_relres": float(max(max(d["relres"]) for d in info_d))},
+           "a_hom_stats": {"mean_diag": float(np.mean(A_all.diagonal(axis1=1, axis2=2))),
+                           "std_diag": float(np.std(A_all.diagonal(axis1=1, axis2=2))),
+                           "count": len(A_all)}}
+    # end to end: host descriptors in, host A_hom out, the copies in the timing
+    t0 = time.perf_counter()
+    n_e2e = 2
+    for k in range(n_e2e):
+        step(args.warmup + args.steps + k)
+        A_host = A_out.cpu()
+    dt = time.perf_counter() - t0
+    out["e2e"] = {"value": n_e2e * B / dt, "unit": UNIT, "h2d_bytes_per_step": B * 48,
+                  "d2h_bytes_per_step": B * 72,
+                  "api": "rve3_gen_field + rve3_solve_correctors + rve3_a_hom (host descriptors, "
+                         "A_hom copied to the host)"}
+    del A_host
+    if not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, 16)
+        rate_cpu, used, A_cpu, dt = cpu_oracle_rate_cubes(cores)
+        out["cpu_baseline"] = {"value": rate_cpu, "unit": UNIT, "cores": used, "kind": "oracle",
+                               "sample": f"{used} realizations (indices 0..{used - 1}) of the same "
+                                         f"workload, one per host thread ({dt:.1f} s)"}
+        # the same realizations on the GPU, against the oracle
+        ds = cubes_descs(0, used)
+        m = rve3.gen_field(ds, device=dev)
+        ug, _ = rve3.solve(ds, mask=m, opts=opts)
+        Ag = rve3.a_hom(ds, ug, mask=m).cpu().numpy()
+        sc = np.abs(A_cpu.diagonal(axis1=1, axis2=2)).max(axis=1)
+        out["a_hom_max_rel_err_vs_oracle"] = float((np.abs(Ag - A_cpu).max(axis=(1, 2)) / sc).max())
+    print(json.dumps(out), flush=True)
+
+
 def extras(args, rve, torch, np, dev, stream):
     """e2e through the host-buffer ABI call, and the FP64 comparison arms."""
     out = {}
@@ -407,6 +584,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "cubes_L4":
+        run_cubes(args)
         return
     run_ours(args)
 

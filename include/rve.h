@@ -451,9 +451,10 @@ void rve_profile_enable(int32_t on);
 int32_t rve_profile_read(double* ms, int64_t* launches);
 /* The same for the 3D solver (enabled by rve_profile_enable as well): every
  * launch of rve3_solve_correctors bracketed by events, totals per kind --
- * 0 stiffness (27-point stencil, with the p.q partials), 1 line transform
- * (x or y Hartley pass), 2 z tridiagonal solve, 3 CG vector steps (dots,
- * updates), 4 CG scalar steps -- reset on read; returns 5. */
+ * 0 stiffness of the CG steps (27-point stencil, with the p.q partials),
+ * 1 line transform (x or y Hartley pass), 2 z tridiagonal solve, 3 CG
+ * vector steps (dots, updates), 4 CG scalar steps, 5 FP64 true residual
+ * (stiffness with the residual fused) -- reset on read; returns 6. */
 int32_t rve3_profile_read(double* ms, int64_t* launches);
 int64_t rve_launch_count(void);
 

@@ -874,9 +874,10 @@ __global__ void k3_report(const MixScal* scs, const U3* __restrict__ desc,
 // ------------------------------------------------------------ profile --
 // Event timing of every 3D launch by kind (diagnostics, enabled together
 // with the fused solver's profiler by rve_profile_enable; process-wide, not
-// thread-safe): 0 stiffness, 1 line transform (x or y), 2 z solve,
-// 3 vector steps of CG (dots, updates), 4 scalar steps (one block per unit).
-enum { P3_STIFF = 0, P3_LINES, P3_ZSOLVE, P3_VECTOR, P3_SCALAR, P3_K };
+// thread-safe): 0 stiffness of the CG steps, 1 line transform (x or y),
+// 2 z solve, 3 vector steps of CG (dots, updates), 4 scalar steps (one block
+// per unit), 5 FP64 true residual (the stiffness with the residual fused).
+enum { P3_STIFF = 0, P3_LINES, P3_ZSOLVE, P3_VECTOR, P3_SCALAR, P3_RESID, P3_K };
 struct Prof3 {
     double ms[P3_K] = {};
     long long launches[P3_K] = {};
@@ -1157,7 +1158,7 @@ static cudaError_t stiffness3(const Ws3& ws, const Group3& g, Cells3T<typename S
     auto kern = scheme == RVE_Q1_LUMPED ? k3_stiffness<1, MODE, V> : k3_stiffness<0, MODE, V>;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    Span3 sp(s, P3_STIFF);
+    Span3 sp(s, MODE == MODE_RESID ? P3_RESID : P3_STIFF);
     kern<<<nblocks(g, per), T3, smem, s>>>(gg, cs, x, y, f, part, sc);
     note_launch();
     return cudaGetLastError();

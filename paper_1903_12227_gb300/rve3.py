@@ -209,7 +209,7 @@ def a_hom(batch, u: torch.Tensor, mask=None, coef=None, scheme=CONSISTENT, ws=No
     return (A, Af.view(b.count, 3, 3)) if want_flux else A
 
 
-PROFILE_KINDS = ("stiffness", "lines", "zsolve", "vector", "scalar")
+PROFILE_KINDS = ("stiffness", "lines", "zsolve", "vector", "scalar", "resid64")
 
 
 def profile_read() -> dict:

@@ -230,10 +230,13 @@ def dos_study(Ls=(4, 8), N=20, lam=0.5, alpha=0.25, m0=8, eta=0.05, K=512, vecto
 # 36 B on average over the four passes); the z solve reads and writes a
 # pair; the CG vector steps of one iteration move 144 B (u, r, p, q read and
 # u, r written; z, p read and p written) over two launches; the scalar
-# launches (one warp) move nothing.  FP32 vectors (the mixed path's cycles)
-# halve the vector bytes.
-CUBE_BYTES = {"stiffness": 33.0, "lines": 36.0, "zsolve": 32.0, "vector": 72.0, "scalar": 0.0}
-CUBE_BYTES_FP32 = {"stiffness": 17.0, "lines": 18.0, "zsolve": 16.0, "vector": 36.0, "scalar": 0.0}
+# launches move nothing; the FP64 true residual reads u, f and the cells and
+# writes r (49 B).  FP32 vectors (the mixed path's cycles) halve the vector
+# bytes.
+CUBE_BYTES = {"stiffness": 33.0, "lines": 36.0, "zsolve": 32.0, "vector": 72.0, "scalar": 0.0,
+              "resid64": 49.0}
+CUBE_BYTES_FP32 = {"stiffness": 17.0, "lines": 18.0, "zsolve": 16.0, "vector": 36.0,
+                   "scalar": 0.0, "resid64": 49.0}
 
 
 def _measured_hbm():
