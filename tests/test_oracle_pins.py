@@ -635,3 +635,33 @@ def test_voigt_reuss3_bounds():
     a = np.where(mask, 10.0, 1.0)
     ev = np.linalg.eigvalsh(0.5 * (r["A_energy"] + r["A_energy"].T))
     assert 1.0 / np.mean(1.0 / a) <= ev[0] and ev[-1] <= np.mean(a)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_a_hom3_permutes_with_the_axes(scheme):
+    # relabelling the coordinate axes of the coefficient relabels A_hom:
+    # A(a o P) = P^T A(a) P; an axis treated differently from the others (a
+    # wrong offset, sign or corner bit on one axis) in the loads, the
+    # stiffness or either A_hom form breaks this
+    n = 8
+    coef = np.exp(np.random.default_rng(12).normal(0.0, 0.8, size=(n, n, n)))
+    ref = oracle.solve_coef3(coef, 2, 4, 2.0, scheme, tol=1e-13)
+    for perm in ((1, 0, 2), (2, 1, 0), (1, 2, 0)):
+        r = oracle.solve_coef3(np.ascontiguousarray(coef.transpose(perm)), 2, 4, 2.0, scheme,
+                               tol=1e-13)
+        P = np.eye(3)[list(perm)]
+        for form in ("A_energy", "A_flux"):
+            np.testing.assert_allclose(r[form], P @ ref[form] @ P.T, atol=1e-11)
+
+
+def test_a_hom3_energy_equals_flux_at_convergence():
+    # at the discrete solution v_j^T E v_i = int a d_j(x_i + phi_i) summed over
+    # cells (the Galerkin orthogonality of the corrector), so both forms agree
+    # to the solver tolerance, and the energy form is symmetric positive definite
+    d = {"L": 2, "m0": 8, "incl_cells": 5, "n_incl": 9, "a_matrix": 1.0, "a_incl": 20.0,
+         "seed": 9, "index": 2}
+    r = oracle.solve_realization3(d, tol=1e-13)
+    A, F = r["A_energy"], r["A_flux"]
+    np.testing.assert_allclose(A, A.T, atol=1e-13)
+    assert np.linalg.eigvalsh(A)[0] > 0.0
+    np.testing.assert_allclose(F, A, atol=1e-9 * np.abs(A).max())
