@@ -284,3 +284,24 @@ def test_solve3_batch_matches_single_solves(prec):
         assert infos[k]["status"] == rve.RVE_OK
         assert rve3.decode_info(i1)[0]["iters"] == infos[k]["iters"]
         np.testing.assert_array_equal(A[k], A1[0])
+
+
+def test_a_hom3_gpu_permutes_with_the_axes():
+    # the GPU path on its own: relabelling the axes of the cell values
+    # relabels A_hom (x lines, y lines and z solves, and the three stencil
+    # axes, all enter differently)
+    d = workloads.realization3(2, 16, 10.0, 15, 0)
+    n = 32
+    coef = np.exp(np.random.default_rng(21).normal(0.0, 0.7, size=(n, n, n)))
+    opts = rve3.make_opts3(tol=1e-12)
+
+    def A_of(c):
+        ct = torch.tensor(np.ascontiguousarray(c).ravel(), device=CUDA)
+        u, info = rve3.solve([d], coef=ct, opts=opts)
+        assert rve3.decode_info(info)[0]["status"] == rve.RVE_OK
+        return rve3.a_hom([d], u, coef=ct)[0].cpu().numpy()
+
+    A = A_of(coef)
+    for perm in ((1, 0, 2), (2, 1, 0), (1, 2, 0)):
+        P = np.eye(3)[list(perm)]
+        assert _rel_A(A_of(coef.transpose(perm)), P @ A @ P.T) < 1e-10
