@@ -75,9 +75,9 @@ struct Plan {
     size_t total = 0;
 };
 
-// Plain FP64 PCG building blocks (rve_plain.cu), shared with the 3D solver:
-// vector kernels over the nodes of realization b (PL_NODES per block, from
-// desc[b].node_off) on corrector pairs, and the per-pair scalar steps.
+// Plain FP64 PCG building blocks (rve_plain.cu): vector kernels over the
+// nodes of realization b (PL_NODES per block, from desc[b].node_off) on
+// corrector pairs, and the per-pair scalar steps.
 constexpr int PL_THREADS = 256;
 constexpr int PL_NODES = 1024;   // nodes per block (n^2 and n^3 are multiples of 1024)
 struct PlainScal {
