@@ -166,11 +166,15 @@ __global__ void k3_gen_field(const U3 d, uint8_t* __restrict__ mask) {
 // for o = 0, 4 for a face neighbour, 2 for an edge neighbour (a pair sum
 // along the axis where o is 0), 1 for a corner neighbour: about 60
 // operations per node and pair instead of 144 for the 8 element rows.
-// A block takes SZ consecutive planes of TJ = 256 / n whole rows: it first
-// copies the planes i0-1 .. i0+SZ, rows j0-1 .. j0+TJ (whole periodic rows)
-// of x and the cell values of planes i0-1 .. i0+SZ-1, rows j0-1 .. j0+TJ-1
-// into shared memory with coalesced loads, then each thread computes its
-// SZ nodes (one (j, k), SZ planes) from there.
+// A thread computes two neighbouring nodes (k0, k0 + 1) of one row in SZ
+// consecutive planes; a block takes TJ = 512 / n whole rows of those planes.
+// It first copies the planes i0-1 .. i0+SZ, rows j0-1 .. j0+TJ of x and the
+// cell values of planes i0-1 .. i0+SZ-1, rows j0-1 .. j0+TJ-1 (whole periodic
+// rows) into shared memory, every load issued before the first store, then
+// each node sums the contributions of its three x-planes: from below (cells
+// of plane i-1), in its own plane (both cell planes and the diagonal term)
+// and from above (cells of plane i).  Per node pair and row one 16-byte and
+// two 8-byte shared loads.
 //   MODE_APPLY: y = A x, partials of x.y per component (the p.q of CG);
 //   MODE_RESID: y = f - A x (the true residual), partials of |y|^2.
 // Blocks of units whose flag (`done`, or `outer_done` for MODE_RESID) is
@@ -182,8 +186,25 @@ __device__ __forceinline__ bool unit_skip(const MixScal* sc, int u, bool outer);
 // Shared memory of a stiffness block for grids of n = 2^lg.
 template <typename V>
 __host__ __device__ constexpr size_t stiff_smem(int lg) {
-    return (size_t)(SZ + 2) * ((T3 >> lg) + 2) * ((size_t)1 << lg) * sizeof(V) +
-           (size_t)(SZ + 1) * ((T3 >> lg) + 1) * ((size_t)1 << lg) * (sizeof(V) / 2);
+    return (size_t)(SZ + 2) * (((2 * T3) >> lg) + 2) * ((size_t)1 << lg) * sizeof(V) +
+           (size_t)(SZ + 1) * (((2 * T3) >> lg) + 1) * ((size_t)1 << lg) * (sizeof(V) / 2);
+}
+
+// Two consecutive elements (16-byte aligned for float2 pairs).
+template <typename V> struct Two { V a, b; };
+__device__ __forceinline__ Two<float2> ld_two(const float2* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Two<double2> ld_two(const double2* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ void st_two(float2* p, const Two<float2>& t) {
+    *reinterpret_cast<float4*>(p) = make_float4(t.a.x, t.a.y, t.b.x, t.b.y);
+}
+__device__ __forceinline__ void st_two(double2* p, const Two<double2>& t) { p[0] = t.a; p[1] = t.b; }
+template <typename T> __device__ __forceinline__ Two<T> ld_two_s(const T* p) { return {p[0], p[1]}; }
+template <> __device__ __forceinline__ Two<float> ld_two_s<float>(const float* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return {v.x, v.y};
 }
 
 template <int SCHEME, int MODE, typename V>
@@ -199,32 +220,42 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
     const U3 d = g.desc[u];   // issued before the flag test
     if (sc && unit_skip(sc, u, MODE == MODE_RESID)) return;
     const int n = d.n, m = n - 1, lg = d.log2n;
-    const int TJ = T3 >> lg;                          // rows of the block
-    const int first = lb * T3;                        // (plane group, j0, 0)
+    const int TJ = (2 * T3) >> lg;                    // rows of the block
+    const int first = lb * (2 * T3);                  // (plane group, j0, 0)
     const int i0 = (first >> (2 * lg)) * SZ;
     const int j0 = (first >> lg) & m;
-    const int jl = threadIdx.x >> lg, k = threadIdx.x & m;
+    const int jl = threadIdx.x >> (lg - 1), k0 = 2 * (threadIdx.x & ((n >> 1) - 1));
     const int RW = TJ + 2, CR = TJ + 1;               // rows of the x and cell tiles
     V* xt = reinterpret_cast<V*>(smem_raw);                          // [SZ+2][RW][n]
     T* ct = reinterpret_cast<T*>(xt + (SZ + 2) * RW * n);            // [SZ+1][CR][n]
     const V* __restrict__ xu = x + d.off;
     const T am = two_values<T>(d, false), ai = two_values<T>(d, true);
-    // thread (jl, k) copies element k of tile rows jl, jl + TJ, jl + 2 TJ (those
-    // below RW, resp. CR) of each plane: every load is issued before the
-    // first shared-memory store, so a block waits for one round trip
-    V xr[SZ + 2][3];
-    T cr[SZ + 1][2];
     const uint8_t* __restrict__ mk8 = cs.mask + d.cell_off;
     const T* __restrict__ cf = cs.coef ? cs.coef + d.cell_off : nullptr;
+    // copy: thread (jl, k0) takes elements k0, k0+1 of tile rows jl, jl + TJ
+    // (those below RW, resp. CR) of each plane; x by asynchronous 16-byte
+    // copies (no registers held), the cell values through registers (they
+    // are converted), every load issued before the first store
+    constexpr int CHUNKS = (int)(2 * sizeof(V) / 16);   // 16-byte pieces of two elements
 #pragma unroll
     for (int pl = 0; pl < SZ + 2; ++pl) {
         const int gp = ((i0 - 1 + pl) & m) << (2 * lg);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < 2; ++q) {
             const int rr = jl + q * TJ;
-            if (rr < RW) xr[pl][q] = xu[gp + (((j0 - 1 + rr) & m) << lg) + k];
+            if (rr < RW) {
+                const char* gsrc = reinterpret_cast<const char*>(xu + gp + (((j0 - 1 + rr) & m) << lg) + k0);
+                const unsigned sdst = (unsigned)__cvta_generic_to_shared(xt + (pl * RW + rr) * n + k0);
+#pragma unroll
+                for (int c = 0; c < CHUNKS; ++c)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * c),
+                                 "l"(gsrc + 16 * c)
+                                 : "memory");
+            }
         }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    Two<T> cr[SZ + 1][2];
 #pragma unroll
     for (int pl = 0; pl < SZ + 1; ++pl) {
         const int gp = ((i0 - 1 + pl) & m) << (2 * lg);
@@ -232,104 +263,143 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
         for (int q = 0; q < 2; ++q) {
             const int rr = jl + q * TJ;
             if (rr < CR) {
-                const int idx = gp + (((j0 - 1 + rr) & m) << lg) + k;
-                cr[pl][q] = cf ? cf[idx] : (mk8[idx] ? ai : am);
+                const int idx = gp + (((j0 - 1 + rr) & m) << lg) + k0;
+                if (cf) {
+                    cr[pl][q] = ld_two_s(cf + idx);
+                } else {
+                    const uchar2 mb = *reinterpret_cast<const uchar2*>(mk8 + idx);
+                    cr[pl][q] = {mb.x ? ai : am, mb.y ? ai : am};
+                }
             }
         }
     }
-#pragma unroll
-    for (int pl = 0; pl < SZ + 2; ++pl)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int rr = jl + q * TJ;
-            if (rr < RW) xt[(pl * RW + rr) * n + k] = xr[pl][q];
-        }
 #pragma unroll
     for (int pl = 0; pl < SZ + 1; ++pl)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int rr = jl + q * TJ;
-            if (rr < CR) ct[(pl * CR + rr) * n + k] = cr[pl][q];
+            if (rr < CR) {
+                T* c = ct + (pl * CR + rr) * n + k0;
+                c[0] = cr[pl][q].a;
+                c[1] = cr[pl][q].b;
+            }
         }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    const int km = (k - 1) & m, kp = (k + 1) & m;
-    auto X = [&](int t, int o1, int o2, int o3) -> V {
-        const int kk = o3 < 0 ? km : (o3 == 0 ? k : kp);
-        return xt[((t + 1 + o1) * RW + (jl + 1 + o2)) * n + kk];
-    };
+    const int kl = (k0 - 1) & m, kr = (k0 + 2) & m;
     const T h = (T)d.h;
     // the cell bit that a neighbour offset fixes on its axis: +1 -> 0, -1 -> 1
     auto cb = [](int o) { return o > 0 ? 0 : 1; };
-    T dx = 0, dy = 0;
-#pragma unroll
-    for (int t = 0; t < SZ; ++t) {
-        T a[8];   // a[c]: the cell at offset (-c1, -c2, -c3), c = 4 c1 + 2 c2 + c3
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            a[c] = ct[((t + 1 - (c >> 2)) * CR + (jl + 1 - ((c >> 1) & 1))) * n + ((c & 1) ? km : k)];
-        T px[4], py[4], pz[4];   // pair sums along each axis, by the other two bits
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            px[q] = a[q] + a[4 + q];                                             // q = 2 c2 + c3
-            py[q] = a[4 * (q >> 1) + (q & 1)] + a[4 * (q >> 1) + 2 + (q & 1)];   // q = 2 c1 + c3
-            pz[q] = a[2 * q] + a[2 * q + 1];                                     // q = 2 c1 + c2
-        }
-        const T A0 = (px[0] + px[1]) + (px[2] + px[3]);
-        const V xc = X(t, 0, 0, 0);
-        V acc;
+    const T e0 = SCHEME == RVE_Q1_CONSISTENT ? h * (T)(1.0 / 3.0) : h * (T)0.75;
+    const T eo = SCHEME == RVE_Q1_CONSISTENT ? -h * (T)(1.0 / 12.0) : -h * (T)0.25;
+    // C[q]: the cell at (j - c2, k - c3) of a cell plane, q = 2 c2 + c3;
+    // X[a][b]: x at (j + a - 1, k + b - 1) of an x-plane
+    auto side = [&](const V (&X)[3][3], const T (&C)[4]) -> V {   // off-plane couplings
+        T sx = 0, sy = 0;
         if (SCHEME == RVE_Q1_CONSISTENT) {
-            T sx = 0, sy = 0;
 #pragma unroll
-            for (int e = 0; e < 12; ++e) {   // edge neighbours: o zero on one axis
-                const int zax = e >> 2, s1 = (e & 2) ? 1 : -1, s2 = (e & 1) ? 1 : -1;
-                V v;
-                T wgt;
-                if (zax == 0) { v = X(t, 0, s1, s2); wgt = px[2 * cb(s1) + cb(s2)]; }
-                else if (zax == 1) { v = X(t, s1, 0, s2); wgt = py[2 * cb(s1) + cb(s2)]; }
-                else { v = X(t, s1, s2, 0); wgt = pz[2 * cb(s1) + cb(s2)]; }
-                sx = fma(wgt, v.x, sx);
-                sy = fma(wgt, v.y, sy);
+            for (int s2 = -1; s2 <= 1; s2 += 2) {
+                const T wy = C[cb(s2)] + C[2 + cb(s2)];           // edge (., 0, s2)
+                sx = fma(wy, X[1][1 + s2].x, sx);
+                sy = fma(wy, X[1][1 + s2].y, sy);
+                const T wz = C[2 * cb(s2)] + C[2 * cb(s2) + 1];   // edge (., s2, 0)
+                sx = fma(wz, X[1 + s2][1].x, sx);
+                sy = fma(wz, X[1 + s2][1].y, sy);
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {    // corner neighbours: one cell each
-                const int o1 = (c & 4) ? 1 : -1, o2 = (c & 2) ? 1 : -1, o3 = (c & 1) ? 1 : -1;
-                const T wgt = a[4 * cb(o1) + 2 * cb(o2) + cb(o3)];
-                const V v = X(t, o1, o2, o3);
-                sx = fma(wgt, v.x, sx);
-                sy = fma(wgt, v.y, sy);
+            for (int c = 0; c < 4; ++c) {                          // corners (., o2, o3)
+                const int o2 = (c & 2) ? 1 : -1, o3 = (c & 1) ? 1 : -1;
+                const T w = C[2 * cb(o2) + cb(o3)];
+                sx = fma(w, X[1 + o2][1 + o3].x, sx);
+                sy = fma(w, X[1 + o2][1 + o3].y, sy);
             }
-            const T e0 = h * (T)(1.0 / 3.0), e23 = -h * (T)(1.0 / 12.0);
-            acc.x = fma(e23, sx, e0 * A0 * xc.x);
-            acc.y = fma(e23, sy, e0 * A0 * xc.y);
-        } else {
-            T sx = 0, sy = 0;
-#pragma unroll
-            for (int fc = 0; fc < 6; ++fc) {  // face neighbours: 4 cells with the bit fixed
-                const int ax = fc >> 1, sg = (fc & 1) ? 1 : -1, v0 = cb(sg);
-                V v;
-                T wgt;
-                if (ax == 0) { v = X(t, sg, 0, 0); wgt = pz[2 * v0] + pz[2 * v0 + 1]; }
-                else if (ax == 1) { v = X(t, 0, sg, 0); wgt = pz[v0] + pz[2 + v0]; }
-                else { v = X(t, 0, 0, sg); wgt = py[v0] + py[2 + v0]; }
-                sx = fma(wgt, v.x, sx);
-                sy = fma(wgt, v.y, sy);
-            }
-            const T e0 = h * (T)0.75, e1 = -h * (T)0.25;
-            acc.x = fma(e1, sx, e0 * A0 * xc.x);
-            acc.y = fma(e1, sy, e0 * A0 * xc.y);
+        } else {                                                    // face (., 0, 0)
+            const T w = (C[0] + C[1]) + (C[2] + C[3]);
+            sx = w * X[1][1].x;
+            sy = w * X[1][1].y;
         }
-        const int64_t node = d.off + ((int64_t)(i0 + t) << (2 * lg)) + ((j0 + jl) << lg) + k;
+        return mk<V>(eo * sx, eo * sy);
+    };
+    auto inplane = [&](const V (&X)[3][3], const T (&Cm)[4], const T (&C0)[4]) -> V {
+        T px[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) px[q] = Cm[q] + C0[q];
+        const T A0 = (px[0] + px[1]) + (px[2] + px[3]);
+        T sx = 0, sy = 0;
+        if (SCHEME == RVE_Q1_CONSISTENT) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {                          // edges (0, s1, s2)
+                const int s1 = (c & 2) ? 1 : -1, s2 = (c & 1) ? 1 : -1;
+                const T w = px[2 * cb(s1) + cb(s2)];
+                sx = fma(w, X[1 + s1][1 + s2].x, sx);
+                sy = fma(w, X[1 + s1][1 + s2].y, sy);
+            }
+        } else {
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const int v0 = cb(sg);
+                const T wj = px[2 * v0] + px[2 * v0 + 1];           // face (0, sg, 0)
+                sx = fma(wj, X[1 + sg][1].x, sx);
+                sy = fma(wj, X[1 + sg][1].y, sy);
+                const T wk = px[v0] + px[2 + v0];                   // face (0, 0, sg)
+                sx = fma(wk, X[1][1 + sg].x, sx);
+                sy = fma(wk, X[1][1 + sg].y, sy);
+            }
+        }
+        const T dA = e0 * A0;
+        return mk<V>(fma(eo, sx, dA * X[1][1].x), fma(eo, sy, dA * X[1][1].y));
+    };
+    // cells of tile plane pl for the two nodes
+    auto cells = [&](int pl, T (&c0)[4], T (&c1)[4]) {
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const T* r = ct + (pl * CR + jl + 1 - c2) * n;
+            const Two<T> M = ld_two_s(r + k0);
+            const T Lv = r[kl];
+            c0[2 * c2] = M.a;       // node k0: c3 = 0 -> k0, c3 = 1 -> k0 - 1
+            c0[2 * c2 + 1] = Lv;
+            c1[2 * c2] = M.b;       // node k0 + 1: c3 = 0 -> k0 + 1, c3 = 1 -> k0
+            c1[2 * c2 + 1] = M.a;
+        }
+    };
+    T dx = 0, dy = 0;
+#pragma unroll 1
+    for (int t = 0; t < SZ; ++t) {
+        T Cm0[4], Cm1[4], C00[4], C01[4];
+        cells(t, Cm0, Cm1);
+        cells(t + 1, C00, C01);
+        V acc0 = mk<V>((T)0, (T)0), acc1 = acc0;
+#pragma unroll
+        for (int o1 = -1; o1 <= 1; ++o1) {
+            V X0[3][3], X1[3][3];
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) {
+                const V* r = xt + ((t + 1 + o1) * RW + jl + a2) * n;
+                const Two<V> M = ld_two(r + k0);
+                const V Lv = r[kl], Rv = r[kr];
+                X0[a2][0] = Lv;  X0[a2][1] = M.a; X0[a2][2] = M.b;
+                X1[a2][0] = M.a; X1[a2][1] = M.b; X1[a2][2] = Rv;
+            }
+            V v0, v1;
+            if (o1 < 0) { v0 = side(X0, Cm0); v1 = side(X1, Cm1); }
+            else if (o1 == 0) { v0 = inplane(X0, Cm0, C00); v1 = inplane(X1, Cm1, C01); }
+            else { v0 = side(X0, C00); v1 = side(X1, C01); }
+            acc0.x += v0.x; acc0.y += v0.y;
+            acc1.x += v1.x; acc1.y += v1.y;
+        }
+        const int64_t node = d.off + ((int64_t)(i0 + t) << (2 * lg)) + ((j0 + jl) << lg) + k0;
+        const Two<V> xc = ld_two(xt + ((t + 1) * RW + jl + 1) * n + k0);
         if (MODE == MODE_RESID) {
-            const V ff = f[node];
-            acc.x = ff.x - acc.x;
-            acc.y = ff.y - acc.y;
-            dx = fma(acc.x, acc.x, dx);
-            dy = fma(acc.y, acc.y, dy);
+            const Two<V> ff = ld_two(f + node);
+            acc0.x = ff.a.x - acc0.x; acc0.y = ff.a.y - acc0.y;
+            acc1.x = ff.b.x - acc1.x; acc1.y = ff.b.y - acc1.y;
+            dx = fma(acc0.x, acc0.x, fma(acc1.x, acc1.x, dx));
+            dy = fma(acc0.y, acc0.y, fma(acc1.y, acc1.y, dy));
         } else {
-            dx = fma(xc.x, acc.x, dx);
-            dy = fma(xc.y, acc.y, dy);
+            dx = fma(xc.a.x, acc0.x, fma(xc.b.x, acc1.x, dx));
+            dy = fma(xc.a.y, acc0.y, fma(xc.b.y, acc1.y, dy));
         }
-        y[node] = acc;
+        st_two(y + node, Two<V>{acc0, acc1});
     }
     if (part) {   // block-uniform
         double tx = 0.0, ty = 0.0;
@@ -1151,7 +1221,7 @@ template <int MODE, typename V>
 static cudaError_t stiffness3(const Ws3& ws, const Group3& g, Cells3T<typename ScalarOf<V>::T> cs,
                               int scheme, const V* x, V* y, const V* f, bool partials,
                               const MixScal* sc, cudaStream_t s) {
-    const int per = (int)(nodes_of(g) / (T3 * SZ));
+    const int per = (int)(nodes_of(g) / (2 * T3 * SZ));
     const Grp gg = ws.grp(g, per);
     double* part = partials ? ws.part() : nullptr;
     const size_t smem = stiff_smem<V>(g.log2n);
@@ -1187,10 +1257,10 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
         Span3 sp(s, P3_VECTOR);
         launch();
     };
-    // partial pairs per unit: n^3 >> shift (rhs: 256 nodes per block;
-    // stiffness and axpy: 1024; last line pass: 2048)
-    constexpr int SH_RHS = 8, SH_STIFF = 10, SH_AXPY = 10, SH_LINES = 11;
-    static_assert(T3 * SZ == (1 << SH_STIFF) && 4 * T3 == (1 << SH_AXPY) && T3 == (1 << SH_RHS),
+    // partial pairs per unit: n^3 >> shift (rhs: 256 nodes per block; axpy:
+    // 1024; stiffness and the last line pass: 2048)
+    constexpr int SH_RHS = 8, SH_STIFF = 11, SH_AXPY = 10, SH_LINES = 11;
+    static_assert(2 * T3 * SZ == (1 << SH_STIFF) && 4 * T3 == (1 << SH_AXPY) && T3 == (1 << SH_RHS),
                   "partial counts");
     auto scalar = [&](const Group3& g, int what, int shift) {
         Span3 sp(s, P3_SCALAR);
