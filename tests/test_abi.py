@@ -96,6 +96,32 @@ def test_host_validation_3d_without_gpu(librve):
                                     None) == rve.RVE_EINVAL
 
 
+def test_solve3_option_validation_without_gpu(librve):
+    # every check below returns before the first CUDA call: the pointers are
+    # never dereferenced on the host
+    from paper_1903_12227_gb300 import rve, rve3, workloads
+    L3 = rve3.lib()
+    b = rve3.Batch3([workloads.realization3(4, 8, 10.0, 0, 0)])
+    fake = ctypes.c_void_p(256)
+    need = L3.rve3_workspace_size(b.ptr, 1)
+
+    def call(opts, ws_bytes=need):
+        return L3.rve3_solve_correctors(b.ptr, 1, fake, None, ctypes.byref(opts), fake, fake, fake,
+                                        ws_bytes, None)
+
+    for bad in (rve3.make_opts3(delta=-1.0), rve3.make_opts3(delta=float("inf")),
+                rve3.make_opts3(tol=2.0), rve3.make_opts3(inner_tol=1.5),
+                rve3.make_opts3(precision=7), rve3.make_opts3(scheme=-1)):
+        assert call(bad) == rve.RVE_EINVAL
+    assert call(rve3.make_opts3(precision=rve.MIXED), ws_bytes=need - 1) == rve.RVE_ENOMEM
+    # the other 3D entry points check their workspace the same way
+    assert L3.rve3_rhs(b.ptr, 1, fake, None, 0, fake, fake, need - 1, None) == rve.RVE_ENOMEM
+    assert L3.rve3_rhs(b.ptr, 1, fake, None, 5, fake, fake, need, None) == rve.RVE_EINVAL
+    assert L3.rve3_apply_stiffness(b.ptr, 1, fake, None, 0, fake, fake, fake, need, None) == rve.RVE_EINVAL
+    assert L3.rve3_apply_precond(b.ptr, 1, -0.5, fake, fake, fake, need, None) == rve.RVE_EINVAL
+    assert L3.rve3_a_hom(b.ptr, 1, None, None, 0, fake, fake, None, fake, need, None) == rve.RVE_EINVAL
+
+
 def test_uneven_batch_sizes_add_up(librve):
     from paper_1903_12227_gb300 import rve, workloads
     ds = workloads.config_batch("uneven_4096", seed=3, count=40)
