@@ -81,9 +81,11 @@ class Clocks:
     """nvidia-smi sampling during the timed region."""
 
     def __init__(self, index: int):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # samples go to a temporary file; their summary goes into the JSON line
+        self.path = os.path.join(tempfile.gettempdir(), f"rve_bench_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
