@@ -29,9 +29,11 @@
  *      covariance / quartic tensor (Eq. "quartic");
  *   8. for a general load (the FEM convergence test of Sec. 3.5): the mass
  *      matrix M1 (x) M1 applied cell by cell, and the solve A u = b;
- *   9. the 3D extension (the paper's remark that the scheme extends to 3D):
- *      cubes, the trilinear element K1(x)M1(x)M1 + M1(x)K1(x)M1 + M1(x)M1(x)K1,
- *      the 7-point Laplacian preconditioner, three correctors, 3x3 A_hom.
+ *   9. the 3D extension (Sec. 2: the setting carries over to d > 2; Sec.
+ *      3.1-3.2 and Eq. "As_Kron_d": multilinear elements on cubes and the
+ *      rank-3 Kronecker Laplacian): cubes, the trilinear element
+ *      K1(x)M1(x)M1 + M1(x)K1(x)M1 + M1(x)M1(x)K1, the 7-point Laplacian
+ *      preconditioner, three correctors, 3x3 A_hom.
  *
  * Readings of the paper that this oracle fixes (where it is silent or
  * garbled) are listed beside each function.  Everything is FP64.
