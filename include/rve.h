@@ -438,6 +438,16 @@ rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* ma
                       const double* coef, int32_t scheme, const double* u, double* A,
                       double* A_flux, void* ws, size_t ws_bytes, void* stream);
 
+/* Ensemble statistics of 3D realizations (host memory, host arithmetic,
+ * FP64, summed in index order).  A: double[N][9] (row-major 3x3 A_hom) of
+ * N >= 2 realizations of RVE size L.  Outputs (each nullable): mean[9]
+ * (Eq. "A_hom_Empir"), var[9] unbiased sample variance of each entry, and
+ * Q[81] = L^3/(N-1) sum_n (A_n - mean)(x)(A_n - mean), the 9x9 unfolding of
+ * the quartic tensor of Eq. "quartic" in d = 3 (entries in row-major order
+ * a11 .. a33).  Errors: RVE_EINVAL (N < 2, L not positive, A NULL). */
+rve_status rve3_statistics(const double* A, int64_t N, double L, double* mean, double* var,
+                           double* Q);
+
 /* Diagnostics for benchmarks (process-wide, not thread-safe).
  * rve_profile_enable(1): the fused solver brackets every launch of its five
  * pipeline kernels with CUDA events on the caller's stream and accumulates

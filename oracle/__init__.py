@@ -101,6 +101,8 @@ def lib():
         L.orc_solve_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, dbl, ctypes.c_int, dbl,
                                       vp, ctypes.c_int]
         L.orc_statistics.argtypes = [i64, vp, dbl, ctypes.c_int, vp, vp, vp, vp, vp]
+        L.orc3_statistics.restype = None
+        L.orc3_statistics.argtypes = [i64, vp, dbl, vp, vp, vp]
         L.orc_mass_element.argtypes = [ctypes.c_int, dbl, vp]
         L.orc3_gen_field.argtypes = [ctypes.POINTER(Realization), vp]
         L.orc3_element_matrix.argtypes = [ctypes.c_int, dbl, vp]
@@ -431,3 +433,11 @@ def statistics(A: np.ndarray, L: float, d: int = 2) -> dict:
                          ctypes.byref(sd), _p(Q))
     return {"mean": mean.reshape(2, 2), "var": var.reshape(2, 2), "std12_paper": s12.value,
             "stddiff_paper": sd.value, "Q": Q.reshape(4, 4)}
+
+
+def statistics3(A: np.ndarray, L: float) -> dict:
+    """Mean, unbiased variance and the 9x9 unfolding of L^3 cov(A) of 3D A_hom [N,3,3]."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(-1, 9))
+    mean, var, Q = np.zeros(9), np.zeros(9), np.zeros(81)
+    lib().orc3_statistics(A.shape[0], _p(A), float(L), _p(mean), _p(var), _p(Q))
+    return {"mean": mean.reshape(3, 3), "var": var.reshape(3, 3), "Q": Q.reshape(9, 9)}

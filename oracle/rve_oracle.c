@@ -665,6 +665,26 @@ void orc_statistics(int64_t N, const double* A, double L, int d, double* mean,
     for (int k = 0; k < 4; ++k) var[k] = Q[4 * k + k] / pow(L, (double)d);
 }
 
+/* The same for 3D: A [N][9] row-major; Q[81] = L^3/(N-1) sum (A-mean)(x)2,
+ * Q[9*p+q] with p, q over the entries a11 .. a33. */
+void orc3_statistics(int64_t N, const double* A, double L, double* mean, double* var, double* Q)
+{
+    for (int k = 0; k < 9; ++k) {
+        double s = 0.0;
+        for (int64_t m = 0; m < N; ++m) s += A[9 * m + k];
+        mean[k] = s / (double)N;
+    }
+    const double L3 = L * L * L;
+    for (int p = 0; p < 9; ++p)
+        for (int q = 0; q < 9; ++q) {
+            double s = 0.0;
+            for (int64_t m = 0; m < N; ++m)
+                s += (A[9 * m + p] - mean[p]) * (A[9 * m + q] - mean[q]);
+            Q[9 * p + q] = L3 * s / (double)(N - 1);
+        }
+    for (int k = 0; k < 9; ++k) var[k] = Q[9 * k + k] / L3;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 9. The 3D extension (the paper's remark on 3D): cubes, trilinear Q1       */
 /* ------------------------------------------------------------------------ */

@@ -76,6 +76,7 @@ int orc_solve_load(int64_t L, int64_t m0, const double* coef, double c0, int sch
                    const double* b, double tol, int max_iter, double delta, double* u,
                    double* relres_true);
 
+void orc3_statistics(int64_t N, const double* A, double L, double* mean, double* var, double* Q);
 /* The 3D extension (cubes, trilinear Q1, 3x3 A_hom). */
 typedef struct {
     int iters[3];

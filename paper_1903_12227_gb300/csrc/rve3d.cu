@@ -1551,6 +1551,30 @@ rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* ma
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
 
+rve_status rve3_statistics(const double* A, int64_t N, double L, double* mean, double* var,
+                           double* Q) {
+    if (!A || N < 2 || !(L > 0.0) || !std::isfinite(L)) return RVE_EINVAL;
+    double m[9] = {};
+    for (int64_t k = 0; k < N; ++k)
+        for (int e = 0; e < 9; ++e) m[e] += A[9 * k + e];
+    for (int e = 0; e < 9; ++e) m[e] /= (double)N;
+    std::vector<double> c(81, 0.0);
+    for (int64_t k = 0; k < N; ++k) {
+        double dev[9];
+        for (int e = 0; e < 9; ++e) dev[e] = A[9 * k + e] - m[e];
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) c[9 * i + j] += dev[i] * dev[j];
+    }
+    const double L3 = L * L * L;
+    for (int e = 0; e < 9; ++e) {
+        if (mean) mean[e] = m[e];
+        if (var) var[e] = c[10 * e] / (double)(N - 1);
+    }
+    if (Q)
+        for (int e = 0; e < 81; ++e) Q[e] = L3 * c[e] / (double)(N - 1);
+    return RVE_OK;
+}
+
 int32_t rve3_profile_read(double* ms, int64_t* launches) {
     for (int j = 0; j < P3_K; ++j) {
         if (ms) ms[j] = g_prof3.ms[j];

@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
         L.rve3_a_hom.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, sz, vp]
         L.rve3_profile_read.restype = i32
         L.rve3_profile_read.argtypes = [vp, vp]
+        L.rve3_statistics.restype = i32
+        L.rve3_statistics.argtypes = [vp, i64, dbl, vp, vp, vp]
         _bound = True
     return L
 
@@ -207,6 +209,19 @@ def a_hom(batch, u: torch.Tensor, mask=None, coef=None, scheme=CONSISTENT, ws=No
                            _ptr(Af), _ptr(ws), ws.numel(), _stream(stream)), "rve3_a_hom")
     A = A.view(b.count, 3, 3)
     return (A, Af.view(b.count, 3, 3)) if want_flux else A
+
+
+def statistics(A, L: float) -> dict:
+    """Ensemble mean, unbiased variance and Q = L^3 cov (9x9 unfolding of the
+    quartic tensor) of 3D A_hom [N, 3, 3] (host arithmetic, index order)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(A.cpu() if hasattr(A, "cpu") else A,
+                                        dtype=np.float64).reshape(-1, 9))
+    mean, var, Q = np.zeros(9), np.zeros(9), np.zeros(81)
+    p = lambda x: ctypes.c_void_p(x.ctypes.data)
+    check(lib().rve3_statistics(p(a), a.shape[0], float(L), p(mean), p(var), p(Q)),
+          "rve3_statistics")
+    return {"mean": mean.reshape(3, 3), "var": var.reshape(3, 3), "Q": Q.reshape(9, 9)}
 
 
 PROFILE_KINDS = ("stiffness", "lines", "zsolve", "vector", "scalar", "resid64")

@@ -297,6 +297,7 @@ def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=None, contrast=10.0, seed=0, tol=1e-1
                            "GBs": round(gbs, 1) if gbs else None,
                            "frac_of_measured": round(gbs / peak, 3) if gbs and peak else None}
         Ad = A.diagonal(dim1=1, dim2=2).cpu().numpy()
+        st = rve3.statistics(A, L) if NL >= 2 else None
         rows.append({"L": L, "m0": m0, "n": n, "N": NL, "contrast": contrast, "tol": tol,
                      "precision": "fp64" if prec == rve.FP64 else "mixed",
                      "refinements_mean": float(np.mean([i["refinements"] for i in infos])),
@@ -309,6 +310,7 @@ def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=None, contrast=10.0, seed=0, tol=1e-1
                      "offdiag_max": float(np.abs(A.cpu().numpy() - np.einsum(
                          "bi,ij->bij", Ad, np.eye(3))).max()),
                      "active_unit_fraction": round(active, 3),
+                     "L3_var_diag": [float(st["Q"][4 * k, 4 * k]) for k in range(3)] if st else None,
                      "kernels": kinds, "hbm_peak_GBs": peak})
     return rows
 

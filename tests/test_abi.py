@@ -122,6 +122,21 @@ def test_solve3_option_validation_without_gpu(librve):
     assert L3.rve3_a_hom(b.ptr, 1, None, None, 0, fake, fake, None, fake, need, None) == rve.RVE_EINVAL
 
 
+def test_statistics3_host_matches_oracle(librve):
+    import numpy as np
+
+    import oracle
+    from paper_1903_12227_gb300 import rve, rve3
+    g = np.random.default_rng(5)
+    A = 3.0 + 0.1 * g.standard_normal((64, 3, 3))
+    s = rve3.statistics(A, 4.0)
+    o = oracle.statistics3(A, 4.0)
+    for k in ("mean", "var", "Q"):
+        np.testing.assert_allclose(s[k], o[k], rtol=1e-13, atol=1e-16)
+    with pytest.raises(rve.RveError):
+        rve3.statistics(A[:1], 4.0)
+
+
 def test_uneven_batch_sizes_add_up(librve):
     from paper_1903_12227_gb300 import rve, workloads
     ds = workloads.config_batch("uneven_4096", seed=3, count=40)

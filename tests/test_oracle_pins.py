@@ -665,3 +665,20 @@ def test_a_hom3_energy_equals_flux_at_convergence():
     np.testing.assert_allclose(A, A.T, atol=1e-13)
     assert np.linalg.eigvalsh(A)[0] > 0.0
     np.testing.assert_allclose(F, A, atol=1e-9 * np.abs(A).max())
+
+
+def test_statistics3_match_numpy():
+    g = np.random.default_rng(8)
+    A = g.standard_normal((40, 3, 3))
+    A = 0.5 * (A + A.transpose(0, 2, 1))
+    L = 8
+    s = oracle.statistics3(A, L)
+    flat = A.reshape(40, 9)
+    np.testing.assert_allclose(s["mean"].ravel(), flat.mean(axis=0), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(s["Q"], L ** 3 * np.cov(flat, rowvar=False, ddof=1), rtol=1e-12,
+                               atol=1e-13)
+    np.testing.assert_allclose(s["var"].ravel(), flat.var(axis=0, ddof=1), rtol=1e-12)
+    # symmetric A: the rows and columns of a_ij and a_ji coincide
+    Q = s["Q"]
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        np.testing.assert_allclose(Q[3 * i + j], Q[3 * j + i], atol=1e-12)
