@@ -682,3 +682,23 @@ def test_statistics3_match_numpy():
     Q = s["Q"]
     for i, j in ((0, 1), (0, 2), (1, 2)):
         np.testing.assert_allclose(Q[3 * i + j], Q[3 * j + i], atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
+def test_rhs3_equals_the_row_sum_closed_form(scheme):
+    # the rows of M1 sum to h/2 (both schemes) and those of K1 to 0, so only
+    # the K1 term along axis i survives in E xi_i and
+    #   f_i(node) = (h^2/4) (sum of the 4 cells above along i - the 4 below)
+    n, h = 6, 0.3
+    a = np.random.default_rng(13).uniform(0.5, 4.0, size=(n, n, n))
+    f = oracle.rhs3(a, h, scheme)
+    ref = np.zeros_like(f)
+    for ax in range(3):
+        above = a                                   # cells whose lower corner is the node
+        below = np.roll(a, 1, axis=ax)              # the cells one step down along ax
+        s_above = sum(np.roll(np.roll(above, o1, axis=(ax + 1) % 3), o2, axis=(ax + 2) % 3)
+                      for o1 in (0, 1) for o2 in (0, 1))
+        s_below = sum(np.roll(np.roll(below, o1, axis=(ax + 1) % 3), o2, axis=(ax + 2) % 3)
+                      for o1 in (0, 1) for o2 in (0, 1))
+        ref[ax] = 0.25 * h * h * (s_above - s_below)
+    np.testing.assert_allclose(f, ref, atol=1e-14 * np.abs(ref).max())
