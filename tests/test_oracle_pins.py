@@ -702,3 +702,32 @@ def test_rhs3_equals_the_row_sum_closed_form(scheme):
                       for o1 in (0, 1) for o2 in (0, 1))
         ref[ax] = 0.25 * h * h * (s_above - s_below)
     np.testing.assert_allclose(f, ref, atol=1e-14 * np.abs(ref).max())
+
+
+# ------------------------------------------- statistical identities (Sec. 4) --
+def test_ensemble_isotropy_and_zero_mean_off_diagonal():
+    # the inclusion law is invariant under swapping the axes and under
+    # reflections, so E a_11 = E a_22 and E a_12 = 0; the Q entries of
+    # Eq. "quartic" inherit the swap symmetry: Q_1111 = Q_2222 (sampling error)
+    ds = [workloads.realization(4, 4, 10.0, 17, k) for k in range(240)]
+    A, _, _ = oracle.solve_batch(ds, tol=1e-10)
+    a11, a22, a12 = A[:, 0, 0], A[:, 1, 1], A[:, 0, 1]
+    se = lambda x: x.std(ddof=1) / np.sqrt(len(x))
+    assert abs(a11.mean() - a22.mean()) < 4 * se(a11 - a22)
+    assert abs(a12.mean()) < 4 * se(a12)
+    s = oracle.statistics(A, 4.0)
+    Q = s["Q"]
+    # var(a11) = var(a22) within the sampling error of a variance (~sqrt(2/N))
+    assert abs(Q[0, 0] - Q[3, 3]) < 4 * np.sqrt(2.0 / len(A)) * max(Q[0, 0], Q[3, 3])
+
+
+def test_ensemble_isotropy3():
+    ds = [{"L": 2, "m0": 4, "incl_cells": 4, "n_incl": 6, "a_matrix": 1.0, "a_incl": 8.0,
+           "seed": 23, "index": k} for k in range(120)]
+    A = np.array([oracle.solve_realization3(d, tol=1e-10, want_u=False)["A_energy"] for d in ds])
+    se = lambda x: x.std(ddof=1) / np.sqrt(len(x))
+    diag = [A[:, i, i] for i in range(3)]
+    for i in range(3):
+        for j in range(i + 1, 3):
+            assert abs(diag[i].mean() - diag[j].mean()) < 4 * se(diag[i] - diag[j])
+            assert abs(A[:, i, j].mean()) < 4 * se(A[:, i, j])
