@@ -385,6 +385,10 @@ def test_workload_inclusion_counts():
     assert workloads.realization(256, 8, 100, 0, 0)["n_incl"] == 45875
     assert workloads.realization(8, 8, 10, 0, 0)["n_incl"] == 45
     assert workloads.realization(16, 8, 10, 0, 0)["n_incl"] == 179
+    # 3D: round(0.7 L^3) unit cubes
+    assert [workloads.realization3(L, 16, 10, 0, 0)["n_incl"] for L in (2, 4, 8, 16)] == \
+        [6, 45, 358, 2867]
+    assert workloads.realization3(4, 16, 10, 0, 0)["incl_cells"] == 16
 
 
 # ------------------------------------------------- general load (Sec. 3.5) --
