@@ -113,19 +113,9 @@ typedef struct {
     int32_t check_every; /* host convergence poll period (0 = 8)            */
     int32_t timeout_us;  /* persistent path: bound on each grid-wide wait, in
                             microseconds (0 = 2 s)                          */
-    int32_t flags;       /* RVE_FLAG_* bits                                 */
+    int32_t flags;       /* must be 0                                       */
     int32_t reserved;    /* must be 0                                       */
 } rve_solve_opts;
-
-/* rve_solve_opts.flags.  RVE_FLAG_CLUSTER: on the fused mixed-precision
- * path, run the update and column passes of a batch of equal-size grids
- * (n = 128..512) as one thread-block-cluster kernel (16 blocks per
- * realization, the row transform kept in distributed shared memory instead
- * of HBM) when the device can host such clusters.  It moves 16 fewer bytes
- * per node and step but runs one block per SM with its phases in sequence;
- * on GB300 it measured slower than the two separate kernels (547 vs 367 us
- * per step for 125 grids of 512^2), so it is off by default. */
-#define RVE_FLAG_CLUSTER 1
 
 /* Per-realization solver report (device memory, one per realization). */
 typedef struct {
@@ -134,8 +124,7 @@ typedef struct {
     int32_t refinements;  /* true-residual evaluations (FP64 or double word)      */
     int32_t steps;        /* fused pipeline steps spent iterating (both correctors
                              advance together; plain path: CG iterations)         */
-    int32_t kernels;      /* bit 0: the update and column passes ran as one
-                             thread-block-cluster kernel (RVE_FLAG_CLUSTER)    */
+    int32_t reserved;     /* 0                                                    */
     double relres[2];     /* last FP64 true relative residual per corrector       */
 } rve_solve_info;         /* 40 bytes */
 
@@ -244,13 +233,24 @@ rve_status rve_solve_rhs(const rve_realization* r, int32_t batch, const uint32_t
 
 /* Homogenized matrix of every realization from its correctors u.
  * A: energy form a_ij = (1/L^2) int (e_j + grad phi_j).a(e_i + grad phi_i)
- * (Eq. "wg01" as rewritten in its symmetry argument), evaluated exactly as
- * mean(a) delta_ij - (f_i.u_j + f_j.u_i - u_i.A u_j)/L^2 in FP64.
- * A_flux (nullable): flux form of Eq. "Ahom_m_entry",
- * a_ij = mean(a) delta_ij - f_j.u_i / L^2.  Both device double[batch][4]. */
+ * (Eq. "wg01" as rewritten in its symmetry argument), summed cell by cell as
+ * (1/L^2) sum_c a_c (xi_i + P_c u_i)^T E (xi_j + P_c u_j) -- equal to the
+ * node form mean(a) delta_ij - (f_i.u_j + f_j.u_i - u_i.A u_j)/L^2, but
+ * without its cancellation.  A_flux (nullable): flux form of Eq.
+ * "Ahom_m_entry", a_ij = mean(a) delta_ij - f_j.u_i / L^2.  Both device
+ * double[batch][4].
+ * precision: RVE_FP64 sums in double-double arithmetic on the FP64 pipe
+ * (differences of u across a cell exact, ~106-bit sums), so A is the
+ * correctly rounded energy of the given u up to a few units in the last
+ * place; A_lo (nullable, RVE_FP64 only) then receives the low parts, and
+ * A + A_lo carries the energy to ~1e-30 relative -- enough to difference two
+ * nearby A_hom (finite differences) without FP64 cancellation.
+ * RVE_MIXED sums in double words on the FP32 pipe (~1e-14 relative; GB300's
+ * FP64 pipe is ~1/64 of FP32), for the mixed-precision pipeline; A_lo must
+ * be NULL.  ws: rve_workspace_size() bytes. */
 rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* mask,
-                     const double* coef, int32_t scheme, const double* u,
-                     double* A, double* A_flux, void* ws, size_t ws_bytes,
+                     const double* coef, int32_t scheme, int32_t precision, const double* u,
+                     double* A, double* A_lo, double* A_flux, void* ws, size_t ws_bytes,
                      void* stream);
 
 /* Adjoint of the energy form: grad_coef[cell] = d(sum_ij gradA_ij a_ij)/d a_c
@@ -333,14 +333,17 @@ rve_status rve_statistics(const double* A, int64_t N, double L, int32_t d, doubl
  * device memory: programs whose device memory is all owned by their own pool
  * allocator, and latency-critical loops that cannot afford cudaMalloc /
  * cudaFree (which may synchronise the device).  It takes no workspace.  The
- * paper has no counterpart; results equal rve_a_hom's (same sums, same
- * order).
+ * paper has no counterpart; results equal those of rve_a_hom with precision
+ * RVE_MIXED (same double-word sums, same order).
  * Scratch: a fixed library-owned device array of 1 MiB (8 partial sums per
  * 1024 nodes) that every GPU loading the library holds until exit; requests
  * above RVE_NOALLOC_MAX_NODES nodes in total return RVE_ESCRATCH before
  * anything is launched.  The first call on a device does a one-time set-up
  * (it looks up the array's device address with that device current): make
- * that first call before any stream capture.  All calls share the array and
+ * that first call before any stream capture.  The set-up is not repeated, so
+ * after cudaDeviceReset (or any other teardown of the device's primary
+ * context) in the same process the recorded address is stale: do not call
+ * this entry point on that device again.  All calls share the array and
  * it keeps the last call's contents; each call writes every partial it reads,
  * so nothing needs clearing, but calls that overlap on the GPU (other streams
  * or host threads) race on it and must be serialised by the caller.

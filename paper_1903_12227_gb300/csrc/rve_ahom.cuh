@@ -137,6 +137,148 @@ __device__ __forceinline__ void a_hom_tile(const RDesc& d, int64_t tile, CoefSrc
 }
 
 
+// FP64 form of a_hom_tile (the A_hom of FP64 solves): the same cell sums in
+// double-double arithmetic on the FP64 pipe.  Differences of u across a cell
+// are exact (TwoSum), products and sums carry ~106 bits, so the only error
+// left in A_hom is that of the correctors themselves -- which enters the
+// energy form only quadratically (it is stationary at the exact solution).
+// Partials out[2k], out[2k+1] = (hi, lo) of the same eight sums, valid in
+// thread 0; `red` holds 32 * AHOM_NP ddouble (shared).  Contains barriers.
+template <int SCHEME>
+__device__ __forceinline__ void a_hom_tile_dd(const RDesc& d, int64_t tile, CoefSrc cs,
+                                              const double2* __restrict__ u, ddouble* red,
+                                              double* out) {
+    const double h = d.h;
+    constexpr double Q = SCHEME == 0 ? 2.0 : 0.0;   // K |E| on the cell diagonals
+    const int n = d.n;
+    auto at = [&](int i, int j) {   // periodic node access
+        return u[d.node_off + ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1))];
+    };
+    ddouble acc[AHOM_NP];
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) acc[k] = ddouble{0.0, 0.0};
+    const int64_t base = tile * AHOM_TILE;
+    for (int t = threadIdx.x; t < AHOM_TILE; t += blockDim.x) {
+        const int64_t cidx = base + t;
+        const int i = (int)(cidx >> d.log2n), j = (int)(cidx & (n - 1));
+        double a;
+        if (cs.coef) {
+            a = __ldg(cs.coef + d.node_off + cidx);
+        } else {
+            const uint32_t w = __ldg(cs.mask + d.word_off + (cidx >> 5));
+            a = ((w >> (cidx & 31)) & 1u) ? d.a_incl : d.a_matrix;
+        }
+        const double2 r00 = at(i, j), r01 = at(i, j + 1);
+        const double2 r10 = at(i + 1, j), r11 = at(i + 1, j + 1);
+        // exact u differences per corrector: 01-00, 10-00, 11-00, 10-01,
+        // 11-01, 11-10
+        ddouble D[2][6];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const double u00 = c ? r00.y : r00.x, u01 = c ? r01.y : r01.x;
+            const double u10 = c ? r10.y : r10.x, u11 = c ? r11.y : r11.x;
+            D[c][0] = dd_sub(u01, u00);
+            D[c][1] = dd_sub(u10, u00);
+            D[c][2] = dd_sub(u11, u00);
+            D[c][3] = dd_sub(u10, u01);
+            D[c][4] = dd_sub(u11, u01);
+            D[c][5] = dd_sub(u11, u10);
+        }
+        // differences of v_i = xi_i + u_i (as in a_hom_tile)
+        ddouble V1[6], V2[6];
+        V1[0] = D[0][0];            V2[0] = dd_add(D[1][0], h);
+        V1[1] = dd_add(D[0][1], h); V2[1] = D[1][1];
+        V1[2] = dd_add(D[0][2], h); V2[2] = dd_add(D[1][2], h);
+        V1[3] = dd_add(D[0][3], h); V2[3] = dd_add(D[1][3], -h);
+        V1[4] = dd_add(D[0][4], h); V2[4] = D[1][4];
+        V1[5] = D[0][5];            V2[5] = dd_add(D[1][5], h);
+        ddouble e11{0.0, 0.0}, e12{0.0, 0.0}, e22{0.0, 0.0};
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const double wgt = (p == 2 || p == 3) ? Q : 1.0;   // diagonals 00-11, 01-10
+            if (wgt == 0.0) continue;
+            e11 = dd_add(e11, dd_scale2(dd_mul(V1[p], V1[p]), wgt));
+            e12 = dd_add(e12, dd_scale2(dd_mul(V1[p], V2[p]), wgt));
+            e22 = dd_add(e22, dd_scale2(dd_mul(V2[p], V2[p]), wgt));
+        }
+        ddouble F[2][2];   // F[j][i] = xi_j^T (K E) P_c u_i, as in a_hom_tile
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const ddouble qd11 = dd_scale2(D[c][2], Q), qd1001 = dd_scale2(D[c][3], Q);
+            F[0][c] = dd_mul(dd_add(dd_add(D[c][1], qd11), dd_add(qd1001, D[c][4])), h);
+            F[1][c] = dd_mul(dd_add(dd_add(D[c][0], qd11), dd_add(dd_neg(qd1001), D[c][5])), h);
+        }
+        acc[0] = dd_add(acc[0], a);
+        acc[1] = dd_add(acc[1], dd_mul(e11, a));
+        acc[2] = dd_add(acc[2], dd_mul(e12, a));
+        acc[3] = dd_add(acc[3], dd_mul(e22, a));
+        acc[4] = dd_add(acc[4], dd_mul(F[0][0], a));
+        acc[5] = dd_add(acc[5], dd_mul(F[0][1], a));
+        acc[6] = dd_add(acc[6], dd_mul(F[1][0], a));
+        acc[7] = dd_add(acc[7], dd_mul(F[1][1], a));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) {
+        const ddouble v = dd_warp_sum(acc[k]);
+        if (lane == 0) red[wid * AHOM_NP + k] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < AHOM_NP; ++k) {
+            ddouble v = lane < nw ? red[lane * AHOM_NP + k] : ddouble{0.0, 0.0};
+            v = dd_warp_sum(v);
+            if (lane == 0) {
+                out[2 * k] = v.hi;
+                out[2 * k + 1] = v.lo;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Energy and flux forms from the double-double tile partials (16 doubles
+// per tile), by one whole warp; lane 0 writes A (rounded to FP64), A_lo (the
+// low parts, nullable) and Af (nullable).
+template <int SCHEME>
+__device__ __forceinline__ void a_hom_finish_dd(const RDesc& d, const double* part, int nt,
+                                                double* A, double* Alo, double* Af) {
+    const int lane = threadIdx.x & 31;
+    ddouble s[AHOM_NP];
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) {
+        ddouble v{0.0, 0.0};
+        for (int t = lane; t < nt; t += 32)
+            v = dd_add(v, ddouble{part[(int64_t)t * 2 * AHOM_NP + 2 * k],
+                                  part[(int64_t)t * 2 * AHOM_NP + 2 * k + 1]});
+        s[k] = dd_warp_sum(v);
+    }
+    if (lane != 0) return;
+    // K L^2 is an integer below 2^53: exact
+    const double kvol = (SCHEME == 0 ? 6.0 : 2.0) * (double)d.L * (double)d.L;
+    const ddouble e11 = dd_div(s[1], kvol), e12 = dd_div(s[2], kvol), e22 = dd_div(s[3], kvol);
+    A[0] = e11.hi;
+    A[1] = e12.hi;
+    A[2] = e12.hi;
+    A[3] = e22.hi;
+    if (Alo) {
+        Alo[0] = e11.lo;
+        Alo[1] = e12.lo;
+        Alo[2] = e12.lo;
+        Alo[3] = e22.lo;
+    }
+    if (Af) {
+        const double nn = (double)d.n * (double)d.n;   // a power of two
+        const ddouble mean_a = dd_scale2(s[0], 1.0 / nn);
+        Af[0] = dd_add(mean_a, dd_div(s[4], kvol)).hi;   // P_11
+        Af[1] = dd_div(s[6], kvol).hi;                   // a_12: P_21
+        Af[2] = dd_div(s[5], kvol).hi;                   // a_21: P_12
+        Af[3] = dd_add(mean_a, dd_div(s[7], kvol)).hi;   // P_22
+    }
+}
+
 // Energy and flux forms of realization d from its nt tile partials, by one
 // whole warp (results written by lane 0):
 //   energy a_ij = E_ij / (K L^2),   flux a_ij = mean(a) d_ij + P_ji / (K L^2).

@@ -49,8 +49,7 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
 // rows in shared memory: the largest power of two <= 8 whose tile fits
 // 110 KB (two blocks per SM; at least 1).  Column blocks use blockC
 // threads, n / col_seg_rows per column.
-static void default_tiles(int n, size_t vb, int blockC, bool uc, const rve_solve_opts& o,
-                          Tiles& t) {
+static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
     const size_t seq = (size_t)seq_stride(n);
     t.tU = std::min(n, 2048 / n);
     // stencil tile: tS own rows + 2 halo rows, transformed G = 2048/n rows
@@ -78,10 +77,6 @@ static void default_tiles(int n, size_t vb, int blockC, bool uc, const rve_solve
     if (tuned_tiles(n, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0, &ts_tuned, &bc_tuned))
         t.tS = ts_tuned;
     t.tC = std::min(n, blockC / (n / col_seg_rows(n, (int)vb)));
-    if (uc) {   // cluster kernel: block `rank` updates and solves n/16 rows / columns
-        t.tU = n / UC_CTAS;
-        t.tC = n / UC_CTAS;
-    }
     if (o.tile_rows > 0) t.tS = o.tile_rows;
     t.tS = std::min(t.tS, n);
 }
@@ -95,6 +90,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     if (o.path != RVE_PATH_FUSED && o.path != RVE_PATH_PLAIN && o.path != RVE_PATH_PERSISTENT)
         return RVE_EINVAL;
     if (o.path == RVE_PATH_PLAIN && o.precision != RVE_FP64) return RVE_EINVAL;
+    if (o.flags != 0 || o.reserved != 0) return RVE_EINVAL;
     if (!std::isfinite(o.delta) || o.delta < 0.0 || !(o.tol < 1.0) || !(o.inner_tol < 1.0))
         return RVE_EINVAL;
     p.batch = batch;
@@ -128,29 +124,6 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             p.blockC = std::min(512, std::max(32, bc_tuned));   // a loaded table may hold anything
     }
     if (o.path == RVE_PATH_PERSISTENT) p.blockC = 256;   // one block shape for all phases
-    // update + column as one cluster kernel (on request): fused mixed path,
-    // one grid size n = 128..512 for the whole batch, and a device that can
-    // host the clusters (t of one realization: n/16 rows per block in shared
-    // memory)
-    p.uc_cluster = false;
-    p.smemUC = 0;
-    {
-        const int64_t n0 = (int64_t)r[0].L * r[0].m0;
-        bool same = n0 >= 128 && n0 <= 512 && pow2((int)n0);
-        for (int b = 1; b < batch && same; ++b) same = ((int64_t)r[b].L * r[b].m0 == n0);
-        if (same && o.path == RVE_PATH_FUSED && o.precision == RVE_MIXED &&
-            (o.flags & RVE_FLAG_CLUSTER)) {
-            const int n = (int)n0;
-            const size_t rows_smem = (size_t)(n / UC_CTAS) * n * sizeof(float2);
-            const size_t rowbuf = (size_t)(UC_THREADS / (n / 8)) * seq_stride(n) * sizeof(float2);
-            const size_t colbuf = (size_t)(2 * (n / UC_CTAS) + 2) * UC_CTAS * sizeof(float2);
-            const size_t smem = rows_smem + std::max(rowbuf, colbuf);
-            if (uc_cluster_ok(ilog2(n), smem)) {
-                p.uc_cluster = true;
-                p.smemUC = smem;
-            }
-        }
-    }
     if (o.col_tile > 0 && o.path != RVE_PATH_PERSISTENT)
         p.blockC = std::min(512, std::max(32, o.col_tile));
     for (int b = 0; b < batch; ++b) {
@@ -165,10 +138,10 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
             !(x.a_incl > 0.0))
             return RVE_EINVAL;
         Tiles t;
-        default_tiles(n, p.vbytes, p.blockC, p.uc_cluster, o, t);
+        default_tiles(n, p.vbytes, p.blockC, o, t);
         const int segs = n / col_seg_rows(n, (int)p.vbytes);   // threads per column
         if (t.tS < 1 || t.tS > n || t.tC < 1 || !pow2(t.tC) || n % t.tC ||
-            t.tC * segs > (p.uc_cluster ? UC_THREADS : p.blockC))
+            t.tC * segs > p.blockC)
             return RVE_EINVAL;
         RDesc& d = p.desc[b];
         std::memset(&d, 0, sizeof(d));
@@ -232,7 +205,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_partS = take(sizeof(double) * 2 * (size_t)std::max<int64_t>(p.tilesS, maxnb));
     p.o_partU = take(sizeof(double) * 2 * (size_t)p.tilesU);
     p.o_partC = take(sizeof(double) * 2 * (size_t)p.tilesC);
-    p.o_partA = take(sizeof(double) * 8 * (size_t)p.tilesA);
+    p.o_partA = take(sizeof(double) * 16 * (size_t)p.tilesA);   // 8 double-double sums
     p.o_ctl = take(sizeof(int32_t) * 64);
     p.o_uscal = take(sizeof(double) * 2 * (size_t)batch);
     p.o_cnt = take(sizeof(int32_t) * (size_t)batch);
@@ -429,18 +402,22 @@ rve_status rve_apply_mass(const rve_realization* r, int32_t batch, int32_t schem
 }
 
 rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* mask,
-                     const double* coef, int32_t scheme, const double* u, double* A,
-                     double* A_flux, void* ws, size_t ws_bytes, void* stream) {
+                     const double* coef, int32_t scheme, int32_t precision, const double* u,
+                     double* A, double* A_lo, double* A_flux, void* ws, size_t ws_bytes,
+                     void* stream) {
     rve_solve_opts o;
     std::memset(&o, 0, sizeof(o));
     o.scheme = scheme;
+    o.precision = precision;
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, false);
     if (st != RVE_OK) return st;
     if (!u || !A || !ws || (!mask && !coef)) return RVE_EINVAL;
+    if (A_lo && precision != RVE_FP64) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     if (upload_plan(p, ws, as_stream(stream)) != RVE_OK) return RVE_ECUDA;
-    return launch_a_hom(p, ws, mask, coef, scheme, u, A, A_flux, as_stream(stream)) == cudaSuccess
+    return launch_a_hom(p, ws, mask, coef, scheme, precision, u, A, A_lo, A_flux,
+                        as_stream(stream)) == cudaSuccess
                ? RVE_OK
                : RVE_ECUDA;
 }
@@ -508,7 +485,8 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
     note_launch();   // the mask clear
     st = rve_solve_correctors(r_host, batch, mask, nullptr, &o, u, info, w + ow, p.total, stream);
     if (st != RVE_OK) return st;
-    st = rve_a_hom(r_host, batch, mask, nullptr, o.scheme, u, A, nullptr, w + ow, p.total, stream);
+    st = rve_a_hom(r_host, batch, mask, nullptr, o.scheme, o.precision, u, A, nullptr, nullptr,
+                   w + ow, p.total, stream);
     if (st != RVE_OK) return st;
     if (cudaMemcpyAsync(A_host, A, sizeof(double) * 4 * (size_t)batch, cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)

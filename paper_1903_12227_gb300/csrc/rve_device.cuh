@@ -257,6 +257,74 @@ struct DotDW {
     __device__ __forceinline__ float value() const { return __fadd_rn(s, comp); }
 };
 
+// ------------------------------------------------------- double-double --
+// The same error-free transformations on FP64 pairs: a value hi + lo with
+// |lo| <= ulp(hi)/2 carries ~106 significant bits.  Used where an FP64 result
+// must be accurate to the last bit or beyond (the FP64 A_hom reduction,
+// whose low part lets a caller difference two nearby values of A_hom).  The
+// _rn intrinsics keep every step as written (no contraction).
+struct ddouble { double hi, lo; };
+
+__device__ __forceinline__ ddouble dd_two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+__device__ __forceinline__ ddouble dd_fast_two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+// Accurate sum (Joldes, Muller & Popescu 2017, "AccurateDWPlusDW"): relative
+// error O(eps^2) even under cancellation.  Commutative bit for bit, so the
+// xor butterflies below leave every lane with the same value.
+__device__ __forceinline__ ddouble dd_add(ddouble x, ddouble y) {
+    const ddouble s = dd_two_sum(x.hi, y.hi);
+    const ddouble t = dd_two_sum(x.lo, y.lo);
+    const ddouble v = dd_fast_two_sum(s.hi, __dadd_rn(s.lo, t.hi));
+    return dd_fast_two_sum(v.hi, __dadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ ddouble dd_add(ddouble x, double y) {
+    const ddouble s = dd_two_sum(x.hi, y);
+    return dd_fast_two_sum(s.hi, __dadd_rn(x.lo, s.lo));
+}
+// Exact difference of two doubles.
+__device__ __forceinline__ ddouble dd_sub(double a, double b) { return dd_two_sum(a, -b); }
+__device__ __forceinline__ ddouble dd_neg(ddouble x) { return {-x.hi, -x.lo}; }
+// Exact scaling by a power of two.
+__device__ __forceinline__ ddouble dd_scale2(ddouble x, double p2) {
+    return {__dmul_rn(x.hi, p2), __dmul_rn(x.lo, p2)};
+}
+// Product (TwoProd of the high parts by a fused multiply-add, cross terms
+// added; relative error O(eps^2)).
+__device__ __forceinline__ ddouble dd_mul(ddouble x, ddouble y) {
+    const double p = __dmul_rn(x.hi, y.hi);
+    const double e = __fma_rn(x.hi, y.hi, -p);
+    const double c = __fma_rn(x.hi, y.lo, __fma_rn(x.lo, y.hi, e));
+    return dd_fast_two_sum(p, c);
+}
+__device__ __forceinline__ ddouble dd_mul(ddouble x, double y) {
+    const double p = __dmul_rn(x.hi, y);
+    const double e = __fma_rn(x.hi, y, -p);
+    return dd_fast_two_sum(p, __fma_rn(x.lo, y, e));
+}
+// Quotient by a double (one long division step plus a correction).
+__device__ __forceinline__ ddouble dd_div(ddouble x, double b) {
+    const double q1 = __ddiv_rn(x.hi, b);
+    const double p = __dmul_rn(q1, b);
+    const double e = __fma_rn(q1, b, -p);
+    const double r = __dadd_rn(__dsub_rn(__dsub_rn(x.hi, p), e), x.lo);
+    return dd_fast_two_sum(q1, __ddiv_rn(r, b));
+}
+// Fixed-order butterfly sum over a warp (every lane gets the same value).
+__device__ __forceinline__ ddouble dd_warp_sum(ddouble v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ddouble w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = dd_add(v, w);
+    }
+    return v;
+}
+
 // ------------------------------------------------------------ radix DFTs --
 // Forward (exp(-2 pi i rs/R)) in-register DFTs.
 template <typename V> __device__ __forceinline__ void dft2(V& a, V& b) {

@@ -62,8 +62,6 @@ struct Plan {
     int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0;
     size_t smemS = 0, smemU = 0, smemC = 0;
     int blockC = 512;               // threads of a column-solve block
-    bool uc_cluster = false;        // update + column as one cluster kernel
-    size_t smemUC = 0;
     int persist_grid = 0;           // blocks of the persistent launch (0 = not prepared)
     size_t persist_smem = 0;
     // workspace offsets (bytes)
@@ -115,11 +113,6 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
 
 // Uploads descriptors/tile tables and fills the lookup tables in ws.
 rve_status upload_plan(const Plan& plan, void* ws, cudaStream_t s);
-// Whether the update + column cluster kernel for grids of 2^log2n can be
-// resident on the current device with `smem` bytes of shared memory.
-bool uc_cluster_ok(int log2n, size_t smem);
-constexpr int UC_CTAS = 16;         // blocks per cluster (one realization)
-constexpr int UC_THREADS = 512;
 // Device pointers of the lookup tables in the workspace, and the kernel that fills them.
 Tables tables_of(const Plan& p, const void* ws);
 cudaError_t launch_tables(const Plan& p, void* ws, cudaStream_t s);
@@ -156,8 +149,11 @@ size_t cheb_workspace_size(const Plan& p);
 cudaError_t launch_cheb(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                         int scheme, const double* v, int K, double lo, double hi, double* mu,
                         cudaStream_t s);
+// precision RVE_FP64: double-double sums on the FP64 pipe (A_lo = low
+// parts, nullable); RVE_MIXED: double-word sums on the FP32 pipe.
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
-                         int scheme, const double* u, double* A, double* A_flux, cudaStream_t s);
+                         int scheme, int precision, const double* u, double* A, double* A_lo,
+                         double* A_flux, cudaStream_t s);
 constexpr int PROFILE_KERNELS = 5;   // refine, stencil, update, column, control
 void profile_enable(bool on);
 bool profile_on();

@@ -13,7 +13,10 @@
 // RVE_NOALLOC_MAX_NODES nodes per call (1 MiB).  Every GPU that loads the
 // library keeps the array until the process exits.  The first call on a
 // device looks up the array's device address (cudaGetSymbolAddress) with that
-// device current; make that first call before any stream capture.  All calls
+// device current; make that first call before any stream capture.  The
+// address is not looked up again: a device reset (cudaDeviceReset, or any
+// teardown of the primary context) leaves it stale, and the entry point must
+// not be called on that device afterwards.  All calls
 // share the array and it keeps the last call's contents: every partial it
 // reads is written earlier in the same call, so nothing needs clearing, but
 // calls whose work overlaps on the GPU (different streams, or different host

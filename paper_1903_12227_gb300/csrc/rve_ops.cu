@@ -169,20 +169,14 @@ __global__ void k_cheb_moments(const __grid_constant__ DescChunk ch, const doubl
 }
 
 // ------------------------------------------------------------- adjoint --
-// Local element action (E v)_a for the unit-coefficient element matrix
-// E = K1 (x) M1 + M1 (x) K1, local order 00, 01, 10, 11.
-template <int SCHEME>
-__device__ __forceinline__ void elem_apply(const double v[4], double Ev[4]) {
-    const double w0 = Weights<SCHEME>::w0, w1 = Weights<SCHEME>::w1;
-    const double dg = 2.0 * w0, e = w1 - w0, g = -2.0 * w1;
-    Ev[0] = dg * v[0] + e * (v[1] + v[2]) + g * v[3];
-    Ev[1] = dg * v[1] + e * (v[0] + v[3]) + g * v[2];
-    Ev[2] = dg * v[2] + e * (v[0] + v[3]) + g * v[1];
-    Ev[3] = dg * v[3] + e * (v[1] + v[2]) + g * v[0];
-}
-
 // grad[c] = (1/L^2) sum_ij G_ij (xi_i + P_c u_i)^T E (xi_j + P_c u_j): the
 // explicit derivative of the energy form (the correctors are stationary).
+// E (unit coefficient, K1 (x) M1 + M1 (x) K1) has zero row sums, so
+//   x^T E y = sum_{k<l} |E_kl| (x_k - x_l)(y_k - y_l)
+// with |E_kl| = w0 - w1 on the four cell edges and 2 w1 on the two
+// diagonals: the quadratic forms are built from differences across the cell
+// (no cancellation between O(|u|) terms, which would cost up to ~1e-10
+// relative accuracy where the local energy is small).
 template <int SCHEME>
 __global__ void k_backward(const __grid_constant__ DescChunk ch, const double2* __restrict__ u,
                            const double* __restrict__ G, double* __restrict__ grad) {
@@ -193,17 +187,22 @@ __global__ void k_backward(const __grid_constant__ DescChunk ch, const double2* 
     const double2 u00 = ldv(u, d, c1, c2), u01 = ldv(u, d, c1, c2 + 1);
     const double2 u10 = ldv(u, d, c1 + 1, c2), u11 = ldv(u, d, c1 + 1, c2 + 1);
     const double h = d.h;
-    double v1[4] = {u00.x, u01.x, h + u10.x, h + u11.x};   // x_1 + phi_1
-    double v2[4] = {u00.y, h + u01.y, u10.y, h + u11.y};   // x_2 + phi_2
-    double E1[4], E2[4];
-    elem_apply<SCHEME>(v1, E1);
-    elem_apply<SCHEME>(v2, E2);
-    double e11 = 0, e12 = 0, e22 = 0;
+    const double we = Weights<SCHEME>::w0 - Weights<SCHEME>::w1;   // edges
+    const double wd = 2.0 * Weights<SCHEME>::w1;                   // diagonals
+    // pairs 00-01, 00-10, 00-11, 01-10, 01-11, 10-11 (second minus first) of
+    // v_1 = x_1 + phi_1 = (u00, u01, h + u10, h + u11) and
+    // v_2 = x_2 + phi_2 = (u00, h + u01, u10, h + u11)
+    const double d1[6] = {u01.x - u00.x,       h + (u10.x - u00.x), h + (u11.x - u00.x),
+                          h + (u10.x - u01.x), h + (u11.x - u01.x), u11.x - u10.x};
+    const double d2[6] = {h + (u01.y - u00.y), u10.y - u00.y,       h + (u11.y - u00.y),
+                          (u10.y - u01.y) - h, u11.y - u01.y,       h + (u11.y - u10.y)};
+    const double w[6] = {we, we, wd, wd, we, we};
+    double e11 = 0.0, e12 = 0.0, e22 = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        e11 += v1[k] * E1[k];
-        e12 += v1[k] * E2[k];
-        e22 += v2[k] * E2[k];
+    for (int k = 0; k < 6; ++k) {
+        e11 = fma(w[k] * d1[k], d1[k], e11);
+        e12 = fma(w[k] * d1[k], d2[k], e12);
+        e22 = fma(w[k] * d2[k], d2[k], e22);
     }
     const double* Gb = G + 4 * (int64_t)b;   // G is offset to the chunk's first realization
     grad[d.node_off + cell] = d.inv_vol * (Gb[0] * e11 + (Gb[1] + Gb[2]) * e12 + Gb[3] * e22);
@@ -222,6 +221,31 @@ __global__ void __launch_bounds__(256) k_a_hom_part(const RDesc* __restrict__ de
     const RDesc d = desc[b];
     a_hom_tile<SCHEME>(d, blockIdx.x - start[b], cs, u, red, sc,
                        part + (int64_t)blockIdx.x * AHOM_NP);
+}
+
+// FP64 solves: double-double partials (16 doubles per tile).
+template <int SCHEME>
+__global__ void __launch_bounds__(256) k_a_hom_part_dd(const RDesc* __restrict__ desc,
+                                                       const int32_t* __restrict__ start, int batch,
+                                                       CoefSrc cs, const double2* __restrict__ u,
+                                                       double* __restrict__ part) {
+    __shared__ ddouble red[32 * AHOM_NP];
+    const int b = find_real(start, batch, blockIdx.x);
+    const RDesc d = desc[b];
+    a_hom_tile_dd<SCHEME>(d, blockIdx.x - start[b], cs, u, red,
+                          part + (int64_t)blockIdx.x * 2 * AHOM_NP);
+}
+
+template <int SCHEME>
+__global__ void k_a_hom_final_dd(const RDesc* __restrict__ desc, const int32_t* __restrict__ start,
+                                 int batch, const double* __restrict__ part, double* __restrict__ A,
+                                 double* __restrict__ Alo, double* __restrict__ Af) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= batch) return;
+    const RDesc d = desc[b];
+    a_hom_finish_dd<SCHEME>(d, part + (int64_t)start[b] * 2 * AHOM_NP, start[b + 1] - start[b],
+                            A + 4 * (int64_t)b, Alo ? Alo + 4 * (int64_t)b : nullptr,
+                            Af ? Af + 4 * (int64_t)b : nullptr);
 }
 
 // One warp per realization.
@@ -370,23 +394,31 @@ cudaError_t launch_backward(const Plan& p, void*, int scheme, const double* u, c
 }
 
 cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
-                         int scheme, const double* u, double* A, double* A_flux, cudaStream_t s) {
+                         int scheme, int precision, const double* u, double* A, double* A_lo,
+                         double* A_flux, cudaStream_t s) {
     char* w = static_cast<char*>(ws);
     const RDesc* desc = reinterpret_cast<const RDesc*>(w + p.o_desc);
     const int32_t* start = reinterpret_cast<const int32_t*>(w + p.o_startA);
     double* part = reinterpret_cast<double*>(w + p.o_partA);
     CoefSrc cs{mask, coef};
     const double2* uu = reinterpret_cast<const double2*>(u);
-    if (scheme == RVE_Q1_LUMPED)
-        k_a_hom_part<1><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
-    else
-        k_a_hom_part<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (scheme == RVE_Q1_LUMPED)
-        k_a_hom_final<1><<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
-    else
-        k_a_hom_final<0><<<(p.batch + 7) / 8, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    const bool lumped = scheme == RVE_Q1_LUMPED;
+    const int gf = (p.batch + 7) / 8;
+    if (precision == RVE_FP64) {
+        if (lumped) k_a_hom_part_dd<1><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+        else k_a_hom_part_dd<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (lumped) k_a_hom_final_dd<1><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_lo, A_flux);
+        else k_a_hom_final_dd<0><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_lo, A_flux);
+    } else {
+        if (lumped) k_a_hom_part<1><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+        else k_a_hom_part<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (lumped) k_a_hom_final<1><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+        else k_a_hom_final<0><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+    }
     note_launch(2);
     return cudaGetLastError();
 }

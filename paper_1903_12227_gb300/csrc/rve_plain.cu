@@ -196,7 +196,7 @@ __global__ void k_pl_report(const PlainScal* sc, rve_solve_info* info, int b) {
     r.status = sc->status;
     r.refinements = 1;
     r.steps = max(sc->iters[0], sc->iters[1]);
-    r.kernels = 0;
+    r.reserved = 0;
     r.relres[0] = sc->relres[0];
     r.relres[1] = sc->relres[1];
     info[b] = r;

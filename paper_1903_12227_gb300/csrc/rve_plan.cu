@@ -63,6 +63,7 @@ struct rve_plan_s {
     void* ws = nullptr;
     double* A = nullptr;
     rve_solve_info* info = nullptr;
+    int kernels = 0;   // kernel nodes of the captured graph (launch diagnostics)
 };
 
 extern "C" {
@@ -111,16 +112,21 @@ rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void
         if (prepare_persistent(plan->p) != RVE_OK)
             return note_error("plan: persistent kernel set-up", cudaGetLastError());
         cudaGraph_t graph = nullptr;
+        const long long noted = g_launches.load();
         cudaError_t be = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (be != cudaSuccess) return note_error("plan: begin capture", be);
         rve_status st = RVE_OK;
         if (launch_gen_field(p, nullptr, mask, s) != cudaSuccess) st = RVE_ECUDA;
         if (st == RVE_OK) st = enqueue_solve_persistent(p, sw, mask, nullptr, plan->o, u, info, s);
         if (st == RVE_OK &&
-            launch_a_hom(p, sw, mask, nullptr, p.scheme, u, A, nullptr, s) != cudaSuccess)
+            launch_a_hom(p, sw, mask, nullptr, p.scheme, p.precision, u, A, nullptr, nullptr, s) != cudaSuccess)
             st = RVE_ECUDA;
         const cudaError_t le = cudaGetLastError();
         const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        // the launches noted while capturing were recorded, not run: they are
+        // counted each time the graph runs instead
+        plan->kernels = (int)(g_launches.load() - noted);
+        g_launches.fetch_sub(plan->kernels);
         if (st != RVE_OK || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             return note_error("plan: capture", ce != cudaSuccess ? ce : le);
@@ -135,7 +141,7 @@ rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void
         plan->A = A;
         plan->info = info;
     }
-    note_launch();
+    note_launch(plan->kernels);
     const cudaError_t ge = cudaGraphLaunch(plan->exec, s);
     return ge == cudaSuccess ? RVE_OK : note_error("plan: graph launch", ge);
 }

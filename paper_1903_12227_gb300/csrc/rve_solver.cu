@@ -26,7 +26,6 @@
 // In MIXED precision x, r, q, t, p are float2 and u is double2: every
 // REFINE step recomputes the true residual in FP64 and restarts the FP32
 // inner iteration on the scaled residual equation (iterative refinement).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -588,135 +587,10 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
                               [&](int r, int k, V val) { out[node_at(d, z, r, k)] = val; });
 }
 
-// Update + row transform of rows row0 .. row0 + rows - 1 of realization b
-// (the cluster kernel's update phase), blockDim / (n/8) rows per pass, with
-// `rowbuf` the padded per-row scratch of one pass.  ITER: r -= alpha q, |r|^2, t = row-Hartley(r).  REFINE:
-// u = w (the new iterate), x = 0, r = r64 / |r64|, |r|^2, t = row-Hartley(r).
-// t goes to out(row, k, value); the block's |r|^2 sums go to part[0..1].
-template <typename V, int LOG2N, typename Out>
-__device__ __forceinline__ void update_rows(const Ctx& c, int b, const RState& s,
-                                            const RDesc& d, int row0, int rows, V* rowbuf,
-                                            typename ScalarOf<V>::T* usc, double* red,
-                                            double* part, Out&& out) {
-    typedef typename ScalarOf<V>::T T;
-    DotAcc<T> ax, ay;
-    auto flush = [&]() {   // block sums of |r|^2 into part[0..1]
-        double sx = 0.0, sy = 0.0;
-        block_sum2(ax, ay, red, sx, sy);
-        if (threadIdx.x == 0) {
-            part[0] = sx;
-            part[1] = sy;
-        }
-    };
-    const int phase = s.phase;
-    const RowLayout<LOG2N> L(d.log2n);
-    const Sz<LOG2N>& z = L.z;
-    V* R = static_cast<V*>(c.R);
-    V* X = static_cast<V*>(c.X);
-    const V* Qv = static_cast<const V*>(c.Q);
-    const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-    const int SEQ = seq_stride(z.n);
-    const V* tw = twiddles<V>(c.tb, z.n);
-    // the step's scalars, converted once (thread 0)
-    if (threadIdx.x == 0) {
-        if (phase == PH_ITER) {   // alpha = rho / p.q, formed by the last stencil block
-            usc[0] = (T)c.uscal[2 * b];
-            usc[1] = (T)c.uscal[2 * b + 1];
-        } else if constexpr (sizeof(T) == 4) {   // the same conversions as refine_tile_dw
-            usc[0] = (float)s.s[0];
-            usc[1] = (float)s.s[1];
-            usc[2] = (float)s.alpha[0];
-            usc[3] = (float)s.alpha[1];
-            usc[4] = (float)c.uscal[2 * b];       // 1 / |r| per corrector (0 once
-            usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
-        }
-    }
-    __syncthreads();
-    for (int g0 = 0; g0 < rows; g0 += L.G) {
-        const int row = row0 + g0 + L.qq;
-        const bool active = (g0 + L.qq) < rows;
-        V* buf = rowbuf + (active ? L.qq : 0) * SEQ;
-        V v[8];
-        if (phase == PH_ITER) {
-            const T alx = usc[0], aly = usc[1];
-            if (active) {
-                V qv[8];
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {   // loads first, stores after
-                    const int64_t node = node_at(d, z, row, L.t + m * z.T);
-                    v[m] = R[node];
-                    qv[m] = Qv[node];
-                }
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const V rr = axpy2(v[m], -alx, -aly, qv[m]);
-                    R[node_at(d, z, row, L.t + m * z.T)] = rr;
-                    v[m] = rr;
-                    ax.add(rr.x, rr.x);
-                    ay.add(rr.y, rr.y);
-                }
-            }
-        } else if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
-            const DWScal k{usc[0], usc[1], usc[2], usc[3]};
-            const float ix = usc[4], iy = usc[5];
-            float4* U4 = reinterpret_cast<float4*>(c.u);
-            if (active) {
-#pragma unroll
-                for (int h = 0; h < 8; h += 4) {
-                    float4 uu[4];
-                    V xx[4], pp[4], qv[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {   // loads first, stores after
-                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                        uu[m] = U4[node];
-                        xx[m] = X[node];
-                        pp[m] = Pold[node];
-                        qv[m] = Qv[node];
-                    }
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                        U4[node] = w_new(uu[m], xx[m], pp[m], k);
-                        X[node] = mk<V>(0.f, 0.f);
-                        const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
-                        R[node] = rr;
-                        v[h + m] = rr;
-                        ax.add(rr.x, rr.x);
-                        ay.add(rr.y, rr.y);
-                    }
-                }
-            }
-        } else {   // REFINE, FP64
-            // 1 / |r64| per corrector (0 once converged), from finish_S
-            const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
-            if (active) {
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int64_t node = node_at(d, z, row, L.t + m * z.T);
-                    const double2 xx = to_d2(X[node]);
-                    const double2 pp = to_d2(Pold[node]);
-                    double2 uu = c.u[node];
-                    uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
-                    uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
-                    c.u[node] = uu;
-                    X[node] = from_d2<V>(make_double2(0.0, 0.0));
-                    const double2 q = to_d2(Qv[node]);
-                    const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
-                    R[node] = rr;
-                    v[m] = rr;
-                    ax.add(rr.x, rr.x);
-                    ay.add(rr.y, rr.y);
-                }
-            }
-        }
-        row_hartley_out<V, LOG2N>(v, buf, z, row, L.t, tw, active, out);
-    }
-    flush();
-}
-
-// The update kernel proper (one pass of tU rows per block).  The same
-// update as update_rows, written out so that the partial sums are formed
-// before the transform and the kernel stays at ~60 registers.
+// The update kernel (one pass of tU rows per block): ITER r -= alpha q,
+// |r|^2, t = row-Hartley(r); REFINE u = w (the new iterate), x = 0,
+// r = r64 / |r64|, |r|^2, t = row-Hartley(r).  The partial sums are formed
+// before the transform, so the kernel stays at ~60 registers.
 template <typename V, int LOG2N>
 __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const RState& s,
                                              const RDesc& d, double* red,
@@ -871,142 +745,6 @@ __device__ void fused_C_tile(const Ctx& c, int blk) {
     col_transform_tile<V>(static_cast<V*>(c.T), d, (blk - c.startC[b]) * d.tC,
                           reinterpret_cast<V*>(smem_raw), c.tb, c.delta, red,
                           c.partC + 2 * (int64_t)blk);
-}
-
-// ------------------------------------------- update + column, one cluster --
-// On request (RVE_FLAG_CLUSTER; measured slower than the separate update and
-// column kernels on GB300: one block per SM, phases in sequence).
-// Mixed path, a batch of one grid size n = 128..512: one cluster of UC_CTAS
-// blocks per realization.  Block `rank` runs the update + row transform of
-// rows rank*n/16 .. and keeps their t in its own shared memory; after a
-// cluster barrier it solves columns rank*n/16 .., reading the column
-// segments of t from all blocks through distributed shared memory (segment
-// s of every column is n/16 rows, held by block s) and writes zhat to global
-// memory for the stencil kernel.  t never goes to HBM (16 of the 96 bytes
-// per node of a CG step) and the two passes are one launch.  A second
-// cluster barrier keeps every block's shared memory alive until all remote
-// reads are done.  Every block of a cluster reads the same realization
-// state, so all of them pass both barriers or none does.
-template <int LOG2N>
-__global__ void __launch_bounds__(UC_THREADS, 1) k_fused_UC(const Ctx c) {
-    namespace cg = cooperative_groups;
-    typedef float2 V;
-    constexpr int n = 1 << LOG2N;
-    constexpr int RPC = n / UC_CTAS;   // rows (and columns) per block
-    static_assert(col_seg_rows(n, 8) == RPC, "column segments must be the blocks' row ranges");
-    __shared__ double red[64];
-    __shared__ float usc[6];
-    __shared__ float csc[1];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int b = blockIdx.x / UC_CTAS;
-    const RState& s = c.st[b];
-    if (s.phase == PH_DONE) return;   // the same decision in every block of the cluster
-    const RDesc d = c.desc[b];
-    const Sz<LOG2N> z(LOG2N);
-    V* ts = reinterpret_cast<V*>(smem_raw);   // [RPC][n]: t of this block's rows
-    V* scratch = ts + RPC * n;                // row buffers, then column-solve scratch
-    const int row0 = rank * RPC;
-    update_rows<V, LOG2N>(c, b, s, d, row0, RPC, scratch, usc, red,
-                                 c.partU + 2 * (int64_t)(c.startU[b] + rank),
-                                 [&](int r, int k, V val) { ts[(r - row0) * n + k] = val; });
-    cl.sync();   // t of all blocks written and visible to the cluster
-    V* Tg = static_cast<V*>(c.T);
-    col_solve_body<V, LOG2N>(
-        [&](int r, int k) {
-            const V* rem = cl.map_shared_rank(ts, r / RPC);
-            return rem[(r % RPC) * n + k];
-        },
-        [&](int r, int k, V val) { Tg[node_at(d, z, r, k)] = val; }, d, rank * RPC, scratch,
-        c.tb, c.delta, red, c.partC + 2 * (int64_t)(c.startC[b] + rank), csc);
-    cl.sync();   // no block leaves while another may still read its t
-}
-
-template <int LG>
-static cudaError_t uc_attrs(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_UC<LG>,
-                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused_UC<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-    return e;
-}
-
-template <int LG>
-static cudaLaunchConfig_t uc_config(int clusters, size_t smem, cudaStream_t s,
-                                    cudaLaunchAttribute* attr) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(UC_CTAS * clusters));
-    cfg.blockDim = dim3(UC_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = UC_CTAS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
-template <int LG>
-static bool uc_ok_t(size_t smem) {
-    if (uc_attrs<LG>(smem) != cudaSuccess) return false;
-    cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = uc_config<LG>(1, smem, nullptr, attr);
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_fused_UC<LG>, &cfg) != cudaSuccess)
-        return false;
-    return clusters >= 1;
-}
-
-bool uc_cluster_ok(int log2n, size_t smem) {
-    static std::mutex mu;
-    static signed char known[64][12];   // per device and size: 0 unknown, 1 yes, -1 no
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || log2n < 7 || log2n > 9) {
-        cudaGetLastError();
-        return false;
-    }
-    std::lock_guard<std::mutex> g(mu);
-    if (known[dev][log2n] == 0) {
-        bool ok = false;
-        switch (log2n) {
-            case 7: ok = uc_ok_t<7>(smem); break;
-            case 8: ok = uc_ok_t<8>(smem); break;
-            default: ok = uc_ok_t<9>(smem); break;
-        }
-        if (!ok) cudaGetLastError();   // a refused query leaves no error behind
-        known[dev][log2n] = ok ? 1 : -1;
-    }
-    return known[dev][log2n] > 0;
-}
-
-static cudaError_t launch_uc(const Plan& p, const Ctx& c, cudaStream_t s) {
-    cudaLaunchAttribute attr[1];
-    switch (p.max_log2n) {
-        case 7: {
-            const cudaLaunchConfig_t cfg = uc_config<7>(p.batch, p.smemUC, s, attr);
-            return cudaLaunchKernelEx(&cfg, k_fused_UC<7>, c);
-        }
-        case 8: {
-            const cudaLaunchConfig_t cfg = uc_config<8>(p.batch, p.smemUC, s, attr);
-            return cudaLaunchKernelEx(&cfg, k_fused_UC<8>, c);
-        }
-        default: {
-            const cudaLaunchConfig_t cfg = uc_config<9>(p.batch, p.smemUC, s, attr);
-            return cudaLaunchKernelEx(&cfg, k_fused_UC<9>, c);
-        }
-    }
-}
-
-static cudaError_t uc_prepare(const Plan& p) {
-    switch (p.max_log2n) {
-        case 7: return uc_attrs<7>(p.smemUC);
-        case 8: return uc_attrs<8>(p.smemUC);
-        default: return uc_attrs<9>(p.smemUC);
-    }
 }
 
 // One launch per pipeline kernel (the fused path).
@@ -1261,7 +999,7 @@ __global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
     }
 }
 
-__global__ void k_report(const Ctx c, rve_solve_info* info, int kernels) {
+__global__ void k_report(const Ctx c, rve_solve_info* info) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= c.batch) return;
     const RState s = c.st[b];
@@ -1272,7 +1010,7 @@ __global__ void k_report(const Ctx c, rve_solve_info* info, int kernels) {
                : (c.ndone[CTL_ERR] ? RVE_ETIMEOUT : RVE_ENOCONV);
     r.refinements = s.refinements;
     r.steps = s.steps;
-    r.kernels = kernels;
+    r.reserved = 0;
     r.relres[0] = s.relres[0];
     r.relres[1] = s.relres[1];
     info[b] = r;
@@ -1402,19 +1140,13 @@ static cudaError_t fused_step(const Plan& p, const Ctx& c, cudaStream_t s, cudaE
     if (ev) cudaEventRecord(ev[1], s);
     k_fused_S<V, SCHEME><<<p.tilesS, 256, p.smemS, s>>>(c);
     if (ev) cudaEventRecord(ev[2], s);
-    if (p.uc_cluster) {   // update + column in one cluster launch (profiled as "update")
-        const cudaError_t le = launch_uc(p, c, s);
-        if (le != cudaSuccess) return le;
-        if (ev) cudaEventRecord(ev[3], s);
-    } else {
-        k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
-        if (ev) cudaEventRecord(ev[3], s);
-        k_fused_C<V><<<p.tilesC, p.blockC, p.smemC, s>>>(c);
-    }
+    k_fused_U<V><<<p.tilesU, 256, p.smemU, s>>>(c);
+    if (ev) cudaEventRecord(ev[3], s);
+    k_fused_C<V><<<p.tilesC, p.blockC, p.smemC, s>>>(c);
     if (ev) cudaEventRecord(ev[4], s);
     k_control<<<(p.batch + 7) / 8, 256, 0, s>>>(c);
     if (ev) cudaEventRecord(ev[5], s);
-    note_launch(p.uc_cluster ? 4 : 5);
+    note_launch(5);
     return cudaGetLastError();
 }
 
@@ -1428,7 +1160,6 @@ static cudaError_t set_smem_attrs(const Plan& p) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fused_C<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)p.smemC);
-    if (e == cudaSuccess && p.uc_cluster) e = uc_prepare(p);
     return e;
 }
 
@@ -1536,7 +1267,7 @@ rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mas
                                          : persistent_launch<double2, 0>(p, c, o, s);
     if (st != RVE_OK) return st;
     if (finalize_u(p, c, s) != cudaSuccess) return RVE_ECUDA;
-    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info, p.uc_cluster ? 1 : 0);
+    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
@@ -1583,7 +1314,7 @@ rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const 
     }
     if (st != RVE_OK) return st;
     if (finalize_u(p, c, s) != cudaSuccess) return RVE_ECUDA;
-    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info, p.uc_cluster ? 1 : 0);
+    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }

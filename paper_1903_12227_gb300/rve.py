@@ -26,7 +26,6 @@ NOALLOC_MAX_NODES = 1 << 24
 FP64, MIXED = 0, 1
 CONSISTENT, LUMPED = 0, 1
 PATH_FUSED, PATH_PLAIN, PATH_PERSISTENT = 0, 1, 2
-FLAG_CLUSTER = 1
 
 
 class Realization(ctypes.Structure):
@@ -51,7 +50,7 @@ class SolveOpts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32 * 2), ("status", ctypes.c_int32),
                 ("refinements", ctypes.c_int32), ("steps", ctypes.c_int32),
-                ("kernels", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double * 2)]
 
 
 INFO_BYTES = ctypes.sizeof(SolveInfo)
@@ -103,7 +102,7 @@ def lib() -> ctypes.CDLL:
         L.rve_cheb_moments.argtypes = [vp, i32, vp, vp, i32, vp, i32, ctypes.c_double,
                                        ctypes.c_double, vp, vp, sz, vp]
         L.rve_a_hom.restype = i32
-        L.rve_a_hom.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, sz, vp]
+        L.rve_a_hom.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, vp, vp, vp, sz, vp]
         L.rve_a_hom_backward.restype = i32
         L.rve_a_hom_backward.argtypes = [vp, i32, i32, vp, vp, vp, vp]
         L.rve_homogenize_workspace_size.restype = sz
@@ -270,8 +269,7 @@ def info_to_dicts(info: torch.Tensor, count: int) -> list:
 
 def _info_dict(a: SolveInfo) -> dict:
     return {"iters": (a.iters[0], a.iters[1]), "status": a.status, "refinements": a.refinements,
-            "steps": a.steps, "relres": (a.relres[0], a.relres[1]),
-            "cluster": bool(a.kernels & 1)}
+            "steps": a.steps, "relres": (a.relres[0], a.relres[1])}
 
 
 def solve(batch, mask=None, coef=None, opts: SolveOpts | None = None, ws=None, u=None,
@@ -335,19 +333,33 @@ def apply_mass(batch, x: torch.Tensor, scheme=CONSISTENT, stream=None) -> torch.
 
 
 def a_hom(batch, u: torch.Tensor, mask=None, coef=None, scheme=CONSISTENT, ws=None,
-          want_flux: bool = False, stream=None):
-    """Energy-form A [batch, 2, 2] (and the flux form if asked), float64."""
+          want_flux: bool = False, stream=None, precision=FP64, want_lo: bool = False):
+    """Energy-form A [batch, 2, 2] (and the flux form if asked), float64.
+
+    precision FP64 sums in double-double arithmetic (A correctly rounded; with
+    want_lo the low parts A_lo [batch, 2, 2] are returned too, A + A_lo being
+    the energy to ~1e-30 relative); MIXED sums in double words on the FP32
+    pipe (the mixed-precision pipeline's reduction).  Returns A, or a tuple
+    (A, A_flux) / (A, A_lo) / (A, A_lo, A_flux) as asked."""
     _require_cuda()
     b = as_batch(batch)
+    if want_lo and precision != FP64:
+        raise ValueError("A_lo exists for precision FP64 only")
     nb = workspace_size(b, make_opts(scheme=scheme))
     if ws is None or ws.numel() < nb:
         ws = workspace(nb, u.device)
     A = torch.empty(b.count, 4, dtype=torch.float64, device=u.device)
     Af = torch.empty(b.count, 4, dtype=torch.float64, device=u.device) if want_flux else None
-    check(lib().rve_a_hom(b.ptr, b.count, _ptr(mask), _ptr(coef), scheme, _ptr(u), _ptr(A),
-                          _ptr(Af), _ptr(ws), ws.numel(), _stream(stream)), "rve_a_hom")
-    A = A.view(b.count, 2, 2)
-    return (A, Af.view(b.count, 2, 2)) if want_flux else A
+    Alo = torch.empty(b.count, 4, dtype=torch.float64, device=u.device) if want_lo else None
+    check(lib().rve_a_hom(b.ptr, b.count, _ptr(mask), _ptr(coef), scheme, precision, _ptr(u),
+                          _ptr(A), _ptr(Alo), _ptr(Af), _ptr(ws), ws.numel(), _stream(stream)),
+          "rve_a_hom")
+    out = [A.view(b.count, 2, 2)]
+    if want_lo:
+        out.append(Alo.view(b.count, 2, 2))
+    if want_flux:
+        out.append(Af.view(b.count, 2, 2))
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 def a_hom_backward(batch, u: torch.Tensor, gradA: torch.Tensor, scheme=CONSISTENT,
@@ -519,7 +531,7 @@ class AHom(torch.autograd.Function):
         opts = opts or make_opts()
         coef = coef.detach().to(torch.float64).contiguous()
         u, info = solve(b, coef=coef, opts=opts)
-        A = a_hom(b, u, coef=coef, scheme=opts.scheme)
+        A = a_hom(b, u, coef=coef, scheme=opts.scheme, precision=opts.precision)
         ctx.save_for_backward(u)
         ctx.batch = b
         ctx.scheme = opts.scheme

@@ -53,7 +53,8 @@ def solve_ensemble(descs: list, opts, batch: int, device=None):
             ws = rve.workspace(nb, dev)
         mask = rve.gen_field(b, device=dev)
         u, info = rve.solve(b, mask=mask, opts=opts, ws=ws)
-        out.append(rve.a_hom(b, u, mask=mask, scheme=opts.scheme).cpu().numpy())
+        out.append(rve.a_hom(b, u, mask=mask, scheme=opts.scheme,
+                             precision=opts.precision).cpu().numpy())
         infos.extend(rve.info_to_dicts(info, b.count))
     return np.concatenate(out), infos
 
@@ -202,7 +203,7 @@ def dos_study(Ls=(4, 8), N=20, lam=0.5, alpha=0.25, m0=8, eta=0.05, K=512, vecto
         means.append(mean)
         # homogenized operator: constant A_hom (sample mean), lumped symbol
         u, _ = rve.solve(ds, mask=mask, opts=rve.make_opts(scheme=scheme, precision=rve.MIXED))
-        A = rve.a_hom(ds, u, mask=mask, scheme=scheme).cpu().numpy().mean(axis=0)
+        A = rve.a_hom(ds, u, mask=mask, scheme=scheme, precision=rve.MIXED).cpu().numpy().mean(axis=0)
         n = L * m0
         th = 2 * np.pi * np.arange(n) / n
         kk = 2.0 - 2.0 * np.cos(th)

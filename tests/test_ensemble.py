@@ -81,6 +81,43 @@ def test_two_gloo_ranks_merge_bit_identical(tmp_path):
     np.testing.assert_array_equal(merged, single)
 
 
+def _real_shard_rank(rank, world, port, total, out_path):
+    """One rank of a sharded ensemble of real realizations: its contiguous
+    index range is solved by the oracle (L = 4, h = 1/8, contrast 10), the
+    A_hom gathered to rank 0 and merged in index order."""
+    import torch.distributed as dist
+    from paper_1903_12227_gb300 import workloads
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    idx = list(ensemble.shard_range(total, rank, world))
+    ds = [workloads.realization(4, 8, 10.0, 3, k) for k in idx]
+    A, _, _ = oracle.solve_batch(ds, tol=1e-12, threads=1) if ds else (np.zeros((0, 2, 2)), 0, 0)
+    merged = ensemble.gather_a_hom(idx, A, total)
+    if rank == 0:
+        np.save(out_path, merged)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_real_realizations_bit_identical(tmp_path):
+    """Each rank solves its shard (the oracle stands in for one GPU per rank);
+    the merged A_hom and their statistics equal a single-process run bit for
+    bit, because every realization is a pure function of (seed, index)."""
+    from paper_1903_12227_gb300 import workloads
+    total = 23
+    out = str(tmp_path / "merged_real.npy")
+    mp.start_processes(_real_shard_rank, args=(2, _free_port(), total, out), nprocs=2,
+                       start_method="spawn")
+    merged = np.load(out)
+    single, _, _ = oracle.solve_batch([workloads.realization(4, 8, 10.0, 3, k)
+                                       for k in range(total)], tol=1e-12, threads=1)
+    np.testing.assert_array_equal(merged, single)
+    s_m, s_s = oracle.statistics(merged, 4.0), oracle.statistics(single, 4.0)
+    for k in ("mean", "var", "Q"):
+        np.testing.assert_array_equal(s_m[k], s_s[k])
+
+
 def test_checkpoint_resume_after_injected_failure(tmp_path):
     ck = ensemble.Checkpoint(str(tmp_path / "run.jsonl"))
     calls = []

@@ -321,28 +321,6 @@ def test_dos_exact_trace_matches_dense_spectrum():
     assert np.abs(phi - ref).max() < 1e-6 * ref.max()
 
 
-@pytest.mark.parametrize("L,m0", [(8, 16), (16, 16), (32, 16)])   # n = 128, 256, 512
-@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
-def test_cluster_update_column_kernel_matches_separate_kernels(L, m0, scheme):
-    # on request a batch of one grid size runs the update and column passes
-    # as one cluster kernel (t in distributed shared memory) instead of the
-    # two separate kernels.  Same per-node arithmetic, so the same answers.
-    ds = [workloads.realization(L, m0, 100.0 if k % 2 else 10.0, 5, k) for k in range(3)]
-    on = rve.make_opts(scheme=scheme, precision=rve.MIXED, tol=1e-10, flags=rve.FLAG_CLUSTER)
-    off = rve.make_opts(scheme=scheme, precision=rve.MIXED, tol=1e-10)
-    mask, _, A1, inf1 = _solve_and_hom(ds, on)
-    _, _, A2, inf2 = _solve_and_hom(ds, off, mask=mask)
-    assert all(i["cluster"] for i in inf1) and not any(i["cluster"] for i in inf2)
-    for k, d in enumerate(ds):
-        assert inf1[k]["status"] == rve.RVE_OK and inf2[k]["status"] == rve.RVE_OK
-        assert max(inf1[k]["relres"]) <= 1e-10 * 1.0001
-        assert _rel_err_A(A1[k], A2[k]) < 1e-9
-        # only the grouping of the |r|^2 partial sums differs
-        for c in range(2):
-            assert abs(inf1[k]["iters"][c] - inf2[k]["iters"][c]) <= 1
-        if L == 8:
-            ref = oracle.solve_realization(d, scheme=scheme, tol=1e-12, want_u=False)
-            assert _rel_err_A(A1[k], ref["A_energy"]) < 1e-7
 
 
 def test_full_size_plain_L32_fp64_and_mixed():

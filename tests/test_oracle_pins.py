@@ -117,6 +117,35 @@ def test_corner_marginals_uniform():
     assert chi2 < 30.0      # 7 dof: p ~ 1e-4
 
 
+def _splitmix64_stream(seed, k):
+    """Output k >= 1 of the SplitMix64 stream seeded with `seed`, restated
+    from the generator's published definition (Steele, Lea & Flood 2014):
+    the state advances by the golden-ratio gamma and each output is the
+    state put through the variant-13 finaliser."""
+    M = (1 << 64) - 1
+    z = (seed + k * 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+@pytest.mark.parametrize("seed,index,L,m0", [(0, 0, 4, 8), (7, 123456, 32, 16),
+                                             (2**63 + 5, 3, 8, 8), (1234567, 2**40 + 9, 64, 16)])
+def test_corner_draws_restated_from_reading_R1(seed, index, L, m0):
+    """Reading R1 written out independently of the oracle: the realization key
+    is output index+1 of the run seed's stream; draw ctr under tag 1 is output
+    (2^40 + ctr + 1) of the key's stream; inclusion k takes draws 2k (row)
+    and 2k+1 (column); a corner is the high word of draw * n (Lemire's
+    multiply-high, no rejection).  A slip in bit order, counter packing or
+    draw pairing in the oracle fails this bit for bit."""
+    d = workloads.realization(L, m0, 10.0, seed, index)
+    n = L * m0
+    key = _splitmix64_stream(seed, index + 1)
+    want = np.array([[(_splitmix64_stream(key, (1 << 40) + 2 * k + a + 1) * n) >> 64
+                      for a in (0, 1)] for k in range(d["n_incl"])], dtype=np.int64)
+    np.testing.assert_array_equal(oracle.corners(d).astype(np.int64), want)
+
+
 # --------------------------------------------------------------- assembly --
 @pytest.mark.parametrize("scheme", [oracle.SCHEME_CONSISTENT, oracle.SCHEME_LUMPED])
 def test_element_matrix_equals_quadrature(scheme):
@@ -504,6 +533,28 @@ def test_dos_gauss_normalised_and_centred():
     assert abs(phi.sum() * dt - 1.0) < 1e-6
     A = oracle.csr_to_dense(oracle.assemble(coef, h), n * n)
     assert abs((t * phi).sum() * dt - np.trace(A) / (n * n)) < 1e-6
+
+
+@pytest.mark.parametrize("eta", [0.05, 0.3])
+def test_dos_gauss_width_from_second_moment(eta):
+    """The broadened density's second central moment is the spectrum's
+    variance plus eta^2 (a Gaussian of standard deviation eta convolved with
+    the eigenvalue distribution), with the spectrum's moments taken from the
+    matrix itself: mean Tr(A)/m and second moment ||A||_F^2 / m = Tr(A^2)/m.
+    A width misread as a variance (eta instead of eta^2) or a wrong
+    normalisation of the exponent fails this."""
+    n, h = 16, 0.25
+    coef = _random_coef(n, 4, lo=0.5, hi=1.0)
+    ev = oracle.spectrum(coef, h)
+    t = np.linspace(ev.min() - 12 * eta, ev.max() + 12 * eta, 20001)
+    phi = oracle.dos_gauss(ev, t, eta)
+    dt = t[1] - t[0]
+    A = oracle.csr_to_dense(oracle.assemble(coef, h), n * n)
+    m = n * n
+    mean = np.trace(A) / m
+    var = (A * A).sum() / m - mean ** 2
+    mom2 = ((t - mean) ** 2 * phi).sum() * dt
+    assert abs(mom2 - (var + eta ** 2)) < 1e-6 * (var + eta ** 2)
 
 
 # ---------------------------------------------------------------- 3D --
