@@ -54,15 +54,15 @@ CONFIG_DESC = ("L=32, h=1/16 (512x512 nodes, 262144 unknowns per corrector), con
                "717 inclusions of side 1 (density 0.7), PCG tol 1e-10 on the true residual")
 
 # Algorithmic bytes per node (both correctors, float2 = 8 B per node pair) of
-# the fused pipeline kernels, per realization-step.  ITER: S reads t, p_old,
-# x and writes p_new, q, x; U reads r, q and writes r, t; C reads and writes
-# t.  REFINE: R reads u (double word, 16 B), x, p and writes q; U reads u,
-# x, p, q and writes u, x, r, t; C as in ITER.  The coefficient bitmask adds
-# 1/8 B per node to R and S.
+# the fused pipeline kernels, per realization-step.  ITER: S reads zhat,
+# p_old, x and writes p_new, q, x; U reads rt (the row transform of r) and q
+# and writes rt; C reads rt and writes zhat.  REFINE: R reads u (double word,
+# 16 B), x, p and writes q; U reads u, x, p, q and writes u, x, rt; C as in
+# ITER.  The coefficient bitmask adds 1/8 B per node to R and S.
 BYTES_PER_NODE = {
     "refine": {"iter": 0.0, "refine": 16 + 8 + 8 + 8 + 0.125},
     "stencil": {"iter": 6 * 8 + 0.125, "refine": 0.0},
-    "update_row": {"iter": 4 * 8, "refine": 16 + 8 + 8 + 8 + 16 + 8 + 8 + 8},
+    "update_row": {"iter": 3 * 8, "refine": 16 + 8 + 8 + 8 + 16 + 8 + 8},
     "column": {"iter": 2 * 8, "refine": 2 * 8},
 }
 
@@ -172,30 +172,35 @@ def per_entry_error(A, ref):
             "mean": e.mean(axis=0).tolist(), "max_all": float(e.max()), "count": int(len(A))}
 
 
-# Thread instructions per node of a refining launch of the double-word true
-# residual pass (k_fused_R), from the ncu instruction count of that launch
-# divided by its nodes (profiles/k_fused_R_plain_L32_batch32.md); None until
-# measured for the current kernel.
-REFINE_INST_PER_NODE = None
+# Thread instructions per node of the double-word true-residual pass
+# (k_fused_R): ncu instruction count of a refining launch divided by its
+# nodes, for the first refinement of a solve (r = f) and the later ones
+# (profiles/k_fused_R_refine_plain_L32_batch32.md).
+REFINE_INST_PER_NODE = 614.7
+REFINE_FIRST_INST_PER_NODE = 479.6
 
 
-def refine_alu(prof, refines, nodes, clk):
-    """FP32-issue roofline of the double-word true-residual pass: thread
-    instructions per node (ncu instruction count of a refining launch / its
-    nodes) against 128 FP32 lanes per SM x 152 SMs x the measured SM clock."""
+def refine_alu(prof, refines, reals, nodes, clk):
+    """Instruction-issue roofline of the double-word true-residual pass: its
+    thread instructions (per node, measured by ncu, times the nodes of the
+    refinements run) over its CUDA-event time, against 152 SMs x 4 schedulers
+    x 32 lanes x the measured SM clock."""
     launches = prof["refine"]["launches"]
-    if launches == 0 or refines == 0 or REFINE_INST_PER_NODE is None:
+    if launches == 0 or refines == 0:
         return None
     # every step launches the refine kernel; only refining realizations work
-    # in it, and idle launches return at once: their time is the floor
+    # in it, and idle launches return at once (their time is included)
     ms = prof["refine"]["ms"]
     mhz = clk.get("sm_mhz") or 2070.0
-    peak_inst = 152 * 128 * mhz * 1e6   # thread instructions/s, FP32 pipes
-    work = REFINE_INST_PER_NODE * nodes * refines
-    return {"inst_per_node": REFINE_INST_PER_NODE, "node_refines": nodes * refines,
-            "ms_total": ms, "achieved_ginst_s": work / (ms / 1e3) / 1e9,
-            "peak_ginst_s": peak_inst / 1e9, "frac": work / (ms / 1e3) / peak_inst,
-            "note": "ms_total includes the idle launches of non-refining steps"}
+    peak_inst = 152 * 4 * 32 * mhz * 1e6   # thread instructions/s
+    work = nodes * (REFINE_INST_PER_NODE * (refines - reals) + REFINE_FIRST_INST_PER_NODE * reals)
+    return {"bound": "alu", "unit": "thread instructions/s",
+            "inst_per_node": REFINE_INST_PER_NODE,
+            "inst_per_node_first": REFINE_FIRST_INST_PER_NODE,
+            "achieved": work / (ms / 1e3), "peak": peak_inst,
+            "frac": work / (ms / 1e3) / peak_inst,
+            "peak_source": "152 SMs x 4 schedulers x 32 lanes x measured SM clock",
+            "note": "time includes the idle launches of non-refining steps"}
 
 
 def e2e_host(args, rve, torch, dev):
@@ -404,7 +409,7 @@ def run_ours(args):
     traffic = None if tr is None else tr * nodes * steps_iter / launches_dom
     # the refine pass is bound by FP32 issue, not HBM: its operation count
     # per node against the FP32 rate of the measured clock
-    rk = refine_alu(prof, refines, nodes, clk)
+    rk = refine_alu(prof, refines, len(pinfo_d), nodes, clk)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_launch": bytes_per_launch,
@@ -640,8 +645,8 @@ def run_cubes(args):
 
 UNEVEN_DESC = ("4096 realizations, L uniform in {8,16,32,64}, h=1/8 (64^2 .. 512^2 nodes), "
                "contrast uniform in {10,100}, round(0.7 L^2) inclusions of side 1, "
-               "mixed precision, PCG tol 1e-10 on the true residual; one persistent launch per "
-               "solve inside a captured CUDA graph (field + solve + A_hom), autotuned tiles")
+               "mixed precision, PCG tol 1e-10 on the true residual; the whole pipeline (field, "
+               "solve, A_hom) as one captured CUDA graph per step, autotuned tiles")
 
 
 def run_uneven(args):
@@ -659,39 +664,56 @@ def run_uneven(args):
     stream = torch.cuda.current_stream()
     ds = workloads.config_batch("uneven_4096", seed=0)
     B = len(ds)
-    opts = rve.make_opts(precision=rve.MIXED, path=rve.PATH_PERSISTENT, tol=1e-10)
-    rve.tuner_clear()
-    rve.autotune(ds[:256], opts, device=dev)
-    plan = rve.Plan(ds, opts, device=dev)
-    for _ in range(args.warmup):
-        plan.execute()
-    torch.cuda.synchronize()
-    rve.launch_count()
-    clocks = Clocks(dev.index)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        A, info = plan.execute()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    launches = rve.launch_count()
+
+    def timed_plan(path):
+        """Autotune, capture, W untimed and K timed executions of a plan."""
+        opts = rve.make_opts(precision=rve.MIXED, path=path, tol=1e-10)
+        rve.tuner_clear()
+        rve.autotune(ds[:256], opts, device=dev)
+        plan = rve.Plan(ds, opts, device=dev)
+        for _ in range(args.warmup):
+            plan.execute()
+        torch.cuda.synchronize()
+        rve.launch_count()
+        clocks = Clocks(dev.index)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            A, info = plan.execute()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        launches = rve.launch_count()
+        tiles = {str(n): rve.tuner_lookup(n, rve.MIXED, path == rve.PATH_PERSISTENT)
+                 for n in (64, 128, 256, 512)}
+        A, info_d = A.cpu().numpy(), rve.info_to_dicts(info, B)
+        plan.close()
+        return ms, clk, launches, A, info_d, tiles, opts
+
+    # the persistent kernel (one cooperative launch per solve) for comparison
+    ms_p, clk_p, _, A_p, info_p, tiles_p, _ = timed_plan(rve.PATH_PERSISTENT)
+    # the headline: the fused kernels inside the graph's conditional loop
+    elapsed_ms, clk, launches, A, info_d, tiles, opts = timed_plan(rve.PATH_FUSED)
     value = B * args.steps / (elapsed_ms / 1e3)
-    A = A.cpu().numpy()
-    info_d = rve.info_to_dicts(info, B)
-    # roofline: the persistent launch carries the whole solve; its algorithmic
-    # bytes (per realization n^2 x (CG steps x 96.125 + refinements x 128.125))
-    # over the time of one plan execution (field and A_hom included: a lower
-    # bound on the solve's rate)
+    # kernels that ran per execution: the captured ones once, the loop body
+    # (4 steps x 5 kernels + the re-arming kernel) once per group of steps
+    groups = -(-max(x["steps"] + x["refinements"] for x in info_d) // 4)
+    launches += args.steps * (groups - 1) * 21
+    # roofline: the algorithmic bytes of the solve (per realization n^2 x (CG
+    # steps x 88.125 + refinements x 120.125)) over the time of one plan
+    # execution (field and A_hom included: a lower bound on the solve's rate)
     iter_b = BYTES_PER_NODE["stencil"]["iter"] + BYTES_PER_NODE["update_row"]["iter"] + \
         BYTES_PER_NODE["column"]["iter"]
     ref_b = BYTES_PER_NODE["refine"]["refine"] + BYTES_PER_NODE["update_row"]["refine"] + \
         BYTES_PER_NODE["column"]["refine"]
-    alg = sum((d["L"] * d["m0"]) ** 2 * (x["steps"] * iter_b + x["refinements"] * ref_b)
-              for d, x in zip(ds, info_d))
+
+    def alg_of(infos):
+        return sum((d["L"] * d["m0"]) ** 2 * (x["steps"] * iter_b + x["refinements"] * ref_b)
+                   for d, x in zip(ds, infos))
+    alg = alg_of(info_d)
     per_exec_s = elapsed_ms / 1e3 / args.steps
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -702,20 +724,24 @@ def run_uneven(args):
            "dtype": "f32 vectors + f64 dots/refinement/A_hom (mixed)", "data": "synthetic",
            "config": {"workload": f"uneven_4096: {UNEVEN_DESC}", "realizations_per_step": B,
                       "l2": "inputs larger than L2 (~5 GB working set per step)",
-                      "precision": "mixed",
-                      "tiles": {str(n): rve.tuner_lookup(n, rve.MIXED, True)
-                                for n in (64, 128, 256, 512)}},
+                      "precision": "mixed", "plan": "fused kernels in a conditional while node",
+                      "tiles": tiles},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
-                        "kernel": "k_persistent (one launch per plan execution)",
+                        "kernel": "whole plan execution (fused pipeline kernels in the graph loop)",
                         "peak_source": f"hbm_gbs of {peak_src}", "bytes_per_launch": alg,
                         "avg_launch_us": per_exec_s * 1e6},
+           "persistent_plan": {"value": B * args.steps / (ms_p / 1e3), "unit": UNIT,
+                               "ms_per_step": ms_p / args.steps, "clocks": clk_p,
+                               "tiles": tiles_p,
+                               "roofline_frac": alg_of(info_p) / (ms_p / 1e3 / args.steps) / 1e9 / peak,
+                               "a_hom_max_abs_diff_vs_loop_plan": float(np.abs(A_p - A).max()),
+                               "note": "one cooperative persistent launch per solve"},
            "gpu_launches": launches, "clocks": clk,
            "solver": {"statuses": sorted({x["status"] for x in info_d}),
                       "mean_steps": float(np.mean([x["steps"] for x in info_d])),
                       "mean_refinements": float(np.mean([x["refinements"] for x in info_d])),
                       "max_relres": float(max(max(x["relres"]) for x in info_d))}}
-    plan.close()
     # end to end: host descriptors in, host A_hom out, same path and options
     ws_h = rve.workspace(rve.lib().rve_homogenize_workspace_size(
         rve.Batch(ds).ptr, B, rve.ctypes.byref(opts)), dev)
@@ -727,8 +753,8 @@ def run_uneven(args):
     dt = time.perf_counter() - t0
     out["e2e"] = {"value": args.steps * B / dt, "unit": UNIT, "h2d_bytes_per_step": B * 48,
                   "d2h_bytes_per_step": B * (32 + 40),
-                  "api": "rve_homogenize_host on the persistent path (host descriptors in, host "
-                         "A_hom and solver report out)"}
+                  "api": "rve_homogenize_host on the fused path (host descriptors in, host "
+                         "A_hom and solver report out; the host polls convergence)"}
     del ws_h
     if not args.no_cpu_baseline:
         # one realization per (L, contrast) pair against the FP64 oracle; the

@@ -188,6 +188,24 @@ rve_status rve_cheb_moments(const rve_realization* r, int32_t batch, const uint3
                             double lo, double hi, double* mu, void* ws, size_t ws_bytes,
                             void* stream);
 
+/* Reconstruction of the broadened density of states from Chebyshev trace
+ * moments (host memory, host arithmetic, FP64; the spectral-density
+ * appendix, Eq. "DOS_gauss", by the kernel polynomial method).
+ * rve_dos_coefficients: c[i][k] (nt x K) = the Chebyshev coefficients of
+ *   lambda -> g_eta(t_i - lambda) on [lo, hi], g_eta the Gaussian of
+ *   standard deviation eta, by Chebyshev-Gauss quadrature with `quad` nodes
+ *   (0 = max(4K, 1024)): c_ik = (2 - [k = 0]) / quad * sum_j g_eta(t_i -
+ *   lambda_j) T_k(x_j), x_j = cos(pi (j + 1/2) / quad), lambda_j the image
+ *   of x_j on [lo, hi].
+ * rve_dos_from_moments: phi[i] = (1/m) sum_k c_ik mu[k] for trace moments
+ *   mu[k] = Tr T_k(A~) (or their estimate; see rve_cheb_moments) of a matrix
+ *   of order m whose spectrum lies in [lo, hi].
+ * Errors: RVE_EINVAL (missing pointers, K < 1, hi <= lo, eta <= 0, m <= 0). */
+rve_status rve_dos_coefficients(const double* t, int32_t nt, int32_t K, double lo, double hi,
+                                double eta, int32_t quad, double* c);
+rve_status rve_dos_from_moments(const double* mu, int32_t K, double m, double lo, double hi,
+                                double eta, const double* t, int32_t nt, double* phi);
+
 /* y = B^{-1} x with B = c0 A_Delta + delta I (Sec. 3.4), A_Delta the
  * periodic 5-point Laplacian (Eq. "Lap_Kron"), c0 = (a_matrix + a_incl)/2
  * (Lemma "Cond_Number").  delta = 0 drops the constant mode.  Applied by
@@ -273,22 +291,32 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
                                rve_solve_info* info_host, void* ws, size_t ws_bytes,
                                void* stream);
 
-/* Plans: the whole pipeline (field, both correctors on the persistent path,
- * A_hom) of a fixed batch, captured once into a CUDA graph and relaunched.
- * The persistent path runs each solve as ONE cooperative launch over all
- * realizations of the batch (sizes may differ), with grid-wide barriers
- * between the pipeline phases; every barrier wait is bounded by
- * opts->timeout_us, after which the launch ends and the affected
- * realizations report RVE_ETIMEOUT (Sec. 3.4 for the solver itself).
+/* Plans: the whole pipeline (field, both correctors, A_hom) of a fixed batch
+ * (sizes may differ), captured once into a CUDA graph and relaunched; the
+ * solve needs no host synchronisation, so one graph launch runs all of it
+ * (Sec. 3.4 for the solver itself).  opts->path selects the solve inside
+ * the graph:
+ *   RVE_PATH_PERSISTENT: ONE cooperative persistent launch over all
+ *     realizations, with grid-wide barriers between the pipeline phases;
+ *     every barrier wait is bounded by opts->timeout_us, after which the
+ *     launch ends and the affected realizations report RVE_ETIMEOUT;
+ *   RVE_PATH_FUSED: the fused pipeline kernels inside a conditional WHILE
+ *     node of the graph (groups of 4 pipeline steps, re-armed on the device
+ *     while a realization is unfinished and the step bound is not reached);
+ *     kernel boundaries separate the phases, each kernel at its own
+ *     occupancy;
+ *   RVE_PATH_PLAIN: RVE_EINVAL.
  * rve_plan_create: validates (host only) and lays out the workspace.
- * rve_plan_execute: A (device double[batch][4], energy form) and info
- * (device rve_solve_info[batch]); ws holds masks, correctors and solver
- * state (rve_plan_workspace_size bytes).  The first call (and any call with
- * different ws/A/info pointers) uploads the descriptors with a host
- * synchronisation and captures the graph on `stream`; later calls only
- * launch the graph.  `stream` must be a created stream (not the legacy
- * default stream, on which CUDA cannot capture; NULL gives RVE_EINVAL).
- * rve_plan_destroy frees the host-side plan. */
+ * rve_plan_execute: A (device double[batch][4], energy form, reduced as
+ * rve_a_hom with opts->precision) and info (device rve_solve_info[batch]);
+ * ws holds masks, correctors and solver state (rve_plan_workspace_size
+ * bytes).  The first call (and any call with different ws/A/info pointers)
+ * uploads the descriptors with a host synchronisation and captures the graph
+ * on `stream`; later calls only launch the graph.  `stream` must be a
+ * created stream (not the legacy default stream, on which CUDA cannot
+ * capture; NULL gives RVE_EINVAL).  rve_launch_count() counts the graph's
+ * kernel nodes once per execution (a RVE_PATH_FUSED plan's loop body once,
+ * however often it ran).  rve_plan_destroy frees the host-side plan. */
 typedef struct rve_plan_s* rve_plan;
 rve_status rve_plan_create(const rve_realization* r, int32_t batch, const rve_solve_opts* opts,
                            rve_plan* plan);

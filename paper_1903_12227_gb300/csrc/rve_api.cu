@@ -529,6 +529,57 @@ rve_status rve_statistics(const double* A, int64_t N, double L, int32_t d, doubl
     return RVE_OK;
 }
 
+rve_status rve_dos_coefficients(const double* t, int32_t nt, int32_t K, double lo, double hi,
+                                double eta, int32_t quad, double* c) {
+    if (!t || !c || nt < 0 || K < 1 || K > (1 << 20) || !std::isfinite(lo) ||
+        !std::isfinite(hi) || !(hi > lo) || !std::isfinite(eta) || !(eta > 0.0) || quad < 0)
+        return RVE_EINVAL;
+    const int q = quad > 0 ? quad : std::max(4 * K, 1024);
+    const double pi = 3.14159265358979323846;
+    const double norm = 1.0 / (std::sqrt(2.0 * pi) * eta);
+    std::fill(c, c + (size_t)nt * K, 0.0);
+    std::vector<double> g(nt), Tk(K);
+    for (int j = 0; j < q; ++j) {
+        const double th = pi * ((double)j + 0.5) / (double)q;
+        const double x = std::cos(th);
+        const double lam = 0.5 * (hi - lo) * x + 0.5 * (hi + lo);
+        for (int i = 0; i < nt; ++i) {
+            const double s = (t[i] - lam) / eta;
+            g[i] = norm * std::exp(-0.5 * s * s);
+        }
+        // T_k(x) = cos(k th) by the three-term recurrence
+        Tk[0] = 1.0;
+        if (K > 1) Tk[1] = x;
+        for (int k = 2; k < K; ++k) Tk[k] = 2.0 * x * Tk[k - 1] - Tk[k - 2];
+        for (int i = 0; i < nt; ++i) {
+            double* ci = c + (size_t)i * K;
+            const double gi = g[i];
+            for (int k = 0; k < K; ++k) ci[k] += gi * Tk[k];
+        }
+    }
+    const double w = 2.0 / (double)q;
+    for (int i = 0; i < nt; ++i) {
+        double* ci = c + (size_t)i * K;
+        for (int k = 0; k < K; ++k) ci[k] *= w;
+        ci[0] *= 0.5;
+    }
+    return RVE_OK;
+}
+
+rve_status rve_dos_from_moments(const double* mu, int32_t K, double m, double lo, double hi,
+                                double eta, const double* t, int32_t nt, double* phi) {
+    if (!mu || !phi || !(m > 0.0)) return RVE_EINVAL;
+    std::vector<double> c((size_t)std::max(nt, 0) * std::max(K, 1));
+    const rve_status st = rve_dos_coefficients(t, nt, K, lo, hi, eta, 0, c.data());
+    if (st != RVE_OK) return st;
+    for (int i = 0; i < nt; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += c[(size_t)i * K + k] * mu[k];
+        phi[i] = s / m;
+    }
+    return RVE_OK;
+}
+
 void rve_profile_enable(int32_t on) { profile_enable(on != 0); }
 
 int32_t rve_profile_read(double* ms, int64_t* launches) {

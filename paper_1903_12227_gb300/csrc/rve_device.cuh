@@ -41,6 +41,26 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 // multiply by -i: (x + iy)(-i) = y - ix
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
 
+// ------------------------------------------------- asynchronous copies --
+// One element global -> shared without passing through registers
+// (cp.async; 8-byte elements through L1, 16-byte ones bypassing it), the
+// commit of the copies issued so far as one group, and the wait until at
+// most N groups of this thread are still in flight.
+__device__ __forceinline__ void cp_async_v(float2* dst, const float2* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_v(double2* dst, const double2* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------- dot accumulator --
 template <typename T> struct DotAcc;
 

@@ -141,6 +141,13 @@ rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s);
 rve_status enqueue_solve_persistent(const Plan& p, void* ws, const uint32_t* mask,
                                     const double* coef, const rve_solve_opts& o, double* u,
                                     rve_solve_info* info, cudaStream_t s, const double* f = nullptr);
+// The fused pipeline steps inside a CUDA graph conditional WHILE node; only
+// while `s` is capturing (RVE_EINVAL otherwise).  prepare_graph_loop sets
+// the kernels' shared-memory attributes (call it before the capture).
+rve_status prepare_graph_loop(const Plan& p);
+rve_status enqueue_solve_graph_loop(const Plan& p, void* ws, const uint32_t* mask,
+                                    const double* coef, const rve_solve_opts& o, double* u,
+                                    rve_solve_info* info, cudaStream_t s, const double* f = nullptr);
 rve_status run_solve_plain(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
                            cudaStream_t s, const double* f = nullptr);

@@ -74,7 +74,9 @@ rve_status rve_plan_create(const rve_realization* r, int32_t batch, const rve_so
     *out = nullptr;
     rve_solve_opts o = {};
     if (opts) o = *opts;
-    o.path = RVE_PATH_PERSISTENT;   // graph-capturable: no host synchronisation
+    // graph-capturable paths only (no host synchronisation): the persistent
+    // kernel, or the fused kernels inside a conditional while node
+    if (o.path == RVE_PATH_PLAIN) return RVE_EINVAL;
     rve_plan_s* pl = new rve_plan_s();
     rve_status st = make_plan(r, batch, &o, pl->p, true);
     if (st != RVE_OK) {
@@ -109,15 +111,18 @@ rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void
         // the capture; everything captured is a kernel or a memset
         if (upload_descriptors(p, sw, s) != RVE_OK || cudaStreamSynchronize(s) != cudaSuccess)
             return note_error("plan: descriptor upload", cudaGetLastError());
-        if (prepare_persistent(plan->p) != RVE_OK)
-            return note_error("plan: persistent kernel set-up", cudaGetLastError());
+        const bool loop = plan->p.path == RVE_PATH_FUSED;
+        if ((loop ? prepare_graph_loop(plan->p) : prepare_persistent(plan->p)) != RVE_OK)
+            return note_error("plan: kernel set-up", cudaGetLastError());
         cudaGraph_t graph = nullptr;
         const long long noted = g_launches.load();
         cudaError_t be = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (be != cudaSuccess) return note_error("plan: begin capture", be);
         rve_status st = RVE_OK;
         if (launch_gen_field(p, nullptr, mask, s) != cudaSuccess) st = RVE_ECUDA;
-        if (st == RVE_OK) st = enqueue_solve_persistent(p, sw, mask, nullptr, plan->o, u, info, s);
+        if (st == RVE_OK)
+            st = loop ? enqueue_solve_graph_loop(p, sw, mask, nullptr, plan->o, u, info, s)
+                      : enqueue_solve_persistent(p, sw, mask, nullptr, plan->o, u, info, s);
         if (st == RVE_OK &&
             launch_a_hom(p, sw, mask, nullptr, p.scheme, p.precision, u, A, nullptr, nullptr, s) != cudaSuccess)
             st = RVE_ECUDA;

@@ -42,7 +42,7 @@ namespace rve {
 
 // Control words (int32) in the workspace: [0] realizations done, then the
 // persistent kernel's grid barrier.
-enum { CTL_ARRIVE = 8, CTL_GEN = 9, CTL_ERR = 10 };
+enum { CTL_ARRIVE = 8, CTL_GEN = 9, CTL_ERR = 10, CTL_GROUPS = 11 };
 
 struct Ctx {
     int batch;
@@ -463,23 +463,82 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
     const T alx = bsc[2], aly = bsc[3];
     const V* Tin = static_cast<const V*>(c.T);
     const V* tw = twiddles<V>(c.tb, n);
+    // t of the rows of a transform group goes straight into the rows' own
+    // shared slots by asynchronous copies (no registers held), one group
+    // ahead: the copies of group g+1 are in flight while group g transforms
+    // and while the stencil runs on the rows group g completed
+    auto prefetch = [&](int g0) {
+        const int q = g0 + L.qq;
+        if (g0 < TR + 2 && q < TR + 2) {
+            const int row = (r0 - 1 + q) & (n - 1);
+            V* buf = Pt + q * SEQ;
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                cp_async_v(buf + pidx(L.t + m * L.z.T), Tin + node_at(d, z, row, L.t + m * L.z.T));
+        }
+        cp_async_commit();   // an empty group past the last: uniform counting
+    };
+    prefetch(0);
+    // q = A p on the own rows: each thread walks down a column keeping the
+    // 3 x 3 neighbourhood (and the two cell columns) in registers, so a node
+    // costs three shared loads and two cell lookups.  Rolled in behind the
+    // transform: the rows whose three neighbours rows are done run after
+    // each group.
+    DotAcc<T> ax, ay;   // p.q
+    int done = 0;       // own rows (tile slots 1 .. TR) whose q is done
+    auto stencil_rows = [&](int q1) {   // own slots done+1 .. q1
+        const int first = done + 1;
+        if (q1 < first) return;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
+            const int pm = pidx(jm), p0 = pidx(j), pp = pidx(jp);
+            const V* up = Pt + (first - 1) * SEQ;
+            V u0 = up[pm], u1 = up[p0], u2 = up[pp];                        // slot first-1
+            V m0 = up[SEQ + pm], m1 = up[SEQ + p0], m2 = up[SEQ + pp];      // slot first
+            T cmm = tc.cell(c.cs, d, first - 1, r0 + first - 2, jm);
+            T cm0 = tc.cell(c.cs, d, first - 1, r0 + first - 2, j);
+            for (int q = first; q <= q1; ++q) {
+                const V* dn = Pt + (q + 1) * SEQ;
+                const V d0 = dn[pm], d1 = dn[p0], d2 = dn[pp];
+                const T c0m = tc.cell(c.cs, d, q, r0 + q - 1, jm);
+                const T c00 = tc.cell(c.cs, d, q, r0 + q - 1, j);
+                CellsT<T> a;
+                a.mm = cmm;
+                a.m0 = cm0;
+                a.z0m = c0m;
+                a.z00 = c00;
+                const V qv = stencil_apply<SCHEME, V>(a, u0, u1, u2, m0, m1, m2, d0, d1, d2);
+                Q[node_at(d, z, r0 + q - 1, j)] = qv;
+                ax.add(m1.x, qv.x);
+                ay.add(m1.y, qv.y);
+                u0 = m0; u1 = m1; u2 = m2;
+                m0 = d0; m1 = d1; m2 = d2;
+                cmm = c0m; cm0 = c00;
+            }
+        }
+        done = q1;
+    };
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
         const int q = g0 + L.qq;
         const bool active = q < TR + 2;
         const int row = (r0 - 1 + q) & (n - 1);
+        const bool own = active && q >= 1 && q <= TR;
+        prefetch(g0 + L.G);
+        cp_async_wait<1>();   // this thread's copies of group g0 have landed
+        __syncthreads();      // ... and everybody's
+        V* buf = Pt + (active ? q : 0) * SEQ;
         V v[8];
         if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = Tin[node_at(d, z, row, L.t + m * L.z.T)];
+            for (int m = 0; m < 8; ++m) v[m] = buf[pidx(L.t + m * L.z.T)];
         }
-        V* buf = Pt + (active ? q : 0) * SEQ;
         fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
         V pn[8];
         if (active) {
-            const bool own = (q >= 1 && q <= TR);
-            // in two halves of four: the global loads of a half first, then
-            // its stores (the compiler cannot prove Pold, Pnew and X
-            // distinct, so a load after a store would wait for it)
+            // p_new = z + beta p_old; own rows: x += alpha p_old (the lagged
+            // solution update) and p_new out.  In two halves of four, the
+            // global loads of a half before its stores (the compiler cannot
+            // prove Pold, Pnew and X distinct)
 #pragma unroll
             for (int h = 0; h < 8; h += 4) {
                 V po[4], xo[4];
@@ -492,8 +551,8 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int k = L.t + (h + m) * L.z.T;
-                    const V z = hartley_pair(v[h + m], buf[pidx((n - k) & (n - 1))]);
-                    pn[h + m] = axpy2(z, bx, by, po[m]);
+                    const V zz = hartley_pair(v[h + m], buf[pidx((n - k) & (n - 1))]);
+                    pn[h + m] = axpy2(zz, bx, by, po[m]);
                 }
                 if (own) {
 #pragma unroll
@@ -511,36 +570,9 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
             for (int m = 0; m < 8; ++m) buf[pidx(L.t + m * L.z.T)] = pn[m];
         }
     }
-    __syncthreads();
-    // q = A p on the own rows: each thread walks down a column keeping the
-    // 3 x 3 neighbourhood (and the two cell columns) in registers, so a node
-    // costs three shared loads and two cell lookups
-    DotAcc<T> ax, ay;   // p.q
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-        const int pm = pidx(jm), p0 = pidx(j), pp = pidx(jp);
-        V u0 = Pt[pm], u1 = Pt[p0], u2 = Pt[pp];                    // row r0-1
-        V m0 = Pt[SEQ + pm], m1 = Pt[SEQ + p0], m2 = Pt[SEQ + pp];  // row r0
-        T cmm = tc.cell(c.cs, d, 0, r0 - 1, jm), cm0 = tc.cell(c.cs, d, 0, r0 - 1, j);
-        for (int q = 0; q < TR; ++q) {
-            const V* dn = Pt + (q + 2) * SEQ;                         // row r0+q+1
-            const V d0 = dn[pm], d1 = dn[p0], d2 = dn[pp];
-            const T c0m = tc.cell(c.cs, d, q + 1, r0 + q, jm);
-            const T c00 = tc.cell(c.cs, d, q + 1, r0 + q, j);
-            CellsT<T> a;
-            a.mm = cmm;
-            a.m0 = cm0;
-            a.z0m = c0m;
-            a.z00 = c00;
-            const V qv = stencil_apply<SCHEME, V>(a, u0, u1, u2, m0, m1, m2, d0, d1, d2);
-            Q[node_at(d, z, r0 + q, j)] = qv;
-            ax.add(m1.x, qv.x);
-            ay.add(m1.y, qv.y);
-            u0 = m0; u1 = m1; u2 = m2;
-            m0 = d0; m1 = d1; m2 = d2;
-            cmm = c0m; cm0 = c00;
-        }
-    }
+    cp_async_wait<0>();
+    __syncthreads();   // p_new of the tile visible
+    stencil_rows(TR);
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {
@@ -587,10 +619,13 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
                               [&](int r, int k, V val) { out[node_at(d, z, r, k)] = val; });
 }
 
-// The update kernel (one pass of tU rows per block): ITER r -= alpha q,
-// |r|^2, t = row-Hartley(r); REFINE u = w (the new iterate), x = 0,
-// r = r64 / |r64|, |r|^2, t = row-Hartley(r).  The partial sums are formed
-// before the transform, so the kernel stays at ~60 registers.
+// The update kernel (one pass of tU rows per block).  The residual is kept
+// in the row-Hartley domain, rt = H r (H the unnormalised Hartley transform
+// along rows, H H = n I): that is exactly what the column pass consumes, so
+// the update writes it once instead of writing r and t = H r.
+//   ITER    rt -= alpha H q  (H q by the row transform of q), |r|^2 = |rt|^2 / n;
+//   REFINE  u = w (the new iterate), x = 0, r = r64 / |r64| (|r|^2 from r),
+//           rt = H r.
 template <typename V, int LOG2N>
 __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const RState& s,
                                              const RDesc& d, double* red,
@@ -603,109 +638,115 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
     const int row = (blk - c.startU[b]) * G + L.qq;
     const bool active = L.qq < G;
     typedef typename ScalarOf<V>::T T;
-    V* R = static_cast<V*>(c.R);
+    V* Rt = static_cast<V*>(c.R);
     V* X = static_cast<V*>(c.X);
     const V* Qv = static_cast<const V*>(c.Q);
     V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(z.n);
+    const V* tw = twiddles<V>(c.tb, z.n);
     DotAcc<T> ax, ay;
     V v[8];
+    double inv_scale = 1.0;   // |r|^2 = (sum of the squares formed here) * inv_scale
     if (phase == PH_ITER) {
         // alpha = rho / p.q, formed by the last stencil block (finish_S)
         if (threadIdx.x == 0) {
             usc[0] = (T)c.uscal[2 * b];
             usc[1] = (T)c.uscal[2 * b + 1];
         }
+        // q and rt of the row: every load issued before the transform, so
+        // the rt loads are in flight while q transforms
+        V rt[8];
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = Qv[node_at(d, z, row, L.t + m * z.T)];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) rt[m] = Rt[node_at(d, z, row, L.t + m * z.T)];
+        }
         __syncthreads();
         const T alx = usc[0], aly = usc[1];
+        fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
         if (active) {
-            V qv[8];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {   // loads first, stores after
-                const int64_t node = node_at(d, z, row, L.t + m * z.T);
-                v[m] = R[node];
-                qv[m] = Qv[node];
-            }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const V rr = axpy2(v[m], -alx, -aly, qv[m]);
-                R[node_at(d, z, row, L.t + m * z.T)] = rr;
-                v[m] = rr;
+                const int k = L.t + m * z.T;
+                const V qt = hartley_pair(v[m], buf[pidx((z.n - k) & (z.n - 1))]);
+                const V rr = axpy2(rt[m], -alx, -aly, qt);
+                Rt[node_at(d, z, row, k)] = rr;
                 ax.add(rr.x, rr.x);
                 ay.add(rr.y, rr.y);
             }
         }
-    } else if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
-        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-        if (threadIdx.x == 0) {   // the same conversions as refine_tile_dw
-            usc[0] = (float)s.s[0];
-            usc[1] = (float)s.s[1];
-            usc[2] = (float)s.alpha[0];
-            usc[3] = (float)s.alpha[1];
-            usc[4] = (float)c.uscal[2 * b];       // 1 / |r| per corrector (0 once
-            usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
-        }
-        __syncthreads();
-        const DWScal k{usc[0], usc[1], usc[2], usc[3]};
-        const float ix = usc[4], iy = usc[5];
-        float4* U4 = reinterpret_cast<float4*>(c.u);
-        if (active) {
+        inv_scale = 1.0 / (double)z.n;
+    } else {
+        if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
+            const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+            if (threadIdx.x == 0) {   // the same conversions as refine_tile_dw
+                usc[0] = (float)s.s[0];
+                usc[1] = (float)s.s[1];
+                usc[2] = (float)s.alpha[0];
+                usc[3] = (float)s.alpha[1];
+                usc[4] = (float)c.uscal[2 * b];       // 1 / |r| per corrector (0 once
+                usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
+            }
+            __syncthreads();
+            const DWScal k{usc[0], usc[1], usc[2], usc[3]};
+            const float ix = usc[4], iy = usc[5];
+            float4* U4 = reinterpret_cast<float4*>(c.u);
+            if (active) {
 #pragma unroll
-            for (int h = 0; h < 8; h += 4) {
-                float4 uu[4];
-                V xx[4], pp[4], qv[4];
+                for (int h = 0; h < 8; h += 4) {
+                    float4 uu[4];
+                    V xx[4], pp[4], qv[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {   // loads first, stores after
-                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                    uu[m] = U4[node];
-                    xx[m] = X[node];
-                    pp[m] = Pold[node];
-                    qv[m] = Qv[node];
+                    for (int m = 0; m < 4; ++m) {   // loads first, stores after
+                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                        uu[m] = U4[node];
+                        xx[m] = X[node];
+                        pp[m] = Pold[node];
+                        qv[m] = Qv[node];
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                        U4[node] = w_new(uu[m], xx[m], pp[m], k);
+                        X[node] = mk<V>(0.f, 0.f);
+                        const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
+                        v[h + m] = rr;
+                        ax.add(rr.x, rr.x);
+                        ay.add(rr.y, rr.y);
+                    }
                 }
+            }
+        } else {   // REFINE, FP64
+            const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+            // 1 / |r64| per corrector (0 once converged), from finish_S
+            const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
+            if (active) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                    U4[node] = w_new(uu[m], xx[m], pp[m], k);
-                    X[node] = mk<V>(0.f, 0.f);
-                    const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
-                    R[node] = rr;
-                    v[h + m] = rr;
+                for (int m = 0; m < 8; ++m) {
+                    const int64_t node = node_at(d, z, row, L.t + m * z.T);
+                    const double2 xx = to_d2(X[node]);
+                    const double2 pp = to_d2(Pold[node]);
+                    double2 uu = c.u[node];
+                    uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
+                    uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
+                    c.u[node] = uu;
+                    X[node] = from_d2<V>(make_double2(0.0, 0.0));
+                    const double2 q = to_d2(Qv[node]);
+                    const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
+                    v[m] = rr;
                     ax.add(rr.x, rr.x);
                     ay.add(rr.y, rr.y);
                 }
             }
         }
-    } else {   // REFINE, FP64
-        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-        // 1 / |r64| per corrector (0 once converged), from finish_S
-        const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
-        if (active) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int64_t node = node_at(d, z, row, L.t + m * z.T);
-                const double2 xx = to_d2(X[node]);
-                const double2 pp = to_d2(Pold[node]);
-                double2 uu = c.u[node];
-                uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
-                uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
-                c.u[node] = uu;
-                X[node] = from_d2<V>(make_double2(0.0, 0.0));
-                const double2 q = to_d2(Qv[node]);
-                const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
-                R[node] = rr;
-                v[m] = rr;
-                ax.add(rr.x, rr.x);
-                ay.add(rr.y, rr.y);
-            }
-        }
+        row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, tw, active, Rt);
     }
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {
-        c.partU[2 * (int64_t)blk] = sx;
-        c.partU[2 * (int64_t)blk + 1] = sy;
+        c.partU[2 * (int64_t)blk] = sx * inv_scale;
+        c.partU[2 * (int64_t)blk + 1] = sy * inv_scale;
     }
-    row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, twiddles<V>(c.tb, z.n), active,
-                                static_cast<V*>(c.T));
 }
 
 template <typename V>
@@ -722,15 +763,18 @@ __device__ void fused_U_tile(const Ctx& c, int blk) {
 // ----------------------------------------------------------- C kernel --
 // (the column solve body is in rve_colsolve.cuh)
 // Column pass of one tile (any size): dispatches to the sized body.
+// Reads the row transform of the residual (rt) from `in` and writes zhat to
+// `out` (in == out allowed: every load of a column segment precedes its
+// stores).
 template <typename V>
-__device__ void col_transform_tile(V* __restrict__ Tg, const RDesc& d, int c0, V* smem,
-                                   const Tables& tb, double delta, double* red,
+__device__ void col_transform_tile(const V* in, V* out, const RDesc& d,
+                                   int c0, V* smem, const Tables& tb, double delta, double* red,
                                    double* rho_part) {
     __shared__ typename ScalarOf<V>::T csc[1];
     dispatch_size(d.log2n, [&]<int LG>() {
         const Sz<LG> z(LG);
-        col_solve_body<V, LG>([&](int r, int k) { return Tg[node_at(d, z, r, k)]; },
-                              [&](int r, int k, V val) { Tg[node_at(d, z, r, k)] = val; }, d,
+        col_solve_body<V, LG>([&](int r, int k) { return in[node_at(d, z, r, k)]; },
+                              [&](int r, int k, V val) { out[node_at(d, z, r, k)] = val; }, d,
                               c0, smem, tb, delta, red, rho_part, csc);
     });
 }
@@ -742,7 +786,8 @@ __device__ void fused_C_tile(const Ctx& c, int blk) {
     const int b = find_real(c.startC, c.batch, blk);
     if (c.st[b].phase == PH_DONE) return;
     const RDesc d = c.desc[b];
-    col_transform_tile<V>(static_cast<V*>(c.T), d, (blk - c.startC[b]) * d.tC,
+    col_transform_tile<V>(static_cast<const V*>(c.R), static_cast<V*>(c.T), d,
+                          (blk - c.startC[b]) * d.tC,
                           reinterpret_cast<V*>(smem_raw), c.tb, c.delta, red,
                           c.partC + 2 * (int64_t)blk);
 }
@@ -996,6 +1041,7 @@ __global__ void k_init(const Ctx c, int64_t nodes, size_t vbytes) {
         c.ndone[CTL_ARRIVE] = 0;                 // grid barrier arrivals
         c.ndone[CTL_GEN] = 0;                    // grid barrier generation
         c.ndone[CTL_ERR] = 0;                    // a bounded wait gave up
+        c.ndone[CTL_GROUPS] = 0;                 // loop groups of a captured plan
     }
 }
 
@@ -1296,6 +1342,105 @@ rve_status run_solve_persistent(const Plan& p, void* ws, const uint32_t* mask, c
     return enqueue_solve_persistent(q, ws, mask, coef, o, u, info, s, f);
 }
 
+// ----------------------------------------------- captured loop of steps --
+// A plan captured with the fused path: the pipeline steps run inside a CUDA
+// graph conditional WHILE node whose body is LOOP_GROUP fused steps (the
+// same kernels as the fused path) followed by a one-thread kernel that
+// re-arms the node while some realization is unfinished and the step bound
+// is not reached.  No host synchronisation, so the whole solve stays inside
+// one graph launch; kernel boundaries separate the phases.
+constexpr int LOOP_GROUP = 4;
+
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int* ctl, int batch,
+                            long long max_groups) {
+    if (threadIdx.x != 0) return;
+    const int g = ctl[CTL_GROUPS] + 1;
+    ctl[CTL_GROUPS] = g;
+    const bool more = *reinterpret_cast<volatile int*>(ctl) < batch && g < max_groups;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+template <typename V, int SCHEME>
+static rve_status loop_body(const Plan& p, const Ctx& c, cudaStream_t s,
+                            cudaGraphConditionalHandle h, long long max_groups) {
+    for (int k = 0; k < LOOP_GROUP; ++k)
+        if (fused_step<V, SCHEME>(p, c, s, nullptr) != cudaSuccess) return RVE_ECUDA;
+    k_loop_cond<<<1, 32, 0, s>>>(h, c.ndone, p.batch, max_groups);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+rve_status prepare_graph_loop(const Plan& p) {
+    cudaError_t e;
+    if (p.precision == RVE_MIXED)
+        e = (p.scheme == RVE_Q1_LUMPED) ? set_smem_attrs<float2, 1>(p) : set_smem_attrs<float2, 0>(p);
+    else
+        e = (p.scheme == RVE_Q1_LUMPED) ? set_smem_attrs<double2, 1>(p) : set_smem_attrs<double2, 0>(p);
+    return e == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
+rve_status enqueue_solve_graph_loop(const Plan& p, void* ws, const uint32_t* mask,
+                                    const double* coef, const rve_solve_opts& o, double* u,
+                                    rve_solve_info* info, cudaStream_t s, const double* f) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return RVE_EINVAL;   // only inside a stream capture
+    Ctx c = make_ctx(p, ws, mask, coef, u, o, f);
+    if (launch_tables(p, ws, s) != cudaSuccess) return RVE_ECUDA;
+    k_init<<<std::min<int64_t>((p.nodes + 255) / 256, 4096), 256, 0, s>>>(c, p.nodes, p.vbytes);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return RVE_ECUDA;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess)
+        return RVE_ECUDA;
+    const std::vector<cudaGraphNode_t> dep(deps, deps + nd);   // valid until the next call
+    // the conditional node, run at least once per graph launch (default 1,
+    // re-assigned on every launch)
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return RVE_ECUDA;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, dep.data(), nullptr, dep.size(), &np) != cudaSuccess)
+        return RVE_ECUDA;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return RVE_ECUDA;
+    // the body: LOOP_GROUP pipeline steps and the re-arming kernel, captured
+    // on a helper stream straight into the node's body graph
+    cudaStream_t sb = nullptr;
+    if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) return RVE_ECUDA;
+    rve_status st = RVE_OK;
+    if (cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = RVE_ECUDA;
+    } else {
+        const long long max_groups = (2LL * o.max_iter + 64) / LOOP_GROUP + 1;
+        if (p.precision == RVE_MIXED)
+            st = (p.scheme == RVE_Q1_LUMPED) ? loop_body<float2, 1>(p, c, sb, h, max_groups)
+                                             : loop_body<float2, 0>(p, c, sb, h, max_groups);
+        else
+            st = (p.scheme == RVE_Q1_LUMPED) ? loop_body<double2, 1>(p, c, sb, h, max_groups)
+                                             : loop_body<double2, 0>(p, c, sb, h, max_groups);
+        cudaGraph_t out = nullptr;
+        if (cudaStreamEndCapture(sb, &out) != cudaSuccess) st = RVE_ECUDA;
+    }
+    cudaStreamDestroy(sb);
+    if (st != RVE_OK) return st;
+    if (finalize_u(p, c, s) != cudaSuccess) return RVE_ECUDA;
+    k_report<<<(p.batch + 127) / 128, 128, 0, s>>>(c, info);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? RVE_OK : RVE_ECUDA;
+}
+
 rve_status run_solve_fused(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                            const rve_solve_opts& o, double* u, rve_solve_info* info,
                            cudaStream_t s, const double* f) {
@@ -1357,7 +1502,7 @@ __global__ void __launch_bounds__(512) k_col_hartley(const RDesc* __restrict__ d
     const int blk = blockIdx.x + tile0;
     const int b = find_real(startC, batch, blk);
     const RDesc d = desc[b];
-    col_transform_tile<V>(T, d, (blk - startC[b]) * d.tC, reinterpret_cast<V*>(smem_raw), tb,
+    col_transform_tile<V>(T, T, d, (blk - startC[b]) * d.tC, reinterpret_cast<V*>(smem_raw), tb,
                           delta, red, nullptr);
 }
 

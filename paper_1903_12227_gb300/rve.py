@@ -101,6 +101,10 @@ def lib() -> ctypes.CDLL:
         L.rve_cheb_moments.restype = i32
         L.rve_cheb_moments.argtypes = [vp, i32, vp, vp, i32, vp, i32, ctypes.c_double,
                                        ctypes.c_double, vp, vp, sz, vp]
+        L.rve_dos_coefficients.restype = i32
+        L.rve_dos_coefficients.argtypes = [vp, i32, i32, dbl, dbl, dbl, i32, vp]
+        L.rve_dos_from_moments.restype = i32
+        L.rve_dos_from_moments.argtypes = [vp, i32, dbl, dbl, dbl, dbl, vp, i32, vp]
         L.rve_a_hom.restype = i32
         L.rve_a_hom.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, vp, vp, vp, sz, vp]
         L.rve_a_hom_backward.restype = i32
@@ -161,6 +165,11 @@ def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
     if t is None:
         return ctypes.c_void_p(None)
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a) -> ctypes.c_void_p:
+    """Address of a C-contiguous numpy array (host memory)."""
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 class Batch:
@@ -395,9 +404,11 @@ def homogenize_host(batch, opts: SolveOpts | None = None, ws=None, stream=None, 
 
 
 class Plan:
-    """Whole pipeline of a fixed batch on the persistent path, captured once
-    into a CUDA graph (rve_plan_*).  execute() returns A [B,2,2] (device,
-    float64) and the raw info tensor; calls after the first relaunch the graph."""
+    """Whole pipeline of a fixed batch captured once into a CUDA graph
+    (rve_plan_*): opts.path PATH_PERSISTENT solves in one persistent launch,
+    PATH_FUSED runs the fused kernels inside a conditional while node.
+    execute() returns A [B,2,2] (device, float64) and the raw info tensor;
+    calls after the first relaunch the graph."""
 
     def __init__(self, batch, opts: SolveOpts | None = None, device=None):
         _require_cuda()

@@ -10,8 +10,10 @@ expanded in Chebyshev polynomials of the spectrum mapped to [-1, 1],
 so phi_eta(t) = (1/m) sum_k c_k(t) Tr T_k(A~), and Tr T_k(A~) is estimated by
 E[v^T T_k(A~) v] over random sign vectors v (Hutchinson), or exactly with
 unit vectors.  The moments v^T T_k(A~) v come from the GPU
-(rve_cheb_moments: matrix-free stencil, FP64); this module only forms the
-coefficients c_k(t) (Chebyshev-Gauss quadrature) and the weighted sums.
+(rve_cheb_moments: matrix-free stencil, FP64); the coefficients c_k(t)
+(Chebyshev-Gauss quadrature) and the weighted sums from the library's host
+functions rve_dos_coefficients / rve_dos_from_moments.  This module only
+marshals arguments.
 """
 from __future__ import annotations
 
@@ -33,25 +35,31 @@ def gauss(t, eta):
     return np.exp(-0.5 * (t / eta) ** 2) / (np.sqrt(2.0 * np.pi) * eta)
 
 
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
 def cheb_coefficients(t: np.ndarray, K: int, lo: float, hi: float, eta: float,
                       quad: int | None = None) -> np.ndarray:
     """c[T, K]: Chebyshev coefficients of lambda -> g_eta(t - lambda) on
-    [lo, hi], by Chebyshev-Gauss quadrature with `quad` nodes."""
-    q = quad or max(4 * K, 1024)
-    th = np.pi * (np.arange(q) + 0.5) / q
-    lam = 0.5 * (hi - lo) * np.cos(th) + 0.5 * (hi + lo)
-    G = gauss(np.asarray(t)[:, None] - lam[None, :], eta)          # [T, q]
-    Tk = np.cos(np.arange(K)[:, None] * th[None, :])               # [K, q]
-    c = (2.0 / q) * G @ Tk.T
-    c[:, 0] *= 0.5
+    [lo, hi], by Chebyshev-Gauss quadrature (rve_dos_coefficients)."""
+    t = _f64(t).ravel()
+    c = np.zeros((t.size, int(K)))
+    rve.check(rve.lib().rve_dos_coefficients(rve._np_ptr(t), t.size, int(K), float(lo), float(hi),
+                                             float(eta), int(quad or 0), rve._np_ptr(c)),
+              "rve_dos_coefficients")
     return c
 
 
 def dos_from_moments(mu: np.ndarray, t: np.ndarray, lo: float, hi: float, eta: float,
                      m: int) -> np.ndarray:
-    """phi_eta(t) from trace moments mu[K] = Tr T_k(A~) (or an estimate)."""
-    c = cheb_coefficients(t, mu.shape[-1], lo, hi, eta)
-    return c @ mu / m
+    """phi_eta(t) from trace moments mu[K] = Tr T_k(A~) (rve_dos_from_moments)."""
+    mu, t = _f64(mu).ravel(), _f64(t).ravel()
+    phi = np.zeros(t.size)
+    rve.check(rve.lib().rve_dos_from_moments(rve._np_ptr(mu), mu.size, float(m), float(lo),
+                                             float(hi), float(eta), rve._np_ptr(t), t.size,
+                                             rve._np_ptr(phi)), "rve_dos_from_moments")
+    return phi
 
 
 def rademacher(nodes: int, count: int, seed: int, device) -> torch.Tensor:

@@ -105,16 +105,29 @@ def paper_study(Ls=(8, 16, 32, 64), N=10000, seed=0, batch_nodes=1 << 26,
                                   batch=max(1, batch_nodes // (n * n)))
         dt = time.perf_counter() - t0
         st = rve.statistics(A, L)
+        Q = st["Q"]
         rows.append({"L": L, "N": N, "count": count, "seconds": dt,
                      "failed": sum(1 for i in infos if i["status"] != rve.RVE_OK),
                      "mean_a11": float(st["mean"][0, 0]), "mean_a22": float(st["mean"][1, 1]),
                      "mean_a12": float(st["mean"][0, 1]),
                      "std12_paper": st["std12_paper"], "stddiff_paper": st["stddiff_paper"],
                      "sem_a11": float(np.sqrt(st["var"][0, 0] / N)),
-                     "Q": st["Q"].tolist()})
+                     # Eq. "quartic" with the Kronecker-product unfolding of
+                     # (A - mean)(x)(A - mean): q_11 = L^2 var a11 and
+                     # q_14 = L^2 var a12 (entry (1,1),(2,2) of X (x) X is
+                     # X_12 X_12); q_14 of the vec unfolding = L^2 cov(a11, a22)
+                     "q11": float(Q[0, 0]), "q14_kron": float(Q[1, 1]),
+                     "q14_vec": float(Q[0, 3]),
+                     "Q": Q.tolist()})
     for a, b in zip(rows, rows[1:]):
         if b["L"] == 2 * a["L"]:
+            # Table 5 / Fig. 7: <a11>_L - <a11>_2L, with its sampling error
+            # (independent ensembles: the two standard errors in quadrature)
             a["systematic_a11_L_minus_2L"] = a["mean_a11"] - b["mean_a11"]
+            a["systematic_sem"] = float(np.hypot(a["sem_a11"], b["sem_a11"]))
+            # Fig. 9: q_L - q_2L
+            a["q11_L_minus_2L"] = a["q11"] - b["q11"]
+            a["q14_kron_L_minus_2L"] = a["q14_kron"] - b["q14_kron"]
     return rows
 
 

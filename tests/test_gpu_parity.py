@@ -159,7 +159,7 @@ def _solve_and_hom(ds, opts, mask=None):
     if mask is None:
         mask = rve.gen_field(ds, device=CUDA)
     u, info = rve.solve(ds, mask=mask, opts=opts)
-    A = rve.a_hom(ds, u, mask=mask, scheme=opts.scheme).cpu().numpy()
+    A = rve.a_hom(ds, u, mask=mask, scheme=opts.scheme, precision=opts.precision).cpu().numpy()
     return mask, u, A, rve.info_to_dicts(info, len(ds))
 
 

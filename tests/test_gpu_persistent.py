@@ -1,5 +1,6 @@
 """GPU: the persistent single-launch path over uneven sizes, plans captured in
-a CUDA graph, the autotuner, and the bounded grid-barrier wait."""
+a CUDA graph (one persistent launch, or the fused kernels in a conditional
+while node), the autotuner, and the bounded grid-barrier wait."""
 import numpy as np
 import pytest
 import torch
@@ -50,6 +51,33 @@ def test_plan_graph_replays_and_matches_fused_path():
     Af = rve.a_hom(ds, u, mask=mask).cpu().numpy()
     for k in range(len(ds)):
         assert _rel_err_A(A1[k], Af[k]) < 1e-9
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [rve.MIXED, rve.FP64])
+def test_plan_graph_loop_equals_fused_path(precision):
+    """A plan on the fused path runs the fused kernels inside a conditional
+    while node of the graph (no host polling): the same kernels on the same
+    data, so the same bits as a fused solve; the graph relaunches; and the
+    results match the oracle."""
+    ds = UNEVEN[:8]
+    opts = rve.make_opts(precision=precision, path=rve.PATH_FUSED,
+                         tol=1e-10 if precision == rve.MIXED else 1e-12)
+    plan = rve.Plan(ds, opts, device=CUDA)
+    A1, info1 = plan.execute()
+    A1 = A1.cpu().numpy().copy()
+    inf1 = rve.info_to_dicts(info1, len(ds))
+    A2, info2 = plan.execute()          # graph relaunch
+    np.testing.assert_array_equal(A1, A2.cpu().numpy())
+    assert all(d["status"] == rve.RVE_OK for d in rve.info_to_dicts(info2, len(ds)))
+    mask = rve.gen_field(ds, device=CUDA)
+    u, info = rve.solve(ds, mask=mask, opts=opts)
+    Af = rve.a_hom(ds, u, mask=mask, precision=precision).cpu().numpy()
+    np.testing.assert_array_equal(A1, Af)
+    assert [d["iters"] for d in inf1] == [d["iters"] for d in rve.info_to_dicts(info, len(ds))]
+    for k in (0, len(ds) - 1):
+        ref = oracle.solve_realization(ds[k], tol=1e-12, want_u=False)
+        assert _rel_err_A(A1[k], ref["A_energy"]) < (1e-7 if precision == rve.MIXED else 1e-10)
     plan.close()
 
 
