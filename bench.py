@@ -21,6 +21,8 @@ FP64 oracle.
     python bench.py [--gpus N --steps K --warmup W --batch B] [--impl reference]
     python bench.py --workload cubes_L4    # the 3D extension (one JSON line too)
     python bench.py --workload uneven_4096 # 4096 uneven realizations, persistent + graph
+    python bench.py --workload large_L256  # 2048^2, contrast 100, mixed; statistics
+    python bench.py --workload adjoint_L64 # 1024^2, contrast 100, FP64, A_hom + gradient
 
 The 3D workload (`--workload cubes_L4`): L = 4, h = 1/16 (64^3 nodes), 45
 unit cubes (density 0.7 per unit volume), contrast 10, three correctors per
@@ -75,7 +77,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=125)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_L32",
-                    choices=["plain_L32", "cubes_L4", "uneven_4096"])
+                    choices=["plain_L32", "cubes_L4", "uneven_4096", "large_L256", "adjoint_L64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison arms")
     return ap.parse_args()
@@ -776,6 +778,135 @@ def run_uneven(args):
     print(json.dumps(out), flush=True)
 
 
+def _single_gpu(name):
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit(f"--workload {name} runs on one GPU")
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    return dev, torch.cuda.current_stream()
+
+
+def _events_loop(torch, stream, fn, steps, warmup, index):
+    """W untimed and K timed calls of fn(k) between CUDA events, with the
+    clock record of the timed region."""
+    for k in range(warmup):
+        fn(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(index)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    outs = [fn(warmup + k) for k in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), clocks.stop(), outs
+
+
+def run_large(args):
+    """Large RVE statistics: L = 256, h = 1/8 (2048^2 nodes), contrast 100,
+    density 0.7, mixed precision; one step = field + both correctors + A_hom
+    for a batch of 16 realizations; the mixed results of the first batch
+    against the FP64 GPU path, and the ensemble statistics (mean, variance,
+    quartic tensor) of all timed realizations."""
+    import numpy as np
+    import torch
+
+    from paper_1903_12227_gb300 import rve, workloads
+    dev, stream = _single_gpu("large_L256")
+    B = args.batch if args.batch != 125 else 16
+    opts = rve.make_opts(precision=rve.MIXED, tol=1e-10)
+    probe = workloads.config_batch("large_L256", seed=0, count=B)
+    ws = rve.workspace(rve.workspace_size(probe, opts), dev)
+    rve.launch_count()
+
+    def step(k):
+        ds = workloads.config_batch("large_L256", seed=0, count=B, start=(k * B) % 256)
+        mask = rve.gen_field(ds, device=dev)
+        u, info = rve.solve(ds, mask=mask, opts=opts, ws=ws)
+        return rve.a_hom(ds, u, mask=mask, precision=rve.MIXED), info
+
+    ms, clk, outs = _events_loop(torch, stream, step, args.steps, args.warmup, dev.index)
+    launches = rve.launch_count()
+    A = torch.cat([o[0] for o in outs]).cpu().numpy()
+    info_d = [d for o in outs for d in rve.info_to_dicts(o[1], B)]
+    del ws
+    # mixed against FP64 on two realizations of the first timed batch
+    ds2 = workloads.config_batch("large_L256", seed=0, count=2, start=(args.warmup * B) % 256)
+    m2 = rve.gen_field(ds2, device=dev)
+    u64, i64 = rve.solve(ds2, mask=m2, opts=rve.make_opts(precision=rve.FP64, tol=1e-10))
+    A64 = rve.a_hom(ds2, u64, mask=m2).cpu().numpy()
+    err = per_entry_error(A[:2], A64)
+    err["sample"] = "2 realizations of the first timed batch, mixed vs the FP64 GPU path"
+    st = rve.statistics(A, 256.0)
+    out = {"metric": METRIC, "value": B * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 vectors + f64 dots/refinement/A_hom (mixed)", "data": "synthetic",
+           "config": {"workload": "large_L256: L=256, h=1/8 (2048x2048 nodes, 4.2M unknowns per "
+                                  "corrector), contrast 100, 45875 inclusions of side 1 (density "
+                                  "0.7), PCG tol 1e-10 on the true residual",
+                      "realizations_per_step": B, "precision": "mixed",
+                      "l2": "inputs larger than L2 (~4 GB working set per step)"},
+           "gpu_launches": launches, "clocks": clk,
+           "solver": {"statuses": sorted({d["status"] for d in info_d}),
+                      "mean_steps": float(np.mean([d["steps"] for d in info_d])),
+                      "mean_refinements": float(np.mean([d["refinements"] for d in info_d])),
+                      "max_relres": float(max(max(d["relres"]) for d in info_d))},
+           "a_hom_err_vs_fp64": err,
+           "statistics": {"count": int(len(A)), "mean": st["mean"].tolist(),
+                          "var": st["var"].tolist(), "Q": st["Q"].tolist(),
+                          "L2_var_a12": float(256.0 ** 2 * st["var"][0, 1])},
+           "cpu_baseline": None,
+           "cpu_baseline_note": "the oracle needs minutes per 2048^2 contrast-100 realization "
+                                "on one host thread: no bounded sample"}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """Adjoint: L = 64, h = 1/16 (1024^2 nodes), contrast 100, FP64 solve to
+    1e-13; one step = AHom forward (field, both correctors, A_hom) and
+    backward (dA/da per cell for a random 2x2 weight) for 16 realizations."""
+    import numpy as np
+    import torch
+
+    from paper_1903_12227_gb300 import rve, workloads
+    dev, stream = _single_gpu("adjoint_L64")
+    B = args.batch if args.batch != 125 else 16
+    opts = rve.make_opts(precision=rve.FP64, tol=1e-13)
+    G = torch.tensor(np.random.default_rng(4).standard_normal((B, 2, 2)), device=dev)
+    rve.launch_count()
+
+    def step(k):
+        ds = workloads.config_batch("adjoint_L64", seed=0, count=B, start=(k * B) % 64)
+        b = rve.Batch(ds)
+        mask = rve.gen_field(b, device=dev)
+        coef = rve.coef_from_mask(b, mask).requires_grad_(True)
+        A = rve.AHom.apply(coef, b, opts)
+        (A * G).sum().backward()
+        return A.detach(), coef.grad
+
+    ms, clk, outs = _events_loop(torch, stream, step, args.steps, args.warmup, dev.index)
+    launches = rve.launch_count()
+    A = torch.cat([o[0] for o in outs])
+    out = {"metric": METRIC, "value": B * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "adjoint_L64: L=64, h=1/16 (1024x1024 nodes), contrast 100, "
+                                  "2867 inclusions, FP64 solve to 1e-13, A_hom and its gradient "
+                                  "per cell (autograd Function, hand-written adjoint kernel)",
+                      "realizations_per_step": B, "precision": "fp64",
+                      "l2": "inputs larger than L2 (~2 GB working set per step)"},
+           "gpu_launches": launches, "clocks": clk,
+           "a_hom_mean_diag": float(A.diagonal(dim1=1, dim2=2).mean().item()),
+           "cpu_baseline": None,
+           "cpu_baseline_note": "the oracle needs minutes per 1024^2 contrast-100 realization at "
+                                "tol 1e-13 on one host thread: no bounded sample"}
+    print(json.dumps(out), flush=True)
+
+
 def extras(args, rve, torch, np, dev, stream):
     """The FP64 comparison arms and the mixed-vs-FP64 agreement."""
     out = {}
@@ -822,6 +953,12 @@ def main():
         return
     if args.workload == "uneven_4096":
         run_uneven(args)
+        return
+    if args.workload == "large_L256":
+        run_large(args)
+        return
+    if args.workload == "adjoint_L64":
+        run_adjoint(args)
         return
     run_ours(args)
 

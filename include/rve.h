@@ -148,6 +148,13 @@ int64_t rve_nodes(const rve_realization* r, int32_t batch);
 rve_status rve_gen_field(const rve_realization* r, int32_t batch, uint32_t* mask,
                          void* stream);
 
+/* Cell values of the coefficient (Eq. "coef_diag": a_matrix outside, a_incl
+ * inside the covered set) from the bitmask: coef (device double per cell)
+ * is overwritten.  The starting point of an explicit coefficient array
+ * (finite differences, the adjoint's inputs). */
+rve_status rve_coef_from_mask(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                              double* coef, void* stream);
+
 /* Galerkin right-hand sides f_i = -int a d_i psi (Eq. "FEM_discr_RHS"),
  * with the stiffness's quadrature (Sec. 4.3): f[node] = (f_1, f_2).
  * Coefficients from coef (device doubles) if non-NULL, else from mask. */

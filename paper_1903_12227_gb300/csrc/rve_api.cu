@@ -30,6 +30,9 @@ static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 constexpr int MIN_N = 32, MAX_N = 2048;
+// Transform groups (2048/n rows each) per update block: the next group's q
+// streams in while the current one transforms.
+constexpr int U_GROUPS = 2;
 constexpr size_t MAX_SMEM = 227 * 1024;
 
 rve_solve_opts resolved_opts(const rve_solve_opts* o) {
@@ -45,13 +48,13 @@ rve_solve_opts resolved_opts(const rve_solve_opts* o) {
 }
 
 // Tile geometry of one realization.  Row kernels use 256 threads, n/8 per
-// row, so tU = 2048/n rows per block.  The stencil tile keeps tS + 2 padded
-// rows in shared memory: the largest power of two <= 8 whose tile fits
-// 110 KB (two blocks per SM; at least 1).  Column blocks use blockC
-// threads, n / col_seg_rows per column.
+// row, so a transform group is 2048/n rows; an update block takes U_GROUPS
+// groups (tU rows).  The stencil tile keeps tS + 2 padded rows in shared
+// memory (see below).  Column blocks use blockC threads, n / col_seg_rows
+// per column.
 static void default_tiles(int n, size_t vb, int blockC, const rve_solve_opts& o, Tiles& t) {
     const size_t seq = (size_t)seq_stride(n);
-    t.tU = std::min(n, 2048 / n);
+    t.tU = std::min(n, U_GROUPS * (2048 / n));   // U_GROUPS transform groups per block
     // stencil tile: tS own rows + 2 halo rows, transformed G = 2048/n rows
     // at a time; choose tS + 2 a multiple of G (no idle row slots) with the
     // tile within ~72 KB (three blocks per SM), tS <= n.  Tiles need not
@@ -172,7 +175,9 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         const size_t vb = p.vbytes;
         const size_t seq = (size_t)seq_stride(n);
         p.smemS = std::max(p.smemS, (size_t)(t.tS + 2) * seq * vb + (size_t)(t.tS + 1) * (n / 32) * 4);
-        p.smemU = std::max(p.smemU, (size_t)t.tU * seq * vb);
+        // two sets of row buffers (one transform group each) for the update
+        // pass's streaming; the preconditioner's row passes use the first
+        p.smemU = std::max(p.smemU, (size_t)2 * std::min(t.tU, 2048 / n) * seq * vb);
         // segment end / start values (2 per column segment) and the
         // singular column's sums (2 per segment)
         p.smemC = std::max(p.smemC, (size_t)(2 * t.tC + 2) * segs * vb);
@@ -276,6 +281,16 @@ rve_status rve_gen_field(const rve_realization* r, int32_t batch, uint32_t* mask
     if (!mask) return RVE_EINVAL;
     return launch_gen_field(p, nullptr, mask, as_stream(stream)) == cudaSuccess ? RVE_OK
                                                                                : RVE_ECUDA;
+}
+
+rve_status rve_coef_from_mask(const rve_realization* r, int32_t batch, const uint32_t* mask,
+                              double* coef, void* stream) {
+    Plan p;
+    rve_status st = make_plan(r, batch, nullptr, p, false);
+    if (st != RVE_OK) return st;
+    if (!mask || !coef) return RVE_EINVAL;
+    return launch_coef_from_mask(p, mask, coef, as_stream(stream)) == cudaSuccess ? RVE_OK
+                                                                                 : RVE_ECUDA;
 }
 
 rve_status rve_rhs(const rve_realization* r, int32_t batch, const uint32_t* mask,

@@ -121,6 +121,8 @@ cudaError_t launch_tables(const Plan& p, void* ws, cudaStream_t s);
 cudaError_t launch_gen_field(const Plan& p, void* ws, uint32_t* mask, cudaStream_t s);
 cudaError_t launch_rhs(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                        double* f, cudaStream_t s);
+cudaError_t launch_coef_from_mask(const Plan& p, const uint32_t* mask, double* coef,
+                                  cudaStream_t s);
 cudaError_t launch_stiffness(const Plan& p, void* ws, const uint32_t* mask, const double* coef,
                              int scheme, int precision, const void* x, void* y, cudaStream_t s);
 // Row, column(+scale), row transform passes for realizations

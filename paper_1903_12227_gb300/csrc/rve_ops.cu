@@ -61,6 +61,16 @@ __global__ void k_rhs(const __grid_constant__ DescChunk ch, CoefSrc cs, double2*
     f[d.node_off + node] = rhs_at(cells_at(cs, d, i, j), d.h);
 }
 
+// Cell values a_c from the bitmask and the two values (one thread per cell).
+__global__ void k_coef_from_mask(const __grid_constant__ DescChunk ch, const uint32_t* __restrict__ mask,
+                                 double* __restrict__ coef) {
+    const int b = find_real(ch.start, ch.count, blockIdx.x);
+    const RDesc& d = ch.d[b];
+    const int64_t cell = (int64_t)(blockIdx.x - ch.start[b]) * NODE_TILE + threadIdx.x;
+    const uint32_t w = __ldg(mask + d.word_off + (cell >> 5));
+    coef[d.node_off + cell] = ((w >> (cell & 31)) & 1u) ? d.a_incl : d.a_matrix;
+}
+
 template <typename V>
 __device__ __forceinline__ V ldv(const V* __restrict__ x, const RDesc& d, int i, int j) {
     return x[d.node_off + ((int64_t)(i & (d.n - 1)) << d.log2n) + (j & (d.n - 1))];
@@ -300,6 +310,14 @@ cudaError_t launch_rhs(const Plan& p, void*, const uint32_t* mask, const double*
     CoefSrc cs{mask, coef};
     return for_chunks(p, node_tiles, [&](const DescChunk& ch, int) {
         k_rhs<<<ch.start[ch.count], NODE_TILE, 0, s>>>(ch, cs, reinterpret_cast<double2*>(f));
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_coef_from_mask(const Plan& p, const uint32_t* mask, double* coef,
+                                  cudaStream_t s) {
+    return for_chunks(p, node_tiles, [&](const DescChunk& ch, int) {
+        k_coef_from_mask<<<ch.start[ch.count], NODE_TILE, 0, s>>>(ch, mask, coef);
         return cudaGetLastError();
     });
 }

@@ -307,7 +307,33 @@ __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, c
         return ((w >> (ci & 31)) & 1u) ? aI : aM;
     };
     dword nx{0.f, 0.f}, ny{0.f, 0.f};   // |r|^2, double-word per thread
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (first) {   // u = x = p = 0: r = f, the same arithmetic without the zero terms
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            dword cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
+            for (int q = 0; q < rows; ++q) {
+                const int i = r0 + q;
+                const dword c0m = cell(i, j - 1), c00 = cell(i, j);
+                dword kfx, kfy;   // K f
+                if (c.cs.f) {
+                    const double2 fl = c.cs.f[d.node_off + ((int64_t)i << d.log2n) + j];
+                    kfx = dw_mulf(dw_split(fl.x), 2.f * KH);
+                    kfy = dw_mulf(dw_split(fl.y), 2.f * KH);
+                } else {
+                    const dword top = dw_add(cmm, cm0), bot = dw_add(c0m, c00);
+                    const dword lft = dw_add(cmm, c0m), rgt = dw_add(cm0, c00);
+                    kfx = dw_mulf(dw_add(bot, dw_neg(top)), kh2);
+                    kfy = dw_mulf(dw_add(rgt, dw_neg(lft)), kh2);
+                }
+                const DotDW rx(kfx), ry(kfy);
+                const float2 r = make_float2(rx.value() * INVK, ry.value() * INVK);
+                Q[d.node_off + ((int64_t)i << d.log2n) + j] = r;
+                nx = dw_add(nx, r.x * r.x);
+                ny = dw_add(ny, r.y * r.y);
+                cmm = c0m; cm0 = c00;
+            }
+        }
+    }
+    for (int j = first ? n : threadIdx.x; j < n; j += blockDim.x) {
         float4 a0 = wat(r0 - 1, j - 1), a1 = wat(r0 - 1, j), a2 = wat(r0 - 1, j + 1);
         float4 b0 = wat(r0, j - 1), b1 = wat(r0, j), b2 = wat(r0, j + 1);
         dword cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
@@ -619,13 +645,17 @@ __device__ __forceinline__ void row_hartley_store(V (&v)[8], V* buf, const RDesc
                               [&](int r, int k, V val) { out[node_at(d, z, r, k)] = val; });
 }
 
-// The update kernel (one pass of tU rows per block).  The residual is kept
-// in the row-Hartley domain, rt = H r (H the unnormalised Hartley transform
-// along rows, H H = n I): that is exactly what the column pass consumes, so
-// the update writes it once instead of writing r and t = H r.
+// The update kernel: tU rows per block, in transform groups of L.G rows
+// (n/8 threads per row).  The residual is kept in the row-Hartley domain,
+// rt = H r (H the unnormalised Hartley transform along rows, H H = n I):
+// that is exactly what the column pass consumes, so the update writes it
+// once instead of writing r and t = H r.
 //   ITER    rt -= alpha H q  (H q by the row transform of q), |r|^2 = |rt|^2 / n;
 //   REFINE  u = w (the new iterate), x = 0, r = r64 / |r64| (|r|^2 from r),
 //           rt = H r.
+// ITER streams: q of the next group arrives by asynchronous copies into the
+// other of two row buffers while the current group transforms, and rt of a
+// group is loaded before its transform.
 template <typename V, int LOG2N>
 __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const RState& s,
                                              const RDesc& d, double* red,
@@ -634,17 +664,16 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
     const int phase = s.phase;
     const RowLayout<LOG2N> L(d.log2n);
     const Sz<LOG2N>& z = L.z;
-    const int G = d.tU;
-    const int row = (blk - c.startU[b]) * G + L.qq;
-    const bool active = L.qq < G;
+    const int row0 = (blk - c.startU[b]) * d.tU;
+    const int ng = (d.tU + L.G - 1) / L.G;   // transform groups of this block
     typedef typename ScalarOf<V>::T T;
     V* Rt = static_cast<V*>(c.R);
     V* X = static_cast<V*>(c.X);
     const V* Qv = static_cast<const V*>(c.Q);
-    V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(z.n);
+    const int SEQ = seq_stride(z.n);
+    V* bufs = reinterpret_cast<V*>(smem_raw);   // two sets of L.G row buffers
     const V* tw = twiddles<V>(c.tb, z.n);
     DotAcc<T> ax, ay;
-    V v[8];
     double inv_scale = 1.0;   // |r|^2 = (sum of the squares formed here) * inv_scale
     if (phase == PH_ITER) {
         // alpha = rho / p.q, formed by the last stencil block (finish_S)
@@ -652,34 +681,60 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
             usc[0] = (T)c.uscal[2 * b];
             usc[1] = (T)c.uscal[2 * b + 1];
         }
-        // q and rt of the row: every load issued before the transform, so
-        // the rt loads are in flight while q transforms
-        V rt[8];
-        if (active) {
+        auto prefetch = [&](int g) {   // q of group g into row buffer set g & 1
+            const int q = g * L.G + L.qq;
+            if (g < ng && q < d.tU) {
+                V* buf = bufs + ((g & 1) * L.G + L.qq) * SEQ;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = Qv[node_at(d, z, row, L.t + m * z.T)];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) rt[m] = Rt[node_at(d, z, row, L.t + m * z.T)];
-        }
+                for (int m = 0; m < 8; ++m)
+                    cp_async_v(buf + pidx(L.t + m * z.T), Qv + node_at(d, z, row0 + q, L.t + m * z.T));
+            }
+            cp_async_commit();
+        };
+        prefetch(0);
         __syncthreads();
         const T alx = usc[0], aly = usc[1];
-        fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
-        if (active) {
+        for (int g = 0; g < ng; ++g) {
+            const int q = g * L.G + L.qq;
+            const bool active = q < d.tU;
+            const int row = row0 + q;
+            // the other buffer set was last read by group g-1: the barrier at
+            // the end of every group makes it free for group g+1's copies
+            prefetch(g + 1);
+            V rt[8];
+            if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int k = L.t + m * z.T;
-                const V qt = hartley_pair(v[m], buf[pidx((z.n - k) & (z.n - 1))]);
-                const V rr = axpy2(rt[m], -alx, -aly, qt);
-                Rt[node_at(d, z, row, k)] = rr;
-                ax.add(rr.x, rr.x);
-                ay.add(rr.y, rr.y);
+                for (int m = 0; m < 8; ++m) rt[m] = Rt[node_at(d, z, row, L.t + m * z.T)];
             }
+            cp_async_wait<1>();
+            __syncthreads();
+            V* buf = bufs + ((g & 1) * L.G + (active ? L.qq : 0)) * SEQ;
+            V v[8];
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) v[m] = buf[pidx(L.t + m * z.T)];
+            }
+            fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int k = L.t + m * z.T;
+                    const V qt = hartley_pair(v[m], buf[pidx((z.n - k) & (z.n - 1))]);
+                    const V rr = axpy2(rt[m], -alx, -aly, qt);
+                    Rt[node_at(d, z, row, k)] = rr;
+                    ax.add(rr.x, rr.x);
+                    ay.add(rr.y, rr.y);
+                }
+            }
+            __syncthreads();   // mirror reads of this buffer set are done
         }
+        cp_async_wait<0>();
         inv_scale = 1.0 / (double)z.n;
     } else {
-        if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
-            const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-            if (threadIdx.x == 0) {   // the same conversions as refine_tile_dw
+        float4* U4 = reinterpret_cast<float4*>(c.u);
+        const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
+        if constexpr (sizeof(T) == 4) {   // the same conversions as refine_tile_dw
+            if (threadIdx.x == 0) {
                 usc[0] = (float)s.s[0];
                 usc[1] = (float)s.s[1];
                 usc[2] = (float)s.alpha[0];
@@ -688,58 +743,66 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
                 usc[5] = (float)c.uscal[2 * b + 1];   // converged), from finish_S
             }
             __syncthreads();
-            const DWScal k{usc[0], usc[1], usc[2], usc[3]};
-            const float ix = usc[4], iy = usc[5];
-            float4* U4 = reinterpret_cast<float4*>(c.u);
-            if (active) {
+        }
+        for (int g = 0; g < ng; ++g) {
+            const int q = g * L.G + L.qq;
+            const bool active = q < d.tU;
+            const int row = row0 + q;
+            V* buf = bufs + (active ? L.qq : 0) * SEQ;
+            V v[8];
+            if constexpr (sizeof(T) == 4) {   // REFINE, mixed: u is a double word
+                const DWScal k{usc[0], usc[1], usc[2], usc[3]};
+                const float ix = usc[4], iy = usc[5];
+                if (active) {
 #pragma unroll
-                for (int h = 0; h < 8; h += 4) {
-                    float4 uu[4];
-                    V xx[4], pp[4], qv[4];
+                    for (int h = 0; h < 8; h += 4) {
+                        float4 uu[4];
+                        V xx[4], pp[4], qv[4];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {   // loads first, stores after
-                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                        uu[m] = U4[node];
-                        xx[m] = X[node];
-                        pp[m] = Pold[node];
-                        qv[m] = Qv[node];
+                        for (int m = 0; m < 4; ++m) {   // loads first, stores after
+                            const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                            uu[m] = U4[node];
+                            xx[m] = X[node];
+                            pp[m] = Pold[node];
+                            qv[m] = Qv[node];
+                        }
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
+                            U4[node] = w_new(uu[m], xx[m], pp[m], k);
+                            X[node] = mk<V>(0.f, 0.f);
+                            const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
+                            v[h + m] = rr;
+                            ax.add(rr.x, rr.x);
+                            ay.add(rr.y, rr.y);
+                        }
                     }
+                }
+            } else {   // REFINE, FP64
+                // 1 / |r64| per corrector (0 once converged), from finish_S
+                const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
+                if (active) {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int64_t node = node_at(d, z, row, L.t + (h + m) * z.T);
-                        U4[node] = w_new(uu[m], xx[m], pp[m], k);
-                        X[node] = mk<V>(0.f, 0.f);
-                        const V rr = mk<V>(qv[m].x * ix, qv[m].y * iy);
-                        v[h + m] = rr;
+                    for (int m = 0; m < 8; ++m) {
+                        const int64_t node = node_at(d, z, row, L.t + m * z.T);
+                        const double2 xx = to_d2(X[node]);
+                        const double2 pp = to_d2(Pold[node]);
+                        double2 uu = c.u[node];
+                        uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
+                        uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
+                        c.u[node] = uu;
+                        X[node] = from_d2<V>(make_double2(0.0, 0.0));
+                        const double2 qq = to_d2(Qv[node]);
+                        const V rr = from_d2<V>(make_double2(qq.x * ix, qq.y * iy));
+                        v[m] = rr;
                         ax.add(rr.x, rr.x);
                         ay.add(rr.y, rr.y);
                     }
                 }
             }
-        } else {   // REFINE, FP64
-            const V* Pold = static_cast<const V*>(s.parity ? c.P1 : c.P0);
-            // 1 / |r64| per corrector (0 once converged), from finish_S
-            const double ix = c.uscal[2 * b], iy = c.uscal[2 * b + 1];
-            if (active) {
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int64_t node = node_at(d, z, row, L.t + m * z.T);
-                    const double2 xx = to_d2(X[node]);
-                    const double2 pp = to_d2(Pold[node]);
-                    double2 uu = c.u[node];
-                    uu.x += s.s[0] * (xx.x + s.alpha[0] * pp.x);
-                    uu.y += s.s[1] * (xx.y + s.alpha[1] * pp.y);
-                    c.u[node] = uu;
-                    X[node] = from_d2<V>(make_double2(0.0, 0.0));
-                    const double2 q = to_d2(Qv[node]);
-                    const V rr = from_d2<V>(make_double2(q.x * ix, q.y * iy));
-                    v[m] = rr;
-                    ax.add(rr.x, rr.x);
-                    ay.add(rr.y, rr.y);
-                }
-            }
+            row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, tw, active, Rt);
+            __syncthreads();   // mirror reads of the buffer are done
         }
-        row_hartley_store<V, LOG2N>(v, buf, d, z, row, L.t, tw, active, Rt);
     }
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
@@ -800,7 +863,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const C
     fused_S_tile<V, SCHEME>(c, blockIdx.x);
 }
 template <typename V>
-__global__ void __launch_bounds__(256) k_fused_U(const Ctx c) { fused_U_tile<V>(c, blockIdx.x); }
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 4 : 2) k_fused_U(const Ctx c) { fused_U_tile<V>(c, blockIdx.x); }
 template <typename V>
 __global__ void __launch_bounds__(512) k_fused_C(const Ctx c) {
     fused_C_tile<V>(c, blockIdx.x);
@@ -1479,16 +1542,20 @@ __global__ void __launch_bounds__(256) k_row_hartley(const RDesc* __restrict__ d
     const RDesc d = desc[b];
     dispatch_size(d.log2n, [&]<int LG>() {
         const RowLayout<LG> L(d.log2n);
-        const int G = d.tU;
-        const int row = (blk - startU[b]) * G + L.qq;
-        const bool active = L.qq < G;
-        V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(L.z.n);
-        V v[8];
-        if (active) {
+        const int row0 = (blk - startU[b]) * d.tU;
+        for (int g0 = 0; g0 < d.tU; g0 += L.G) {
+            const bool active = g0 + L.qq < d.tU;
+            const int row = row0 + g0 + L.qq;
+            V* buf = reinterpret_cast<V*>(smem_raw) + (active ? L.qq : 0) * seq_stride(L.z.n);
+            V v[8];
+            if (active) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = in[node_at(d, L.z, row, L.t + m * L.z.T)];
+                for (int m = 0; m < 8; ++m) v[m] = in[node_at(d, L.z, row, L.t + m * L.z.T)];
+            }
+            row_hartley_store<V, LG>(v, buf, d, L.z, row, L.t, twiddles<V>(tb, L.z.n), active,
+                                     out);
+            __syncthreads();   // mirror reads of the buffers are done
         }
-        row_hartley_store<V, LG>(v, buf, d, L.z, row, L.t, twiddles<V>(tb, L.z.n), active, out);
     });
 }
 

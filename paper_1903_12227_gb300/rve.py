@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
         L.rve_nodes.argtypes = [vp, i32]
         L.rve_gen_field.restype = i32
         L.rve_gen_field.argtypes = [vp, i32, vp, vp]
+        L.rve_coef_from_mask.restype = i32
+        L.rve_coef_from_mask.argtypes = [vp, i32, vp, vp, vp]
         L.rve_rhs.restype = i32
         L.rve_rhs.argtypes = [vp, i32, vp, vp, vp, vp]
         L.rve_apply_stiffness.restype = i32
@@ -339,6 +341,16 @@ def apply_mass(batch, x: torch.Tensor, scheme=CONSISTENT, stream=None) -> torch.
     check(lib().rve_apply_mass(b.ptr, b.count, scheme, _ptr(x), _ptr(y), _stream(stream)),
           "rve_apply_mass")
     return y
+
+
+def coef_from_mask(batch, mask: torch.Tensor, stream=None) -> torch.Tensor:
+    """Cell values [nodes] float64 (a_matrix / a_incl) from the bitmask."""
+    _require_cuda()
+    b = as_batch(batch)
+    coef = torch.empty(b.nodes, dtype=torch.float64, device=mask.device)
+    check(lib().rve_coef_from_mask(b.ptr, b.count, _ptr(mask), _ptr(coef), _stream(stream)),
+          "rve_coef_from_mask")
+    return coef
 
 
 def a_hom(batch, u: torch.Tensor, mask=None, coef=None, scheme=CONSISTENT, ws=None,

@@ -57,6 +57,18 @@ def test_gen_field_bit_exact(case):
         np.testing.assert_array_equal(m, oracle.gen_field(d).astype(bool))
 
 
+def test_coef_from_mask_bit_exact():
+    ds = FIELD_CASES[1] + FIELD_CASES[2][:6]
+    mask = rve.gen_field(ds, device=CUDA)
+    coef = rve.coef_from_mask(ds, mask).cpu().numpy()
+    off = 0
+    for d in ds:
+        n = d["L"] * d["m0"]
+        ref = oracle.coef_from_mask(oracle.gen_field(d), d["a_matrix"], d["a_incl"])
+        np.testing.assert_array_equal(coef[off:off + n * n].reshape(n, n), ref)
+        off += n * n
+
+
 # ------------------------------------------------------- rhs / stiffness --
 def _setup(ds):
     mask = rve.gen_field(ds, device=CUDA)
