@@ -109,7 +109,7 @@ typedef struct {
     int32_t tile_rows;   /* stencil tile height in node rows (1..n; n need
                             not be a multiple), 0 = tuned or default       */
     int32_t col_tile;    /* threads of a column-solve block (power of two,
-                            32..512); 0 = 256 (mixed) or 512 (FP64)         */
+                            32..512); 0 = 128 (mixed) or 512 (FP64)         */
     int32_t check_every; /* host convergence poll period (0 = 8)            */
     int32_t timeout_us;  /* persistent path: bound on each grid-wide wait, in
                             microseconds (0 = 2 s)                          */
@@ -334,7 +334,7 @@ void rve_plan_destroy(rve_plan plan);
 
 /* Autotuner.  For every distinct grid size n of the batch, times short
  * trial solves of up to 16 of its realizations for each candidate tile shape
- * (stencil tile heights; column-block threads 256/512/1024 on the fused
+ * (stencil tile heights; column-block threads 128/256/512 on the fused
  * path, 256 on the persistent path) and records the fastest in the
  * process-wide tuner table, keyed by (n, precision, persistent).  Plans and
  * solves with opts->tile_rows == 0 and opts->col_tile == 0 then use the

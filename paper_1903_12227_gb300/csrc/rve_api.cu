@@ -32,7 +32,7 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int MIN_N = 32, MAX_N = 2048;
 // Transform groups (2048/n rows each) per update block: the next group's q
 // streams in while the current one transforms.
-constexpr int U_GROUPS = 2;
+constexpr int U_GROUPS = 4;
 constexpr size_t MAX_SMEM = 227 * 1024;
 
 rve_solve_opts resolved_opts(const rve_solve_opts* o) {
@@ -117,9 +117,10 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         if (nn > 0 && nn <= MAX_N) maxn = std::max(maxn, (int)nn);
     }
     // column blocks: a segment of up to 32 rows per thread in registers;
-    // 256 threads for the mixed path (~2 % faster than 512 on 512^2 grids,
-    // measured), 512 for FP64 (its shorter segments need more threads)
-    p.blockC = (p.vbytes == 8) ? 256 : 512;
+    // 128 threads for the mixed path (3 % faster than 256 and 13 % faster
+    // than 512 on 512^2 grids, measured), 512 for FP64 (its shorter
+    // segments need more threads)
+    p.blockC = (p.vbytes == 8) ? 128 : 512;
     {
         int ts_tuned = 0, bc_tuned = 0;
         if (maxn > 0 && tuned_tiles(maxn, o.precision, o.path == RVE_PATH_PERSISTENT ? 1 : 0,

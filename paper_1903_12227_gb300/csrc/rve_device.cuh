@@ -414,9 +414,15 @@ enum { FFT_TO_SMEM = 0, FFT_TO_REGS = 1, FFT_TO_BOTH = 2 };
 // BS: element x of the sequence sits at buf[pidx(x) * BS], so that BS
 // sequences can be interleaved element by element (BS consecutive lanes
 // working on BS sequences then touch consecutive words).
-template <int FINAL, int LOG2N = 0, int BS = 1, typename V>
+// The barriers between stages come from `bar` (default: the whole block;
+// a row team's own barrier when every row is transformed by its own threads,
+// see TeamBar).
+struct BlockBar {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int FINAL, int LOG2N = 0, int BS = 1, typename V, typename Bar = BlockBar>
 __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
-                                        const V* __restrict__ tw, bool active) {
+                                        const V* __restrict__ tw, bool active, Bar bar = Bar()) {
     const int log2n = LOG2N ? LOG2N : log2n_rt;
     const int T = 1 << (log2n - 3);
     const int nstages = (log2n + 2) / 3;   // radix 8, then one radix-4 or -2 tail
@@ -431,7 +437,7 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
         const bool last = (rem == lr);
         const bool to_smem = !last || FINAL != FFT_TO_REGS;
         const bool to_regs = last && FINAL != FFT_TO_SMEM;
-        __syncthreads();   // earlier readers of buf are done
+        bar();   // earlier readers of buf are done
         if (active) {
             if (lr == 3) {
                 const int k = t & (Ns - 1);
@@ -492,16 +498,29 @@ __device__ __forceinline__ void fft_reg(V (&v)[8], V* buf, int log2n_rt, int t,
             }
         }
         if (last) {
-            if (FINAL != FFT_TO_REGS) __syncthreads();
+            if (FINAL != FFT_TO_REGS) bar();
             break;
         }
-        __syncthreads();
+        bar();
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) v[m] = buf[pidx(t + m * T) * BS];
         }
     }
 }
+
+// Barrier of the T = n/8 threads that transform one row (a "row team"):
+// named barrier 1 + team (T >= 64, a multiple of the warp size; at most four
+// teams in a 256-thread block), the warp's own barrier when a team fits in a
+// warp (T <= 32: the warp's teams sync together, which is all they need).
+struct TeamBar {
+    int id, count;
+    __device__ __forceinline__ TeamBar(int team, int T) : id(1 + team), count(T) {}
+    __device__ __forceinline__ void operator()() const {
+        if (count >= 64) asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+        else __syncwarp();
+    }
+};
 
 // Grid size as compile-time constants (LOG2N > 0) or run-time values (0).
 template <int LOG2N> struct Sz {

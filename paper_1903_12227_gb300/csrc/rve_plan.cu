@@ -190,7 +190,7 @@ rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve
         tss.erase(std::unique(tss.begin(), tss.end()), tss.end());
         tss.erase(std::remove_if(tss.begin(), tss.end(), [&](int v) { return v < 1 || v > n; }),
                   tss.end());
-        std::vector<int> bcs = {256, 512};
+        std::vector<int> bcs = {128, 256, 512};
         if (base.path == RVE_PATH_PERSISTENT) bcs = {256};
         float best = 1e30f;
         int best_ts = 0, best_bc = 0;

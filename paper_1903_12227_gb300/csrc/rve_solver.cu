@@ -544,21 +544,25 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
         }
         done = q1;
     };
+    // every row's transform is done by its own team of n/8 threads: the
+    // barriers of the group loop are the team's, so the teams of a block
+    // drift independently (one waits on its loads while another transforms)
+    const TeamBar team(L.qq, L.z.T);
     for (int g0 = 0; g0 < TR + 2; g0 += L.G) {
         const int q = g0 + L.qq;
         const bool active = q < TR + 2;
         const int row = (r0 - 1 + q) & (n - 1);
         const bool own = active && q >= 1 && q <= TR;
         prefetch(g0 + L.G);
-        cp_async_wait<1>();   // this thread's copies of group g0 have landed
-        __syncthreads();      // ... and everybody's
+        cp_async_wait<1>();   // this thread's copies of slot q have landed
+        team();               // ... and those of the whole team
         V* buf = Pt + (active ? q : 0) * SEQ;
         V v[8];
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) v[m] = buf[pidx(L.t + m * L.z.T)];
         }
-        fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
+        fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active, team);
         V pn[8];
         if (active) {
             // p_new = z + beta p_old; own rows: x += alpha p_old (the lagged
@@ -590,14 +594,14 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
                 }
             }
         }
-        __syncthreads();   // partner reads of this group are done
+        team();   // the team's mirror reads of this row are done
         if (active) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) buf[pidx(L.t + m * L.z.T)] = pn[m];
         }
     }
     cp_async_wait<0>();
-    __syncthreads();   // p_new of the tile visible
+    __syncthreads();   // p_new of the whole tile visible
     stencil_rows(TR);
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
@@ -694,6 +698,9 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
         prefetch(0);
         __syncthreads();
         const T alx = usc[0], aly = usc[1];
+        // each row by its own team of n/8 threads, which touches only its own
+        // row buffers: team barriers only
+        const TeamBar team(L.qq, z.T);
         for (int g = 0; g < ng; ++g) {
             const int q = g * L.G + L.qq;
             const bool active = q < d.tU;
@@ -707,14 +714,14 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
                 for (int m = 0; m < 8; ++m) rt[m] = Rt[node_at(d, z, row, L.t + m * z.T)];
             }
             cp_async_wait<1>();
-            __syncthreads();
+            team();
             V* buf = bufs + ((g & 1) * L.G + (active ? L.qq : 0)) * SEQ;
             V v[8];
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 8; ++m) v[m] = buf[pidx(L.t + m * z.T)];
             }
-            fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active);
+            fft_reg<FFT_TO_BOTH, LOG2N>(v, buf, z.log2n, L.t, tw, active, team);
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
@@ -726,7 +733,7 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
                     ay.add(rr.y, rr.y);
                 }
             }
-            __syncthreads();   // mirror reads of this buffer set are done
+            team();   // mirror reads of this row buffer are done
         }
         cp_async_wait<0>();
         inv_scale = 1.0 / (double)z.n;

@@ -150,15 +150,15 @@ def test_tuner_table_save_load_roundtrip(librve, tmp_path):
     rve.tuner_clear()
     assert rve.tuner_lookup(512, rve.MIXED, False) is None
     path = tmp_path / "tune.txt"
-    path.write_text("# n precision persistent tile_rows block_threads\n512 1 0 4 128\n64 0 1 8 256\n")
+    path.write_text("# n precision persistent tile_rows block_threads\n512 1 0 4 512\n64 0 1 8 256\n")
     rve.tuner_load(str(path))
-    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 128)
+    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 512)
     assert rve.tuner_lookup(64, rve.FP64, True) == (8, 256)
     out = tmp_path / "out.txt"
     rve.tuner_save(str(out))
     rve.tuner_clear()
     rve.tuner_load(str(out))
-    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 128)
+    assert rve.tuner_lookup(512, rve.MIXED, False) == (4, 512)
     # the tuned shape changes the plan (tile counts, hence the partial-sum arrays)
     from paper_1903_12227_gb300 import workloads
     b = rve.Batch([workloads.realization(32, 16, 10.0, 0, 0)])
