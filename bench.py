@@ -484,9 +484,10 @@ CUBES_DESC = ("L=4, h=1/16 (64^3 nodes, 262144 unknowns per corrector), contrast
 # realization) of one launch of each 3D kernel kind in the mixed solve:
 # FP32 stencil 17 (x, cells, y); line pass 18 on average (16, the last of
 # four also reads r); z solve 16; vector steps 36 on average (axpy 48, xpby
-# 24); FP64 true residual 49 (u, f, cells in; r out).
+# 24); true residual in double words 81 (the split of u into double words:
+# u in, 16-byte words out; the residual pass: words, f, cells in, r out).
 CUBES_BYTES = {"stiffness": 17.0, "lines": 18.0, "zsolve": 16.0, "vector": 36.0, "scalar": 0.0,
-               "resid64": 49.0}
+               "resid64": 81.0}
 
 
 def cubes_descs(start: int, count: int):

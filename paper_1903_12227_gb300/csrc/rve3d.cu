@@ -411,6 +411,111 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
     }
 }
 
+// ------------------------------------------- double-word true residual --
+// The mixed path's true residual r64 = f - A u without FP64 arithmetic per
+// node (GB300's FP64 pipe is ~1/64 of FP32): u is split once into double
+// words (hi, lo floats from its IEEE fields, k3_split_dw), and the row of
+// node i is scaled by K = 12/h (consistent) or 4/h (lumped), which makes
+// every Hamming-distance weight an integer multiple of a sum of cell values:
+//   consistent  K e = (4, 0, -1, -1)    K r = K f - 4 S8 u_i + sum_edges S2 u + sum_corners S1 u
+//   lumped      K e = (3, -1, 0, 0)     K r = K f - 3 S8 u_i + sum_faces S4 u
+// (S_m the sum of the m cells the two nodes share).  The sum is a
+// compensated dot product of double words (DotDW: the products' rounding
+// errors gather in a compensation term), so its absolute error is
+// O(eps_32^2) times the size of its terms -- far below the outer tolerance
+// -- like the 2D refinement pass.  One node per thread; the neighbours'
+// double words come through L1.  Partials: |r|^2 per component (FP32 per
+// thread, 256 nodes per block).
+__global__ void __launch_bounds__(T3) k3_split_dw(Grp g, const double2* __restrict__ u,
+                                                  float4* __restrict__ w, const MixScal* sc) {
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3 d = g.desc[un];
+    if (unit_skip(sc, un, true)) return;
+    const int64_t node = d.off + (int64_t)lb * T3 + threadIdx.x;
+    const double2 v = u[node];
+    const dword x = dw_split(v.x), y = dw_split(v.y);
+    w[node] = make_float4(x.hi, y.hi, x.lo, y.lo);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
+                                                  const float4* __restrict__ w,
+                                                  const double2* __restrict__ f,
+                                                  double2* __restrict__ r, double* part,
+                                                  const MixScal* sc) {
+    __shared__ double red[16];
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3 d = g.desc[un];
+    if (unit_skip(sc, un, true)) return;
+    const int lg = d.log2n;
+    const int loc = lb * T3 + threadIdx.x;
+    const int i = loc >> (2 * lg), j = (loc >> lg) & (d.n - 1), k = loc & (d.n - 1);
+    const float4* __restrict__ wu = w + d.off;
+    const dword aI = dw_split(d.ai), aM = dw_split(d.am);
+    // the 8 cells around the node: C[4 c1 + 2 c2 + c3] = cell (i - c1, j - c2, k - c3)
+    dword C[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int idx = l3(d, i - (q >> 2), j - ((q >> 1) & 1), k - (q & 1));
+        if (cs.coef) C[q] = dw_split(__ldg(cs.coef + d.cell_off + idx));
+        else C[q] = __ldg(cs.mask + d.cell_off + idx) ? aI : aM;
+    }
+    // the cell bit an offset fixes on its axis: +1 -> 0, -1 -> 1
+    auto cb = [](int o) { return o > 0 ? 0 : 1; };
+    // K = 12/h or 4/h: an integer (h = 1/m0)
+    const float K = (SCHEME == 0 ? 12.f : 4.f) * rintf((float)(1.0 / d.h));
+    const double2 ff = f[d.off + loc];
+    DotDW rx(dw_mulf(dw_split(ff.x), K)), ry(dw_mulf(dw_split(ff.y), K));
+    auto term = [&](dword wgt, int o1, int o2, int o3) {   // r -= wgt * u(i + o)
+        const float4 v = wu[l3(d, i + o1, j + o2, k + o3)];
+        const dword nw = dw_neg(wgt);
+        rx.add(nw, v.x, v.z);
+        ry.add(nw, v.y, v.w);
+    };
+    dword S8 = dw_add(dw_add(dw_add(C[0], C[1]), dw_add(C[2], C[3])),
+                      dw_add(dw_add(C[4], C[5]), dw_add(C[6], C[7])));
+    term(dw_scale2(S8, SCHEME == 0 ? 4.f : 2.f), 0, 0, 0);
+    if (SCHEME != 0) term(S8, 0, 0, 0);   // 3 S8 = 2 S8 + S8 (exact scalings only)
+#pragma unroll
+    for (int o1 = -1; o1 <= 1; ++o1)
+#pragma unroll
+        for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+            for (int o3 = -1; o3 <= 1; ++o3) {
+                const int zeros = (o1 == 0) + (o2 == 0) + (o3 == 0);
+                if (zeros == 3) continue;
+                if (SCHEME == 0 && zeros == 2) continue;   // faces: K e_1 = 0
+                if (SCHEME != 0 && zeros != 2) continue;   // lumped: faces only
+                // sum of the cells shared with the neighbour: the bits of
+                // the non-zero offsets are fixed, the others run over 0, 1
+                dword S{0.f, 0.f};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int c1 = q >> 2, c2 = (q >> 1) & 1, c3 = q & 1;
+                    if (o1 != 0 && c1 != cb(o1)) continue;
+                    if (o2 != 0 && c2 != cb(o2)) continue;
+                    if (o3 != 0 && c3 != cb(o3)) continue;
+                    S = dw_add(S, C[q]);
+                }
+                term(dw_neg(S), o1, o2, o3);   // K e = -1: r += S u
+            }
+    const double invK = 1.0 / (double)K;
+    const double rxd = ((double)rx.s + (double)rx.comp) * invK;
+    const double ryd = ((double)ry.s + (double)ry.comp) * invK;
+    r[d.off + loc] = make_double2(rxd, ryd);
+    if (part) {
+        const float fx = (float)rxd, fy = (float)ryd;
+        double tx = 0.0, ty = 0.0;
+        block_pair_sum(fx * fx, fy * fy, red, tx, ty);
+        if (threadIdx.x == 0) {
+            part[d.part_off + 2 * lb] = tx;
+            part[d.part_off + 2 * lb + 1] = ty;
+        }
+    }
+}
+
 // -------------------------------------------------------------- loads --
 // Corrector loads f_i = -sum_c a_c P_c^T E xi_i (xi_i = h x corner bit i).
 // Every row of M1 sums to h/2 (both schemes) and every row of K1 to 0, so
@@ -1234,6 +1339,24 @@ static cudaError_t stiffness3(const Ws3& ws, const Group3& g, Cells3T<typename S
     return cudaGetLastError();
 }
 
+// r64 = f - A u of the units of group g in double words (the mixed path):
+// u split into double words in the q slot, then the residual pass.
+static cudaError_t resid3_dw(const Ws3& ws, const Group3& g, Cells3T<double> cs, int scheme,
+                             const double2* u, double2* r, const double2* f, const MixScal* sc,
+                             cudaStream_t s) {
+    const int per = (int)(nodes_of(g) / T3);
+    float4* wdw = reinterpret_cast<float4*>(ws.vec<double2>(V_Q));   // 16 bytes per node
+    const Grp gg = ws.grp(g, per);
+    Span3 sp(s, P3_RESID);
+    k3_split_dw<<<nblocks(g, per), T3, 0, s>>>(gg, u, wdw, ws.sc());
+    if (scheme == RVE_Q1_LUMPED)
+        k3_resid_dw<1><<<nblocks(g, per), T3, 0, s>>>(gg, cs, wdw, f, r, ws.part(), sc);
+    else
+        k3_resid_dw<0><<<nblocks(g, per), T3, 0, s>>>(gg, cs, wdw, f, r, ws.part(), sc);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
 // The correctors of every unit: cycles of PCG in the precision of V between
 // FP64 true residuals (see the head of the file).
 template <typename V>
@@ -1303,13 +1426,18 @@ static rve_status solve_units(const Plan3& p, char* w, Cells3T<double> cs64,
     for (int cycle = 0; cycle <= MAX_REFINE + 1; ++cycle) {
         // FP64 true residual r64 = f - A u and the refinement step
         st = per_group([&](const Group3& g) {
-            if (cycle > 0) {
+            int shift = SH_RHS;   // u = 0: r64 = f, the partials of |f|^2 are still in place
+            if (cycle > 0 && fp64) {
                 if (stiffness3<MODE_RESID, double2>(ws, g, cs64, o.scheme, uv, r64, f, true, sc, s) !=
                     cudaSuccess)
                     return RVE_ECUDA;
-            } else {   // u = 0: r64 = f, the partials of |f|^2 are still in place
+                shift = SH_STIFF;
+            } else if (cycle > 0) {   // mixed: the double-word residual
+                if (resid3_dw(ws, g, cs64, o.scheme, uv, r64, f, sc, s) != cudaSuccess)
+                    return RVE_ECUDA;
+                shift = SH_RHS;
             }
-            scalar(g, M_REFINE, cycle > 0 ? SH_STIFF : SH_RHS);
+            scalar(g, M_REFINE, shift);
             return RVE_OK;
         });
         if (st != RVE_OK) return st;
