@@ -178,8 +178,8 @@ def per_entry_error(A, ref):
 # (k_fused_R): ncu instruction count of a refining launch divided by its
 # nodes, for the first refinement of a solve (r = f) and the later ones
 # (profiles/k_fused_R_refine_plain_L32_batch32.md).
-REFINE_INST_PER_NODE = 614.7
-REFINE_FIRST_INST_PER_NODE = 479.6
+REFINE_INST_PER_NODE = 617.7
+REFINE_FIRST_INST_PER_NODE = 212.5
 
 
 def refine_alu(prof, refines, reals, nodes, clk):

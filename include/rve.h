@@ -486,7 +486,11 @@ rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* ma
 rve_status rve3_statistics(const double* A, int64_t N, double L, double* mean, double* var,
                            double* Q);
 
-/* Diagnostics for benchmarks (process-wide, not thread-safe).
+/* Diagnostics for benchmarks.  The profiler state is process-wide and NOT
+ * thread-safe: enable it only while a single host thread solves on a single
+ * stream (two streams or threads solving while it is on share, and race
+ * on, its event pool and totals).  The launch counter is an atomic and safe
+ * to read from any thread.
  * rve_profile_enable(1): the fused solver brackets every launch of its five
  * pipeline kernels with CUDA events on the caller's stream and accumulates
  * their durations.  rve_profile_read(ms[5], launches[5]) returns the totals

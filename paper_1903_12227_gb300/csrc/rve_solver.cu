@@ -505,44 +505,58 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
         cp_async_commit();   // an empty group past the last: uniform counting
     };
     prefetch(0);
-    // q = A p on the own rows: each thread walks down a column keeping the
-    // 3 x 3 neighbourhood (and the two cell columns) in registers, so a node
-    // costs three shared loads and two cell lookups.  Rolled in behind the
-    // transform: the rows whose three neighbours rows are done run after
-    // each group.
+    // q = A p on the own rows, once every row of the tile is transformed:
+    // each thread walks down a column keeping the 3 x 3 neighbourhood (and
+    // the two cell columns) in registers, so a node costs three shared loads
+    // and two cell lookups.
     DotAcc<T> ax, ay;   // p.q
-    int done = 0;       // own rows (tile slots 1 .. TR) whose q is done
-    auto stencil_rows = [&](int q1) {   // own slots done+1 .. q1
-        const int first = done + 1;
-        if (q1 < first) return;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-            const int pm = pidx(jm), p0 = pidx(j), pp = pidx(jp);
-            const V* up = Pt + (first - 1) * SEQ;
-            V u0 = up[pm], u1 = up[p0], u2 = up[pp];                        // slot first-1
-            V m0 = up[SEQ + pm], m1 = up[SEQ + p0], m2 = up[SEQ + pp];      // slot first
-            T cmm = tc.cell(c.cs, d, first - 1, r0 + first - 2, jm);
-            T cm0 = tc.cell(c.cs, d, first - 1, r0 + first - 2, j);
-            for (int q = first; q <= q1; ++q) {
-                const V* dn = Pt + (q + 1) * SEQ;
-                const V d0 = dn[pm], d1 = dn[p0], d2 = dn[pp];
-                const T c0m = tc.cell(c.cs, d, q, r0 + q - 1, jm);
-                const T c00 = tc.cell(c.cs, d, q, r0 + q - 1, j);
-                CellsT<T> a;
-                a.mm = cmm;
-                a.m0 = cm0;
-                a.z0m = c0m;
-                a.z00 = c00;
-                const V qv = stencil_apply<SCHEME, V>(a, u0, u1, u2, m0, m1, m2, d0, d1, d2);
-                Q[node_at(d, z, r0 + q - 1, j)] = qv;
-                ax.add(m1.x, qv.x);
-                ay.add(m1.y, qv.y);
-                u0 = m0; u1 = m1; u2 = m2;
-                m0 = d0; m1 = d1; m2 = d2;
-                cmm = c0m; cm0 = c00;
+    // a thread walks down two columns j and j + 256 at once (n >= 512, the
+    // kernel runs 256 threads): two independent chains of shared loads and
+    // multiply-adds per row
+    struct Win {
+        V u0, u1, u2, m0, m1, m2;
+        T cmm, cm0;
+        int j, pm, p0, pp;
+    };
+    auto win_start = [&](Win& w, int j) {
+        w.j = j;
+        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
+        w.pm = pidx(jm); w.p0 = pidx(j); w.pp = pidx(jp);
+        w.u0 = Pt[w.pm]; w.u1 = Pt[w.p0]; w.u2 = Pt[w.pp];                    // slot 0
+        w.m0 = Pt[SEQ + w.pm]; w.m1 = Pt[SEQ + w.p0]; w.m2 = Pt[SEQ + w.pp];  // slot 1
+        w.cmm = tc.cell(c.cs, d, 0, r0 - 1, jm);
+        w.cm0 = tc.cell(c.cs, d, 0, r0 - 1, j);
+    };
+    auto win_step = [&](Win& w, int q) {   // own slot q: node row r0 + q - 1
+        const V* dn = Pt + (q + 1) * SEQ;
+        const V d0 = dn[w.pm], d1 = dn[w.p0], d2 = dn[w.pp];
+        const int jm = (w.j - 1) & (n - 1);
+        const T c0m = tc.cell(c.cs, d, q, r0 + q - 1, jm);
+        const T c00 = tc.cell(c.cs, d, q, r0 + q - 1, w.j);
+        CellsT<T> a;
+        a.mm = w.cmm;
+        a.m0 = w.cm0;
+        a.z0m = c0m;
+        a.z00 = c00;
+        const V qv = stencil_apply<SCHEME, V>(a, w.u0, w.u1, w.u2, w.m0, w.m1, w.m2, d0, d1, d2);
+        Q[node_at(d, z, r0 + q - 1, w.j)] = qv;
+        ax.add(w.m1.x, qv.x);
+        ay.add(w.m1.y, qv.y);
+        w.u0 = w.m0; w.u1 = w.m1; w.u2 = w.m2;
+        w.m0 = d0; w.m1 = d1; w.m2 = d2;
+        w.cmm = c0m; w.cm0 = c00;
+    };
+    auto stencil_rows = [&]() {
+        constexpr bool TWO = LOG2N >= 9;   // n >= 512 = 2 x 256 threads
+        for (int j = threadIdx.x; j < n; j += TWO ? 512 : 256) {
+            Win wa, wb;
+            win_start(wa, j);
+            if (TWO) win_start(wb, j + 256);
+            for (int q = 1; q <= TR; ++q) {
+                win_step(wa, q);
+                if (TWO) win_step(wb, q);
             }
         }
-        done = q1;
     };
     // every row's transform is done by its own team of n/8 threads: the
     // barriers of the group loop are the team's, so the teams of a block
@@ -602,7 +616,7 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
     }
     cp_async_wait<0>();
     __syncthreads();   // p_new of the whole tile visible
-    stencil_rows(TR);
+    stencil_rows();
     double sx = 0.0, sy = 0.0;
     block_sum2(ax, ay, red, sx, sy);
     if (threadIdx.x == 0) {

@@ -329,9 +329,72 @@ def cubes_study(Ls=(2, 4, 8, 16), m0=16, N=None, contrast=10.0, seed=0, tol=1e-1
     return rows
 
 
+# FP64 instructions per node pair of the two study kernels, counted from
+# their formulas: the mass stencil 9 FMA per component (consistent) plus the
+# h^2 scaling; the Chebyshev step the 9-point stiffness (cell sums and 9
+# multiply-adds per component), the three-term update and four partial-sum
+# products.
+MASS_FP64_PER_NODE = 20
+CHEB_FP64_PER_NODE = 40
+
+
+def kernel_rates(L=32, m0=16, batch=64, K=64, reps=10) -> list:
+    """Measured rates of the study kernels of the FEM convergence test
+    (rve_apply_mass) and the density of states (rve_cheb_moments, one
+    stiffness application per two moments) on `batch` realizations of
+    (L m0)^2 nodes: algorithmic bytes against the measured HBM peak and
+    FP64 instructions against GB300's FP64 issue rate (152 SMs x 2 per clock
+    x the clock)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ds = workloads.batch(L, m0, 10.0, 0, batch)
+    b = rve.Batch(ds)
+    nodes = b.nodes
+    peak = _hbm_peak()
+    mhz = 2070.0
+    fp64_peak = 152 * 2 * mhz * 1e6
+    x = torch.randn(nodes, 2, dtype=torch.float64, device=dev)
+    mask = rve.gen_field(b, device=dev)
+    rows = []
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t = timed(lambda: rve.apply_mass(b, x))
+    rows.append({"kernel": "k_mass (rve_apply_mass, consistent)", "nodes": nodes,
+                 "us_per_launch": t * 1e6, "bytes_per_node": 32,
+                 "GBs": 32 * nodes / t / 1e9, "frac_hbm": 32 * nodes / t / 1e9 / peak,
+                 "fp64_inst_per_node": MASS_FP64_PER_NODE,
+                 "frac_fp64_issue": MASS_FP64_PER_NODE * nodes / t / fp64_peak})
+    lo, hi = 0.0, 16.0 / 3.0 * 10.0
+    steps = (K + 1) // 2
+    t = timed(lambda: rve.cheb_moments(b, x, K, lo, hi, mask=mask)) / steps
+    rows.append({"kernel": "k_cheb (rve_cheb_moments, per stiffness application)", "nodes": nodes,
+                 "us_per_launch": t * 1e6, "bytes_per_node": 48.125,
+                 "GBs": 48.125 * nodes / t / 1e9, "frac_hbm": 48.125 * nodes / t / 1e9 / peak,
+                 "fp64_inst_per_node": CHEB_FP64_PER_NODE,
+                 "frac_fp64_issue": CHEB_FP64_PER_NODE * nodes / t / fp64_peak})
+    return rows
+
+
+def _hbm_peak() -> float:
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        return float(json.load(open(os.path.join(here, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["variance", "paper", "fem", "dos", "cubes"])
+    ap.add_argument("study", choices=["variance", "paper", "fem", "dos", "cubes", "kernels"])
     ap.add_argument("--Ls", type=int, nargs="+")
     ap.add_argument("--N", type=int)
     ap.add_argument("--seed", type=int, default=0)
@@ -340,7 +403,9 @@ def main(argv=None):
     ap.add_argument("--prec", choices=["both", "fp64", "mixed"], default="both",
                     help="cubes: which solver precision(s) to measure")
     a = ap.parse_args(argv)
-    if a.study == "cubes":
+    if a.study == "kernels":
+        rows = kernel_rates()
+    elif a.study == "cubes":
         precs = {"both": (rve.FP64, rve.MIXED), "fp64": (rve.FP64,), "mixed": (rve.MIXED,)}[a.prec]
         rows = cubes_study(Ls=tuple(a.Ls or (2, 4, 8, 16)), N=a.N, seed=a.seed, precisions=precs)
     elif a.study == "dos":
