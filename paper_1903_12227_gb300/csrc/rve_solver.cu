@@ -14,18 +14,24 @@
 //
 // Fused pipeline (one CG step = three passes over the vectors + a control
 // kernel; both correctors of a realization travel together as a pair):
-//   S  z = row-Hartley(t) on the tile + halo rows, p_new = z + beta p_old,
-//      x += alpha_prev p_old (the solution update lags one step),
-//      q = A p_new, partial p.q                                  (ITER)
-//      or r64 = f - A(u + s (x + alpha p)) in FP64, partial |r64|^2 (REFINE)
-//   U  alpha = rho / p.q, r -= alpha q, partial |r|^2, t = row-Hartley(r)
-//      (REFINE: u += s (x + alpha p), x = 0, r = r64 / |r64|)
-//   C  column Hartley, scale 1/(n^2 sigma), partial rho, column Hartley
+//   R  (REFINE steps only) r64 = f - A(u + s (x + alpha p)), the true
+//      residual in double words (FP64 for the FP64 path), partial |r64|^2
+//   S  z = inverse row-Hartley(zhat) on the tile + halo rows, p_new = z +
+//      beta p_old, x += alpha_prev p_old (the solution update lags one
+//      step), q = A p_new, partial p.q; the last block of a realization
+//      forms alpha = rho / p.q
+//   U  rt -= alpha H q (the residual kept as its row transform rt = H r),
+//      partial |r|^2 = |rt|^2 / n (REFINE: u += s (x + alpha p), x = 0,
+//      rt = H (r64 / |r64|))
+//   C  periodic tridiagonal solve along every column of rt (the row
+//      transform diagonalises the row factor of A_Delta), scaled, into
+//      zhat; partial rho = r.z
 //   K  per realization: reduce the partials in a fixed order, set alpha,
 //      beta, convergence and the next phase.
-// In MIXED precision x, r, q, t, p are float2 and u is double2: every
-// REFINE step recomputes the true residual in FP64 and restarts the FP32
-// inner iteration on the scaled residual equation (iterative refinement).
+// In MIXED precision x, rt, q, zhat, p are float2 and u is the double-word
+// iterate: every REFINE step recomputes the true residual in double words
+// and restarts the FP32 inner iteration on the scaled residual equation
+// (iterative refinement).
 #include <cuda_runtime.h>
 
 #include <algorithm>
