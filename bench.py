@@ -5,9 +5,10 @@ Workload (the method at scale): L = 32 unit cells per axis, h = 1/16
 inclusions of side 1 (density 0.7), PCG to a true relative residual of 1e-10,
 seeded synthetic realizations (seed 0, indices 0..999 cycled).  One step =
 field generation + both corrector solves + A_hom for a batch of B
-realizations through the C ABI, mixed precision (FP32 stencil / transforms /
+realizations (default 1000: the whole seeded set of the workload in one
+step) through the C ABI, mixed precision (FP32 stencil / transforms /
 vectors, FP64 dots and true-residual refinement, double-word A_hom).  The
-per-step working set (~2 GB) is far larger than L2.
+per-step working set (~17 GB at B = 1000) is far larger than L2.
 
 Timing: K steps between CUDA events on the launching stream (the headline
 `value`, no per-launch instrumentation); the same K steps again with every
@@ -15,8 +16,8 @@ pipeline launch bracketed by CUDA events give the per-kernel times of the
 roofline; `e2e` runs K steps through rve_homogenize_host (host descriptors
 in, host A_hom out).  Also reported: the FP64 fused path and the plain FP64
 path on a small sample, the oracle on the host cores (all cores, and one
-thread), and the per-entry A_hom error of the first timed batch against the
-FP64 oracle.
+thread), and the per-entry A_hom error of the first 125 realizations of the
+first timed batch against the FP64 oracle.
 
     python bench.py [--gpus N --steps K --warmup W --batch B] [--impl reference]
     python bench.py --workload cubes_L4    # the 3D extension (one JSON line too)
@@ -32,8 +33,9 @@ realizations (67 M nodes, ~17 GB of state).
 
 The uneven workload (`--workload uneven_4096`): 4096 realizations with L
 drawn from {8, 16, 32, 64} at h = 1/8 and contrast from {10, 100}; one step
-= one execution of a captured plan (field, every corrector in one persistent
-launch, A_hom), tile shapes from the autotuner.
+= one execution of a captured plan (field, the correctors' fused kernels in
+a conditional while node, A_hom), tile shapes from the autotuner; the same
+plan as one persistent launch is timed beside it.
 """
 from __future__ import annotations
 
@@ -74,7 +76,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=125)
+    ap.add_argument("--batch", type=int, default=None,
+                    help="realizations per step and GPU (default: the workload's own)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_L32",
                     choices=["plain_L32", "cubes_L4", "uneven_4096", "large_L256", "adjoint_L64"])
@@ -429,7 +432,8 @@ def run_ours(args):
            "dtype": "f32 vectors + f64 dots/refinement/A_hom (mixed)", "data": "synthetic",
            "config": {"workload": f"{WORKLOAD['name']}: {CONFIG_DESC}", "batch_per_gpu": B,
                       "realizations_per_step": B * world, "l2": "inputs larger than L2 "
-                      "(~2 GB working set per step, 129 MB L2)", "precision": "mixed"},
+                      f"(~{B * 262144 * 64 / 1e9:.0f} GB working set per step, 129 MB L2)",
+                      "precision": "mixed"},
            "roofline": roofline, "gpu_launches": launches,
            "clocks": clk,
            "solver": {"statuses": statuses,
@@ -452,7 +456,7 @@ def run_ours(args):
         # the oracle on the realizations of the first timed batch: the first
         # 32 timed on all host cores (the baseline), the rest for the
         # per-entry error of the mixed path against the FP64 oracle
-        first = [(args.warmup * B + k) % WORKLOAD["realizations"] for k in range(B)]
+        first = [(args.warmup * B + k) % WORKLOAD["realizations"] for k in range(min(B, 125))]
         k0 = min(32, B)
         rate, cores, A_cpu, dt = cpu_oracle_rate(first[:k0])
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -462,13 +466,14 @@ def run_ours(args):
         out["cpu_baseline_1thread"] = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
                                        "sample": f"1 realization (index {first[0]}), one thread "
                                                  f"({dt1:.1f} s)"}
-        if B > k0:
+        if len(first) > k0:
             _, _, A_rest, _ = cpu_oracle_rate(first[k0:])
             A_cpu = np.concatenate([A_cpu, A_rest])
-        A_gpu = As[0].cpu().numpy().reshape(-1, 2, 2)
+        A_gpu = As[0].cpu().numpy().reshape(-1, 2, 2)[:len(first)]
         out["a_hom_err_vs_oracle"] = per_entry_error(A_gpu, A_cpu)
-        out["a_hom_err_vs_oracle"]["sample"] = (f"{B} realizations (the first timed batch), "
-                                                f"mixed precision vs the FP64 oracle")
+        out["a_hom_err_vs_oracle"]["sample"] = (f"{len(first)} realizations (the first of the "
+                                                f"first timed batch), mixed precision vs the "
+                                                f"FP64 oracle")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -525,7 +530,7 @@ def run_cubes(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    B = args.batch if args.batch != 125 else CUBES["batch"]
+    B = args.batch or CUBES["batch"]
     opts = rve3.make_opts3(precision=rve.MIXED, tol=CUBES["tol"])
     probe = rve3.Batch3(cubes_descs(0, B))
     L3 = rve3.lib()
@@ -816,7 +821,7 @@ def run_large(args):
 
     from paper_1903_12227_gb300 import rve, workloads
     dev, stream = _single_gpu("large_L256")
-    B = args.batch if args.batch != 125 else 16
+    B = args.batch or 16
     opts = rve.make_opts(precision=rve.MIXED, tol=1e-10)
     probe = workloads.config_batch("large_L256", seed=0, count=B)
     ws = rve.workspace(rve.workspace_size(probe, opts), dev)
@@ -874,7 +879,7 @@ def run_adjoint(args):
 
     from paper_1903_12227_gb300 import rve, workloads
     dev, stream = _single_gpu("adjoint_L64")
-    B = args.batch if args.batch != 125 else 16
+    B = args.batch or 16
     opts = rve.make_opts(precision=rve.FP64, tol=1e-13)
     G = torch.tensor(np.random.default_rng(4).standard_normal((B, 2, 2)), device=dev)
     rve.launch_count()
@@ -961,6 +966,8 @@ def main():
     if args.workload == "adjoint_L64":
         run_adjoint(args)
         return
+    if args.batch is None:
+        args.batch = WORKLOAD["realizations"]   # one step = the whole seeded set
     run_ours(args)
 
 

@@ -207,11 +207,12 @@ template <> __device__ __forceinline__ Two<float> ld_two_s<float>(const float* p
     return {v.x, v.y};
 }
 
+// FP32: three blocks per SM (80 registers, no spills) with the register
+// window below.
 template <int SCHEME, int MODE, typename V>
-__global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename ScalarOf<V>::T> cs,
-                                                   const V* __restrict__ x, V* __restrict__ y,
-                                                   const V* __restrict__ f, double* part,
-                                                   const MixScal* sc) {
+__global__ void __launch_bounds__(T3, sizeof(V) == 8 ? (SCHEME == RVE_Q1_LUMPED ? 4 : 3) : 2)
+    k3_stiffness(Grp g, Cells3T<typename ScalarOf<V>::T> cs, const V* __restrict__ x,
+                 V* __restrict__ y, const V* __restrict__ f, double* part, const MixScal* sc) {
     typedef typename ScalarOf<V>::T T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[16];
@@ -363,32 +364,20 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
         }
     };
     T dx = 0, dy = 0;
-#pragma unroll 1
-    for (int t = 0; t < SZ; ++t) {
-        T Cm0[4], Cm1[4], C00[4], C01[4];
-        cells(t, Cm0, Cm1);
-        cells(t + 1, C00, C01);
-        V acc0 = mk<V>((T)0, (T)0), acc1 = acc0;
-#pragma unroll
-        for (int o1 = -1; o1 <= 1; ++o1) {
-            V X0[3][3], X1[3][3];
-#pragma unroll
-            for (int a2 = 0; a2 < 3; ++a2) {
-                const V* r = xt + ((t + 1 + o1) * RW + jl + a2) * n;
-                const Two<V> M = ld_two(r + k0);
-                const V Lv = r[kl], Rv = r[kr];
-                X0[a2][0] = Lv;  X0[a2][1] = M.a; X0[a2][2] = M.b;
-                X1[a2][0] = M.a; X1[a2][1] = M.b; X1[a2][2] = Rv;
-            }
-            V v0, v1;
-            if (o1 < 0) { v0 = side(X0, Cm0); v1 = side(X1, Cm1); }
-            else if (o1 == 0) { v0 = inplane(X0, Cm0, C00); v1 = inplane(X1, Cm1, C01); }
-            else { v0 = side(X0, C00); v1 = side(X1, C01); }
-            acc0.x += v0.x; acc0.y += v0.y;
-            acc1.x += v1.x; acc1.y += v1.y;
-        }
+    // adds the couplings through x-plane t + o1 (X0, X1: [row][k] windows of
+    // the two nodes) to acc0, acc1; cell planes t - 1 (Cm*) and t (C0*)
+    auto couple = [&](int o1, const V (&X0)[3][3], const V (&X1)[3][3], const T (&Cm0)[4],
+                      const T (&Cm1)[4], const T (&C00)[4], const T (&C01)[4], V& acc0, V& acc1) {
+        V v0, v1;
+        if (o1 < 0) { v0 = side(X0, Cm0); v1 = side(X1, Cm1); }
+        else if (o1 == 0) { v0 = inplane(X0, Cm0, C00); v1 = inplane(X1, Cm1, C01); }
+        else { v0 = side(X0, C00); v1 = side(X1, C01); }
+        acc0.x += v0.x; acc0.y += v0.y;
+        acc1.x += v1.x; acc1.y += v1.y;
+    };
+    // output plane t of the two nodes (xa, xb: their own x values)
+    auto emit = [&](int t, V acc0, V acc1, const V& xa, const V& xb) {
         const int64_t node = d.off + ((int64_t)(i0 + t) << (2 * lg)) + ((j0 + jl) << lg) + k0;
-        const Two<V> xc = ld_two(xt + ((t + 1) * RW + jl + 1) * n + k0);
         if (MODE == MODE_RESID) {
             const Two<V> ff = ld_two(f + node);
             acc0.x = ff.a.x - acc0.x; acc0.y = ff.a.y - acc0.y;
@@ -396,10 +385,88 @@ __global__ void __launch_bounds__(T3) k3_stiffness(Grp g, Cells3T<typename Scala
             dx = fma(acc0.x, acc0.x, fma(acc1.x, acc1.x, dx));
             dy = fma(acc0.y, acc0.y, fma(acc1.y, acc1.y, dy));
         } else {
-            dx = fma(xc.a.x, acc0.x, fma(xc.b.x, acc1.x, dx));
-            dy = fma(xc.a.y, acc0.y, fma(xc.b.y, acc1.y, dy));
+            dx = fma(xa.x, acc0.x, fma(xb.x, acc1.x, dx));
+            dy = fma(xa.y, acc0.y, fma(xb.y, acc1.y, dy));
         }
         st_two(y + node, Two<V>{acc0, acc1});
+    };
+    if constexpr (sizeof(T) == 4) {
+        // FP32: a window of three x-planes (rows jl .. jl + 2, k0 - 1 ..
+        // k0 + 2) and two cell planes rolls down the block's planes in
+        // registers, so each tile plane is read from shared memory once
+        // instead of three times and each cell plane once instead of twice.
+        // The arithmetic and its order are those of the FP64 branch.
+        V W[3][3][4];
+        auto xplane = [&](int pl, V (&P)[3][4]) {
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) {
+                const V* r = xt + (pl * RW + jl + a2) * n;
+                const Two<V> M = ld_two(r + k0);
+                P[a2][0] = r[kl];
+                P[a2][1] = M.a;
+                P[a2][2] = M.b;
+                P[a2][3] = r[kr];
+            }
+        };
+        auto step = [&](int t, const T (&Cm0)[4], const T (&Cm1)[4], const T (&C00)[4],
+                        const T (&C01)[4]) {
+            V acc0 = mk<V>((T)0, (T)0), acc1 = acc0;
+#pragma unroll
+            for (int o1 = -1; o1 <= 1; ++o1) {
+                const V (&P)[3][4] = W[(t + 1 + o1) % 3];
+                V X0[3][3], X1[3][3];
+#pragma unroll
+                for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        X0[a2][q] = P[a2][q];
+                        X1[a2][q] = P[a2][q + 1];
+                    }
+                couple(o1, X0, X1, Cm0, Cm1, C00, C01, acc0, acc1);
+            }
+            const V (&P0)[3][4] = W[(t + 1) % 3];
+            emit(t, acc0, acc1, P0[1][1], P0[1][2]);
+        };
+        T Ca0[4], Ca1[4], Cb0[4], Cb1[4];
+        xplane(0, W[0]);
+        xplane(1, W[1]);
+        cells(0, Ca0, Ca1);
+#pragma unroll
+        for (int t = 0; t < SZ; ++t) {
+            xplane(t + 2, W[(t + 2) % 3]);
+            if (t % 2 == 0) {
+                cells(t + 1, Cb0, Cb1);
+                step(t, Ca0, Ca1, Cb0, Cb1);
+            } else {
+                cells(t + 1, Ca0, Ca1);
+                step(t, Cb0, Cb1, Ca0, Ca1);
+            }
+        }
+    } else {
+        // FP64: a register window would not fit; each plane step reads its
+        // three x-planes and two cell planes from shared memory
+#pragma unroll 1
+        for (int t = 0; t < SZ; ++t) {
+            T Cm0[4], Cm1[4], C00[4], C01[4];
+            cells(t, Cm0, Cm1);
+            cells(t + 1, C00, C01);
+            V acc0 = mk<V>((T)0, (T)0), acc1 = acc0;
+#pragma unroll
+            for (int o1 = -1; o1 <= 1; ++o1) {
+                V X0[3][3], X1[3][3];
+#pragma unroll
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    const V* r = xt + ((t + 1 + o1) * RW + jl + a2) * n;
+                    const Two<V> M = ld_two(r + k0);
+                    const V Lv = r[kl], Rv = r[kr];
+                    X0[a2][0] = Lv;  X0[a2][1] = M.a; X0[a2][2] = M.b;
+                    X1[a2][0] = M.a; X1[a2][1] = M.b; X1[a2][2] = Rv;
+                }
+                couple(o1, X0, X1, Cm0, Cm1, C00, C01, acc0, acc1);
+            }
+            const Two<V> xc = ld_two(xt + ((t + 1) * RW + jl + 1) * n + k0);
+            emit(t, acc0, acc1, xc.a, xc.b);
+        }
     }
     if (part) {   // block-uniform
         double tx = 0.0, ty = 0.0;
