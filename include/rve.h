@@ -35,7 +35,9 @@
  * Memory ownership.  The caller allocates every buffer (device memory unless
  * stated otherwise) and keeps it alive until the work on `stream` is done.
  * The library allocates no device memory: solvers take a caller-provided
- * workspace whose size rve_workspace_size() returns.  Every call is
+ * workspace whose size rve_workspace_size() returns, starting on a 256-byte
+ * boundary as cudaMalloc's blocks do (another start gives RVE_EINVAL).
+ * Every call is
  * asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
  * default stream) unless stated otherwise.
  *

@@ -1608,7 +1608,7 @@ rve_status rve3_rhs(const rve_realization* r, int32_t batch, const uint8_t* mask
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !f || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
+    if ((!mask && !coef) || !f || !ws || ws_misaligned(ws) || !valid_scheme(scheme)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1630,7 +1630,8 @@ rve_status rve3_apply_stiffness(const rve_realization* r, int32_t batch, const u
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !x || !y || x == y || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
+    if ((!mask && !coef) || !x || !y || x == y || !ws || ws_misaligned(ws) || !valid_scheme(scheme))
+        return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1656,7 +1657,7 @@ rve_status rve3_apply_precond(const rve_realization* r, int32_t batch, double de
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if (!x || !y || !ws || !std::isfinite(delta) || delta < 0.0) return RVE_EINVAL;
+    if (!x || !y || !ws || ws_misaligned(ws) || !std::isfinite(delta) || delta < 0.0) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1690,7 +1691,7 @@ rve_status rve3_solve_correctors(const rve_realization* r, int32_t batch, const 
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !u || !info || !ws) return RVE_EINVAL;
+    if ((!mask && !coef) || !u || !info || !ws || ws_misaligned(ws)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
@@ -1726,7 +1727,7 @@ rve_status rve3_a_hom(const rve_realization* r, int32_t batch, const uint8_t* ma
     Plan3 p;
     rve_status st = make_plan3(r, batch, p);
     if (st != RVE_OK) return st;
-    if ((!mask && !coef) || !u || !A || !ws || !valid_scheme(scheme)) return RVE_EINVAL;
+    if ((!mask && !coef) || !u || !A || !ws || ws_misaligned(ws) || !valid_scheme(scheme)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);

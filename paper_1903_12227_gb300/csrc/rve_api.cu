@@ -339,7 +339,7 @@ rve_status rve_apply_precond(const rve_realization* r, int32_t batch, double del
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, true);
     if (st != RVE_OK) return st;
-    if (!x || !y || !ws) return RVE_EINVAL;
+    if (!x || !y || !ws || ws_misaligned(ws)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     return launch_precond(p, ws, delta, precision, x, y, as_stream(stream)) == cudaSuccess
                ? RVE_OK
@@ -354,7 +354,7 @@ static rve_status solve_any(const rve_realization* r, int32_t batch, const uint3
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, true);
     if (st != RVE_OK) return st;
-    if (!u || !info || !ws || (!mask && !coef)) return RVE_EINVAL;
+    if (!u || !info || !ws || ws_misaligned(ws) || (!mask && !coef)) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     if (o.path == RVE_PATH_PLAIN)
         return run_solve_plain(p, ws, mask, coef, o, u, info, as_stream(stream), f);
@@ -395,7 +395,7 @@ rve_status rve_cheb_moments(const rve_realization* r, int32_t batch, const uint3
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, false);
     if (st != RVE_OK) return st;
-    if (!v || !mu || !ws || (!mask && !coef) || K < 2 || K > (1 << 20) || !std::isfinite(lo) ||
+    if (!v || !mu || !ws || ws_misaligned(ws) || (!mask && !coef) || K < 2 || K > (1 << 20) || !std::isfinite(lo) ||
         !std::isfinite(hi) || !(hi > lo))
         return RVE_EINVAL;
     if (ws_bytes < cheb_workspace_size(p)) return RVE_ENOMEM;
@@ -428,7 +428,7 @@ rve_status rve_a_hom(const rve_realization* r, int32_t batch, const uint32_t* ma
     Plan p;
     rve_status st = make_plan(r, batch, &o, p, false);
     if (st != RVE_OK) return st;
-    if (!u || !A || !ws || (!mask && !coef)) return RVE_EINVAL;
+    if (!u || !A || !ws || ws_misaligned(ws) || (!mask && !coef)) return RVE_EINVAL;
     if (A_lo && precision != RVE_FP64) return RVE_EINVAL;
     if (ws_bytes < p.total) return RVE_ENOMEM;
     if (upload_plan(p, ws, as_stream(stream)) != RVE_OK) return RVE_ECUDA;
@@ -487,7 +487,7 @@ rve_status rve_homogenize_host(const rve_realization* r_host, int32_t batch,
     Plan p;
     rve_status st = make_plan(r_host, batch, &o, p, true);
     if (st != RVE_OK) return st;
-    if (!A_host || !ws) return RVE_EINVAL;
+    if (!A_host || !ws || ws_misaligned(ws)) return RVE_EINVAL;
     size_t om, ou, oa, oi, ow;
     const size_t need = homog_layout(p, &om, &ou, &oa, &oi, &ow);
     if (ws_bytes < need) return RVE_ENOMEM;

@@ -18,6 +18,10 @@ struct RDesc;
 // Kernel launches issued by the library (diagnostics).
 extern std::atomic<long long> g_launches;
 inline void note_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// Workspaces start on a 256-byte boundary (cudaMalloc's alignment): the
+// library carves them into 256-byte aligned vectors and moves whole rows of
+// them with 16-byte aligned bulk operations.
+inline bool ws_misaligned(const void* ws) { return ((uintptr_t)ws & 255) != 0; }
 
 // Solver phases of one realization (fused pipeline).
 enum : int32_t { PH_REFINE = 0, PH_ITER = 1, PH_DONE = 2 };

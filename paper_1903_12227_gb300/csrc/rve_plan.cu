@@ -94,7 +94,7 @@ size_t rve_plan_workspace_size(rve_plan plan) { return plan ? plan->l.total : 0;
 rve_status rve_plan_execute(rve_plan plan, double* A, rve_solve_info* info, void* ws,
                             size_t ws_bytes, void* stream) {
     // a graph cannot be captured on the legacy default stream
-    if (!plan || !A || !info || !ws || !stream) return RVE_EINVAL;
+    if (!plan || !A || !info || !ws || ws_misaligned(ws) || !stream) return RVE_EINVAL;
     if (ws_bytes < plan->l.total) return RVE_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!plan->exec || plan->ws != ws || plan->A != A || plan->info != info) {
@@ -163,7 +163,7 @@ rve_status rve_autotune(const rve_realization* r, int32_t batch, const rve_solve
     Plan all;
     rve_status st = make_plan(r, batch, opts, all, false);
     if (st != RVE_OK) return st;
-    if (!ws) return RVE_EINVAL;
+    if (!ws || ws_misaligned(ws)) return RVE_EINVAL;
     const rve_solve_opts base = resolved_opts(opts);
     if (base.path == RVE_PATH_PLAIN) return RVE_OK;   // nothing to tune
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -468,6 +468,15 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
     typedef typename ScalarOf<V>::T T;
 
     // ---- ITER ----
+    // p_old (own and halo rows) and x (own rows) are read only after the
+    // rows' transforms: one thread per row asks for them in L2 now, so those
+    // loads wait on L2 instead of DRAM
+    {
+        const unsigned rb = (unsigned)(n * sizeof(V));
+        const int k = threadIdx.x;
+        if (k < TR + 2) prefetch_l2(Pold + node_at(d, z, (r0 - 1 + k) & (n - 1), 0), rb);
+        else if (k >= 64 && k < 64 + TR) prefetch_l2(X + node_at(d, z, r0 + k - 64, 0), rb);
+    }
     // scalars of this step, converted once (thread 0) to the vector type
     if (threadIdx.x == 0) {
         bsc[0] = (T)s.beta[0];
@@ -705,6 +714,10 @@ __device__ __forceinline__ void fused_U_body(const Ctx& c, int blk, int b, const
             usc[0] = (T)c.uscal[2 * b];
             usc[1] = (T)c.uscal[2 * b + 1];
         }
+        // rt of the block's rows is read group by group: one thread per row
+        // asks for it in L2 now
+        if (threadIdx.x < d.tU)
+            prefetch_l2(Rt + node_at(d, z, row0 + threadIdx.x, 0), (unsigned)(z.n * sizeof(V)));
         auto prefetch = [&](int g) {   // q of group g into row buffer set g & 1
             const int q = g * L.G + L.qq;
             if (g < ng && q < d.tU) {

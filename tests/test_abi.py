@@ -122,6 +122,28 @@ def test_solve3_option_validation_without_gpu(librve):
     assert L3.rve3_a_hom(b.ptr, 1, None, None, 0, fake, fake, None, fake, need, None) == rve.RVE_EINVAL
 
 
+def test_misaligned_workspace_rejected_without_gpu(librve):
+    # a workspace must start on a 256-byte boundary; the check precedes the
+    # first CUDA call, so fake device pointers are never dereferenced
+    from paper_1903_12227_gb300 import rve, rve3, workloads
+    b = rve.Batch([workloads.realization(4, 8, 10.0, 0, 0)])
+    opts = rve.make_opts(precision=rve.MIXED)
+    need = librve.rve_workspace_size(b.ptr, 1, ctypes.byref(opts))
+    fake, mis = ctypes.c_void_p(256), ctypes.c_void_p(256 + 16)
+    assert librve.rve_solve_correctors(b.ptr, 1, fake, None, ctypes.byref(opts), fake, fake, mis,
+                                       need, None) == rve.RVE_EINVAL
+    assert librve.rve_solve_correctors(b.ptr, 1, fake, None, ctypes.byref(opts), fake, fake, fake,
+                                       need - 1, None) == rve.RVE_ENOMEM
+    assert librve.rve_a_hom(b.ptr, 1, fake, None, 0, rve.MIXED, fake, fake, None, None, mis, need,
+                            None) == rve.RVE_EINVAL
+    L3 = rve3.lib()
+    b3 = rve3.Batch3([workloads.realization3(4, 8, 10.0, 0, 0)])
+    need3 = L3.rve3_workspace_size(b3.ptr, 1)
+    o3 = rve3.make_opts3(precision=rve.MIXED)
+    assert L3.rve3_solve_correctors(b3.ptr, 1, fake, None, ctypes.byref(o3), fake, fake, mis,
+                                    need3, None) == rve.RVE_EINVAL
+
+
 def test_statistics3_host_matches_oracle(librve):
     import numpy as np
 
