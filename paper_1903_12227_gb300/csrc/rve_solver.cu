@@ -469,13 +469,15 @@ __device__ __forceinline__ void fused_S_body(const Ctx& c, int tile, int b, cons
 
     // ---- ITER ----
     // p_old (own and halo rows) and x (own rows) are read only after the
-    // rows' transforms: one thread per row asks for them in L2 now, so those
-    // loads wait on L2 instead of DRAM
+    // rows' transforms, t group by group: one thread per row asks for them
+    // in L2 now, so those loads and copies wait on L2 instead of DRAM
     {
         const unsigned rb = (unsigned)(n * sizeof(V));
         const int k = threadIdx.x;
         if (k < TR + 2) prefetch_l2(Pold + node_at(d, z, (r0 - 1 + k) & (n - 1), 0), rb);
         else if (k >= 64 && k < 64 + TR) prefetch_l2(X + node_at(d, z, r0 + k - 64, 0), rb);
+        else if (k >= 128 && k < 128 + TR + 2)
+            prefetch_l2(static_cast<const V*>(c.T) + node_at(d, z, (r0 - 1 + k - 128) & (n - 1), 0), rb);
     }
     // scalars of this step, converted once (thread 0) to the vector type
     if (threadIdx.x == 0) {
