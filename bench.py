@@ -180,9 +180,9 @@ def per_entry_error(A, ref):
 # Thread instructions per node of the double-word true-residual pass
 # (k_fused_R): ncu instruction count of a refining launch divided by its
 # nodes, for the first refinement of a solve (r = f) and the later ones
-# (profiles/k_fused_R_refine_plain_L32_batch32.md).
-REFINE_INST_PER_NODE = 617.7
-REFINE_FIRST_INST_PER_NODE = 212.5
+# (profiles/k_fused_R_refine_plain_L32_32copies.md).
+REFINE_INST_PER_NODE = 485.4
+REFINE_FIRST_INST_PER_NODE = 95.9
 
 
 def refine_alu(prof, refines, reals, nodes, clk):
@@ -206,6 +206,30 @@ def refine_alu(prof, refines, reals, nodes, clk):
             "frac": work / (ms / 1e3) / peak_inst,
             "peak_source": "152 SMs x 4 schedulers x 32 lanes x measured SM clock",
             "note": "time includes the idle launches of non-refining steps"}
+
+
+def graph_plan(args, rve, torch, np, dev, stream, ds, A_first):
+    """K executions of a plan of the first timed batch (field + solve + A_hom
+    captured once as a CUDA graph, the solve as the fused kernels in a
+    conditional while node), timed like `value`."""
+    opts = rve.make_opts(precision=rve.MIXED, tol=WORKLOAD["tol"], path=rve.PATH_FUSED)
+    plan = rve.Plan(ds, opts, device=dev)
+    for _ in range(args.warmup):
+        plan.execute()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        A, _ = plan.execute()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    diff = float(np.abs(A.cpu().numpy().reshape(-1, 4) - A_first.cpu().numpy().reshape(-1, 4)).max())
+    plan.close()
+    return {"value": len(ds) * args.steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "a_hom_max_abs_diff_vs_value_path": diff,
+            "api": "rve_plan_create / rve_plan_execute (one CUDA graph per step, no host "
+                   "synchronisation inside the solve)"}
 
 
 def e2e_host(args, rve, torch, dev):
@@ -447,6 +471,12 @@ def run_ours(args):
     if rank == 0:
         # end to end through the host-buffer entry point over the same K steps
         out["e2e"] = e2e_host(args, rve, torch, dev)
+    if world == 1:
+        # the same step as one captured CUDA graph (rve_plan_execute): the
+        # solve's fused kernels inside a conditional while node, so the host
+        # never waits on the device between steps
+        out["graph_plan"] = graph_plan(args, rve, torch, np, dev, stream,
+                                       descs(base + args.warmup * B, B), As[0])
 
     if rank == 0 and not args.no_extras:
         out.update(extras(args, rve, torch, np, dev, stream))

@@ -279,6 +279,16 @@ struct DotDW {
         s = t.hi;
         comp = __fadd_rn(comp, __fadd_rn(t.lo, x));
     }
+    // the same with a weight that is a single float (a double word with a
+    // zero low part, without its zero products)
+    __device__ __forceinline__ void add(float a, float whi, float wlo) {
+        const float p = __fmul_rn(a, whi);
+        const float e = __fmaf_rn(a, whi, -p);
+        const float x = __fmaf_rn(a, wlo, e);
+        const dword t = two_sum(s, p);
+        s = t.hi;
+        comp = __fadd_rn(comp, __fadd_rn(t.lo, x));
+    }
     __device__ __forceinline__ float value() const { return __fadd_rn(s, comp); }
 };
 

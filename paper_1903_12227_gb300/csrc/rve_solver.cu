@@ -38,6 +38,7 @@
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "rve_colsolve.cuh"
@@ -272,8 +273,13 @@ __device__ __forceinline__ float4 w_new(float4 u, float2 x, float2 p, const DWSc
 // O(eps_32^2) times the size of the stencil terms -- far below the outer
 // tolerance -- and r = r_K / K is rounded to FP32 (the inner iteration's
 // type).  Each thread walks down one column with a 3 x 3 window of w.
-template <int SCHEME>
+// EXACT: both cell values are integers of magnitude <= 2^20 (the paper's
+// two-valued coefficients 1 and the contrast), so every cell sum and scaled
+// weight below is exact in one float; the weights are then floats (CW)
+// instead of double words, with the same values and so the same results.
+template <int SCHEME, bool EXACT>
 __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, const RDesc& d) {
+    typedef std::conditional_t<EXACT, float, dword> CW;
     __shared__ double red[64];
     __shared__ float sc[9];
     const int n = d.n;
@@ -306,29 +312,52 @@ __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, c
         const int64_t node = d.node_off + ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1));
         return w_new(U[node], X[node], P[node], k);
     };
-    auto cell = [&](int i, int j) -> dword {
+    auto cell = [&](int i, int j) -> CW {
         const int64_t ci = ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1));
-        if (c.cs.coef) return dw_of(__ldg(c.cs.coef + d.node_off + ci));
-        const uint32_t w = __ldg(c.cs.mask + d.word_off + (ci >> 5));
-        return ((w >> (ci & 31)) & 1u) ? aI : aM;
+        if constexpr (EXACT) {   // mask only (no explicit coefficients)
+            const uint32_t w = __ldg(c.cs.mask + d.word_off + (ci >> 5));
+            return ((w >> (ci & 31)) & 1u) ? aI.hi : aM.hi;
+        } else {
+            if (c.cs.coef) return dw_of(__ldg(c.cs.coef + d.node_off + ci));
+            const uint32_t w = __ldg(c.cs.mask + d.word_off + (ci >> 5));
+            return ((w >> (ci & 31)) & 1u) ? aI : aM;
+        }
+    };
+    // cell-weight arithmetic in CW: exact float operations, or double words
+    auto wadd = [](CW x, CW y) -> CW {
+        if constexpr (EXACT) return __fadd_rn(x, y); else return dw_add(x, y);
+    };
+    auto wsub = [](CW x, CW y) -> CW {
+        if constexpr (EXACT) return __fsub_rn(x, y); else return dw_add(x, dw_neg(y));
+    };
+    auto wscale2 = [](CW x, float p2) -> CW {
+        if constexpr (EXACT) return x * p2; else return dw_scale2(x, p2);
+    };
+    auto wmulf = [](CW x, float f) -> dword {
+        if constexpr (EXACT) {
+            const float p = __fmul_rn(x, f);
+            return {p, __fmaf_rn(x, f, -p)};
+        } else {
+            return dw_mulf(x, f);
+        }
     };
     dword nx{0.f, 0.f}, ny{0.f, 0.f};   // |r|^2, double-word per thread
     if (first) {   // u = x = p = 0: r = f, the same arithmetic without the zero terms
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            dword cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
+            CW cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
             for (int q = 0; q < rows; ++q) {
                 const int i = r0 + q;
-                const dword c0m = cell(i, j - 1), c00 = cell(i, j);
+                const CW c0m = cell(i, j - 1), c00 = cell(i, j);
                 dword kfx, kfy;   // K f
                 if (c.cs.f) {
                     const double2 fl = c.cs.f[d.node_off + ((int64_t)i << d.log2n) + j];
                     kfx = dw_mulf(dw_split(fl.x), 2.f * KH);
                     kfy = dw_mulf(dw_split(fl.y), 2.f * KH);
                 } else {
-                    const dword top = dw_add(cmm, cm0), bot = dw_add(c0m, c00);
-                    const dword lft = dw_add(cmm, c0m), rgt = dw_add(cm0, c00);
-                    kfx = dw_mulf(dw_add(bot, dw_neg(top)), kh2);
-                    kfy = dw_mulf(dw_add(rgt, dw_neg(lft)), kh2);
+                    const CW top = wadd(cmm, cm0), bot = wadd(c0m, c00);
+                    const CW lft = wadd(cmm, c0m), rgt = wadd(cm0, c00);
+                    kfx = wmulf(wsub(bot, top), kh2);
+                    kfy = wmulf(wsub(rgt, lft), kh2);
                 }
                 const DotDW rx(kfx), ry(kfy);
                 const float2 r = make_float2(rx.value() * INVK, ry.value() * INVK);
@@ -342,24 +371,24 @@ __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, c
     for (int j = first ? n : threadIdx.x; j < n; j += blockDim.x) {
         float4 a0 = wat(r0 - 1, j - 1), a1 = wat(r0 - 1, j), a2 = wat(r0 - 1, j + 1);
         float4 b0 = wat(r0, j - 1), b1 = wat(r0, j), b2 = wat(r0, j + 1);
-        dword cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
+        CW cmm = cell(r0 - 1, j - 1), cm0 = cell(r0 - 1, j);
         for (int q = 0; q < rows; ++q) {
             const int i = r0 + q;
             const float4 e0 = wat(i + 1, j - 1), e1 = wat(i + 1, j), e2 = wat(i + 1, j + 1);
-            const dword c0m = cell(i, j - 1), c00 = cell(i, j);
-            const dword top = dw_add(cmm, cm0);   // cells shared with (i-1, j)
-            const dword bot = dw_add(c0m, c00);   // with (i+1, j)
-            const dword lft = dw_add(cmm, c0m);   // with (i, j-1)
-            const dword rgt = dw_add(cm0, c00);   // with (i, j+1)
-            const dword cen = dw_scale2(dw_add(top, bot), -CEN);
+            const CW c0m = cell(i, j - 1), c00 = cell(i, j);
+            const CW top = wadd(cmm, cm0);   // cells shared with (i-1, j)
+            const CW bot = wadd(c0m, c00);   // with (i+1, j)
+            const CW lft = wadd(cmm, c0m);   // with (i, j-1)
+            const CW rgt = wadd(cm0, c00);   // with (i, j+1)
+            const CW cen = wscale2(wadd(top, bot), -CEN);
             dword kfx, kfy;   // K f
             if (c.cs.f) {
                 const double2 fl = c.cs.f[d.node_off + ((int64_t)i << d.log2n) + j];
                 kfx = dw_mulf(dw_split(fl.x), 2.f * KH);
                 kfy = dw_mulf(dw_split(fl.y), 2.f * KH);
             } else {
-                kfx = dw_mulf(dw_add(bot, dw_neg(top)), kh2);
-                kfy = dw_mulf(dw_add(rgt, dw_neg(lft)), kh2);
+                kfx = wmulf(wsub(bot, top), kh2);
+                kfy = wmulf(wsub(rgt, lft), kh2);
             }
             DotDW rx(kfx), ry(kfy);
             rx.add(cen, b1.x, b1.z); ry.add(cen, b1.y, b1.w);
@@ -368,8 +397,8 @@ __device__ void refine_tile_dw(const Ctx& c, int tile, int b, const RState& s, c
             rx.add(lft, b0.x, b0.z); ry.add(lft, b0.y, b0.w);
             rx.add(rgt, b2.x, b2.z); ry.add(rgt, b2.y, b2.w);
             if (COR != 0.f) {
-                const dword kmm = dw_scale2(cmm, COR), km0 = dw_scale2(cm0, COR);
-                const dword k0m = dw_scale2(c0m, COR), k00 = dw_scale2(c00, COR);
+                const CW kmm = wscale2(cmm, COR), km0 = wscale2(cm0, COR);
+                const CW k0m = wscale2(c0m, COR), k00 = wscale2(c00, COR);
                 rx.add(kmm, a0.x, a0.z); ry.add(kmm, a0.y, a0.w);
                 rx.add(km0, a2.x, a2.z); ry.add(km0, a2.y, a2.w);
                 rx.add(k0m, e0.x, e0.z); ry.add(k0m, e0.y, e0.w);
@@ -444,9 +473,15 @@ __device__ void fused_R_tile(const Ctx& c, int tile) {
     const RState& s = c.st[b];
     if (s.phase != PH_REFINE) return;
     const RDesc d = c.desc[b];
-    if constexpr (sizeof(V) == 8)
-        refine_tile_dw<SCHEME>(c, tile, b, s, d);
-    else
+    if constexpr (sizeof(V) == 8) {
+        // integer cell values of magnitude <= 2^20: sums of up to four of
+        // them, scaled by 2, 4 or 3 h (h a power of two), stay below 2^24
+        auto small_int = [](double a) { return a == floor(a) && fabs(a) <= 1048576.0; };
+        if (!c.cs.coef && small_int(d.a_incl) && small_int(d.a_matrix))
+            refine_tile_dw<SCHEME, true>(c, tile, b, s, d);
+        else
+            refine_tile_dw<SCHEME, false>(c, tile, b, s, d);
+    } else
         refine_tile_fp64<SCHEME>(c, tile, b, s, d);
 }
 
@@ -899,7 +934,7 @@ __device__ void fused_C_tile(const Ctx& c, int blk) {
 
 // One launch per pipeline kernel (the fused path).
 template <typename V, int SCHEME>
-__global__ void __launch_bounds__(256) k_fused_R(const Ctx c) { fused_R_tile<V, SCHEME>(c, blockIdx.x); }
+__global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_R(const Ctx c) { fused_R_tile<V, SCHEME>(c, blockIdx.x); }
 template <typename V, int SCHEME>
 __global__ void __launch_bounds__(256, sizeof(V) == 8 ? 3 : 2) k_fused_S(const Ctx c) {
     fused_S_tile<V, SCHEME>(c, blockIdx.x);

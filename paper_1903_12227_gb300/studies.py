@@ -381,7 +381,34 @@ def kernel_rates(L=32, m0=16, batch=64, K=64, reps=10) -> list:
                  "GBs": 48.125 * nodes / t / 1e9, "frac_hbm": 48.125 * nodes / t / 1e9 / peak,
                  "fp64_inst_per_node": CHEB_FP64_PER_NODE,
                  "frac_fp64_issue": CHEB_FP64_PER_NODE * nodes / t / fp64_peak})
+    rows.append(refine_rate(L, m0))
     return rows
+
+
+def refine_rate(L=32, m0=16, copies=32) -> dict:
+    """The double-word true-residual pass (k_fused_R) of the mixed solver on
+    `copies` copies of one realization, so that every refining launch works
+    on all of them at once: its CUDA-event time per launch over one solve
+    (idle launches of the iteration steps included) from the library's
+    per-kernel profiler."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ds = [workloads.realization(L, m0, 10.0, 0, 5)] * copies
+    opts = rve.make_opts(precision=rve.MIXED, tol=1e-10)
+    mask = rve.gen_field(ds, device=dev)
+    ws = rve.workspace(rve.workspace_size(ds, opts), dev)
+    rve.solve(ds, mask=mask, opts=opts, ws=ws)   # warm-up
+    torch.cuda.synchronize()
+    rve.profile_enable(True)
+    rve.profile_read()
+    u, info = rve.solve(ds, mask=mask, opts=opts, ws=ws)
+    torch.cuda.synchronize()
+    prof = rve.profile_read()["refine"]
+    rve.profile_enable(False)
+    d = rve.info_to_dicts(info, copies)[0]
+    return {"kernel": "k_fused_R (double-word true residual, mixed solver)",
+            "nodes": (L * m0) ** 2 * copies, "launches": prof["launches"],
+            "refining_launches": d["refinements"], "steps": d["steps"],
+            "ms_total": prof["ms"], "us_per_launch": 1e3 * prof["ms"] / max(prof["launches"], 1)}
 
 
 def _hbm_peak() -> float:

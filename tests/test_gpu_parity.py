@@ -214,6 +214,25 @@ def test_solve_matches_oracle(case, scheme, precision, path, bound):
         off += n * n
 
 
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_mixed_refine_integer_cells_same_bits_as_double_words(scheme):
+    """With integer cell values (1 and the contrast) the mixed refinement
+    forms its cell weights as exact floats instead of double words: the same
+    values, so the same solve, bit for bit, as through the explicit
+    coefficient input, which always takes the double-word weights."""
+    ds = SOLVE_CASES["mixed_sizes"]
+    opts = rve.make_opts(scheme=scheme, precision=rve.MIXED, tol=1e-10)
+    mask = rve.gen_field(ds, device=CUDA)
+    coef = rve.coef_from_mask(ds, mask)
+    u1, i1 = rve.solve(ds, mask=mask, opts=opts)
+    u2, i2 = rve.solve(ds, coef=coef, opts=opts)
+    np.testing.assert_array_equal(u1.cpu().numpy(), u2.cpu().numpy())
+    d1, d2 = rve.info_to_dicts(i1, len(ds)), rve.info_to_dicts(i2, len(ds))
+    assert [d["iters"] for d in d1] == [d["iters"] for d in d2]
+    assert [d["refinements"] for d in d1] == [d["refinements"] for d in d2]
+    assert all(d["status"] == rve.RVE_OK for d in d1)
+
+
 # ------------------------------------------ general load (Sec. 3.5) --
 def _nodal_loads(ds):
     """Per realization the nodal loads sin(2 pi x/L) cos(6 pi y/L) and
