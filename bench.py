@@ -306,7 +306,7 @@ def source_hash() -> str:
 def ncu_traffic(kernel: str):
     """Per-node DRAM traffic of `kernel` from the committed ncu summary, if it
     was measured on the current sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic_k_fused_S_U_C_plain_L32_batch32.json")
+    path = os.path.join(ROOT, "profiles", "dram_traffic_k_fused_S_U_C_plain_L32_batch128.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):

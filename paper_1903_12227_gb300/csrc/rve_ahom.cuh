@@ -34,6 +34,94 @@ __device__ __forceinline__ dword dw_sub(dword a, dword b) {
     return {s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo))};
 }
 
+// One cell's contributions to the AHOM_NP partial sums (K-scaled double
+// words): cell value a, the corrector pair at the cell's corners 00, 01, 10,
+// 11 (local order), already split into double words (u[c][corner]).
+template <int SCHEME>
+__device__ __forceinline__ void a_hom_cell(dword a, const dword (&u)[2][4], float h,
+                                           dword (&acc)[AHOM_NP]) {
+    constexpr float Q = SCHEME == 0 ? 2.f : 0.f;   // K |E| on the cell diagonals
+    // u differences across the cell, per corrector c: 01-00, 10-00, 11-00,
+    // 10-01, 11-01, 11-10
+    dword D[2][6];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const dword u00 = u[c][0], u01 = u[c][1], u10 = u[c][2], u11 = u[c][3];
+        D[c][0] = dw_sub(u01, u00);
+        D[c][1] = dw_sub(u10, u00);
+        D[c][2] = dw_sub(u11, u00);
+        D[c][3] = dw_sub(u10, u01);
+        D[c][4] = dw_sub(u11, u01);
+        D[c][5] = dw_sub(u11, u10);
+    }
+    // differences of v_i = xi_i + u_i: xi_1 = h(0,0,1,1) adds h to pairs
+    // 10-00, 11-00, 10-01, 11-01; xi_2 = h(0,1,0,1) adds h to 01-00,
+    // 11-00, 11-10 and -h to 10-01
+    dword V1[6], V2[6];
+    V1[0] = D[0][0];            V2[0] = dw_add(D[1][0], h);
+    V1[1] = dw_add(D[0][1], h); V2[1] = D[1][1];
+    V1[2] = dw_add(D[0][2], h); V2[2] = dw_add(D[1][2], h);
+    V1[3] = dw_add(D[0][3], h); V2[3] = dw_add(D[1][3], -h);
+    V1[4] = dw_add(D[0][4], h); V2[4] = D[1][4];
+    V1[5] = D[0][5];            V2[5] = dw_add(D[1][5], h);
+    dword e11{0.f, 0.f}, e12{0.f, 0.f}, e22{0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        const float wgt = (p == 2 || p == 3) ? Q : 1.f;   // diagonals 00-11, 01-10
+        if (wgt == 0.f) continue;
+        dw_acc(e11, dw_scale2(dw_mul(V1[p], V1[p]), wgt));
+        dw_acc(e12, dw_scale2(dw_mul(V1[p], V2[p]), wgt));
+        dw_acc(e22, dw_scale2(dw_mul(V2[p], V2[p]), wgt));
+    }
+    // xi_j^T (K E) P_c u_i = sum_pairs K|E_kl| (xi_k - xi_l)(u_k - u_l):
+    //   xi_1: h (D10 + Q D11 + Q D(10-01) + D(11-01))
+    //   xi_2: h (D01 + Q D11 - Q D(10-01) + D(11-10))
+    dword F[2][2];   // F[j][i]
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const dword qd11 = dw_scale2(D[c][2], Q), qd1001 = dw_scale2(D[c][3], Q);
+        F[0][c] = dw_scale2(dw_add(dw_add(D[c][1], qd11), dw_add(qd1001, D[c][4])), h);
+        F[1][c] = dw_scale2(dw_add(dw_add(D[c][0], qd11), dw_add(dw_neg(qd1001), D[c][5])), h);
+    }
+    dw_acc(acc[0], a);
+    dw_acc(acc[1], dw_mul(a, e11));
+    dw_acc(acc[2], dw_mul(a, e12));
+    dw_acc(acc[3], dw_mul(a, e22));
+    dw_acc(acc[4], dw_mul(a, F[0][0]));
+    dw_acc(acc[5], dw_mul(a, F[0][1]));
+    dw_acc(acc[6], dw_mul(a, F[1][0]));
+    dw_acc(acc[7], dw_mul(a, F[1][1]));
+}
+
+// The AHOM_NP block sums of the per-thread partials into out[0..AHOM_NP)
+// (valid in thread 0).  `red` holds 64 doubles.  Contains barriers.
+__device__ __forceinline__ void a_hom_block_sums(const dword (&acc)[AHOM_NP], double* red,
+                                                 double* out) {
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; k += 2) {
+        DotAcc<float> ax, ay;
+        ax.hi = acc[k].hi; ax.lo = acc[k].lo;
+        ay.hi = acc[k + 1].hi; ay.lo = acc[k + 1].lo;
+        double sx = 0.0, sy = 0.0;
+        block_sum2(ax, ay, red, sx, sy);
+        if (threadIdx.x == 0) {
+            out[k] = sx;
+            out[k + 1] = sy;
+        }
+    }
+}
+
+// The two cell values and h of realization d as floats in sc[0..5)
+// (thread 0 writes, then a barrier).
+__device__ __forceinline__ void a_hom_scalars(const RDesc& d, float* sc) {
+    if (threadIdx.x == 0) {
+        const dword ai = dw_split(d.a_incl), am = dw_split(d.a_matrix);
+        sc[0] = ai.hi; sc[1] = ai.lo; sc[2] = am.hi; sc[3] = am.lo;
+        sc[4] = dw_split(d.h).hi;   // h = 2^-k: exact
+    }
+    __syncthreads();
+}
+
 // Partial sums of tile `tile` (AHOM_TILE cells from cell tile*AHOM_TILE) of
 // realization d into out[0..AHOM_NP): valid in thread 0.  `red` holds 64
 // doubles, `sc` 5 floats (shared).  Contains barriers.
@@ -41,15 +129,9 @@ template <int SCHEME>
 __device__ __forceinline__ void a_hom_tile(const RDesc& d, int64_t tile, CoefSrc cs,
                                            const double2* __restrict__ u, double* red,
                                            float* sc, double* out) {
-    if (threadIdx.x == 0) {
-        const dword ai = dw_split(d.a_incl), am = dw_split(d.a_matrix);
-        sc[0] = ai.hi; sc[1] = ai.lo; sc[2] = am.hi; sc[3] = am.lo;
-        sc[4] = dw_split(d.h).hi;   // h = 2^-k: exact
-    }
-    __syncthreads();
+    a_hom_scalars(d, sc);
     const dword aI{sc[0], sc[1]}, aM{sc[2], sc[3]};
     const float h = sc[4];
-    constexpr float Q = SCHEME == 0 ? 2.f : 0.f;   // K |E| on the cell diagonals
     const int n = d.n;
     auto at = [&](int i, int j) {   // periodic node access
         return u[d.node_off + ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1))];
@@ -70,72 +152,72 @@ __device__ __forceinline__ void a_hom_tile(const RDesc& d, int64_t tile, CoefSrc
         }
         const double2 r00 = at(i, j), r01 = at(i, j + 1);
         const double2 r10 = at(i + 1, j), r11 = at(i + 1, j + 1);
-        // u differences across the cell, per corrector c: 01-00, 10-00, 11-00,
-        // 10-01, 11-01, 11-10
-        dword D[2][6];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const dword u00 = dw_split(c ? r00.y : r00.x), u01 = dw_split(c ? r01.y : r01.x);
-            const dword u10 = dw_split(c ? r10.y : r10.x), u11 = dw_split(c ? r11.y : r11.x);
-            D[c][0] = dw_sub(u01, u00);
-            D[c][1] = dw_sub(u10, u00);
-            D[c][2] = dw_sub(u11, u00);
-            D[c][3] = dw_sub(u10, u01);
-            D[c][4] = dw_sub(u11, u01);
-            D[c][5] = dw_sub(u11, u10);
-        }
-        // differences of v_i = xi_i + u_i: xi_1 = h(0,0,1,1) adds h to pairs
-        // 10-00, 11-00, 10-01, 11-01; xi_2 = h(0,1,0,1) adds h to 01-00,
-        // 11-00, 11-10 and -h to 10-01
-        dword V1[6], V2[6];
-        V1[0] = D[0][0];            V2[0] = dw_add(D[1][0], h);
-        V1[1] = dw_add(D[0][1], h); V2[1] = D[1][1];
-        V1[2] = dw_add(D[0][2], h); V2[2] = dw_add(D[1][2], h);
-        V1[3] = dw_add(D[0][3], h); V2[3] = dw_add(D[1][3], -h);
-        V1[4] = dw_add(D[0][4], h); V2[4] = D[1][4];
-        V1[5] = D[0][5];            V2[5] = dw_add(D[1][5], h);
-        dword e11{0.f, 0.f}, e12{0.f, 0.f}, e22{0.f, 0.f};
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            const float wgt = (p == 2 || p == 3) ? Q : 1.f;   // diagonals 00-11, 01-10
-            if (wgt == 0.f) continue;
-            dw_acc(e11, dw_scale2(dw_mul(V1[p], V1[p]), wgt));
-            dw_acc(e12, dw_scale2(dw_mul(V1[p], V2[p]), wgt));
-            dw_acc(e22, dw_scale2(dw_mul(V2[p], V2[p]), wgt));
-        }
-        // xi_j^T (K E) P_c u_i = sum_pairs K|E_kl| (xi_k - xi_l)(u_k - u_l):
-        //   xi_1: h (D10 + Q D11 + Q D(10-01) + D(11-01))
-        //   xi_2: h (D01 + Q D11 - Q D(10-01) + D(11-10))
-        dword F[2][2];   // F[j][i]
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const dword qd11 = dw_scale2(D[c][2], Q), qd1001 = dw_scale2(D[c][3], Q);
-            F[0][c] = dw_scale2(dw_add(dw_add(D[c][1], qd11), dw_add(qd1001, D[c][4])), h);
-            F[1][c] = dw_scale2(dw_add(dw_add(D[c][0], qd11), dw_add(dw_neg(qd1001), D[c][5])), h);
-        }
-        dw_acc(acc[0], a);
-        dw_acc(acc[1], dw_mul(a, e11));
-        dw_acc(acc[2], dw_mul(a, e12));
-        dw_acc(acc[3], dw_mul(a, e22));
-        dw_acc(acc[4], dw_mul(a, F[0][0]));
-        dw_acc(acc[5], dw_mul(a, F[0][1]));
-        dw_acc(acc[6], dw_mul(a, F[1][0]));
-        dw_acc(acc[7], dw_mul(a, F[1][1]));
+        const dword uc[2][4] = {{dw_split(r00.x), dw_split(r01.x), dw_split(r10.x), dw_split(r11.x)},
+                                {dw_split(r00.y), dw_split(r01.y), dw_split(r10.y), dw_split(r11.y)}};
+        a_hom_cell<SCHEME>(a, uc, h, acc);
     }
-#pragma unroll
-    for (int k = 0; k < AHOM_NP; k += 2) {
-        DotAcc<float> ax, ay;
-        ax.hi = acc[k].hi; ax.lo = acc[k].lo;
-        ay.hi = acc[k + 1].hi; ay.lo = acc[k + 1].lo;
-        double sx = 0.0, sy = 0.0;
-        block_sum2(ax, ay, red, sx, sy);
-        if (threadIdx.x == 0) {
-            out[k] = sx;
-            out[k + 1] = sy;
-        }
-    }
+    a_hom_block_sums(acc, red, out);
 }
 
+// Rows of a strip of a_hom_strip: min(n, AHOM_STRIP / n) rows of n cells.
+constexpr int AHOM_STRIP = 8192;
+__host__ __device__ constexpr int a_hom_strip_rows(int n) {
+    return n < AHOM_STRIP / n ? n : AHOM_STRIP / n;
+}
+
+// Partial sums of strip `strip` (rows strip*RT .. +RT of realization d,
+// RT = a_hom_strip_rows(n)) into out[0..AHOM_NP), the same cell arithmetic as
+// a_hom_tile.  256 threads: min(n, 256) threads across a row band, each
+// walking down a column segment of RT / (256 / min(n, 256)) rows (its
+// columns j, j + 256, ... for n > 256), so every node is loaded and split
+// into double words twice (as the cell below and beside it) instead of four
+// times, and a block reduces up to 8192 cells instead of 1024.
+template <int SCHEME>
+__device__ __forceinline__ void a_hom_strip(const RDesc& d, int strip, CoefSrc cs,
+                                            const double2* __restrict__ u, double* red,
+                                            float* sc, double* out) {
+    a_hom_scalars(d, sc);
+    const dword aI{sc[0], sc[1]}, aM{sc[2], sc[3]};
+    const float h = sc[4];
+    const int n = d.n;
+    const int RT = a_hom_strip_rows(n);
+    const int W = n < 256 ? n : 256;            // threads across the band
+    const int seg = RT / (256 / W);             // rows of a thread's segment
+    const int col0 = threadIdx.x & (W - 1);
+    const int i0 = strip * RT + (threadIdx.x / W) * seg;
+    auto split2 = [&](int i, int j, dword& x, dword& y) {   // periodic node, split
+        const double2 r = __ldg(u + d.node_off + ((int64_t)(i & (n - 1)) << d.log2n) + (j & (n - 1)));
+        x = dw_split(r.x);
+        y = dw_split(r.y);
+    };
+    dword acc[AHOM_NP];
+#pragma unroll
+    for (int k = 0; k < AHOM_NP; ++k) acc[k] = dword{0.f, 0.f};
+    for (int j = col0; j < n; j += W) {
+        dword uc[2][4];   // [corrector][corner 00, 01, 10, 11]
+        split2(i0, j, uc[0][0], uc[1][0]);
+        split2(i0, j + 1, uc[0][1], uc[1][1]);
+        for (int i = i0; i < i0 + seg; ++i) {
+            split2(i + 1, j, uc[0][2], uc[1][2]);
+            split2(i + 1, j + 1, uc[0][3], uc[1][3]);
+            const int64_t cidx = ((int64_t)i << d.log2n) + j;
+            dword a;
+            if (cs.coef) {
+                a = dw_split(__ldg(cs.coef + d.node_off + cidx));
+            } else {
+                const uint32_t w = __ldg(cs.mask + d.word_off + (cidx >> 5));
+                a = ((w >> (cidx & 31)) & 1u) ? aI : aM;
+            }
+            a_hom_cell<SCHEME>(a, uc, h, acc);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uc[c][0] = uc[c][2];
+                uc[c][1] = uc[c][3];
+            }
+        }
+    }
+    a_hom_block_sums(acc, red, out);
+}
 
 // FP64 form of a_hom_tile (the A_hom of FP64 solves): the same cell sums in
 // double-double arithmetic on the FP64 pipe.  Differences of u across a cell

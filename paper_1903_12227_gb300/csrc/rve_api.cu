@@ -8,6 +8,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rve_ahom.cuh"
 #include "rve_common.cuh"
 #include "rve_internal.h"
 
@@ -106,6 +107,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.startU.assign(batch + 1, 0);
     p.startC.assign(batch + 1, 0);
     p.startA.assign(batch + 1, 0);
+    p.startA2.assign(batch + 1, 0);
     p.nodes = 0;
     p.words = 0;
     p.max_log2n = 5;
@@ -172,6 +174,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
         p.startU[b + 1] = p.startU[b] + n / t.tU;
         p.startC[b + 1] = p.startC[b] + n / t.tC;
         p.startA[b + 1] = p.startA[b] + (int32_t)(((int64_t)n * n) / 1024);
+        p.startA2[b + 1] = p.startA2[b] + n / a_hom_strip_rows(n);
         maxnb = std::max<int64_t>(maxnb, ((int64_t)n * n) / 1024);
         const size_t vb = p.vbytes;
         const size_t seq = (size_t)seq_stride(n);
@@ -188,6 +191,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.tilesU = p.startU[batch];
     p.tilesC = p.startC[batch];
     p.tilesA = p.startA[batch];
+    p.tilesA2 = p.startA2[batch];
     // workspace layout
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -201,6 +205,7 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_startU = take(sizeof(int32_t) * (batch + 1));
     p.o_startC = take(sizeof(int32_t) * (batch + 1));
     p.o_startA = take(sizeof(int32_t) * (batch + 1));
+    p.o_startA2 = take(sizeof(int32_t) * (batch + 1));
     p.o_tw64 = take(sizeof(double2) * tab);
     p.o_tw32 = take(sizeof(float2) * tab);
     p.o_lap = take(sizeof(double) * tab);
@@ -211,7 +216,8 @@ rve_status make_plan(const rve_realization* r, int32_t batch, const rve_solve_op
     p.o_partS = take(sizeof(double) * 2 * (size_t)std::max<int64_t>(p.tilesS, maxnb));
     p.o_partU = take(sizeof(double) * 2 * (size_t)p.tilesU);
     p.o_partC = take(sizeof(double) * 2 * (size_t)p.tilesC);
-    p.o_partA = take(sizeof(double) * 16 * (size_t)p.tilesA);   // 8 double-double sums
+    // 8 double-double sums per tile (FP64), or 8 doubles per strip (mixed)
+    p.o_partA = take(sizeof(double) * 16 * (size_t)p.tilesA);
     p.o_ctl = take(sizeof(int32_t) * 64);
     p.o_uscal = take(sizeof(double) * 2 * (size_t)batch);
     p.o_cnt = take(sizeof(int32_t) * (size_t)batch);

@@ -62,14 +62,16 @@ struct Plan {
     int64_t nodes = 0, words = 0;
     int max_log2n = 0;
     std::vector<RDesc> desc;        // host copy
-    std::vector<int32_t> startS, startU, startC, startA;
-    int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0;
+    // startA: tiles of 1024 cells (FP64 A_hom); startA2: strips of
+    // a_hom_strip_rows(n) rows (mixed A_hom)
+    std::vector<int32_t> startS, startU, startC, startA, startA2;
+    int tilesS = 0, tilesU = 0, tilesC = 0, tilesA = 0, tilesA2 = 0;
     size_t smemS = 0, smemU = 0, smemC = 0;
     int blockC = 512;               // threads of a column-solve block
     int persist_grid = 0;           // blocks of the persistent launch (0 = not prepared)
     size_t persist_smem = 0;
     // workspace offsets (bytes)
-    size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0;
+    size_t o_desc = 0, o_startS = 0, o_startU = 0, o_startC = 0, o_startA = 0, o_startA2 = 0;
     size_t o_tw64 = 0, o_tw32 = 0, o_lap = 0, o_lap32 = 0, o_rho64 = 0, o_rho32 = 0;
     size_t o_state = 0, o_partS = 0, o_partU = 0, o_partC = 0, o_partA = 0, o_ctl = 0;
     size_t o_uscal = 0, o_cnt = 0;

@@ -219,18 +219,18 @@ __global__ void k_backward(const __grid_constant__ DescChunk ch, const double2* 
 }
 
 // ---------------------------------------------------------------- A_hom --
-// Cell-form partial sums per tile and the final reduction (rve_ahom.cuh).
+// Cell-form partial sums and the final reduction (rve_ahom.cuh).
+// Mixed solves: one block per strip (a_hom_strip).
 template <int SCHEME>
-__global__ void __launch_bounds__(256) k_a_hom_part(const RDesc* __restrict__ desc,
-                                                    const int32_t* __restrict__ start, int batch,
-                                                    CoefSrc cs, const double2* __restrict__ u,
-                                                    double* __restrict__ part) {
+__global__ void __launch_bounds__(256, 3)
+    k_a_hom_strip(const RDesc* __restrict__ desc, const int32_t* __restrict__ start, int batch,
+                  CoefSrc cs, const double2* __restrict__ u, double* __restrict__ part) {
     __shared__ double red[64];
     __shared__ float sc[5];
     const int b = find_real(start, batch, blockIdx.x);
     const RDesc d = desc[b];
-    a_hom_tile<SCHEME>(d, blockIdx.x - start[b], cs, u, red, sc,
-                       part + (int64_t)blockIdx.x * AHOM_NP);
+    a_hom_strip<SCHEME>(d, blockIdx.x - start[b], cs, u, red, sc,
+                        part + (int64_t)blockIdx.x * AHOM_NP);
 }
 
 // FP64 solves: double-double partials (16 doubles per tile).
@@ -430,12 +430,13 @@ cudaError_t launch_a_hom(const Plan& p, void* ws, const uint32_t* mask, const do
         if (lumped) k_a_hom_final_dd<1><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_lo, A_flux);
         else k_a_hom_final_dd<0><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_lo, A_flux);
     } else {
-        if (lumped) k_a_hom_part<1><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
-        else k_a_hom_part<0><<<p.tilesA, 256, 0, s>>>(desc, start, p.batch, cs, uu, part);
+        const int32_t* start2 = reinterpret_cast<const int32_t*>(w + p.o_startA2);
+        if (lumped) k_a_hom_strip<1><<<p.tilesA2, 256, 0, s>>>(desc, start2, p.batch, cs, uu, part);
+        else k_a_hom_strip<0><<<p.tilesA2, 256, 0, s>>>(desc, start2, p.batch, cs, uu, part);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        if (lumped) k_a_hom_final<1><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
-        else k_a_hom_final<0><<<gf, 256, 0, s>>>(desc, start, p.batch, part, A, A_flux);
+        if (lumped) k_a_hom_final<1><<<gf, 256, 0, s>>>(desc, start2, p.batch, part, A, A_flux);
+        else k_a_hom_final<0><<<gf, 256, 0, s>>>(desc, start2, p.batch, part, A, A_flux);
     }
     note_launch(2);
     return cudaGetLastError();

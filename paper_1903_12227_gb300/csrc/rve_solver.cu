@@ -1315,6 +1315,9 @@ rve_status upload_plan(const Plan& p, void* ws, cudaStream_t s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w + p.o_startA, p.startA.data(), sizeof(int32_t) * (p.batch + 1),
                             cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + p.o_startA2, p.startA2.data(), sizeof(int32_t) * (p.batch + 1),
+                            cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return RVE_ECUDA;
     return launch_tables(p, ws, s) == cudaSuccess ? RVE_OK : RVE_ECUDA;
 }
@@ -1464,9 +1467,9 @@ rve_status upload_descriptors(const Plan& p, void* ws, cudaStream_t s) {
     char* w = static_cast<char*>(ws);
     cudaError_t e = cudaMemcpyAsync(w + p.o_desc, p.desc.data(), sizeof(RDesc) * p.batch,
                                     cudaMemcpyHostToDevice, s);
-    const std::vector<int32_t>* tabs[4] = {&p.startS, &p.startU, &p.startC, &p.startA};
-    const size_t offs[4] = {p.o_startS, p.o_startU, p.o_startC, p.o_startA};
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    const std::vector<int32_t>* tabs[5] = {&p.startS, &p.startU, &p.startC, &p.startA, &p.startA2};
+    const size_t offs[5] = {p.o_startS, p.o_startU, p.o_startC, p.o_startA, p.o_startA2};
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(w + offs[k], tabs[k]->data(), sizeof(int32_t) * (p.batch + 1),
                             cudaMemcpyHostToDevice, s);
     return e == cudaSuccess ? RVE_OK : RVE_ECUDA;
