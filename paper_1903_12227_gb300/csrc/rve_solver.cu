@@ -1202,13 +1202,27 @@ __global__ void k_report(const Ctx c, rve_solve_info* info) {
     info[b] = r;
 }
 
+// (double)f from the IEEE fields of a normal float or a zero, with integer
+// instructions (the conversion instruction runs on the narrow FP64 pipe);
+// subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 // Mixed path: the double-word iterate (float4 per node) becomes the caller's
-// FP64 solution, in place (each thread rewrites the 16 bytes it read).
+// FP64 solution, in place (each thread rewrites the 16 bytes it read):
+// hi + lo rounded once to double (one FP64 addition per component).
 __global__ void k_u_finalize(double2* u, int64_t nodes) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nodes; k += stride) {
         const float4 w = reinterpret_cast<const float4*>(u)[k];
-        u[k] = make_double2((double)w.x + (double)w.z, (double)w.y + (double)w.w);
+        u[k] = make_double2(f2d(w.x) + f2d(w.z), f2d(w.y) + f2d(w.w));
     }
 }
 
