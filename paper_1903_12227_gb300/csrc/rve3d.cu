@@ -41,6 +41,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "rve_colsolve.cuh"
@@ -505,29 +506,43 @@ __global__ void __launch_bounds__(T3) k3_split_dw(Grp g, const double2* __restri
     w[node] = make_float4(x.hi, y.hi, x.lo, y.lo);
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
-                                                  const float4* __restrict__ w,
-                                                  const double2* __restrict__ f,
-                                                  double2* __restrict__ r, double* part,
-                                                  const MixScal* sc) {
-    __shared__ double red[16];
-    int lb;
-    const int un = unit_of(g, lb);
-    const U3 d = g.desc[un];
-    if (unit_skip(sc, un, true)) return;
+// EXACT: both cell values are integers of magnitude <= 2^20 (the paper's
+// two-valued coefficients), so every cell sum below (at most 8 cells, below
+// 2^24) and its power-of-two scalings are exact in one float; the weights
+// are then floats instead of double words, with the same values and so the
+// same result.
+template <int SCHEME, bool EXACT>
+__device__ __forceinline__ void resid_dw_body(const U3& d, int lb, Cells3T<double> cs,
+                                              const float4* __restrict__ w,
+                                              const double2* __restrict__ f,
+                                              double2* __restrict__ r, double* part,
+                                              double* red) {
+    typedef std::conditional_t<EXACT, float, dword> CW;
+    auto wadd = [](CW x, CW y) -> CW {
+        if constexpr (EXACT) return __fadd_rn(x, y); else return dw_add(x, y);
+    };
+    auto wneg = [](CW x) -> CW {
+        if constexpr (EXACT) return -x; else return dw_neg(x);
+    };
+    auto wscale2 = [](CW x, float p2) -> CW {
+        if constexpr (EXACT) return x * p2; else return dw_scale2(x, p2);
+    };
     const int lg = d.log2n;
     const int loc = lb * T3 + threadIdx.x;
     const int i = loc >> (2 * lg), j = (loc >> lg) & (d.n - 1), k = loc & (d.n - 1);
     const float4* __restrict__ wu = w + d.off;
     const dword aI = dw_split(d.ai), aM = dw_split(d.am);
     // the 8 cells around the node: C[4 c1 + 2 c2 + c3] = cell (i - c1, j - c2, k - c3)
-    dword C[8];
+    CW C[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int idx = l3(d, i - (q >> 2), j - ((q >> 1) & 1), k - (q & 1));
-        if (cs.coef) C[q] = dw_split(__ldg(cs.coef + d.cell_off + idx));
-        else C[q] = __ldg(cs.mask + d.cell_off + idx) ? aI : aM;
+        if constexpr (EXACT) {   // mask only
+            C[q] = __ldg(cs.mask + d.cell_off + idx) ? aI.hi : aM.hi;
+        } else {
+            if (cs.coef) C[q] = dw_split(__ldg(cs.coef + d.cell_off + idx));
+            else C[q] = __ldg(cs.mask + d.cell_off + idx) ? aI : aM;
+        }
     }
     // the cell bit an offset fixes on its axis: +1 -> 0, -1 -> 1
     auto cb = [](int o) { return o > 0 ? 0 : 1; };
@@ -535,15 +550,15 @@ __global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
     const float K = (SCHEME == 0 ? 12.f : 4.f) * rintf((float)(1.0 / d.h));
     const double2 ff = f[d.off + loc];
     DotDW rx(dw_mulf(dw_split(ff.x), K)), ry(dw_mulf(dw_split(ff.y), K));
-    auto term = [&](dword wgt, int o1, int o2, int o3) {   // r -= wgt * u(i + o)
+    auto term = [&](CW wgt, int o1, int o2, int o3) {   // r -= wgt * u(i + o)
         const float4 v = wu[l3(d, i + o1, j + o2, k + o3)];
-        const dword nw = dw_neg(wgt);
+        const CW nw = wneg(wgt);
         rx.add(nw, v.x, v.z);
         ry.add(nw, v.y, v.w);
     };
-    dword S8 = dw_add(dw_add(dw_add(C[0], C[1]), dw_add(C[2], C[3])),
-                      dw_add(dw_add(C[4], C[5]), dw_add(C[6], C[7])));
-    term(dw_scale2(S8, SCHEME == 0 ? 4.f : 2.f), 0, 0, 0);
+    const CW S8 = wadd(wadd(wadd(C[0], C[1]), wadd(C[2], C[3])),
+                       wadd(wadd(C[4], C[5]), wadd(C[6], C[7])));
+    term(wscale2(S8, SCHEME == 0 ? 4.f : 2.f), 0, 0, 0);
     if (SCHEME != 0) term(S8, 0, 0, 0);   // 3 S8 = 2 S8 + S8 (exact scalings only)
 #pragma unroll
     for (int o1 = -1; o1 <= 1; ++o1)
@@ -557,16 +572,16 @@ __global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
                 if (SCHEME != 0 && zeros != 2) continue;   // lumped: faces only
                 // sum of the cells shared with the neighbour: the bits of
                 // the non-zero offsets are fixed, the others run over 0, 1
-                dword S{0.f, 0.f};
+                CW S{};
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int c1 = q >> 2, c2 = (q >> 1) & 1, c3 = q & 1;
                     if (o1 != 0 && c1 != cb(o1)) continue;
                     if (o2 != 0 && c2 != cb(o2)) continue;
                     if (o3 != 0 && c3 != cb(o3)) continue;
-                    S = dw_add(S, C[q]);
+                    S = wadd(S, C[q]);
                 }
-                term(dw_neg(S), o1, o2, o3);   // K e = -1: r += S u
+                term(wneg(S), o1, o2, o3);   // K e = -1: r += S u
             }
     const double invK = 1.0 / (double)K;
     const double rxd = ((double)rx.s + (double)rx.comp) * invK;
@@ -581,6 +596,24 @@ __global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
             part[d.part_off + 2 * lb + 1] = ty;
         }
     }
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(T3) k3_resid_dw(Grp g, Cells3T<double> cs,
+                                                  const float4* __restrict__ w,
+                                                  const double2* __restrict__ f,
+                                                  double2* __restrict__ r, double* part,
+                                                  const MixScal* sc) {
+    __shared__ double red[16];
+    int lb;
+    const int un = unit_of(g, lb);
+    const U3 d = g.desc[un];
+    if (unit_skip(sc, un, true)) return;
+    auto small_int = [](double a) { return a == floor(a) && fabs(a) <= 1048576.0; };
+    if (!cs.coef && small_int(d.ai) && small_int(d.am))
+        resid_dw_body<SCHEME, true>(d, lb, cs, w, f, r, part, red);
+    else
+        resid_dw_body<SCHEME, false>(d, lb, cs, w, f, r, part, red);
 }
 
 // -------------------------------------------------------------- loads --

@@ -257,6 +257,25 @@ def test_solve3_general_coefficients_both_precisions():
         assert _rel_A(A, ref["A_energy"]) < bar
 
 
+@pytest.mark.parametrize("scheme", [rve.CONSISTENT, rve.LUMPED])
+def test_mixed3_integer_cells_same_bits_as_double_words(scheme):
+    """With integer cell values (1 and the contrast) the mixed true residual
+    forms its cell weights as exact floats instead of double words: the same
+    values, so the same solve, bit for bit, as through the explicit
+    coefficient input, which always takes the double-word weights."""
+    ds = [workloads.realization3(4, 8, 10.0, 21, k) for k in range(2)]
+    mask = rve3.gen_field(ds, device=CUDA)
+    coef = torch.where(mask.bool(), torch.tensor(ds[0]["a_incl"], dtype=torch.float64, device=CUDA),
+                       torch.tensor(ds[0]["a_matrix"], dtype=torch.float64, device=CUDA))
+    opts = rve3.make_opts3(tol=1e-10, precision=rve.MIXED, scheme=scheme)
+    u1, i1 = rve3.solve(ds, mask=mask, opts=opts)
+    u2, i2 = rve3.solve(ds, coef=coef, opts=opts)
+    np.testing.assert_array_equal(u1.cpu().numpy(), u2.cpu().numpy())
+    d1, d2 = rve3.decode_info(i1), rve3.decode_info(i2)
+    assert [x["iters"] for x in d1] == [x["iters"] for x in d2]
+    assert all(x["status"] == rve.RVE_OK for x in d1)
+
+
 def test_solve3_mixed_constant_coefficient():
     d = dict(workloads.realization3(4, 8, 10.0, 0, 0), n_incl=0, a_matrix=2.5)
     A, infos = rve3.homogenize([d], precision=rve.MIXED)
