@@ -612,8 +612,11 @@ int orc_solve_batch(const orc_realization* r, int batch, int scheme, double tol,
 {
     int used = 1;
 #ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#pragma omp parallel
+    /* the thread count applies to this call only (omp_set_num_threads would
+     * carry it over to every later call in the process); 0 = the default
+     * team size (OMP_NUM_THREADS, else every core) */
+    const int nt = threads > 0 ? threads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt)
     {
 #pragma omp single
         used = omp_get_num_threads();

@@ -144,3 +144,21 @@ def test_checkpoint_resume_after_injected_failure(tmp_path):
     assert [k for c in calls for k in c] == list(range(8, 20))   # resumed, nothing redone
     A = ensemble.records_to_array(recs, range(20))
     np.testing.assert_array_equal(A, _fake_A(range(20)))
+
+
+def test_oracle_thread_count_is_per_call():
+    """A one-thread oracle call (the single-thread baseline) leaves later
+    calls on the default team: the thread count is a property of the call,
+    not of the process.  Results do not depend on the thread count."""
+    import os
+    from paper_1903_12227_gb300 import workloads
+    ds = [workloads.realization(4, 8, 10.0, 5, k) for k in range(4)]
+    A_all, _, used_all = oracle.solve_batch(ds, tol=1e-10)
+    A_one, _, used_one = oracle.solve_batch(ds[:1], tol=1e-10, threads=1)
+    A_again, _, used_again = oracle.solve_batch(ds, tol=1e-10)
+    assert used_one == 1
+    assert used_again == used_all
+    if (os.cpu_count() or 1) > 1 and "OMP_NUM_THREADS" not in os.environ:
+        assert used_all > 1
+    np.testing.assert_array_equal(A_one[0], A_all[0])
+    np.testing.assert_array_equal(A_again, A_all)
