@@ -484,7 +484,7 @@ def run_ours(args):
         out.update(extras(args, rve, torch, np, dev, stream))
         if "fp64_plain" in out:
             out["speedup_vs_fp64_plain"] = value / out["fp64_plain"]["value"]
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on the realizations of the first timed batch: the first
         # 32 timed on all host cores (the baseline), the rest for the
         # per-entry error of the mixed path against the FP64 oracle
